@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""Benchmark of the 2.7K virtual-stereo pair: remap -> 64-label BP -> JBU -> xyz.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step is one frame pair of 2704 x 1520 RGB through the whole hot path:
+radial undistort/rectify remap of both frames fused with the x4 downsample
+(Section 2.1, 2.2), hierarchical min-sum BP with 64 labels, 4 levels x 10
+iterations on 676 x 380 (Eq. 1), joint bilateral upsampling of the labels to
+2704 x 1520 fused with the reprojection to an FP32 point cloud (Eq. 2, 3).
+Inputs are seeded synthetic terrain pairs rendered on the host; eight distinct
+pairs (197 MB, more than the 126 MB L2) are resident in HBM and rotated so no
+step reads its inputs from L2.  Each step is one CUDA-graph replay of the
+library's kernels.
+
+Prints ONE JSON line (rank 0).  Pairs are independent, so N GPUs run N
+replicas ("scaling": "weak") and the value is all pairs over the slowest rank.
+``--impl reference`` times the CPU oracle instead (rank 0 only), on bounded
+crops of the same workload scaled to pairs/s.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2.7K pairs/s (BP 64 lbl + JBU)"
+UNIT = "pairs/s"
+W_FULL, H_FULL, SCALE = 2704, 1520, 4
+WORKLOAD = ("2704x1520 RGB pair: remap+downsample x4 -> 676x380 min-sum BP 64 labels, "
+            "4 levels x 10 iters -> JBU 5x5 (sigma_s 1, sigma_r 12) + reprojection B=0.5 m to FP32 xyz")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8000)
+    ap.add_argument("--warmup", type=int, default=40)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=24)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle pipeline (the reference arm and the cpu_baseline leg only)
+
+
+def oracle_pipeline(left, right, cam, baseline):
+    import oracle
+    dl = oracle.rectify_remap(left, cam)
+    dr = oracle.rectify_remap(right, cam)
+    lrl, lgl = oracle.downsample_luma(dl, SCALE)
+    _, lgr = oracle.downsample_luma(dr, SCALE)
+    lab = oracle.bp(lgl, lgr, 64, 4, 10, 20, 10, 40, mode=oracle.MSG_DT)
+    disp = oracle.guided_upsample(lab, lrl, dl, SCALE, 2, 1.0, 12.0)
+    return oracle.reproject(disp, cam, baseline)
+
+
+def crop_pair(left, right, cam, wc, hc):
+    """A centred wc x hc crop treated as its own frame (principal point moved)."""
+    x0 = (W_FULL - wc) // 2 // 4 * 4
+    y0 = (H_FULL - hc) // 2 // 4 * 4
+    c = list(cam)
+    c[2] -= x0
+    c[3] -= y0
+    return (np.ascontiguousarray(left[y0:y0 + hc, x0:x0 + wc]),
+            np.ascontiguousarray(right[y0:y0 + hc, x0:x0 + wc]), tuple(c))
+
+
+def time_oracle_sample(left, right, cam, frac_budget_s):
+    """The largest centred crop (wc, hc) whose oracle run fits the budget."""
+    wc, hc = 256, 128
+    l, r, c = crop_pair(left, right, cam, wc, hc)
+    t0 = time.perf_counter()
+    oracle_pipeline(l, r, c, 0.5)
+    t_small = time.perf_counter() - t0
+    per_px = t_small / (wc * hc)
+    area = min(W_FULL * H_FULL, max(64 * 32, frac_budget_s / per_px))
+    if area >= W_FULL * H_FULL:
+        wc, hc = W_FULL, H_FULL
+    else:
+        aspect = W_FULL / H_FULL
+        hc = max(32, int(np.sqrt(area / aspect)) // 32 * 32)
+        wc = max(64, int(hc * aspect) // 32 * 32)
+    return wc, hc
+
+
+def cpu_sample_run(left, right, cam, wc, hc):
+    l, r, c = crop_pair(left, right, cam, wc, hc)
+    t0 = time.perf_counter()
+    oracle_pipeline(l, r, c, 0.5)
+    return time.perf_counter() - t0, (wc * hc) / (W_FULL * H_FULL)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1902_09733_b300 import synth
+    oracle.build()
+    left, right = synth.terrain_pair(0)
+    cam = synth.TERRAIN_CAMERA
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    wc, hc = time_oracle_sample(left, right, cam, budget)
+    for _ in range(args.warmup):
+        cpu_sample_run(left, right, cam, wc, hc)
+    tot, frac = 0.0, 0.0
+    for _ in range(args.steps):
+        t, f = cpu_sample_run(left, right, cam, wc, hc)
+        tot += t
+        frac += f
+    value = frac / tot
+    sample = f"centred {wc}x{hc} crop of the 2704x1520 pair per step, oracle pipeline (DT messages), scaled by area"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32+f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "oracle": "plain C, single thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        self.t0 = time.time()
+
+    def stop(self):
+        self.t1 = time.time()
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if re.match(r"^[0-9.]+$", r[1])]
+        smax = [float(r[2]) for r in rows if re.match(r"^[0-9.]+$", r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        busy = [v for v in sm if smax and v > 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(busy) if busy else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+
+
+def sweep_bytes_per_launch(w, h, L):
+    """Algorithmic bytes of one level-0 sweep launch, averaged over the two
+    colours: each active pixel reads its data term (L bytes) and its in-frame
+    incoming messages (L bytes each) and writes one message (L bytes) to each
+    in-frame neighbour."""
+    yy, xx = np.mgrid[0:h, 0:w]
+    deg = (xx > 0).astype(int) + (xx < w - 1) + (yy > 0) + (yy < h - 1)
+    per = (1 + 2 * deg) * L
+    col = (xx + yy) & 1
+    return 0.5 * (per[col == 0].sum() + per[col == 1].sum())
+
+
+def committed_traffic(kernel_src: str):
+    """DRAM bytes per launch of the level-0 sweep from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "k_bp_sweep_level0_2704x1520.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    sh = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
+    if not m or not sh:
+        return None
+    cur = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    return float(m.group(1)) if sh.group(1) == cur else None
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1902_09733_b300 as vs
+    from paper_1902_09733_b300 import build, synth
+    build.build()
+    dev = torch.device("cuda", local)
+
+    cam = vs.Camera(*synth.TERRAIN_CAMERA)
+    bp = vs.BPParams(labels=64, levels=4, iters=10, data_trunc=20, smooth_slope=10, smooth_trunc=40)
+    jbu = vs.JBUParams(scale=SCALE, radius=2, sigma_s=1.0, sigma_r=12.0)
+    cfg = vs.PairConfig(W_FULL, H_FULL, cam, 0.5, bp, jbu)
+
+    # eight distinct resident pairs (197 MB > L2)
+    host_pairs = []
+    for seed in (2 * rank, 2 * rank + 1):
+        l, r = synth.terrain_pair(seed)
+        host_pairs.extend(synth.pair_variants(l, r))
+    pairs = [(torch.from_numpy(l).to(dev), torch.from_numpy(r).to(dev)) for l, r in host_pairs]
+    ws = torch.empty(vs.pair_workspace_size(cfg), dtype=torch.uint8, device=dev)
+    xyz = [torch.empty((H_FULL, W_FULL, 3), dtype=torch.float32, device=dev) for _ in range(2)]
+
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        vs.pair_run(cfg, *pairs[0], xyz=xyz[0], workspace=ws)   # load every kernel once
+    torch.cuda.synchronize()
+
+    def capture(i):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            vs.pair_run(cfg, *pairs[i], xyz=xyz[i % 2], workspace=ws)
+        return g
+
+    n0 = vs.kernel_launches()
+    graphs = [capture(i) for i in range(len(pairs))]
+    launches_per_step = (vs.kernel_launches() - n0) // len(pairs)
+    # a second set of graphs whose launches are bracketed by CUDA events
+    vs.profile_enable(4096)
+    prof_graphs = [capture(i) for i in range(len(pairs))]
+    torch.cuda.synchronize()
+    vs.profile_collect()   # drop the capture-time records; the graphs keep their events
+
+    # warm-up
+    for k in range(args.warmup):
+        graphs[k % len(graphs)].replay()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    K = args.steps
+    n_prof = min(len(graphs), K)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for k in range(K):
+            # the last steps replay the event-bracketed copies of the graphs
+            (prof_graphs if k >= K - n_prof else graphs)[k % len(graphs)].replay()
+        ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    slowest_ms = elapsed_ms
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        slowest_ms = float(t.item())
+    recs = vs.profile_collect()
+    vs.profile_enable(0)
+
+    # per-kernel durations from the event pairs of the last replays
+    by_tag = {}
+    for tag, ms in recs:
+        by_tag.setdefault(tag, []).append(ms)
+    sweep_ms = statistics.mean(by_tag["sweep_level0"]) if by_tag.get("sweep_level0") else None
+    w, h = W_FULL // SCALE, H_FULL // SCALE
+    alg_bytes = sweep_bytes_per_launch(w, h, 64)
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6400.0
+    achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9 if sweep_ms else None
+    traffic = committed_traffic(os.path.join(ROOT, "paper_1902_09733_b300", "csrc", "vs_bp.cu"))
+    kernel_share = None
+    if recs:
+        tot = sum(ms for _, ms in recs)
+        kernel_share = {k: round(sum(v) / tot, 4) for k, v in by_tag.items()}
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if args.e2e_steps > 0:
+        lh = torch.from_numpy(host_pairs[0][0]).pin_memory()
+        rh = torch.from_numpy(host_pairs[0][1]).pin_memory()
+        xh = torch.empty((H_FULL, W_FULL, 3), dtype=torch.float32).pin_memory()
+        dev_in = torch.empty(2 * W_FULL * H_FULL * 3, dtype=torch.uint8, device=dev)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                vs.pair_run_host(cfg, lh, rh, xh, dev_in, xyz[0], ws)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.e2e_steps):
+                vs.pair_run_host(cfg, lh, rh, xh, dev_in, xyz[0], ws)
+            t_e2e = time.perf_counter() - t0
+        e2e = {"value": world * args.e2e_steps / t_e2e if world == 1 else None, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * W_FULL * H_FULL * 3, "d2h_bytes_per_step": W_FULL * H_FULL * 3 * 4,
+               "steps": args.e2e_steps}
+        if world > 1:
+            t = torch.tensor([t_e2e], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e["value"] = world * args.e2e_steps / float(t.item())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cam_t = synth.TERRAIN_CAMERA
+        tsec, frac = cpu_sample_run(host_pairs[0][0], host_pairs[0][1], cam_t, W_FULL, H_FULL)
+        cpu = {"value": frac / tsec, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "one full 2704x1520 pair through the oracle pipeline (FP64 remap/JBU, int32 BP with "
+                         f"DT messages), single thread, {tsec:.1f} s"}
+
+    if rank == 0:
+        value = world * K / (slowest_ms * 1e-3)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": slowest_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int16+f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}",
+                       "l2": "8 distinct input pairs (197 MB) rotated per step, larger than L2",
+                       "launch": "one CUDA graph replay per step"},
+            "roofline": {"bound": "hbm", "kernel": "k_bp_sweep (level 0)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak if achieved else None, "traffic": traffic,
+                         "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": sweep_ms,
+                         "peak_source": f"{peak_src} hbm_gbs"},
+            "kernel_share": kernel_share,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step * K,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,230 @@
+/*
+ * vstereo.h -- C ABI of the B300 (sm_103a) virtual-stereo hot path of
+ * "Towards Real-time 3D Reconstruction using Consumer UAVs" (arXiv 1902.09733).
+ *
+ * One frame pair flows through four steps, each a hand-written CUDA kernel:
+ *   vs_rectify_remap     Section 2.1 undistort/rectify remap, fused with the
+ *                        Section 2.2 downsample to the stereo resolution
+ *   vs_bp_stereo         Eq. 1 hierarchical min-sum belief propagation
+ *   vs_guided_upsample   Eq. 2 joint bilateral upsampling to full resolution
+ *   vs_reproject         Eq. 3 reprojection to a camera-frame point cloud
+ * plus the fused Eq. 2 + Eq. 3 kernel and whole-pair drivers.
+ *
+ * Conventions shared by every entry point
+ *  - Pointers are DEVICE pointers owned by the caller unless a parameter says
+ *    "host".  The library never allocates device memory: scratch space is a
+ *    caller-provided workspace whose size comes from the matching *_size call.
+ *  - Images are row-major.  RGB images are interleaved R,G,B bytes; a pitch is
+ *    the distance in bytes between the starts of two rows (>= the row bytes).
+ *    Float outputs are contiguous (pitch = width elements).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Every call only enqueues work and returns; results are ready when the
+ *    stream reaches that point.  The host-buffer driver is the one exception:
+ *    it synchronises the stream before returning.
+ *  - Every call checks its arguments on the host before launching anything
+ *    and returns a status: VS_OK (0) or a negative VS_E* code; nothing is
+ *    enqueued when a check fails.  VS_ECUDA reports a launch or copy error
+ *    (cudaGetLastError after the launch); vs_status_string() names each code.
+ *  - Calls on different streams that share a workspace or an output race.
+ */
+#ifndef VSTEREO_H
+#define VSTEREO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VS_OK 0
+#define VS_EINVAL (-1)      /* a size, count or parameter is out of range   */
+#define VS_EALIGN (-2)      /* a pointer or pitch breaks an alignment rule  */
+#define VS_EWORKSPACE (-3)  /* workspace NULL, misaligned or too small      */
+#define VS_ECUDA (-4)       /* the CUDA runtime reported an error           */
+
+/* Pinhole camera with radial distortion (Section 2.1 and Eq. 3), in pixels of
+ * the full-resolution frame: focal lengths fx = f/du, fy = f/dv, principal
+ * point (cx, cy) = (u0, v0), radial coefficients k1, k2 (no tangential term). */
+typedef struct {
+    float fx, fy, cx, cy, k1, k2;
+} vs_camera;
+
+/* Eq. 1 parameters.  Data term min(|IL - IR|, data_trunc); smoothness
+ * min(smooth_slope * |dp - dq|, smooth_trunc); `labels` disparities
+ * 0..labels-1 of the left image (IL(x) is compared with IR(x - d));
+ * `levels` pyramid levels with `iters` red-black iterations each.
+ * Ranges: 2 <= labels <= 128, 1 <= levels <= 8, 1 <= iters <= 1000,
+ * 0 <= data_trunc <= 127, 0 <= smooth_slope, 0 <= smooth_trunc <= 127, and
+ * data_trunc * 4^(levels-1) + 4 * smooth_trunc <= 32767 (messages are kept
+ * in 8 bits and sums of a data term and four messages in 16 bits). */
+typedef struct {
+    int32_t labels, levels, iters, data_trunc, smooth_slope, smooth_trunc;
+} vs_bp_params;
+
+/* Eq. 2 parameters: `scale` s between the full-res and the low-res grid
+ * (1..16); window of (2 radius + 1)^2 low-res pixels (0 <= radius <= 3);
+ * spatial sigma in low-res pixels, range sigma on 0..255 RGB (both > 0). */
+typedef struct {
+    int32_t scale, radius;
+    float sigma_s, sigma_r;
+} vs_jbu_params;
+
+/*
+ * Section 2.1 + Section 2.2.  For every destination pixel (u, v) of the
+ * W x H frame: the normalised ray ((u-cx)/fx, (v-cy)/fy) is rotated by R^T
+ * (R9 = row-major 3x3 rectifying rotation, host pointer, NULL = identity, as
+ * when the extrinsics are ignored), distorted by 1 + k1 r^2 + k2 r^4 and
+ * mapped back through (fx, fy, cx, cy); the source is sampled bilinearly per
+ * channel (taps outside the frame read 0), rounded half to even and clamped.
+ * Rays with a non-positive depth after the rotation give 0.  Arithmetic is
+ * FP32.  Optionally the same kernel writes the low-resolution RGB
+ * (ceil(W/s) x ceil(H/s), mean of the in-frame pixels of each s x s block,
+ * rounded half up) and its grey (77 R + 150 G + 29 B + 128) >> 8.
+ *   src, dst      W x H RGB; src_pitch, dst_pitch >= 3 W.  src and dst must
+ *                 not overlap.
+ *   scale         1..16; ignored when low_rgb and low_gray are both NULL.
+ *   low_rgb       nullable, ceil(W/s) x ceil(H/s) RGB with low_rgb_pitch.
+ *   low_gray      nullable, ceil(W/s) x ceil(H/s) bytes with low_gray_pitch.
+ * Errors: VS_EINVAL (sizes <= 0, pitch too small, NULL src/dst/cam, bad
+ * scale, non-finite camera), VS_ECUDA.
+ */
+int vs_rectify_remap(const uint8_t *src, int W, int H, int src_pitch,
+                     const vs_camera *cam, const float *R9,
+                     uint8_t *dst, int dst_pitch, int scale,
+                     uint8_t *low_rgb, int low_rgb_pitch,
+                     uint8_t *low_gray, int low_gray_pitch, void *stream);
+
+/* Bytes of device workspace vs_bp_stereo needs for a w x h pair, or 0 when
+ * the parameters are invalid.  The workspace holds the cost pyramid and the
+ * message arrays of every level; it may be reused by consecutive calls on one
+ * stream and needs no initialisation. */
+size_t vs_bp_workspace_size(int w, int h, const vs_bp_params *p);
+
+/*
+ * Eq. 1 on a rectified, downsampled grey pair of w x h bytes (row pitch
+ * `pitch` for both images).  Level 0 is w x h and every coarser level halves
+ * rounding up; the coarse data term of a label is the sum over the in-frame
+ * 2 x 2 children.  The coarsest level starts from zero messages and every
+ * finer level from its parent pixel's messages (x>>1, y>>1).  At iteration t
+ * of a level each pixel with (x + y + t) even sends to its in-frame
+ * 4-neighbours the min-sum message of Eq. 1 (its data term plus the messages
+ * from its other neighbours, minimised against the truncated-linear
+ * smoothness, then shifted to minimum 0); missing neighbours contribute 0.
+ * After the last level-0 iteration each pixel gets the smallest d minimising
+ * its data term plus its four incoming messages.  Integer arithmetic: the
+ * labels are exact, not approximations of a float computation.
+ *   labels        w x h bytes out, row pitch labels_pitch >= w.
+ *   workspace     >= vs_bp_workspace_size() bytes, 256-byte aligned.
+ * Errors: VS_EINVAL, VS_EWORKSPACE, VS_ECUDA.
+ */
+int vs_bp_stereo(const uint8_t *left, const uint8_t *right, int w, int h, int pitch,
+                 const vs_bp_params *p, uint8_t *labels, int labels_pitch,
+                 void *workspace, size_t ws_bytes, void *stream);
+
+/* Debug read-out after vs_bp_stereo on the same workspace and stream: the
+ * final level-0 incoming messages as int32 [4][h][w][labels], directions
+ * 0 = from the left neighbour, 1 = right, 2 = up, 3 = down (zero where the
+ * neighbour is missing).  out is a device buffer of 16 h w labels bytes. */
+int vs_bp_export_messages(const void *workspace, size_t ws_bytes, int w, int h,
+                          const vs_bp_params *p, int32_t *out, void *stream);
+
+/*
+ * Eq. 2.  Full-res pixel p = (x, y) of the W x H guide sits at the low-res
+ * position p_down = ((x + 0.5)/s - 0.5, (y + 0.5)/s - 0.5); its window is the
+ * (2r+1)^2 low-res pixels around round-half-up(p_down), clipped to the w x h
+ * grid.  Weight of q: exp(-|p_down - q|^2 / (2 sigma_s^2)
+ * - |I_p - I_q|^2 / (2 sigma_r^2)) with I_p the full-res RGB and I_q the
+ * low-res RGB; disp = s * sum(w * label_q) / sum(w), in full-res pixels.
+ * FP32, exponents taken relative to one of the largest weights of the window.
+ *   labels        w x h bytes, pitch labels_pitch.
+ *   guide_low     w x h RGB, pitch guide_low_pitch (the downsampled frame).
+ *   guide_full    W x H RGB, pitch guide_full_pitch; w must equal ceil(W/s)
+ *                 and h ceil(H/s).
+ *   disp          W x H float out.
+ * Errors: VS_EINVAL, VS_ECUDA.
+ */
+int vs_guided_upsample(const uint8_t *labels, int w, int h, int labels_pitch,
+                       const uint8_t *guide_low, int guide_low_pitch,
+                       const uint8_t *guide_full, int W, int H, int guide_full_pitch,
+                       const vs_jbu_params *jp, float *disp, void *stream);
+
+/*
+ * Eq. 3.  For each pixel (u, v) with disparity d > 0 (full-res pixels):
+ * z = fx B / d, x = (u - cx) B / d, y = (v - cy) (fx / fy) B / d; pixels with
+ * d <= 0 or NaN give NaN in all three.  FP32.
+ *   disp          W x H float.   xyz  W x H x 3 float out (x, y, z per pixel).
+ * Errors: VS_EINVAL (sizes, baseline <= 0), VS_ECUDA.
+ */
+int vs_reproject(const float *disp, int W, int H, const vs_camera *cam, float baseline,
+                 float *xyz, void *stream);
+
+/* Eq. 2 followed by Eq. 3 in one kernel: the same arguments as the two calls
+ * above; disp may be NULL when only the point cloud is wanted. */
+int vs_guided_upsample_reproject(const uint8_t *labels, int w, int h, int labels_pitch,
+                                 const uint8_t *guide_low, int guide_low_pitch,
+                                 const uint8_t *guide_full, int W, int H, int guide_full_pitch,
+                                 const vs_jbu_params *jp, const vs_camera *cam, float baseline,
+                                 float *disp, float *xyz, void *stream);
+
+/* Whole-pair configuration for the drivers below. */
+typedef struct {
+    int32_t W, H;           /* full-resolution frame size                  */
+    vs_camera cam;          /* intrinsics + radial distortion              */
+    float baseline;         /* metres between the two views                */
+    vs_bp_params bp;        /* Eq. 1                                       */
+    vs_jbu_params jbu;      /* Eq. 2; jbu.scale is also the downsample s   */
+} vs_pair_config;
+
+/* Bytes of device workspace for one pair: both rectified frames, their
+ * low-res RGB and grey, the labels and the BP workspace.  0 if invalid. */
+size_t vs_pair_workspace_size(const vs_pair_config *cfg);
+
+/*
+ * One virtual-stereo pair, device buffers: rectify + downsample both frames
+ * (Section 2.1, 2.2), BP on the grey pair (Eq. 1), fused upsample and
+ * reprojection of the left view (Eq. 2, Eq. 3).
+ *   left_src, right_src   W x H RGB (pitch 3 W), device.
+ *   disp                  nullable W x H float out.   xyz  W x H x 3 float out.
+ * Errors: as the steps.
+ */
+int vs_pair_run(const vs_pair_config *cfg, const uint8_t *left_src, const uint8_t *right_src,
+                float *disp, float *xyz, void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * The same pair from and to HOST buffers: copies both frames to the device,
+ * runs vs_pair_run and copies the point cloud (and disp if non-NULL) back,
+ * then synchronises `stream`.  Host buffers should be page-locked for full
+ * copy speed.  `dev_in` is a device buffer of 2 * 3 W H bytes for the frames;
+ * dev_xyz (W H 3 floats) and dev_disp (W H floats, nullable) are device
+ * outputs the copies read back from.
+ *   left_host, right_host   W x H RGB host input.
+ *   xyz_host                W x H x 3 float host output.  disp_host nullable.
+ */
+int vs_pair_run_host(const vs_pair_config *cfg, const uint8_t *left_host, const uint8_t *right_host,
+                     float *disp_host, float *xyz_host, uint8_t *dev_in, float *dev_disp, float *dev_xyz,
+                     void *workspace, size_t ws_bytes, void *stream);
+
+/* Name of a status code. */
+const char *vs_status_string(int status);
+
+/* Total number of kernels this library has enqueued since it was loaded. */
+uint64_t vs_kernel_launches(void);
+
+/* Measurement aid (no counterpart in the paper).  vs_profile_enable(n)
+ * creates n pairs of CUDA events (0 switches timing off and frees them);
+ * while on, each launch of the timed kernels is bracketed by an event pair
+ * on its stream, also when the stream is being captured into a CUDA graph.
+ * vs_profile_collect synchronises the pending pairs and writes up to `max`
+ * (tag, milliseconds) records, oldest first; it returns the count or a
+ * negative status.  Tags: 0 level-0 message sweep, 1 coarser-level sweep,
+ * 2 remap, 3 upsample (+ reprojection), 4 other BP kernels (cost, pyramid,
+ * labels).  Slots are reused round-robin, so collect before n more launches. */
+int vs_profile_enable(int capacity);
+int vs_profile_collect(int *tags, float *ms, int max);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VSTEREO_H */

@@ -1,0 +1,392 @@
+"""Python binding of ``libvstereo.so``, the sm_103a virtual-stereo hot path.
+
+Argument marshalling only: every step runs in the library's CUDA kernels,
+reached through its C ABI (``include/vstereo.h``).  PyTorch supplies device
+memory and streams; tensors are passed as raw pointers.  There is no CPU
+fallback: importing works anywhere, but the first call raises if the built
+library is missing.
+
+Steps of the method (arXiv 1902.09733):
+
+* :func:`rectify_remap`               Section 2.1 remap + Section 2.2 downsample
+* :func:`bp_stereo`                   Eq. 1 hierarchical min-sum BP
+* :func:`guided_upsample`             Eq. 2 joint bilateral upsampling
+* :func:`reproject`                   Eq. 3 point cloud
+* :func:`guided_upsample_reproject`   Eq. 2 + Eq. 3 fused
+* :func:`pair_run`, :func:`pair_run_host`  a whole pair (device / host buffers)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+__all__ = [
+    "Camera", "BPParams", "JBUParams", "PairConfig", "VSError", "lib", "library_path",
+    "rectify_remap", "bp_workspace_size", "bp_stereo", "bp_export_messages",
+    "guided_upsample", "reproject", "guided_upsample_reproject",
+    "pair_workspace_size", "pair_run", "pair_run_host", "kernel_launches", "status_string",
+    "profile_enable", "profile_collect",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(_HERE, "libvstereo.so")
+
+VS_OK, VS_EINVAL, VS_EALIGN, VS_EWORKSPACE, VS_ECUDA = 0, -1, -2, -3, -4
+
+
+class VSError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        super().__init__(f"{fn} failed: status {code} ({status_string(code)})")
+        self.code = code
+
+
+# ---------------------------------------------------------------------------
+# C structs (mirrors of include/vstereo.h)
+
+class _Camera(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_float) for n in ("fx", "fy", "cx", "cy", "k1", "k2")]
+
+
+class _BPParams(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in
+                ("labels", "levels", "iters", "data_trunc", "smooth_slope", "smooth_trunc")]
+
+
+class _JBUParams(ctypes.Structure):
+    _fields_ = [("scale", ctypes.c_int32), ("radius", ctypes.c_int32),
+                ("sigma_s", ctypes.c_float), ("sigma_r", ctypes.c_float)]
+
+
+class _PairConfig(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_int32), ("H", ctypes.c_int32), ("cam", _Camera),
+                ("baseline", ctypes.c_float), ("bp", _BPParams), ("jbu", _JBUParams)]
+
+
+@dataclass(frozen=True)
+class Camera:
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    k1: float = 0.0
+    k2: float = 0.0
+
+    def c(self) -> _Camera:
+        return _Camera(self.fx, self.fy, self.cx, self.cy, self.k1, self.k2)
+
+
+@dataclass(frozen=True)
+class BPParams:
+    labels: int = 64
+    levels: int = 4
+    iters: int = 10
+    data_trunc: int = 20
+    smooth_slope: int = 10
+    smooth_trunc: int = 40
+
+    def c(self) -> _BPParams:
+        return _BPParams(self.labels, self.levels, self.iters, self.data_trunc,
+                         self.smooth_slope, self.smooth_trunc)
+
+
+@dataclass(frozen=True)
+class JBUParams:
+    scale: int = 4
+    radius: int = 2
+    sigma_s: float = 1.0
+    sigma_r: float = 12.0
+
+    def c(self) -> _JBUParams:
+        return _JBUParams(self.scale, self.radius, self.sigma_s, self.sigma_r)
+
+
+@dataclass(frozen=True)
+class PairConfig:
+    W: int
+    H: int
+    cam: Camera
+    baseline: float
+    bp: BPParams
+    jbu: JBUParams
+
+    def c(self) -> _PairConfig:
+        return _PairConfig(self.W, self.H, self.cam.c(), self.baseline, self.bp.c(), self.jbu.c())
+
+
+# ---------------------------------------------------------------------------
+# loading
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(library_path):
+            raise RuntimeError(
+                f"{library_path} is missing: build it with "
+                "`python -m paper_1902_09733_b300.build` (nvcc, sm_103a); there is no CPU fallback")
+        L = ctypes.CDLL(library_path)
+        P, I, F, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_size_t
+        cam_p, bp_p = ctypes.POINTER(_Camera), ctypes.POINTER(_BPParams)
+        jbu_p, cfg_p = ctypes.POINTER(_JBUParams), ctypes.POINTER(_PairConfig)
+        sig = {
+            "vs_rectify_remap": ([P, I, I, I, cam_p, P, P, I, I, P, I, P, I, P], I),
+            "vs_bp_workspace_size": ([I, I, bp_p], S),
+            "vs_bp_stereo": ([P, P, I, I, I, bp_p, P, I, P, S, P], I),
+            "vs_bp_export_messages": ([P, S, I, I, bp_p, P, P], I),
+            "vs_guided_upsample": ([P, I, I, I, P, I, P, I, I, I, jbu_p, P, P], I),
+            "vs_reproject": ([P, I, I, cam_p, F, P, P], I),
+            "vs_guided_upsample_reproject": ([P, I, I, I, P, I, P, I, I, I, jbu_p, cam_p, F, P, P, P], I),
+            "vs_pair_workspace_size": ([cfg_p], S),
+            "vs_pair_run": ([cfg_p, P, P, P, P, P, S, P], I),
+            "vs_pair_run_host": ([cfg_p, P, P, P, P, P, P, P, P, S, P], I),
+            "vs_status_string": ([I], ctypes.c_char_p),
+            "vs_kernel_launches": ([], ctypes.c_uint64),
+            "vs_profile_enable": ([I], I),
+            "vs_profile_collect": ([P, P, I], I),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+        return L
+
+
+def status_string(code: int) -> str:
+    try:
+        return lib().vs_status_string(code).decode()
+    except RuntimeError:
+        return "library not built"
+
+
+def kernel_launches() -> int:
+    return int(lib().vs_kernel_launches())
+
+
+PROFILE_TAGS = {0: "sweep_level0", 1: "sweep_coarse", 2: "remap", 3: "upsample", 4: "bp_other"}
+
+
+def profile_enable(capacity: int) -> None:
+    """Bracket every later launch with a CUDA event pair (0 switches off)."""
+    _check("vs_profile_enable", lib().vs_profile_enable(int(capacity)))
+
+
+def profile_collect(max_records: int = 1 << 16):
+    """[(tag name, milliseconds)] of the launches timed since the last collect."""
+    tags = (ctypes.c_int * max_records)()
+    ms = (ctypes.c_float * max_records)()
+    n = lib().vs_profile_collect(ctypes.cast(tags, ctypes.c_void_p), ctypes.cast(ms, ctypes.c_void_p), max_records)
+    if n < 0:
+        raise VSError("vs_profile_collect", n)
+    return [(PROFILE_TAGS.get(tags[i], str(tags[i])), float(ms[i])) for i in range(n)]
+
+
+def _check(fn: str, rc: int) -> None:
+    if rc != VS_OK:
+        raise VSError(fn, rc)
+
+
+def _stream(stream) -> int | None:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _dev(t: torch.Tensor, dtype: torch.dtype, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    return t
+
+
+def _pitched(t: torch.Tensor, channels: int, name: str) -> int:
+    """Row pitch in bytes of an image tensor whose rows may be padded."""
+    if channels == 1:
+        ok = t.dim() == 2 and t.stride(1) == 1
+    else:
+        ok = t.dim() == 3 and t.shape[2] == channels and t.stride(2) == 1 and t.stride(1) == channels
+    if not ok:
+        raise ValueError(f"{name} must be an (H, W{'' if channels == 1 else ', 3'}) image with contiguous rows")
+    return t.stride(0) * t.element_size()
+
+
+# ---------------------------------------------------------------------------
+# steps
+
+
+def rectify_remap(src: torch.Tensor, cam: Camera, R=None, scale: int = 4, dst=True, low_rgb=True,
+                  low_gray=True, stream=None):
+    """Section 2.1 remap of an (H, W, 3) uint8 frame fused with the Section 2.2
+    downsample.  ``dst``/``low_rgb``/``low_gray`` are tensors to write, True to
+    allocate, or None/False to skip.  Returns (dst, low_rgb, low_gray)."""
+    _dev(src, torch.uint8, "src")
+    H, W = src.shape[0], src.shape[1]
+    w, h = -(-W // scale), -(-H // scale)
+
+    def out(spec, shape):
+        if spec is True:
+            return torch.empty(shape, dtype=torch.uint8, device=src.device)
+        return spec if isinstance(spec, torch.Tensor) else None
+
+    dst_t, lr_t, lg_t = out(dst, (H, W, 3)), out(low_rgb, (h, w, 3)), out(low_gray, (h, w))
+    Rm = None
+    if R is not None:
+        Rf = (ctypes.c_float * 9)(*[float(v) for v in torch.as_tensor(R, dtype=torch.float64).reshape(9)])
+        Rm = ctypes.cast(Rf, ctypes.c_void_p)
+    c = cam.c()
+    rc = lib().vs_rectify_remap(
+        src.data_ptr(), W, H, _pitched(src, 3, "src"), ctypes.byref(c), Rm,
+        dst_t.data_ptr() if dst_t is not None else None, _pitched(dst_t, 3, "dst") if dst_t is not None else 0,
+        scale,
+        lr_t.data_ptr() if lr_t is not None else None, _pitched(lr_t, 3, "low_rgb") if lr_t is not None else 0,
+        lg_t.data_ptr() if lg_t is not None else None, _pitched(lg_t, 1, "low_gray") if lg_t is not None else 0,
+        _stream(stream))
+    _check("vs_rectify_remap", rc)
+    return dst_t, lr_t, lg_t
+
+
+def bp_workspace_size(w: int, h: int, params: BPParams) -> int:
+    p = params.c()
+    return int(lib().vs_bp_workspace_size(w, h, ctypes.byref(p)))
+
+
+def bp_stereo(left: torch.Tensor, right: torch.Tensor, params: BPParams, labels=None, workspace=None,
+              stream=None) -> torch.Tensor:
+    """Eq. 1 on an (h, w) uint8 grey pair; returns (h, w) uint8 labels."""
+    _dev(left, torch.uint8, "left")
+    _dev(right, torch.uint8, "right")
+    if left.shape != right.shape or left.stride() != right.stride():
+        raise ValueError("left and right must have the same shape and strides")
+    h, w = left.shape
+    pitch = _pitched(left, 1, "left")
+    need = bp_workspace_size(w, h, params)
+    if need == 0:
+        raise VSError("vs_bp_workspace_size", VS_EINVAL)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=left.device)
+    if labels is None:
+        labels = torch.empty((h, w), dtype=torch.uint8, device=left.device)
+    p = params.c()
+    rc = lib().vs_bp_stereo(left.data_ptr(), right.data_ptr(), w, h, pitch, ctypes.byref(p),
+                            labels.data_ptr(), _pitched(labels, 1, "labels"), workspace.data_ptr(),
+                            workspace.numel() * workspace.element_size(), _stream(stream))
+    _check("vs_bp_stereo", rc)
+    return labels
+
+
+def bp_export_messages(workspace: torch.Tensor, w: int, h: int, params: BPParams, stream=None) -> torch.Tensor:
+    """Final level-0 incoming messages of the last bp_stereo on ``workspace``,
+    (4, h, w, labels) int32, directions left, right, up, down."""
+    out = torch.empty((4, h, w, params.labels), dtype=torch.int32, device=workspace.device)
+    p = params.c()
+    rc = lib().vs_bp_export_messages(workspace.data_ptr(), workspace.numel(), w, h, ctypes.byref(p),
+                                     out.data_ptr(), _stream(stream))
+    _check("vs_bp_export_messages", rc)
+    return out
+
+
+def guided_upsample(labels: torch.Tensor, guide_low: torch.Tensor, guide_full: torch.Tensor,
+                    jbu: JBUParams, disp=None, stream=None) -> torch.Tensor:
+    """Eq. 2; returns the (H, W) float32 full-resolution disparity."""
+    h, w = labels.shape
+    H, W = guide_full.shape[0], guide_full.shape[1]
+    if disp is None:
+        disp = torch.empty((H, W), dtype=torch.float32, device=labels.device)
+    j = jbu.c()
+    rc = lib().vs_guided_upsample(
+        _dev(labels, torch.uint8, "labels").data_ptr(), w, h, _pitched(labels, 1, "labels"),
+        _dev(guide_low, torch.uint8, "guide_low").data_ptr(), _pitched(guide_low, 3, "guide_low"),
+        _dev(guide_full, torch.uint8, "guide_full").data_ptr(), W, H, _pitched(guide_full, 3, "guide_full"),
+        ctypes.byref(j), _dev(disp, torch.float32, "disp").data_ptr(), _stream(stream))
+    _check("vs_guided_upsample", rc)
+    return disp
+
+
+def reproject(disp: torch.Tensor, cam: Camera, baseline: float, xyz=None, stream=None) -> torch.Tensor:
+    """Eq. 3; returns (H, W, 3) float32 camera-frame points (NaN where d <= 0)."""
+    _dev(disp, torch.float32, "disp")
+    if not disp.is_contiguous():
+        raise ValueError("disp must be contiguous")
+    H, W = disp.shape
+    if xyz is None:
+        xyz = torch.empty((H, W, 3), dtype=torch.float32, device=disp.device)
+    c = cam.c()
+    rc = lib().vs_reproject(disp.data_ptr(), W, H, ctypes.byref(c), float(baseline),
+                            _dev(xyz, torch.float32, "xyz").data_ptr(), _stream(stream))
+    _check("vs_reproject", rc)
+    return xyz
+
+
+def guided_upsample_reproject(labels, guide_low, guide_full, jbu: JBUParams, cam: Camera, baseline: float,
+                              xyz=None, disp=None, want_disp: bool = True, stream=None):
+    """Eq. 2 + Eq. 3 in one kernel; returns (disp or None, xyz)."""
+    h, w = labels.shape
+    H, W = guide_full.shape[0], guide_full.shape[1]
+    dev = labels.device
+    if xyz is None:
+        xyz = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+    if disp is None and want_disp:
+        disp = torch.empty((H, W), dtype=torch.float32, device=dev)
+    j, c = jbu.c(), cam.c()
+    rc = lib().vs_guided_upsample_reproject(
+        _dev(labels, torch.uint8, "labels").data_ptr(), w, h, _pitched(labels, 1, "labels"),
+        _dev(guide_low, torch.uint8, "guide_low").data_ptr(), _pitched(guide_low, 3, "guide_low"),
+        _dev(guide_full, torch.uint8, "guide_full").data_ptr(), W, H, _pitched(guide_full, 3, "guide_full"),
+        ctypes.byref(j), ctypes.byref(c), float(baseline),
+        disp.data_ptr() if disp is not None else None, _dev(xyz, torch.float32, "xyz").data_ptr(),
+        _stream(stream))
+    _check("vs_guided_upsample_reproject", rc)
+    return disp, xyz
+
+
+def pair_workspace_size(cfg: PairConfig) -> int:
+    c = cfg.c()
+    return int(lib().vs_pair_workspace_size(ctypes.byref(c)))
+
+
+def pair_run(cfg: PairConfig, left_src: torch.Tensor, right_src: torch.Tensor, xyz=None, disp=None,
+             workspace=None, stream=None):
+    """A whole pair on device buffers; returns (disp or None, xyz)."""
+    dev = left_src.device
+    for t, n in ((left_src, "left_src"), (right_src, "right_src")):
+        _dev(t, torch.uint8, n)
+        if not t.is_contiguous() or tuple(t.shape) != (cfg.H, cfg.W, 3):
+            raise ValueError(f"{n} must be a contiguous ({cfg.H}, {cfg.W}, 3) uint8 tensor")
+    if xyz is None:
+        xyz = torch.empty((cfg.H, cfg.W, 3), dtype=torch.float32, device=dev)
+    if workspace is None:
+        workspace = torch.empty(pair_workspace_size(cfg), dtype=torch.uint8, device=dev)
+    c = cfg.c()
+    rc = lib().vs_pair_run(ctypes.byref(c), left_src.data_ptr(), right_src.data_ptr(),
+                           disp.data_ptr() if disp is not None else None, xyz.data_ptr(),
+                           workspace.data_ptr(), workspace.numel(), _stream(stream))
+    _check("vs_pair_run", rc)
+    return disp, xyz
+
+
+def pair_run_host(cfg: PairConfig, left_host: torch.Tensor, right_host: torch.Tensor, xyz_host: torch.Tensor,
+                  dev_in: torch.Tensor, dev_xyz: torch.Tensor, workspace: torch.Tensor, disp_host=None,
+                  dev_disp=None, stream=None):
+    """A whole pair from host (ideally pinned) frames to a host point cloud;
+    copies in and out inside the call and returns when the cloud is on the host."""
+    for t, n in ((left_host, "left_host"), (right_host, "right_host"), (xyz_host, "xyz_host")):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{n} must be a contiguous host tensor")
+    c = cfg.c()
+    rc = lib().vs_pair_run_host(
+        ctypes.byref(c), left_host.data_ptr(), right_host.data_ptr(),
+        disp_host.data_ptr() if disp_host is not None else None, xyz_host.data_ptr(),
+        dev_in.data_ptr(), dev_disp.data_ptr() if dev_disp is not None else None, dev_xyz.data_ptr(),
+        workspace.data_ptr(), workspace.numel(), _stream(stream))
+    _check("vs_pair_run_host", rc)
+    return xyz_host

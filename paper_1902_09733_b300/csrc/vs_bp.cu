@@ -1,0 +1,559 @@
+// Eq. 1: hierarchical loopy min-sum belief propagation on the downsampled
+// grey pair, red-black schedule, truncated-linear smoothness.
+//
+// Data layout (all in the caller's workspace, every array 256-byte aligned):
+//   every level splits its pixels by colour c = (x + y) & 1, so that one
+//   iteration reads one colour and writes the other, both contiguously:
+//     cost_l[c][y][x >> 1][Lp]     level 0 uint8, coarser levels uint16
+//     msg_l [c][k][y][x >> 1][Lp]  uint8 incoming message from direction k
+//   with k = 0 left, 1 right, 2 up, 3 down and Lp = labels rounded up to 16.
+//   Messages live in [0, smooth_trunc] after normalisation, so 8 bits hold
+//   them exactly; all message arithmetic is integer.
+//
+// Kernels per call: k_cost0 (level-0 data term), k_cost_down per coarse
+// level, one k_bp_sweep per iteration and level, k_bp_labels.
+//
+// k_bp_sweep: two threads per active pixel, each owning a pair of outgoing
+// directions (left/right or up/down).  A thread packs the pair into the two
+// 16-bit halves of 32-bit words, one word per label, and runs the O(L)
+// distance transform of the truncated-linear cost (forward pass, backward
+// pass, cap at min + Ts, shift to min 0) for both directions at once with
+// packed 16-bit min operations; the forward results stay in registers.
+#include "vs_common.cuh"
+
+#include <algorithm>
+
+namespace vs {
+namespace {
+
+constexpr int kMaxLevels = 8;
+constexpr uint32_t kBig2 = 0x7FFF7FFFu;   // "label does not exist" in both halves
+
+struct BpLayout {
+    int L, Lp, levels;
+    int w[kMaxLevels], h[kMaxLevels], wh[kMaxLevels];
+    size_t cost_off[kMaxLevels], msg_off[kMaxLevels];
+    size_t total;
+};
+
+bool params_ok(int w, int h, const vs_bp_params *p)
+{
+    if (!p || w <= 0 || h <= 0)
+        return false;
+    if (p->labels < 2 || p->labels > 128 || p->levels < 1 || p->levels > kMaxLevels)
+        return false;
+    if (p->iters < 1 || p->iters > 1000)
+        return false;
+    if (p->data_trunc < 0 || p->data_trunc > 127 || p->smooth_slope < 0 || p->smooth_trunc < 0 ||
+        p->smooth_trunc > 127)
+        return false;
+    const long long coarse = (long long)p->data_trunc << (2 * (p->levels - 1));
+    if (coarse + 4LL * p->smooth_trunc > 32767)
+        return false;
+    if ((long long)w * h > (1LL << 30))
+        return false;
+    return true;
+}
+
+BpLayout make_layout(int w, int h, const vs_bp_params *p)
+{
+    BpLayout lay;
+    lay.L = p->labels;
+    lay.Lp = (p->labels + 15) / 16 * 16;
+    lay.levels = p->levels;
+    size_t off = 0;
+    for (int l = 0; l < p->levels; ++l) {
+        lay.w[l] = l == 0 ? w : (lay.w[l - 1] + 1) / 2;
+        lay.h[l] = l == 0 ? h : (lay.h[l - 1] + 1) / 2;
+        lay.wh[l] = (lay.w[l] + 1) / 2;
+        const size_t slots = (size_t)2 * lay.h[l] * lay.wh[l];
+        lay.cost_off[l] = off;
+        off = align_up(off + slots * lay.Lp * (l == 0 ? 1 : 2), 256);
+        lay.msg_off[l] = off;
+        off = align_up(off + slots * 4 * lay.Lp, 256);
+    }
+    lay.total = off;
+    return lay;
+}
+
+// ---------------------------------------------------------------------------
+// data term
+
+struct Cost0Args {
+    const uint8_t *left, *right;
+    int pitch, w, h, wh, L, Lp, Td;
+    uint8_t *cost;
+};
+
+// D0(x, y, d) = min(|IL(x,y) - IR(x-d,y)|, Td), Td where x - d < 0; 16 labels
+// per thread, padding labels hold 0.
+__global__ void k_cost0(Cost0Args a)
+{
+    const int chunks = a.Lp / 16;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = (long long)2 * a.h * a.wh * chunks;
+    if (idx >= total)
+        return;
+    const int j = (int)(idx % chunks);
+    const long long slot = idx / chunks;
+    const int xh = (int)(slot % a.wh);
+    const int y = (int)((slot / a.wh) % a.h);
+    const int c = (int)(slot / ((long long)a.wh * a.h));
+    const int x = 2 * xh + ((c + y) & 1);
+    if (x >= a.w)
+        return;
+    const uint8_t *rowL = a.left + (size_t)y * a.pitch;
+    const uint8_t *rowR = a.right + (size_t)y * a.pitch;
+    const int il = __ldg(rowL + x);
+    uint32_t wv[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int d = 16 * j + i;
+        int v = 0;
+        if (d < a.L) {
+            v = a.Td;
+            if (x - d >= 0)
+                v = min(abs(il - (int)__ldg(rowR + x - d)), a.Td);
+        }
+        wv[i >> 2] |= (uint32_t)v << (8 * (i & 3));
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(a.cost + (size_t)slot * a.Lp) + j;
+    *dst = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+}
+
+struct CostDownArgs {
+    const void *fine;      // level l-1 (uint8 at level 0, uint16 above)
+    uint16_t *coarse;      // level l
+    int fine_is_u8;
+    int wf, hf, whf;       // fine dims
+    int wc, hc, whc;       // coarse dims
+    int Lp;
+};
+
+// Coarse data term: the sum over the in-frame 2x2 children.  Child
+// (2x+i, 2y+j) has colour (i+j)&1 and column slot x.  8 labels per thread.
+__global__ void k_cost_down(CostDownArgs a)
+{
+    const int chunks = a.Lp / 8;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = (long long)2 * a.hc * a.whc * chunks;
+    if (idx >= total)
+        return;
+    const int j = (int)(idx % chunks);
+    const long long slot = idx / chunks;
+    const int xh = (int)(slot % a.whc);
+    const int y = (int)((slot / a.whc) % a.hc);
+    const int c = (int)(slot / ((long long)a.whc * a.hc));
+    const int x = 2 * xh + ((c + y) & 1);
+    if (x >= a.wc)
+        return;
+    uint32_t acc[4] = {0, 0, 0, 0};   // 8 x u16
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
+#pragma unroll
+        for (int ii = 0; ii < 2; ++ii) {
+            const int xf = 2 * x + ii, yf = 2 * y + jj;
+            if (xf >= a.wf || yf >= a.hf)
+                continue;
+            const int cf = (ii + jj) & 1;
+            const size_t fslot = ((size_t)cf * a.hf + yf) * a.whf + x;
+            if (a.fine_is_u8) {
+                const uint2 v = *(reinterpret_cast<const uint2 *>(
+                                    reinterpret_cast<const uint8_t *>(a.fine) + fslot * a.Lp) + j);
+                // widen 8 bytes to 8 u16 lanes
+                acc[0] += prmt(v.x, 0, 0x4140);
+                acc[1] += prmt(v.x, 0, 0x4342);
+                acc[2] += prmt(v.y, 0, 0x4140);
+                acc[3] += prmt(v.y, 0, 0x4342);
+            } else {
+                const uint4 v = *(reinterpret_cast<const uint4 *>(
+                                    reinterpret_cast<const uint16_t *>(a.fine) + fslot * a.Lp) + j);
+                acc[0] += v.x;
+                acc[1] += v.y;
+                acc[2] += v.z;
+                acc[3] += v.w;
+            }
+        }
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(a.coarse + (size_t)slot * a.Lp) + j;
+    *dst = make_uint4(acc[0], acc[1], acc[2], acc[3]);
+}
+
+// ---------------------------------------------------------------------------
+// message sweep
+
+struct SweepArgs {
+    const void *cost;       // this level
+    uint8_t *msg;           // this level
+    const uint8_t *pmsg;    // parent level (coarse-to-fine initialisation)
+    int w, h, wh, L;
+    int pw, ph, pwh;
+    int color;              // active colour, = t & 1
+    int from_parent;        // incoming = parent's messages (first iteration, not coarsest)
+    int zero_in;            // incoming = 0 (first iteration of the coarsest level)
+    int materialize;        // also store the incoming used into the own slots
+    uint32_t c2, ts2;       // (c, c) and (Ts, Ts) packed
+};
+
+// Byte i of word a in the low half and byte i of word b in the high half,
+// each zero-extended to 16 bits (the bytes are < 128, so sign fill is 0).
+__device__ __forceinline__ uint32_t pair_bytes(uint32_t a, uint32_t b, int i)
+{
+    const uint32_t sel = (uint32_t)i | ((uint32_t)(8 | i) << 4) | ((uint32_t)(4 + i) << 8) |
+                         ((uint32_t)(12 + i) << 12);
+    return prmt(a, b, sel);
+}
+
+template <typename CostT>
+struct CostChunk;
+
+template <>
+struct CostChunk<uint8_t> {
+    uint4 v;
+    __device__ __forceinline__ void load(const uint8_t *base, int j) { v = reinterpret_cast<const uint4 *>(base)[j]; }
+    __device__ __forceinline__ uint32_t dup(int i) const
+    {
+        const uint32_t wv = (&v.x)[i >> 2];
+        return pair_bytes(wv, wv, i & 3);
+    }
+};
+
+template <>
+struct CostChunk<uint16_t> {
+    uint4 v0, v1;
+    __device__ __forceinline__ void load(const uint16_t *base, int j)
+    {
+        v0 = reinterpret_cast<const uint4 *>(base)[2 * j];
+        v1 = reinterpret_cast<const uint4 *>(base)[2 * j + 1];
+    }
+    __device__ __forceinline__ uint32_t dup(int i) const
+    {
+        const uint32_t wv = i < 8 ? (&v0.x)[i >> 1] : (&v1.x)[(i - 8) >> 1];
+        return prmt(wv, wv, (i & 1) ? 0x3232u : 0x1010u);
+    }
+};
+
+template <int LP, typename CostT>
+__global__ void __launch_bounds__(128) k_bp_sweep(SweepArgs a)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int pair = (int)(idx & 1);
+    const long long slot = idx >> 1;
+    if (slot >= (long long)a.h * a.wh)
+        return;
+    const int y = (int)(slot / a.wh);
+    const int xh = (int)(slot - (long long)y * a.wh);
+    const int x = 2 * xh + ((a.color + y) & 1);
+    if (x >= a.w)
+        return;
+    const bool has[4] = {x > 0, x < a.w - 1, y > 0, y < a.h - 1};
+
+    // where the incoming messages of this pixel are read from
+    const uint8_t *in[4];
+    {
+        if (a.from_parent) {
+            const int px = x >> 1, py = y >> 1, pc = (px + py) & 1;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                in[k] = a.pmsg + ((((size_t)pc * 4 + k) * a.ph + py) * a.pwh + (px >> 1)) * LP;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                in[k] = a.msg + ((((size_t)a.color * 4 + k) * a.h + y) * a.wh + xh) * LP;
+        }
+    }
+    bool use[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        use[k] = has[k] && !a.zero_in;
+    const CostT *cost = reinterpret_cast<const CostT *>(a.cost) + ((size_t)a.color * a.h + y) * a.wh * LP +
+                        (size_t)xh * LP;
+    uint8_t *own = a.msg + ((((size_t)a.color * 4) * a.h + y) * a.wh + xh) * LP;
+    const size_t dir_stride = (size_t)a.h * a.wh * LP;
+
+    uint32_t F[LP];
+    uint32_t H2 = kBig2;
+    // excluded incoming pair: (left, right) for pair 0, (up, down) for pair 1
+#pragma unroll
+    for (int j = 0; j < LP / 16; ++j) {
+        uint4 m[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            m[k] = use[k] ? reinterpret_cast<const uint4 *>(in[k])[j] : make_uint4(0, 0, 0, 0);
+        if (a.materialize) {
+            const size_t k0 = 2 * pair;
+            reinterpret_cast<uint4 *>(own + k0 * dir_stride)[j] = pair ? m[2] : m[0];
+            reinterpret_cast<uint4 *>(own + (k0 + 1) * dir_stride)[j] = pair ? m[3] : m[1];
+        }
+        CostChunk<CostT> cc;
+        cc.load(cost, j);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int d = 16 * j + i;
+            const int wi = i >> 2;
+            const uint32_t plr = pair_bytes((&m[0].x)[wi], (&m[1].x)[wi], i & 3);
+            const uint32_t pud = pair_bytes((&m[2].x)[wi], (&m[3].x)[wi], i & 3);
+            const uint32_t t = plr + pud;                       // (L+U, R+D), no carry
+            const uint32_t s2 = t + prmt(t, t, 0x1032u) + cc.dup(i);   // (S, S)
+            uint32_t wv = s2 - (pair ? pud : plr);              // (h_A, h_B)
+            if (d >= a.L)
+                wv = kBig2;
+            F[d] = d == 0 ? wv : min_u16x2(wv, F[d - 1] + a.c2);
+            H2 = min_u16x2(H2, wv);
+        }
+    }
+
+    // destinations: A = left / up neighbour, B = right / down neighbour
+    const int ncolor = a.color ^ 1;
+    uint8_t *dstA = nullptr, *dstB = nullptr;
+    if (pair == 0) {
+        if (has[0])
+            dstA = a.msg + ((((size_t)ncolor * 4 + 1) * a.h + y) * a.wh + ((x - 1) >> 1)) * LP;
+        if (has[1])
+            dstB = a.msg + ((((size_t)ncolor * 4 + 0) * a.h + y) * a.wh + ((x + 1) >> 1)) * LP;
+    } else {
+        if (has[2])
+            dstA = a.msg + ((((size_t)ncolor * 4 + 3) * a.h + (y - 1)) * a.wh + (x >> 1)) * LP;
+        if (has[3])
+            dstB = a.msg + ((((size_t)ncolor * 4 + 2) * a.h + (y + 1)) * a.wh + (x >> 1)) * LP;
+    }
+
+    uint32_t G = F[LP - 1];
+#pragma unroll
+    for (int j = LP / 16 - 1; j >= 0; --j) {
+        uint32_t o[16];
+#pragma unroll
+        for (int i = 15; i >= 0; --i) {
+            const int d = 16 * j + i;
+            if (d < LP - 1)
+                G = min_u16x2(F[d], G + a.c2);
+            o[i] = min_u16x2(G - H2, a.ts2);                    // (m_A(d), m_B(d))
+        }
+        uint32_t oa[4], ob[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t t01 = prmt(o[4 * q], o[4 * q + 1], 0x6420u);
+            const uint32_t t23 = prmt(o[4 * q + 2], o[4 * q + 3], 0x6420u);
+            oa[q] = prmt(t01, t23, 0x6420u);
+            ob[q] = prmt(t01, t23, 0x7531u);
+        }
+        if (dstA)
+            reinterpret_cast<uint4 *>(dstA)[j] = make_uint4(oa[0], oa[1], oa[2], oa[3]);
+        if (dstB)
+            reinterpret_cast<uint4 *>(dstB)[j] = make_uint4(ob[0], ob[1], ob[2], ob[3]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// labels and read-out
+
+struct LabelArgs {
+    const uint8_t *cost;   // level 0
+    const uint8_t *msg;    // level 0
+    uint8_t *labels;
+    int labels_pitch, w, h, wh, L, Lp;
+};
+
+// d* = argmin_d D0(d) + sum of the in-frame incoming messages, smallest d wins.
+__global__ void k_bp_labels(LabelArgs a)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= a.w || y >= a.h)
+        return;
+    const int c = (x + y) & 1, xh = x >> 1;
+    const bool has[4] = {x > 0, x < a.w - 1, y > 0, y < a.h - 1};
+    const uint8_t *cost = a.cost + (((size_t)c * a.h + y) * a.wh + xh) * a.Lp;
+    const uint8_t *in[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        in[k] = a.msg + ((((size_t)c * 4 + k) * a.h + y) * a.wh + xh) * a.Lp;
+    int best = 0x7FFFFFFF, bestd = 0;
+    for (int j = 0; j < a.Lp / 16; ++j) {
+        uint4 cv = reinterpret_cast<const uint4 *>(cost)[j];
+        uint4 m[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            m[k] = has[k] ? reinterpret_cast<const uint4 *>(in[k])[j] : make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int d = 16 * j + i;
+            const int sh = 8 * (i & 3);
+            int b = (int)(((&cv.x)[i >> 2] >> sh) & 0xFF);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                b += (int)(((&m[k].x)[i >> 2] >> sh) & 0xFF);
+            if (d < a.L && b < best) {
+                best = b;
+                bestd = d;
+            }
+        }
+    }
+    a.labels[(size_t)y * a.labels_pitch + x] = (uint8_t)bestd;
+}
+
+struct ExportArgs {
+    const uint8_t *msg;
+    int32_t *out;
+    int w, h, wh, L, Lp;
+};
+
+__global__ void k_bp_export(ExportArgs a)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = 4LL * a.h * a.w * a.L;
+    if (idx >= total)
+        return;
+    const int d = (int)(idx % a.L);
+    const int x = (int)((idx / a.L) % a.w);
+    const int y = (int)((idx / ((long long)a.L * a.w)) % a.h);
+    const int k = (int)(idx / ((long long)a.L * a.w * a.h));
+    const bool has = k == 0 ? x > 0 : k == 1 ? x < a.w - 1 : k == 2 ? y > 0 : y < a.h - 1;
+    const int c = (x + y) & 1;
+    int v = 0;
+    if (has)
+        v = a.msg[((((size_t)c * 4 + k) * a.h + y) * a.wh + (x >> 1)) * a.Lp + d];
+    a.out[idx] = v;
+}
+
+// ---------------------------------------------------------------------------
+// host dispatch
+
+template <int LP>
+void launch_sweep_lp(const SweepArgs &a, bool level0, cudaStream_t st)
+{
+    const long long threads = 2LL * a.h * a.wh;
+    const int block = 128;
+    const unsigned grid = (unsigned)((threads + block - 1) / block);
+    if (level0)
+        k_bp_sweep<LP, uint8_t><<<grid, block, 0, st>>>(a);
+    else
+        k_bp_sweep<LP, uint16_t><<<grid, block, 0, st>>>(a);
+}
+
+void launch_sweep(int Lp, const SweepArgs &a, bool level0, cudaStream_t st)
+{
+    switch (Lp) {
+    case 16: launch_sweep_lp<16>(a, level0, st); break;
+    case 32: launch_sweep_lp<32>(a, level0, st); break;
+    case 48: launch_sweep_lp<48>(a, level0, st); break;
+    case 64: launch_sweep_lp<64>(a, level0, st); break;
+    case 80: launch_sweep_lp<80>(a, level0, st); break;
+    case 96: launch_sweep_lp<96>(a, level0, st); break;
+    case 112: launch_sweep_lp<112>(a, level0, st); break;
+    default: launch_sweep_lp<128>(a, level0, st); break;
+    }
+}
+
+int check_workspace(const BpLayout &lay, const void *ws, size_t ws_bytes)
+{
+    if (!ws || !aligned(ws, 256) || ws_bytes < lay.total)
+        return VS_EWORKSPACE;
+    return VS_OK;
+}
+
+}  // namespace
+}  // namespace vs
+
+extern "C" size_t vs_bp_workspace_size(int w, int h, const vs_bp_params *p)
+{
+    using namespace vs;
+    if (!params_ok(w, h, p))
+        return 0;
+    return make_layout(w, h, p).total;
+}
+
+extern "C" int vs_bp_stereo(const uint8_t *left, const uint8_t *right, int w, int h, int pitch,
+                            const vs_bp_params *p, uint8_t *labels, int labels_pitch,
+                            void *workspace, size_t ws_bytes, void *stream)
+{
+    using namespace vs;
+    if (!params_ok(w, h, p) || !left || !right || !labels || pitch < w || labels_pitch < w)
+        return VS_EINVAL;
+    const BpLayout lay = make_layout(w, h, p);
+    int rc = check_workspace(lay, workspace, ws_bytes);
+    if (rc != VS_OK)
+        return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint8_t *ws = reinterpret_cast<uint8_t *>(workspace);
+    const int block = 256;
+
+    {   // level-0 data term
+        Cost0Args a{left, right, pitch, w, h, lay.wh[0], lay.L, lay.Lp, p->data_trunc, ws + lay.cost_off[0]};
+        const long long n = 2LL * h * lay.wh[0] * (lay.Lp / 16);
+        const int slot = prof_begin(kProfBpOther, st);
+        k_cost0<<<(unsigned)((n + block - 1) / block), block, 0, st>>>(a);
+        prof_end(slot, st);
+        note_launch();
+    }
+    for (int l = 1; l < lay.levels; ++l) {   // coarse data terms
+        CostDownArgs a;
+        a.fine = ws + lay.cost_off[l - 1];
+        a.coarse = reinterpret_cast<uint16_t *>(ws + lay.cost_off[l]);
+        a.fine_is_u8 = l == 1;
+        a.wf = lay.w[l - 1];
+        a.hf = lay.h[l - 1];
+        a.whf = lay.wh[l - 1];
+        a.wc = lay.w[l];
+        a.hc = lay.h[l];
+        a.whc = lay.wh[l];
+        a.Lp = lay.Lp;
+        const long long n = 2LL * a.hc * a.whc * (lay.Lp / 8);
+        const int slot = prof_begin(kProfBpOther, st);
+        k_cost_down<<<(unsigned)((n + block - 1) / block), block, 0, st>>>(a);
+        prof_end(slot, st);
+        note_launch();
+    }
+    const int ceff = std::min(p->smooth_slope, p->smooth_trunc);   // same V for any larger slope
+    for (int l = lay.levels - 1; l >= 0; --l) {
+        SweepArgs a;
+        a.cost = ws + lay.cost_off[l];
+        a.msg = ws + lay.msg_off[l];
+        a.pmsg = l + 1 < lay.levels ? ws + lay.msg_off[l + 1] : nullptr;
+        a.w = lay.w[l];
+        a.h = lay.h[l];
+        a.wh = lay.wh[l];
+        a.L = lay.L;
+        a.pw = l + 1 < lay.levels ? lay.w[l + 1] : 0;
+        a.ph = l + 1 < lay.levels ? lay.h[l + 1] : 0;
+        a.pwh = l + 1 < lay.levels ? lay.wh[l + 1] : 0;
+        a.c2 = (uint32_t)ceff * 0x10001u;
+        a.ts2 = (uint32_t)p->smooth_trunc * 0x10001u;
+        for (int t = 0; t < p->iters; ++t) {
+            a.color = t & 1;
+            a.from_parent = (t == 0 && l + 1 < lay.levels);
+            a.zero_in = (t == 0 && l + 1 == lay.levels);
+            a.materialize = (t == 0 && p->iters == 1);
+            const int slot = prof_begin(l == 0 ? kProfSweepL0 : kProfSweepCoarse, st);
+            launch_sweep(lay.Lp, a, l == 0, st);
+            prof_end(slot, st);
+            note_launch();
+        }
+    }
+    {
+        LabelArgs a{ws + lay.cost_off[0], ws + lay.msg_off[0], labels, labels_pitch, w, h, lay.wh[0], lay.L, lay.Lp};
+        dim3 grid((w + 127) / 128, h);
+        const int slot = prof_begin(kProfBpOther, st);
+        k_bp_labels<<<grid, 128, 0, st>>>(a);
+        prof_end(slot, st);
+        note_launch();
+    }
+    return launch_status();
+}
+
+extern "C" int vs_bp_export_messages(const void *workspace, size_t ws_bytes, int w, int h,
+                                     const vs_bp_params *p, int32_t *out, void *stream)
+{
+    using namespace vs;
+    if (!params_ok(w, h, p) || !out)
+        return VS_EINVAL;
+    const BpLayout lay = make_layout(w, h, p);
+    int rc = check_workspace(lay, workspace, ws_bytes);
+    if (rc != VS_OK)
+        return rc;
+    ExportArgs a{reinterpret_cast<const uint8_t *>(workspace) + lay.msg_off[0], out, w, h, lay.wh[0], lay.L, lay.Lp};
+    const long long n = 4LL * h * w * lay.L;
+    k_bp_export<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(a);
+    note_launch();
+    return launch_status();
+}

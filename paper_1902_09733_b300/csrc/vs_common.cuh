@@ -1,0 +1,46 @@
+// Shared helpers of the CUDA virtual-stereo library (device code, launch
+// bookkeeping).  Nothing here is shared with the CPU checker.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/vstereo.h"
+
+namespace vs {
+
+// Counts every kernel the library enqueues (vs_kernel_launches()).
+void note_launch(unsigned n = 1);
+
+// Status after a launch: VS_ECUDA if the runtime reports an error.
+int launch_status();
+
+// Optional CUDA-event timing of selected launches (vs_profile_enable).
+// prof_begin returns a slot (or -1 when timing is off) and records its start
+// event on `st`; prof_end records the matching stop event.
+enum ProfTag { kProfSweepL0 = 0, kProfSweepCoarse = 1, kProfRemap = 2, kProfJbu = 3, kProfBpOther = 4 };
+int prof_begin(int tag, cudaStream_t st);
+void prof_end(int slot, cudaStream_t st);
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+inline bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Packed 2 x 16-bit unsigned minimum (PTX ISA 8.0+, sm_90 and later).
+__device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+// Byte permute: result byte i = byte sel[i] of {b:a} (a = bytes 0..3); a
+// selector nibble with bit 3 set replicates the sign bit of that byte.
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
+{
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+}  // namespace vs

@@ -1,0 +1,226 @@
+// Whole-pair drivers (Section 2.1 -> Eq. 1 -> Eq. 2 -> Eq. 3), status names
+// and launch bookkeeping.
+#include "vs_common.cuh"
+
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+namespace vs {
+namespace {
+
+std::atomic<uint64_t> g_launches{0};
+
+// event ring for vs_profile_*: slots are handed out in order; a slot stays
+// pending until vs_profile_collect reads it
+struct ProfState {
+    std::mutex mu;
+    std::vector<cudaEvent_t> start, stop;
+    std::vector<int> tag;
+    std::vector<int> pending;
+    int next = 0;
+    bool on = false;
+} g_prof;
+
+struct PairLayout {
+    int w, h;
+    size_t rect_l, rect_r, low_rgb, gray_l, gray_r, labels, bp;
+    size_t bp_bytes, total;
+};
+
+bool pair_layout(const vs_pair_config *cfg, PairLayout *out)
+{
+    if (!cfg || cfg->W <= 0 || cfg->H <= 0)
+        return false;
+    const int s = cfg->jbu.scale;
+    if (s < 1 || s > 16)
+        return false;
+    PairLayout lay;
+    lay.w = (cfg->W + s - 1) / s;
+    lay.h = (cfg->H + s - 1) / s;
+    const size_t full = (size_t)cfg->W * cfg->H * 3;
+    const size_t low = (size_t)lay.w * lay.h;
+    size_t off = 0;
+    lay.rect_l = off;
+    off = align_up(off + full, 256);
+    lay.rect_r = off;
+    off = align_up(off + full, 256);
+    lay.low_rgb = off;
+    off = align_up(off + 3 * low, 256);
+    lay.gray_l = off;
+    off = align_up(off + low, 256);
+    lay.gray_r = off;
+    off = align_up(off + low, 256);
+    lay.labels = off;
+    off = align_up(off + low, 256);
+    lay.bp = off;
+    lay.bp_bytes = vs_bp_workspace_size(lay.w, lay.h, &cfg->bp);
+    if (lay.bp_bytes == 0)
+        return false;
+    off = align_up(off + lay.bp_bytes, 256);
+    lay.total = off;
+    *out = lay;
+    return true;
+}
+
+}  // namespace
+
+void note_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int launch_status()
+{
+    return cudaGetLastError() == cudaSuccess ? VS_OK : VS_ECUDA;
+}
+
+int prof_begin(int tag, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    if (!g_prof.on || g_prof.start.empty())
+        return -1;
+    const int slot = g_prof.next;
+    g_prof.next = (g_prof.next + 1) % (int)g_prof.start.size();
+    g_prof.tag[slot] = tag;
+    g_prof.pending.push_back(slot);
+    cudaEventRecord(g_prof.start[slot], st);
+    return slot;
+}
+
+void prof_end(int slot, cudaStream_t st)
+{
+    if (slot < 0)
+        return;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    cudaEventRecord(g_prof.stop[slot], st);
+}
+
+}  // namespace vs
+
+extern "C" int vs_profile_enable(int capacity)
+{
+    using namespace vs;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    for (size_t i = 0; i < g_prof.start.size(); ++i) {
+        cudaEventDestroy(g_prof.start[i]);
+        cudaEventDestroy(g_prof.stop[i]);
+    }
+    g_prof.start.clear();
+    g_prof.stop.clear();
+    g_prof.tag.clear();
+    g_prof.pending.clear();
+    g_prof.next = 0;
+    g_prof.on = false;
+    if (capacity < 0 || capacity > (1 << 20))
+        return VS_EINVAL;
+    for (int i = 0; i < capacity; ++i) {
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess)
+            return VS_ECUDA;
+        if (cudaEventCreate(&b) != cudaSuccess) {
+            cudaEventDestroy(a);
+            return VS_ECUDA;
+        }
+        g_prof.start.push_back(a);
+        g_prof.stop.push_back(b);
+        g_prof.tag.push_back(-1);
+    }
+    g_prof.on = capacity > 0;
+    return VS_OK;
+}
+
+extern "C" int vs_profile_collect(int *tags, float *ms, int max)
+{
+    using namespace vs;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    int n = 0;
+    for (int slot : g_prof.pending) {
+        if (n >= max)
+            break;
+        if (cudaEventSynchronize(g_prof.stop[slot]) != cudaSuccess)
+            return VS_ECUDA;
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, g_prof.start[slot], g_prof.stop[slot]) != cudaSuccess)
+            return VS_ECUDA;
+        tags[n] = g_prof.tag[slot];
+        ms[n] = t;
+        ++n;
+    }
+    g_prof.pending.clear();
+    return n;
+}
+
+extern "C" const char *vs_status_string(int status)
+{
+    switch (status) {
+    case VS_OK: return "ok";
+    case VS_EINVAL: return "invalid argument (size, count or parameter out of range)";
+    case VS_EALIGN: return "pointer or pitch breaks an alignment rule";
+    case VS_EWORKSPACE: return "workspace missing, misaligned or too small";
+    case VS_ECUDA: return "CUDA runtime error";
+    default: return "unknown status";
+    }
+}
+
+extern "C" uint64_t vs_kernel_launches(void) { return vs::g_launches.load(std::memory_order_relaxed); }
+
+extern "C" size_t vs_pair_workspace_size(const vs_pair_config *cfg)
+{
+    vs::PairLayout lay;
+    return vs::pair_layout(cfg, &lay) ? lay.total : 0;
+}
+
+extern "C" int vs_pair_run(const vs_pair_config *cfg, const uint8_t *left_src, const uint8_t *right_src,
+                           float *disp, float *xyz, void *workspace, size_t ws_bytes, void *stream)
+{
+    using namespace vs;
+    PairLayout lay;
+    if (!pair_layout(cfg, &lay) || !left_src || !right_src || !xyz)
+        return VS_EINVAL;
+    if (!workspace || !aligned(workspace, 256) || ws_bytes < lay.total)
+        return VS_EWORKSPACE;
+    uint8_t *ws = reinterpret_cast<uint8_t *>(workspace);
+    const int W = cfg->W, H = cfg->H, s = cfg->jbu.scale;
+    int rc = vs_rectify_remap(left_src, W, H, 3 * W, &cfg->cam, nullptr, ws + lay.rect_l, 3 * W, s,
+                              ws + lay.low_rgb, 3 * lay.w, ws + lay.gray_l, lay.w, stream);
+    if (rc != VS_OK)
+        return rc;
+    // the right frame only feeds the matcher: its full-res copy is not needed
+    rc = vs_rectify_remap(right_src, W, H, 3 * W, &cfg->cam, nullptr, nullptr, 0, s, nullptr, 0,
+                          ws + lay.gray_r, lay.w, stream);
+    if (rc != VS_OK)
+        return rc;
+    rc = vs_bp_stereo(ws + lay.gray_l, ws + lay.gray_r, lay.w, lay.h, lay.w, &cfg->bp, ws + lay.labels, lay.w,
+                      ws + lay.bp, lay.bp_bytes, stream);
+    if (rc != VS_OK)
+        return rc;
+    return vs_guided_upsample_reproject(ws + lay.labels, lay.w, lay.h, lay.w, ws + lay.low_rgb, 3 * lay.w,
+                                        ws + lay.rect_l, W, H, 3 * W, &cfg->jbu, &cfg->cam, cfg->baseline, disp,
+                                        xyz, stream);
+}
+
+extern "C" int vs_pair_run_host(const vs_pair_config *cfg, const uint8_t *left_host, const uint8_t *right_host,
+                                float *disp_host, float *xyz_host, uint8_t *dev_in, float *dev_disp,
+                                float *dev_xyz, void *workspace, size_t ws_bytes, void *stream)
+{
+    using namespace vs;
+    PairLayout lay;
+    if (!pair_layout(cfg, &lay) || !left_host || !right_host || !xyz_host || !dev_in || !dev_xyz)
+        return VS_EINVAL;
+    if (disp_host && !dev_disp)
+        return VS_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t frame = (size_t)cfg->W * cfg->H * 3;
+    const size_t npx = (size_t)cfg->W * cfg->H;
+    if (cudaMemcpyAsync(dev_in, left_host, frame, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(dev_in + frame, right_host, frame, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return VS_ECUDA;
+    int rc = vs_pair_run(cfg, dev_in, dev_in + frame, disp_host ? dev_disp : nullptr, dev_xyz, workspace,
+                         ws_bytes, stream);
+    if (rc != VS_OK)
+        return rc;
+    if (cudaMemcpyAsync(xyz_host, dev_xyz, npx * 3 * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return VS_ECUDA;
+    if (disp_host &&
+        cudaMemcpyAsync(disp_host, dev_disp, npx * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return VS_ECUDA;
+    return cudaStreamSynchronize(st) == cudaSuccess ? VS_OK : VS_ECUDA;
+}

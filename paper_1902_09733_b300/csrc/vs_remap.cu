@@ -1,0 +1,209 @@
+// Section 2.1 undistort/rectify remap fused with the Section 2.2 downsample.
+//
+// One CTA owns a tile of TLW x TLH low-resolution pixels, i.e. an aligned
+// block of (TLW s) x (TLH s) full-resolution pixels.  Each thread maps its
+// destination pixels through the radial lens model (FP32), samples the
+// source bilinearly, rounds, writes the full-resolution RGB and keeps a copy
+// in shared memory; the CTA then reduces every s x s block to the low-res RGB
+// mean and its grey.  One launch per frame, no intermediate buffers.
+#include "vs_common.cuh"
+
+namespace vs {
+namespace {
+
+constexpr int kRemapThreads = 256;
+constexpr int kTileFullW = 64;   // full-res tile width target
+constexpr int kTileFullH = 16;   // full-res tile height target
+constexpr int kTilePixMax = kTileFullW * kTileFullH;
+
+struct RemapArgs {
+    const uint8_t *src;
+    uint8_t *dst;
+    uint8_t *low_rgb;
+    uint8_t *low_gray;
+    int W, H, src_pitch, dst_pitch, low_rgb_pitch, low_gray_pitch;
+    int s, w, h;                // scale and low-res size
+    int tlw, tlh;               // tile size in low-res pixels
+    float fx, fy, cx, cy, k1, k2;
+    float R[9];
+    int has_R;
+};
+
+__device__ __forceinline__ float tap(const uint8_t *src, int pitch, int W, int H, int x, int y, int ch)
+{
+    if (x < 0 || y < 0 || x >= W || y >= H)
+        return 0.0f;
+    return (float)__ldg(src + (size_t)y * pitch + (size_t)x * 3 + ch);
+}
+
+__global__ void __launch_bounds__(kRemapThreads) k_remap_down(RemapArgs a)
+{
+    __shared__ uint8_t tile[kTilePixMax * 3];
+    const int tfw = a.tlw * a.s, tfh = a.tlh * a.s;   // full-res tile size
+    const int u0 = blockIdx.x * tfw, v0 = blockIdx.y * tfh;
+    const bool want_low = (a.low_rgb != nullptr) || (a.low_gray != nullptr);
+
+    for (int i = threadIdx.x; i < tfw * tfh; i += blockDim.x) {
+        const int lu = i % tfw, lv = i / tfw;
+        const int u = u0 + lu, v = v0 + lv;
+        if (u >= a.W || v >= a.H)
+            continue;
+        float xn = ((float)u - a.cx) / a.fx;
+        float yn = ((float)v - a.cy) / a.fy;
+        bool valid = true;
+        if (a.has_R) {
+            const float X = a.R[0] * xn + a.R[3] * yn + a.R[6];
+            const float Y = a.R[1] * xn + a.R[4] * yn + a.R[7];
+            const float Z = a.R[2] * xn + a.R[5] * yn + a.R[8];
+            if (Z <= 0.0f) {
+                valid = false;
+            } else {
+                xn = X / Z;
+                yn = Y / Z;
+            }
+        }
+        float val[3] = {0.0f, 0.0f, 0.0f};
+        if (valid) {
+            const float r2 = xn * xn + yn * yn;
+            const float radial = 1.0f + a.k1 * r2 + a.k2 * r2 * r2;
+            const float sx = a.fx * (xn * radial) + a.cx;
+            const float sy = a.fy * (yn * radial) + a.cy;
+            if (sx > -1.0f && sx < (float)a.W && sy > -1.0f && sy < (float)a.H) {
+                const float fx0 = floorf(sx), fy0 = floorf(sy);
+                const int x0 = (int)fx0, y0 = (int)fy0;
+                const float ax = sx - fx0, ay = sy - fy0;
+                const float w00 = (1.0f - ax) * (1.0f - ay), w10 = ax * (1.0f - ay);
+                const float w01 = (1.0f - ax) * ay, w11 = ax * ay;
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    val[ch] = w00 * tap(a.src, a.src_pitch, a.W, a.H, x0, y0, ch)
+                            + w10 * tap(a.src, a.src_pitch, a.W, a.H, x0 + 1, y0, ch)
+                            + w01 * tap(a.src, a.src_pitch, a.W, a.H, x0, y0 + 1, ch)
+                            + w11 * tap(a.src, a.src_pitch, a.W, a.H, x0 + 1, y0 + 1, ch);
+                }
+            }
+        }
+        uint8_t out[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            int r = __float2int_rn(val[ch]);   // round half to even
+            out[ch] = (uint8_t)min(max(r, 0), 255);
+        }
+        if (a.dst) {
+            uint8_t *d = a.dst + (size_t)v * a.dst_pitch + (size_t)u * 3;
+            d[0] = out[0];
+            d[1] = out[1];
+            d[2] = out[2];
+        }
+        if (want_low) {
+            tile[i * 3 + 0] = out[0];
+            tile[i * 3 + 1] = out[1];
+            tile[i * 3 + 2] = out[2];
+        }
+    }
+    if (!want_low)
+        return;
+    __syncthreads();
+    for (int j = threadIdx.x; j < a.tlw * a.tlh; j += blockDim.x) {
+        const int lx = j % a.tlw, ly = j / a.tlw;
+        const int xl = blockIdx.x * a.tlw + lx, yl = blockIdx.y * a.tlh + ly;
+        if (xl >= a.w || yl >= a.h)
+            continue;
+        int sum[3] = {0, 0, 0};
+        int n = 0;
+        for (int jj = 0; jj < a.s; ++jj) {
+            const int v = yl * a.s + jj;
+            if (v >= a.H)
+                break;
+            for (int ii = 0; ii < a.s; ++ii) {
+                const int u = xl * a.s + ii;
+                if (u >= a.W)
+                    break;
+                const int t = ((ly * a.s + jj) * tfw + lx * a.s + ii) * 3;
+                sum[0] += tile[t];
+                sum[1] += tile[t + 1];
+                sum[2] += tile[t + 2];
+                ++n;
+            }
+        }
+        int mean[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch)
+            mean[ch] = (sum[ch] + n / 2) / n;
+        if (a.low_rgb) {
+            uint8_t *d = a.low_rgb + (size_t)yl * a.low_rgb_pitch + (size_t)xl * 3;
+            d[0] = (uint8_t)mean[0];
+            d[1] = (uint8_t)mean[1];
+            d[2] = (uint8_t)mean[2];
+        }
+        if (a.low_gray)
+            a.low_gray[(size_t)yl * a.low_gray_pitch + xl] =
+                (uint8_t)((77 * mean[0] + 150 * mean[1] + 29 * mean[2] + 128) >> 8);
+    }
+}
+
+}  // namespace
+}  // namespace vs
+
+extern "C" int vs_rectify_remap(const uint8_t *src, int W, int H, int src_pitch,
+                                const vs_camera *cam, const float *R9,
+                                uint8_t *dst, int dst_pitch, int scale,
+                                uint8_t *low_rgb, int low_rgb_pitch,
+                                uint8_t *low_gray, int low_gray_pitch, void *stream)
+{
+    using namespace vs;
+    if (!src || !cam || W <= 0 || H <= 0 || src_pitch < 3 * W)
+        return VS_EINVAL;
+    if (!dst && !low_rgb && !low_gray)
+        return VS_EINVAL;
+    if (dst && dst_pitch < 3 * W)
+        return VS_EINVAL;
+    const float cv[6] = {cam->fx, cam->fy, cam->cx, cam->cy, cam->k1, cam->k2};
+    for (float f : cv)
+        if (!isfinite(f))
+            return VS_EINVAL;
+    if (cam->fx == 0.0f || cam->fy == 0.0f)
+        return VS_EINVAL;
+    const bool want_low = low_rgb || low_gray;
+    if (want_low && (scale < 1 || scale > 16))
+        return VS_EINVAL;
+    const int s = want_low ? scale : 1;
+    const int w = (W + s - 1) / s, h = (H + s - 1) / s;
+    if (low_rgb && low_rgb_pitch < 3 * w)
+        return VS_EINVAL;
+    if (low_gray && low_gray_pitch < w)
+        return VS_EINVAL;
+
+    RemapArgs a;
+    a.src = src;
+    a.dst = dst;
+    a.low_rgb = low_rgb;
+    a.low_gray = low_gray;
+    a.W = W;
+    a.H = H;
+    a.src_pitch = src_pitch;
+    a.dst_pitch = dst_pitch;
+    a.low_rgb_pitch = low_rgb_pitch;
+    a.low_gray_pitch = low_gray_pitch;
+    a.s = s;
+    a.w = w;
+    a.h = h;
+    a.tlw = kTileFullW / s > 0 ? kTileFullW / s : 1;
+    a.tlh = kTileFullH / s > 0 ? kTileFullH / s : 1;
+    a.fx = cam->fx;
+    a.fy = cam->fy;
+    a.cx = cam->cx;
+    a.cy = cam->cy;
+    a.k1 = cam->k1;
+    a.k2 = cam->k2;
+    a.has_R = R9 != nullptr;
+    for (int i = 0; i < 9; ++i)
+        a.R[i] = R9 ? R9[i] : (i % 4 == 0 ? 1.0f : 0.0f);
+    const int tfw = a.tlw * s, tfh = a.tlh * s;
+    dim3 grid((W + tfw - 1) / tfw, (H + tfh - 1) / tfh);
+    const int slot = prof_begin(kProfRemap, (cudaStream_t)stream);
+    k_remap_down<<<grid, kRemapThreads, 0, (cudaStream_t)stream>>>(a);
+    prof_end(slot, (cudaStream_t)stream);
+    note_launch();
+    return launch_status();
+}

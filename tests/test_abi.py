@@ -1,0 +1,83 @@
+"""Host-side checks of the C ABI: the library loads, exports every entry point
+that include/vstereo.h declares, and rejects bad arguments before touching
+the GPU.  No CUDA device is needed (no kernel is launched)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1902_09733_b300 as vs
+from paper_1902_09733_b300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return vs.lib()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "vstereo.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(vs_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings(lib):
+    for code in (0, -1, -2, -3, -4):
+        assert lib.vs_status_string(code)
+    assert vs.status_string(-3).startswith("workspace")
+
+
+def test_workspace_sizes_and_parameter_ranges(lib):
+    ok = vs.BPParams(labels=64, levels=4, iters=10, data_trunc=20, smooth_slope=10, smooth_trunc=40)
+    n = vs.bp_workspace_size(676, 380, ok)
+    # level 0: costs 2*380*338*64 + messages 8*380*338*64 bytes; coarser levels add about a third
+    lvl0 = 10 * 380 * 338 * 64
+    assert lvl0 < n < 1.45 * lvl0
+    bad = [
+        dict(labels=1), dict(labels=129), dict(levels=0), dict(levels=9), dict(iters=0),
+        dict(data_trunc=128), dict(smooth_trunc=128), dict(smooth_slope=-1),
+        dict(levels=7, data_trunc=20),            # 20 * 4^6 overflows the 16-bit sums
+    ]
+    for b in bad:
+        p = vs.BPParams(**{**ok.__dict__, **b})
+        assert vs.bp_workspace_size(676, 380, p) == 0, b
+    assert vs.bp_workspace_size(0, 10, ok) == 0
+    cfg = vs.PairConfig(2704, 1520, vs.Camera(1400, 1400, 1351.5, 759.5, -0.25, 0.07), 0.5, ok, vs.JBUParams())
+    assert vs.pair_workspace_size(cfg) > n + 2 * 2704 * 1520 * 3
+
+
+def test_bad_arguments_are_rejected_on_the_host(lib):
+    p = vs._BPParams(16, 3, 5, 20, 10, 40)
+    # NULL images, bad pitch, missing workspace: rejected before any launch
+    assert lib.vs_bp_stereo(None, None, 160, 120, 160, ctypes.byref(p), None, 160, None, 0, None) == vs.VS_EINVAL
+    fake = 1 << 20   # never dereferenced: the checks fail first
+    assert lib.vs_bp_stereo(fake, fake, 160, 120, 100, ctypes.byref(p), fake, 160, fake, 1 << 30, None) == vs.VS_EINVAL
+    assert lib.vs_bp_stereo(fake, fake, 160, 120, 160, ctypes.byref(p), fake, 160, None, 0, None) == vs.VS_EWORKSPACE
+    assert lib.vs_bp_stereo(fake, fake, 160, 120, 160, ctypes.byref(p), fake, 160, fake + 16, 1 << 30, None) == vs.VS_EWORKSPACE
+    assert lib.vs_bp_stereo(fake, fake, 160, 120, 160, ctypes.byref(p), fake, 160, fake, 100, None) == vs.VS_EWORKSPACE
+    cam = vs._Camera(1400, 1400, 1351.5, 759.5, -0.25, 0.07)
+    assert lib.vs_rectify_remap(None, 10, 10, 30, ctypes.byref(cam), None, fake, 30, 4, None, 0, None, 0, None) == vs.VS_EINVAL
+    assert lib.vs_rectify_remap(fake, 10, 10, 20, ctypes.byref(cam), None, fake, 30, 4, None, 0, None, 0, None) == vs.VS_EINVAL
+    assert lib.vs_rectify_remap(fake, 10, 10, 30, ctypes.byref(cam), None, fake, 30, 17, fake, 9, None, 0, None) == vs.VS_EINVAL
+    badcam = vs._Camera(0, 1400, 1351.5, 759.5, 0, 0)
+    assert lib.vs_rectify_remap(fake, 10, 10, 30, ctypes.byref(badcam), None, fake, 30, 4, None, 0, None, 0, None) == vs.VS_EINVAL
+    j = vs._JBUParams(4, 2, 1.0, 12.0)
+    # low-res size must be ceil(W / s)
+    assert lib.vs_guided_upsample(fake, 10, 10, 10, fake, 30, fake, 48, 40, 144, ctypes.byref(j), fake, None) == vs.VS_EINVAL
+    j0 = vs._JBUParams(4, 2, 0.0, 12.0)
+    assert lib.vs_guided_upsample(fake, 12, 10, 12, fake, 36, fake, 48, 40, 144, ctypes.byref(j0), fake, None) == vs.VS_EINVAL
+    jr = vs._JBUParams(4, 4, 1.0, 12.0)
+    assert lib.vs_guided_upsample(fake, 12, 10, 12, fake, 36, fake, 48, 40, 144, ctypes.byref(jr), fake, None) == vs.VS_EINVAL
+    assert lib.vs_reproject(fake, 10, 10, ctypes.byref(cam), 0.0, fake, None) == vs.VS_EINVAL
+    assert lib.vs_reproject(fake, 10, 10, ctypes.byref(cam), -1.0, fake, None) == vs.VS_EINVAL
