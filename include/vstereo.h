@@ -216,8 +216,9 @@ uint64_t vs_kernel_launches(void);
  * while on, each launch of the timed kernels is bracketed by an event pair
  * on its stream, also when the stream is being captured into a CUDA graph.
  * vs_profile_collect synchronises the pending pairs and writes up to `max`
- * (tag, milliseconds) records, oldest first; it returns the count or a
- * negative status.  Tags: 0 level-0 message sweep, 1 coarser-level sweep,
+ * (tag, milliseconds) records, oldest first, skipping pairs that have no
+ * time (recorded during capture of a graph that has not run); it returns the
+ * count.  Tags: 0 level-0 message sweep, 1 coarser-level sweep,
  * 2 remap, 3 upsample (+ reprojection), 4 other BP kernels (cost, pyramid,
  * labels).  Slots are reused round-robin, so collect before n more launches. */
 int vs_profile_enable(int capacity);

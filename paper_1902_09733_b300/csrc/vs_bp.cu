@@ -262,10 +262,17 @@ __global__ void __launch_bounds__(128) k_bp_sweep(SweepArgs a)
                 in[k] = a.msg + ((((size_t)a.color * 4 + k) * a.h + y) * a.wh + xh) * LP;
         }
     }
+    // a slot is read only if the neighbour exists here and, when the messages
+    // come from the parent, the parent has that neighbour too (otherwise the
+    // parent never received from it and its message is 0)
     bool use[4];
+    {
+        const int px = x >> 1, py = y >> 1;
+        const bool phas[4] = {px > 0, px < a.pw - 1, py > 0, py < a.ph - 1};
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-        use[k] = has[k] && !a.zero_in;
+        for (int k = 0; k < 4; ++k)
+            use[k] = has[k] && !a.zero_in && (!a.from_parent || phas[k]);
+    }
     const CostT *cost = reinterpret_cast<const CostT *>(a.cost) + ((size_t)a.color * a.h + y) * a.wh * LP +
                         (size_t)xh * LP;
     uint8_t *own = a.msg + ((((size_t)a.color * 4) * a.h + y) * a.wh + xh) * LP;

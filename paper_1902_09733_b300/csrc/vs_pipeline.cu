@@ -135,11 +135,14 @@ extern "C" int vs_profile_collect(int *tags, float *ms, int max)
     for (int slot : g_prof.pending) {
         if (n >= max)
             break;
-        if (cudaEventSynchronize(g_prof.stop[slot]) != cudaSuccess)
-            return VS_ECUDA;
+        // a pair recorded only during stream capture has no time until its
+        // graph has run; such pairs are skipped
         float t = 0.0f;
-        if (cudaEventElapsedTime(&t, g_prof.start[slot], g_prof.stop[slot]) != cudaSuccess)
-            return VS_ECUDA;
+        if (cudaEventSynchronize(g_prof.stop[slot]) != cudaSuccess ||
+            cudaEventElapsedTime(&t, g_prof.start[slot], g_prof.stop[slot]) != cudaSuccess) {
+            (void)cudaGetLastError();
+            continue;
+        }
         tags[n] = g_prof.tag[slot];
         ms[n] = t;
         ++n;
