@@ -122,6 +122,26 @@ int vs_bp_stereo(const uint8_t *left, const uint8_t *right, int w, int h, int pi
                  const vs_bp_params *p, uint8_t *labels, int labels_pitch,
                  void *workspace, size_t ws_bytes, void *stream);
 
+/* vs_bp_stereo for callers that cannot allocate device memory -- code running
+ * where cudaMalloc is off limits (inside a host allocator or memory-pool
+ * callback, a plugin whose host owns every allocation, a tight real-time loop
+ * that must not allocate).  The paper has no counterpart; this is a
+ * deployment convenience.  It runs exactly vs_bp_stereo (same arguments, same
+ * results) on a scratch array built into the library: VS_BP_NOALLOC_SCRATCH_BYTES
+ * (8 MiB) of device memory that every GPU loading the library keeps until
+ * the process exits.  That fits, for example, 320 x 180 with 16 labels and 3
+ * levels (the paper's own setting) or 160 x 120 with up to 48 labels; a pair
+ * whose vs_bp_workspace_size() exceeds it is rejected with VS_EWORKSPACE
+ * before anything is enqueued.  The call allocates nothing.  Its first call
+ * on a device looks up the scratch address for that device (the device must
+ * be current), so make that first call before any stream capture.  All calls
+ * share the one scratch and it keeps the last call's contents (nothing needs
+ * clearing between calls); calls whose work overlaps on the GPU -- other
+ * streams, other host threads -- race on it. */
+#define VS_BP_NOALLOC_SCRATCH_BYTES (8u << 20)
+int vs_bp_stereo_noalloc(const uint8_t *left, const uint8_t *right, int w, int h, int pitch,
+                         const vs_bp_params *p, uint8_t *labels, int labels_pitch, void *stream);
+
 /* Debug read-out after vs_bp_stereo on the same workspace and stream: the
  * final level-0 incoming messages as int32 [4][h][w][labels], directions
  * 0 = from the left neighbour, 1 = right, 2 = up, 3 = down (zero where the
