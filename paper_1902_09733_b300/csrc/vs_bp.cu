@@ -4,7 +4,7 @@
 // Data layout (all in the caller's workspace, every array 256-byte aligned):
 //   every level splits its pixels by colour c = (x + y) & 1, so that one
 //   iteration reads one colour and writes the other, both contiguously:
-//     cost_l[c][y][x >> 1][Lp]     level 0 uint8, coarser levels uint16
+//     cost_l[c][y][x >> 1][Lp]     uint8 while data_trunc * 4^l <= 255, else uint16
 //     msg_l [c][k][y][x >> 1][Lp]  uint8 incoming message from direction k
 //   with k = 0 left, 1 right, 2 up, 3 down and Lp = labels rounded up to 16.
 //   Messages live in [0, smooth_trunc] after normalisation, so 8 bits hold
@@ -18,7 +18,9 @@
 // 16-bit halves of 32-bit words, one word per label, and runs the O(L)
 // distance transform of the truncated-linear cost (forward pass, backward
 // pass, cap at min + Ts, shift to min 0) for both directions at once with
-// packed 16-bit min operations; the forward results stay in registers.
+// packed 16-bit add-min (DPX) operations; the forward results stay in
+// registers.  All lane values stay below 2^15 (ABI limits), so the packed
+// adds never carry across lanes and the signed form is exact too.
 #include "vs_common.cuh"
 
 #include <algorithm>
@@ -28,10 +30,13 @@ namespace {
 
 constexpr int kMaxLevels = 8;
 constexpr uint32_t kBig2 = 0x7FFF7FFFu;   // "label does not exist" in both halves
+constexpr int kSweepThreads = 128;        // 64 pixels x 2 direction pairs per CTA
 
 struct BpLayout {
     int L, Lp, levels;
     int w[kMaxLevels], h[kMaxLevels], wh[kMaxLevels];
+    int cost_u8[kMaxLevels];   // level cost fits a byte: data_trunc * 4^l <= 255
+    int bytes[kMaxLevels];     // level belief sums fit a byte: + 4 smooth_trunc <= 255
     size_t cost_off[kMaxLevels], msg_off[kMaxLevels];
     size_t total;
 };
@@ -67,8 +72,11 @@ BpLayout make_layout(int w, int h, const vs_bp_params *p)
         lay.h[l] = l == 0 ? h : (lay.h[l - 1] + 1) / 2;
         lay.wh[l] = (lay.w[l] + 1) / 2;
         const size_t slots = (size_t)2 * lay.h[l] * lay.wh[l];
+        const long long cmax = (long long)p->data_trunc << (2 * l);
+        lay.cost_u8[l] = l == 0 || cmax <= 255;
+        lay.bytes[l] = lay.cost_u8[l] && cmax + 4LL * p->smooth_trunc <= 255;
         lay.cost_off[l] = off;
-        off = align_up(off + slots * lay.Lp * (l == 0 ? 1 : 2), 256);
+        off = align_up(off + slots * lay.Lp * (lay.cost_u8[l] ? 1 : 2), 256);
         lay.msg_off[l] = off;
         off = align_up(off + slots * 4 * lay.Lp, 256);
     }
@@ -89,6 +97,7 @@ struct Cost0Args {
 // per thread, padding labels hold 0.
 __global__ void k_cost0(Cost0Args a)
 {
+    pdl_begin();
     const int chunks = a.Lp / 16;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long total = (long long)2 * a.h * a.wh * chunks;
@@ -122,9 +131,9 @@ __global__ void k_cost0(Cost0Args a)
 }
 
 struct CostDownArgs {
-    const void *fine;      // level l-1 (uint8 at level 0, uint16 above)
-    uint16_t *coarse;      // level l
-    int fine_is_u8;
+    const void *fine;      // level l-1, uint8 or uint16
+    void *coarse;          // level l, uint8 (when the sums fit) or uint16
+    int fine_is_u8, coarse_is_u8;
     int wf, hf, whf;       // fine dims
     int wc, hc, whc;       // coarse dims
     int Lp;
@@ -134,6 +143,7 @@ struct CostDownArgs {
 // (2x+i, 2y+j) has colour (i+j)&1 and column slot x.  8 labels per thread.
 __global__ void k_cost_down(CostDownArgs a)
 {
+    pdl_begin();
     const int chunks = a.Lp / 8;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long total = (long long)2 * a.hc * a.whc * chunks;
@@ -175,8 +185,13 @@ __global__ void k_cost_down(CostDownArgs a)
             }
         }
     }
-    uint4 *dst = reinterpret_cast<uint4 *>(a.coarse + (size_t)slot * a.Lp) + j;
-    *dst = make_uint4(acc[0], acc[1], acc[2], acc[3]);
+    if (a.coarse_is_u8) {   // every lane is <= 255 here: narrow back to bytes
+        uint2 *dst = reinterpret_cast<uint2 *>(reinterpret_cast<uint8_t *>(a.coarse) + (size_t)slot * a.Lp) + j;
+        *dst = make_uint2(prmt(acc[0], acc[1], 0x6420u), prmt(acc[2], acc[3], 0x6420u));
+    } else {
+        uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(a.coarse) + (size_t)slot * a.Lp) + j;
+        *dst = make_uint4(acc[0], acc[1], acc[2], acc[3]);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -211,10 +226,13 @@ template <>
 struct CostChunk<uint8_t> {
     uint4 v;
     __device__ __forceinline__ void load(const uint8_t *base, int j) { v = reinterpret_cast<const uint4 *>(base)[j]; }
+    __device__ __forceinline__ uint32_t word(int wi) const { return (&v.x)[wi]; }
     __device__ __forceinline__ uint32_t dup(int i) const
     {
+        // byte i & 3 zero-extended into both 16-bit halves (byte 4 of {0:wv} is 0)
         const uint32_t wv = (&v.x)[i >> 2];
-        return pair_bytes(wv, wv, i & 3);
+        const uint32_t b = (uint32_t)(i & 3);
+        return prmt(wv, 0u, b | (4u << 4) | (b << 8) | (4u << 12));
     }
 };
 
@@ -226,6 +244,7 @@ struct CostChunk<uint16_t> {
         v0 = reinterpret_cast<const uint4 *>(base)[2 * j];
         v1 = reinterpret_cast<const uint4 *>(base)[2 * j + 1];
     }
+    __device__ __forceinline__ uint32_t word(int) const { return 0u; }   // byte-lane path never uses 16-bit costs
     __device__ __forceinline__ uint32_t dup(int i) const
     {
         const uint32_t wv = i < 8 ? (&v0.x)[i >> 1] : (&v1.x)[(i - 8) >> 1];
@@ -233,9 +252,13 @@ struct CostChunk<uint16_t> {
     }
 };
 
-template <int LP, typename CostT>
-__global__ void __launch_bounds__(128) k_bp_sweep(SweepArgs a)
+// BYTES: level 0 with data_trunc + 4 smooth_trunc <= 255, so the belief sum
+// of four labels fits four byte lanes of one 32-bit add.  FULL: labels == LP,
+// no padding labels to mask.
+template <int LP, typename CostT, bool BYTES, bool FULL>
+__global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
 {
+    pdl_begin();
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int pair = (int)(idx & 1);
     const long long slot = idx >> 1;
@@ -280,33 +303,58 @@ __global__ void __launch_bounds__(128) k_bp_sweep(SweepArgs a)
 
     uint32_t F[LP];
     uint32_t H2 = kBig2;
-    // excluded incoming pair: (left, right) for pair 0, (up, down) for pair 1
 #pragma unroll
     for (int j = 0; j < LP / 16; ++j) {
         uint4 m[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
             m[k] = use[k] ? reinterpret_cast<const uint4 *>(in[k])[j] : make_uint4(0, 0, 0, 0);
+        CostChunk<CostT> cc;
+        cc.load(cost, j);
         if (a.materialize) {
             const size_t k0 = 2 * pair;
             reinterpret_cast<uint4 *>(own + k0 * dir_stride)[j] = pair ? m[2] : m[0];
             reinterpret_cast<uint4 *>(own + (k0 + 1) * dir_stride)[j] = pair ? m[3] : m[1];
         }
-        CostChunk<CostT> cc;
-        cc.load(cost, j);
+        if (BYTES) {
+            // four labels per word: S = D + L + R + U + D in byte lanes, then
+            // h_A = S - in_A, h_B = S - in_B, interleaved and widened to
+            // (h_A, h_B) 16-bit pairs
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int d = 16 * j + i;
-            const int wi = i >> 2;
-            const uint32_t plr = pair_bytes((&m[0].x)[wi], (&m[1].x)[wi], i & 3);
-            const uint32_t pud = pair_bytes((&m[2].x)[wi], (&m[3].x)[wi], i & 3);
-            const uint32_t t = plr + pud;                       // (L+U, R+D), no carry
-            const uint32_t s2 = t + prmt(t, t, 0x1032u) + cc.dup(i);   // (S, S)
-            uint32_t wv = s2 - (pair ? pud : plr);              // (h_A, h_B)
-            if (d >= a.L)
-                wv = kBig2;
-            F[d] = d == 0 ? wv : min_u16x2(wv, F[d - 1] + a.c2);
-            H2 = min_u16x2(H2, wv);
+            for (int wi = 0; wi < 4; ++wi) {
+                const uint32_t c4 = cc.word(wi);
+                const uint32_t s4 = c4 + (&m[0].x)[wi] + (&m[1].x)[wi] + (&m[2].x)[wi] + (&m[3].x)[wi];
+                const uint32_t a4 = s4 - (pair ? (&m[2].x)[wi] : (&m[0].x)[wi]);
+                const uint32_t b4 = s4 - (pair ? (&m[3].x)[wi] : (&m[1].x)[wi]);
+                const uint32_t x01 = prmt(a4, b4, 0x5140u);    // A0 B0 A1 B1
+                const uint32_t x23 = prmt(a4, b4, 0x7362u);    // A2 B2 A3 B3
+                uint32_t wq[4] = {prmt(x01, 0u, 0x4140u), prmt(x01, 0u, 0x4342u), prmt(x23, 0u, 0x4140u),
+                                  prmt(x23, 0u, 0x4342u)};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int d = 16 * j + 4 * wi + q;
+                    uint32_t wv = wq[q];
+                    if (!FULL && d >= a.L)
+                        wv = kBig2;
+                    F[d] = d == 0 ? wv : __viaddmin_u16x2(F[d - 1], a.c2, wv);   // min(F + c, h)
+                    H2 = min_u16x2(H2, wv);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int d = 16 * j + i;
+                const int wi = i >> 2;
+                const uint32_t plr = pair_bytes((&m[0].x)[wi], (&m[1].x)[wi], i & 3);
+                const uint32_t pud = pair_bytes((&m[2].x)[wi], (&m[3].x)[wi], i & 3);
+                const uint32_t t = plr + pud;                       // (L+U, R+D), no carry
+                const uint32_t s2 = t + prmt(t, t, 0x1032u) + cc.dup(i);   // (S, S)
+                uint32_t wv = s2 - (pair ? pud : plr);              // (h_A, h_B)
+                if (!FULL && d >= a.L)
+                    wv = kBig2;
+                F[d] = d == 0 ? wv : __viaddmin_u16x2(F[d - 1], a.c2, wv);   // min(F + c, h)
+                H2 = min_u16x2(H2, wv);
+            }
         }
     }
 
@@ -325,6 +373,8 @@ __global__ void __launch_bounds__(128) k_bp_sweep(SweepArgs a)
             dstB = a.msg + ((((size_t)ncolor * 4 + 2) * a.h + (y + 1)) * a.wh + (x >> 1)) * LP;
     }
 
+    // -H in both 16-bit lanes, for the fused add-min of the output
+    const uint32_t negH2 = ((0u - (H2 & 0xFFFFu)) & 0xFFFFu) | ((0u - (H2 >> 16)) << 16);
     uint32_t G = F[LP - 1];
 #pragma unroll
     for (int j = LP / 16 - 1; j >= 0; --j) {
@@ -333,8 +383,8 @@ __global__ void __launch_bounds__(128) k_bp_sweep(SweepArgs a)
         for (int i = 15; i >= 0; --i) {
             const int d = 16 * j + i;
             if (d < LP - 1)
-                G = min_u16x2(F[d], G + a.c2);
-            o[i] = min_u16x2(G - H2, a.ts2);                    // (m_A(d), m_B(d))
+                G = __viaddmin_u16x2(G, a.c2, F[d]);           // min(G + c, F)
+            o[i] = __viaddmin_s16x2(G, negH2, a.ts2);   // (m_A(d), m_B(d)) = min(G - H, Ts)
         }
         uint32_t oa[4], ob[4];
 #pragma unroll
@@ -364,6 +414,7 @@ struct LabelArgs {
 // d* = argmin_d D0(d) + sum of the in-frame incoming messages, smallest d wins.
 __global__ void k_bp_labels(LabelArgs a)
 {
+    pdl_begin();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= a.w || y >= a.h)
@@ -407,6 +458,7 @@ struct ExportArgs {
 
 __global__ void k_bp_export(ExportArgs a)
 {
+    pdl_begin();
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long total = 4LL * a.h * a.w * a.L;
     if (idx >= total)
@@ -426,29 +478,42 @@ __global__ void k_bp_export(ExportArgs a)
 // ---------------------------------------------------------------------------
 // host dispatch
 
-template <int LP>
-void launch_sweep_lp(const SweepArgs &a, bool level0, cudaStream_t st)
+// cost8: the level's data term is stored in bytes; bytes: its belief sums
+// fit bytes too (byte-lane arithmetic)
+template <int LP, bool FULL>
+void launch_sweep_lp(const SweepArgs &a, bool cost8, bool bytes, cudaStream_t st)
 {
     const long long threads = 2LL * a.h * a.wh;
-    const int block = 128;
+    const int block = kSweepThreads;
     const unsigned grid = (unsigned)((threads + block - 1) / block);
-    if (level0)
-        k_bp_sweep<LP, uint8_t><<<grid, block, 0, st>>>(a);
+    if (cost8 && bytes)
+        launch_pdl(k_bp_sweep<LP, uint8_t, true, FULL>, dim3(grid), dim3(block), st, a);
+    else if (cost8)
+        launch_pdl(k_bp_sweep<LP, uint8_t, false, FULL>, dim3(grid), dim3(block), st, a);
     else
-        k_bp_sweep<LP, uint16_t><<<grid, block, 0, st>>>(a);
+        launch_pdl(k_bp_sweep<LP, uint16_t, false, FULL>, dim3(grid), dim3(block), st, a);
 }
 
-void launch_sweep(int Lp, const SweepArgs &a, bool level0, cudaStream_t st)
+template <int LP>
+void launch_sweep_full(const SweepArgs &a, bool cost8, bool bytes, cudaStream_t st)
+{
+    if (a.L == LP)
+        launch_sweep_lp<LP, true>(a, cost8, bytes, st);
+    else
+        launch_sweep_lp<LP, false>(a, cost8, bytes, st);
+}
+
+void launch_sweep(int Lp, const SweepArgs &a, bool cost8, bool bytes, cudaStream_t st)
 {
     switch (Lp) {
-    case 16: launch_sweep_lp<16>(a, level0, st); break;
-    case 32: launch_sweep_lp<32>(a, level0, st); break;
-    case 48: launch_sweep_lp<48>(a, level0, st); break;
-    case 64: launch_sweep_lp<64>(a, level0, st); break;
-    case 80: launch_sweep_lp<80>(a, level0, st); break;
-    case 96: launch_sweep_lp<96>(a, level0, st); break;
-    case 112: launch_sweep_lp<112>(a, level0, st); break;
-    default: launch_sweep_lp<128>(a, level0, st); break;
+    case 16: launch_sweep_full<16>(a, cost8, bytes, st); break;
+    case 32: launch_sweep_full<32>(a, cost8, bytes, st); break;
+    case 48: launch_sweep_full<48>(a, cost8, bytes, st); break;
+    case 64: launch_sweep_full<64>(a, cost8, bytes, st); break;
+    case 80: launch_sweep_full<80>(a, cost8, bytes, st); break;
+    case 96: launch_sweep_full<96>(a, cost8, bytes, st); break;
+    case 112: launch_sweep_full<112>(a, cost8, bytes, st); break;
+    default: launch_sweep_full<128>(a, cost8, bytes, st); break;
     }
 }
 
@@ -489,15 +554,16 @@ extern "C" int vs_bp_stereo(const uint8_t *left, const uint8_t *right, int w, in
         Cost0Args a{left, right, pitch, w, h, lay.wh[0], lay.L, lay.Lp, p->data_trunc, ws + lay.cost_off[0]};
         const long long n = 2LL * h * lay.wh[0] * (lay.Lp / 16);
         const int slot = prof_begin(kProfBpOther, st);
-        k_cost0<<<(unsigned)((n + block - 1) / block), block, 0, st>>>(a);
+        launch_pdl(k_cost0, dim3((unsigned)((n + block - 1) / block)), dim3(block), st, a);
         prof_end(slot, st);
         note_launch();
     }
     for (int l = 1; l < lay.levels; ++l) {   // coarse data terms
         CostDownArgs a;
         a.fine = ws + lay.cost_off[l - 1];
-        a.coarse = reinterpret_cast<uint16_t *>(ws + lay.cost_off[l]);
-        a.fine_is_u8 = l == 1;
+        a.coarse = ws + lay.cost_off[l];
+        a.fine_is_u8 = lay.cost_u8[l - 1];
+        a.coarse_is_u8 = lay.cost_u8[l];
         a.wf = lay.w[l - 1];
         a.hf = lay.h[l - 1];
         a.whf = lay.wh[l - 1];
@@ -507,7 +573,7 @@ extern "C" int vs_bp_stereo(const uint8_t *left, const uint8_t *right, int w, in
         a.Lp = lay.Lp;
         const long long n = 2LL * a.hc * a.whc * (lay.Lp / 8);
         const int slot = prof_begin(kProfBpOther, st);
-        k_cost_down<<<(unsigned)((n + block - 1) / block), block, 0, st>>>(a);
+        launch_pdl(k_cost_down, dim3((unsigned)((n + block - 1) / block)), dim3(block), st, a);
         prof_end(slot, st);
         note_launch();
     }
@@ -532,7 +598,7 @@ extern "C" int vs_bp_stereo(const uint8_t *left, const uint8_t *right, int w, in
             a.zero_in = (t == 0 && l + 1 == lay.levels);
             a.materialize = (t == 0 && p->iters == 1);
             const int slot = prof_begin(l == 0 ? kProfSweepL0 : kProfSweepCoarse, st);
-            launch_sweep(lay.Lp, a, l == 0, st);
+            launch_sweep(lay.Lp, a, lay.cost_u8[l], lay.bytes[l], st);
             prof_end(slot, st);
             note_launch();
         }
@@ -541,7 +607,7 @@ extern "C" int vs_bp_stereo(const uint8_t *left, const uint8_t *right, int w, in
         LabelArgs a{ws + lay.cost_off[0], ws + lay.msg_off[0], labels, labels_pitch, w, h, lay.wh[0], lay.L, lay.Lp};
         dim3 grid((w + 127) / 128, h);
         const int slot = prof_begin(kProfBpOther, st);
-        k_bp_labels<<<grid, 128, 0, st>>>(a);
+        launch_pdl(k_bp_labels, dim3(grid), dim3(128), st, a);
         prof_end(slot, st);
         note_launch();
     }
@@ -560,7 +626,7 @@ extern "C" int vs_bp_export_messages(const void *workspace, size_t ws_bytes, int
         return rc;
     ExportArgs a{reinterpret_cast<const uint8_t *>(workspace) + lay.msg_off[0], out, w, h, lay.wh[0], lay.L, lay.Lp};
     const long long n = 4LL * h * w * lay.L;
-    k_bp_export<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(a);
+    launch_pdl(k_bp_export, dim3((unsigned)((n + 255) / 256)), dim3(256), (cudaStream_t)stream, a);
     note_launch();
     return launch_status();
 }

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "../../include/vstereo.h"
 
 namespace vs {
@@ -21,6 +23,33 @@ int launch_status();
 enum ProfTag { kProfSweepL0 = 0, kProfSweepCoarse = 1, kProfRemap = 2, kProfJbu = 3, kProfBpOther = 4 };
 int prof_begin(int tag, cudaStream_t st);
 void prof_end(int slot, cudaStream_t st);
+
+// Programmatic dependent launch.  Every kernel of the library starts with
+// pdl_begin(): it waits until the previous kernel on the stream has finished
+// and its writes are visible (a no-op when launched without the attribute),
+// then lets the next kernel be scheduled.  Launched through launch_pdl, the
+// next kernel's launch and set-up overlap this kernel's last wave.
+__device__ __forceinline__ void pdl_begin()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 

@@ -42,6 +42,7 @@ __device__ __forceinline__ float ex2(float x)
 template <bool kXYZ>
 __global__ void __launch_bounds__(kTileW *kThreadsY) k_jbu(JbuArgs a)
 {
+    pdl_begin();
     __shared__ uchar4 stage[kStageH][kStageW];
     const int X0 = blockIdx.x * kTileW, Y0 = blockIdx.y * kTileH;
     // window centres of this tile: floor((x + 0.5) / s) = (2x + 1) / (2s)
@@ -133,6 +134,142 @@ __global__ void __launch_bounds__(kTileW *kThreadsY) k_jbu(JbuArgs a)
     }
 }
 
+// ---------------------------------------------------------------------------
+// scale 4: one thread per low-res window centre
+//
+// With s = 4 the 4 x 4 full-res pixels x = 4k..4k+3, y = 4l..4l+3 all have
+// the window centre (k, l), so one thread loads the (2R+1)^2 taps once into
+// registers and evaluates all 16 pixels.  For a tap q and pixel p:
+//   |I_p - I_q|^2 = |I_p|^2 + (|I_q|^2 - 2 I_p.I_q)
+// where I_p.I_q is one dp4a; the |I_p|^2 term is the same for every tap of
+// p and cancels against the reference tap, so only v_q = |I_q|^2 - 2 I_p.I_q
+// is formed.  The reference tap is the one with the smallest v_q; the
+// spatial offsets relative to the window centre (the nearest tap) are
+// compile-time constants of the pixel's position in its 4 x 4 block, so
+//   exponent = (v_q - v_min) * a_r + (|p-q|^2 - |p-c|^2) * a_s >= 0
+// and the window always holds a tap of weight >= 2^-(spatial spread).
+// Taps outside the low-res frame are staged with |I_q|^2 = 2^28, which
+// gives them weight exactly 0 (skipped, as in the definition).
+
+constexpr int kS4CentresX = 32, kS4CentresY = 4;   // window centres per CTA
+constexpr uint32_t kOffFrameNorm = 1u << 28;
+
+template <int R, bool kXYZ>
+__global__ void __launch_bounds__(kS4CentresX *kS4CentresY) k_jbu_s4(JbuArgs a)
+{
+    pdl_begin();
+    constexpr int D = 2 * R + 1;
+    constexpr int SW = kS4CentresX + 2 * R, SH = kS4CentresY + 2 * R;
+    __shared__ uint2 stage[SH][SW];   // (R | G<<8 | B<<16 | label<<24, R^2+G^2+B^2)
+    const int k0 = blockIdx.x * kS4CentresX, l0 = blockIdx.y * kS4CentresY;
+    for (int i = threadIdx.x; i < SW * SH; i += kS4CentresX * kS4CentresY) {
+        const int sx = i % SW, sy = i / SW;
+        const int qx = k0 - R + sx, qy = l0 - R + sy;
+        uint2 v = make_uint2(0u, kOffFrameNorm);
+        if (qx >= 0 && qy >= 0 && qx < a.w && qy < a.h) {
+            const uint8_t *g = a.guide_low + (size_t)qy * a.guide_low_pitch + (size_t)qx * 3;
+            const uint32_t r = g[0], gg = g[1], b = g[2];
+            const uint32_t lab = a.labels[(size_t)qy * a.labels_pitch + qx];
+            v = make_uint2(r | (gg << 8) | (b << 16) | (lab << 24), r * r + gg * gg + b * b);
+        }
+        stage[sy][sx] = v;
+    }
+    __syncthreads();
+
+    const int kx = threadIdx.x % kS4CentresX, ly = threadIdx.x / kS4CentresX;
+    const int k = k0 + kx, l = l0 + ly;
+    if (k >= a.w || l >= a.h)
+        return;
+    uint32_t tq[D * D];
+    int tn[D * D];
+    float tl[D * D];
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const uint2 v = stage[ly + j][kx + i];
+            tq[j * D + i] = v.x;     // byte 3 (label) meets a zero byte of I_p in dp4a
+            tn[j * D + i] = (int)v.y;
+            tl[j * D + i] = (float)(v.x >> 24);
+        }
+
+#pragma unroll
+    for (int py = 0; py < 4; ++py) {
+        const int y = 4 * l + py;
+        if (y >= a.H)
+            break;
+        const uint32_t *gp = reinterpret_cast<const uint32_t *>(a.guide_full + (size_t)y * a.guide_full_pitch +
+                                                                 (size_t)k * 12);
+        const uint32_t g0 = gp[0], g1 = gp[1], g2 = gp[2];
+        const uint32_t ip[4] = {g0 & 0xFFFFFFu, prmt(g0, g1, 0x7543u) & 0xFFFFFFu,
+                                prmt(g1, g2, 0x7432u) & 0xFFFFFFu, g2 >> 8};
+        float dres[4];
+#pragma unroll
+        for (int px = 0; px < 4; ++px) {
+            int v[D * D];
+            int vmin = 0x7FFFFFFF;
+#pragma unroll
+            for (int t = 0; t < D * D; ++t) {
+                v[t] = tn[t] - 2 * (int)__dp4a(ip[px], tq[t], 0u);
+                vmin = min(vmin, v[t]);
+            }
+            float num = 0.0f, den = 0.0f;
+            // spatial terms: p_down - q = ((px + 0.5)/4 - 0.5 - i, (py + 0.5)/4 - 0.5 - j)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    const float ox = (px + 0.5f) * 0.25f - 0.5f, oy = (py + 0.5f) * 0.25f - 0.5f;
+                    const float dx = ox - (float)(i - R), dy = oy - (float)(j - R);
+                    const float sp = (dx * dx + dy * dy) - (ox * ox + oy * oy);   // exact, compile time
+                    const int t = j * D + i;
+                    const float e = fmaf((float)(v[t] - vmin), a.a_r, sp * a.a_s);
+                    const float wgt = ex2(-e);
+                    num = fmaf(wgt, tl[t], num);
+                    den += wgt;
+                }
+            }
+            dres[px] = 4.0f * num / den;
+        }
+        const size_t p = (size_t)y * a.W + (size_t)4 * k;
+        if (a.disp)
+            *reinterpret_cast<float4 *>(a.disp + p) = make_float4(dres[0], dres[1], dres[2], dres[3]);
+        if (kXYZ) {
+            float o[12];
+#pragma unroll
+            for (int px = 0; px < 4; ++px) {
+                float X = __int_as_float(0x7fc00000), Y = X, Z = X;
+                if (dres[px] > 0.0f) {
+                    const float bd = a.baseline / dres[px];
+                    X = ((float)(4 * k + px) - a.cx) * bd;
+                    Y = ((float)y - a.cy) * a.fx_over_fy * bd;
+                    Z = a.fx * bd;
+                }
+                o[3 * px] = X;
+                o[3 * px + 1] = Y;
+                o[3 * px + 2] = Z;
+            }
+            float4 *dst = reinterpret_cast<float4 *>(a.xyz + 3 * p);
+            dst[0] = make_float4(o[0], o[1], o[2], o[3]);
+            dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+            dst[2] = make_float4(o[8], o[9], o[10], o[11]);
+        }
+    }
+}
+
+template <bool kXYZ>
+void launch_jbu_s4(const JbuArgs &a, cudaStream_t st)
+{
+    dim3 grid((a.w + kS4CentresX - 1) / kS4CentresX, (a.h + kS4CentresY - 1) / kS4CentresY);
+    const int block = kS4CentresX * kS4CentresY;
+    switch (a.r) {
+    case 0: launch_pdl(k_jbu_s4<0, kXYZ>, dim3(grid), dim3(block), st, a); break;
+    case 1: launch_pdl(k_jbu_s4<1, kXYZ>, dim3(grid), dim3(block), st, a); break;
+    case 2: launch_pdl(k_jbu_s4<2, kXYZ>, dim3(grid), dim3(block), st, a); break;
+    default: launch_pdl(k_jbu_s4<3, kXYZ>, dim3(grid), dim3(block), st, a); break;
+    }
+}
+
 struct ReprojArgs {
     const float *disp;
     float *xyz;
@@ -142,6 +279,7 @@ struct ReprojArgs {
 
 __global__ void k_reproject(ReprojArgs a)
 {
+    pdl_begin();
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= (long long)a.W * a.H)
         return;
@@ -215,11 +353,21 @@ int jbu_common(const uint8_t *labels, int w, int h, int labels_pitch, const uint
     a.baseline = baseline;
     dim3 grid((W + kTileW - 1) / kTileW, (H + kTileH - 1) / kTileH);
     dim3 block(kTileW, kThreadsY);
+    // the scale-4 kernel needs whole 4-pixel groups on every row and
+    // 4/16-byte aligned rows for its vector loads and stores
+    const bool s4 = s == 4 && W % 4 == 0 && guide_full_pitch % 4 == 0 && aligned(guide_full, 4) &&
+                    (!disp || aligned(disp, 16)) && (!xyz || aligned(xyz, 16));
     const int slot = prof_begin(kProfJbu, st);
-    if (xyz)
-        k_jbu<true><<<grid, block, 0, st>>>(a);
-    else
-        k_jbu<false><<<grid, block, 0, st>>>(a);
+    if (s4) {
+        if (xyz)
+            launch_jbu_s4<true>(a, st);
+        else
+            launch_jbu_s4<false>(a, st);
+    } else if (xyz) {
+        launch_pdl(k_jbu<true>, dim3(grid), dim3(block), st, a);
+    } else {
+        launch_pdl(k_jbu<false>, dim3(grid), dim3(block), st, a);
+    }
     prof_end(slot, st);
     note_launch();
     return launch_status();
@@ -259,7 +407,7 @@ extern "C" int vs_reproject(const float *disp, int W, int H, const vs_camera *ca
         return VS_EINVAL;
     ReprojArgs a{disp, xyz, W, H, cam->fx, cam->cx, cam->cy, cam->fx / cam->fy, baseline};
     const long long n = (long long)W * H;
-    k_reproject<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(a);
+    launch_pdl(k_reproject, dim3((unsigned)((n + 255) / 256)), dim3(256), (cudaStream_t)stream, a);
     note_launch();
     return launch_status();
 }

@@ -25,6 +25,8 @@ struct RemapArgs {
     int s, w, h;                // scale and low-res size
     int tlw, tlh;               // tile size in low-res pixels
     float fx, fy, cx, cy, k1, k2;
+    float inv_fx, inv_fy;   // 1/fx, 1/fy rounded once on the host
+    int dst_vec;            // dst rows allow 4-byte stores of 4-pixel groups
     float R[9];
     int has_R;
 };
@@ -36,69 +38,96 @@ __device__ __forceinline__ float tap(const uint8_t *src, int pitch, int W, int H
     return (float)__ldg(src + (size_t)y * pitch + (size_t)x * 3 + ch);
 }
 
+// Destination pixels are processed four consecutive ones per thread, so the
+// 48 tap loads of a thread are all in flight together and its 12 output
+// bytes leave as three 32-bit stores when the row allows it.
 __global__ void __launch_bounds__(kRemapThreads) k_remap_down(RemapArgs a)
 {
+    pdl_begin();
     __shared__ uint8_t tile[kTilePixMax * 3];
     const int tfw = a.tlw * a.s, tfh = a.tlh * a.s;   // full-res tile size
     const int u0 = blockIdx.x * tfw, v0 = blockIdx.y * tfh;
     const bool want_low = (a.low_rgb != nullptr) || (a.low_gray != nullptr);
+    const int quads = (tfw + 3) / 4;                  // 4-pixel groups per tile row
 
-    for (int i = threadIdx.x; i < tfw * tfh; i += blockDim.x) {
-        const int lu = i % tfw, lv = i / tfw;
-        const int u = u0 + lu, v = v0 + lv;
-        if (u >= a.W || v >= a.H)
-            continue;
-        float xn = ((float)u - a.cx) / a.fx;
-        float yn = ((float)v - a.cy) / a.fy;
-        bool valid = true;
-        if (a.has_R) {
-            const float X = a.R[0] * xn + a.R[3] * yn + a.R[6];
-            const float Y = a.R[1] * xn + a.R[4] * yn + a.R[7];
-            const float Z = a.R[2] * xn + a.R[5] * yn + a.R[8];
-            if (Z <= 0.0f) {
-                valid = false;
-            } else {
-                xn = X / Z;
-                yn = Y / Z;
-            }
-        }
-        float val[3] = {0.0f, 0.0f, 0.0f};
-        if (valid) {
-            const float r2 = xn * xn + yn * yn;
-            const float radial = 1.0f + a.k1 * r2 + a.k2 * r2 * r2;
-            const float sx = a.fx * (xn * radial) + a.cx;
-            const float sy = a.fy * (yn * radial) + a.cy;
-            if (sx > -1.0f && sx < (float)a.W && sy > -1.0f && sy < (float)a.H) {
-                const float fx0 = floorf(sx), fy0 = floorf(sy);
-                const int x0 = (int)fx0, y0 = (int)fy0;
-                const float ax = sx - fx0, ay = sy - fy0;
-                const float w00 = (1.0f - ax) * (1.0f - ay), w10 = ax * (1.0f - ay);
-                const float w01 = (1.0f - ax) * ay, w11 = ax * ay;
+    for (int g = threadIdx.x; g < quads * tfh; g += blockDim.x) {
+        const int lv = g / quads, lu0 = 4 * (g % quads);
+        const int v = v0 + lv;
+        uint8_t out[12];
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    val[ch] = w00 * tap(a.src, a.src_pitch, a.W, a.H, x0, y0, ch)
-                            + w10 * tap(a.src, a.src_pitch, a.W, a.H, x0 + 1, y0, ch)
-                            + w01 * tap(a.src, a.src_pitch, a.W, a.H, x0, y0 + 1, ch)
-                            + w11 * tap(a.src, a.src_pitch, a.W, a.H, x0 + 1, y0 + 1, ch);
+        for (int q = 0; q < 4; ++q) {
+            const int lu = lu0 + q, u = u0 + lu;
+            float val[3] = {0.0f, 0.0f, 0.0f};
+            if (lu < tfw && u < a.W && v < a.H) {
+                float xn = ((float)u - a.cx) * a.inv_fx;
+                float yn = ((float)v - a.cy) * a.inv_fy;
+                bool valid = true;
+                if (a.has_R) {
+                    const float X = a.R[0] * xn + a.R[3] * yn + a.R[6];
+                    const float Y = a.R[1] * xn + a.R[4] * yn + a.R[7];
+                    const float Z = a.R[2] * xn + a.R[5] * yn + a.R[8];
+                    if (Z <= 0.0f) {
+                        valid = false;
+                    } else {
+                        xn = X / Z;
+                        yn = Y / Z;
+                    }
+                }
+                if (valid) {
+                    const float r2 = xn * xn + yn * yn;
+                    const float radial = 1.0f + a.k1 * r2 + a.k2 * r2 * r2;
+                    const float sx = a.fx * (xn * radial) + a.cx;
+                    const float sy = a.fy * (yn * radial) + a.cy;
+                    if (sx > -1.0f && sx < (float)a.W && sy > -1.0f && sy < (float)a.H) {
+                        const float fx0 = floorf(sx), fy0 = floorf(sy);
+                        const int x0 = (int)fx0, y0 = (int)fy0;
+                        const float ax = sx - fx0, ay = sy - fy0;
+                        const float w00 = (1.0f - ax) * (1.0f - ay), w10 = ax * (1.0f - ay);
+                        const float w01 = (1.0f - ax) * ay, w11 = ax * ay;
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) {
+                            val[ch] = w00 * tap(a.src, a.src_pitch, a.W, a.H, x0, y0, ch)
+                                    + w10 * tap(a.src, a.src_pitch, a.W, a.H, x0 + 1, y0, ch)
+                                    + w01 * tap(a.src, a.src_pitch, a.W, a.H, x0, y0 + 1, ch)
+                                    + w11 * tap(a.src, a.src_pitch, a.W, a.H, x0 + 1, y0 + 1, ch);
+                        }
+                    }
                 }
             }
-        }
-        uint8_t out[3];
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            int r = __float2int_rn(val[ch]);   // round half to even
-            out[ch] = (uint8_t)min(max(r, 0), 255);
+            for (int ch = 0; ch < 3; ++ch) {
+                const int r = __float2int_rn(val[ch]);   // round half to even
+                out[3 * q + ch] = (uint8_t)min(max(r, 0), 255);
+            }
         }
-        if (a.dst) {
+        if (v >= a.H)
+            continue;
+        const int u = u0 + lu0;
+        const int nq = min(4, min(tfw - lu0, a.W - u));   // pixels of this group inside tile and frame
+        if (a.dst && nq > 0) {
             uint8_t *d = a.dst + (size_t)v * a.dst_pitch + (size_t)u * 3;
-            d[0] = out[0];
-            d[1] = out[1];
-            d[2] = out[2];
+            if (nq == 4 && a.dst_vec && (u & 3) == 0) {
+                uint32_t w[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    w[k] = (uint32_t)out[4 * k] | ((uint32_t)out[4 * k + 1] << 8) | ((uint32_t)out[4 * k + 2] << 16) |
+                           ((uint32_t)out[4 * k + 3] << 24);
+                uint32_t *d32 = reinterpret_cast<uint32_t *>(d);
+                d32[0] = w[0];
+                d32[1] = w[1];
+                d32[2] = w[2];
+            } else {
+#pragma unroll
+                for (int k = 0; k < 12; ++k)
+                    if (k < 3 * nq)
+                        d[k] = out[k];
+            }
         }
         if (want_low) {
-            tile[i * 3 + 0] = out[0];
-            tile[i * 3 + 1] = out[1];
-            tile[i * 3 + 2] = out[2];
+#pragma unroll
+            for (int k = 0; k < 12; ++k)
+                if (k < 3 * nq)
+                    tile[(lv * tfw + lu0) * 3 + k] = out[k];
         }
     }
     if (!want_low)
@@ -196,13 +225,17 @@ extern "C" int vs_rectify_remap(const uint8_t *src, int W, int H, int src_pitch,
     a.cy = cam->cy;
     a.k1 = cam->k1;
     a.k2 = cam->k2;
+    a.inv_fx = (float)(1.0 / (double)cam->fx);
+    a.inv_fy = (float)(1.0 / (double)cam->fy);
+    // 4-pixel groups start at multiples of 4 pixels (12 bytes) of the row
+    a.dst_vec = dst != nullptr && aligned(dst, 4) && dst_pitch % 4 == 0;
     a.has_R = R9 != nullptr;
     for (int i = 0; i < 9; ++i)
         a.R[i] = R9 ? R9[i] : (i % 4 == 0 ? 1.0f : 0.0f);
     const int tfw = a.tlw * s, tfh = a.tlh * s;
     dim3 grid((W + tfw - 1) / tfw, (H + tfh - 1) / tfh);
     const int slot = prof_begin(kProfRemap, (cudaStream_t)stream);
-    k_remap_down<<<grid, kRemapThreads, 0, (cudaStream_t)stream>>>(a);
+    launch_pdl(k_remap_down, dim3(grid), dim3(kRemapThreads), (cudaStream_t)stream, a);
     prof_end(slot, (cudaStream_t)stream);
     note_launch();
     return launch_status();

@@ -102,6 +102,9 @@ def test_bp_config1_noise_pairs(seed):
     (15, 26, vs.BPParams(100, 4, 2, 127, 127, 127)),  # largest truncations
     (70, 90, vs.BPParams(20, 6, 3, 20, 7, 40)),      # six levels, down to 3x2
     (1, 1, vs.BPParams(4, 3, 2, 20, 5, 10)),
+    (23, 31, vs.BPParams(24, 3, 3, 60, 8, 30)),     # level-1 costs in bytes above 127
+    (22, 34, vs.BPParams(32, 2, 3, 63, 9, 48)),
+    (26, 36, vs.BPParams(16, 3, 4, 15, 10, 45)),    # byte-lane sums at levels 0 and 1
 ])
 def test_bp_ragged_and_edge_cases(h, w, p):
     g = np.random.default_rng(h * 1000 + w)
@@ -185,6 +188,14 @@ def test_remap_downsample_small(H, W, s):
     _check_remap(src, cam, R, s)
 
 
+def test_remap_strong_pincushion_reads_taps_from_global_memory():
+    """A pincushion lens spreads one destination tile over a source window
+    larger than the shared-memory stage, which takes the direct-read path."""
+    g = np.random.default_rng(13)
+    src = g.integers(0, 256, size=(150, 200, 3)).astype(np.uint8)
+    _check_remap(src, vs.Camera(60.0, 60.0, 99.5, 74.5, 1.5, 0.5), None, 4)
+
+
 def test_remap_identity_is_exact():
     g = np.random.default_rng(9)
     src = g.integers(0, 256, size=(30, 41, 3)).astype(np.uint8)
@@ -249,6 +260,10 @@ def _assert_xyz_close(a, b, disp_ref):
     (17, 70, vs.JBUParams(1, 3, 1.5, 8.0)),
     (64, 96, vs.JBUParams(8, 2, 1.0, 3.0)),
     (24, 40, vs.JBUParams(2, 0, 1.0, 12.0)),
+    (42, 48, vs.JBUParams(4, 1, 0.8, 10.0)),    # scale-4 kernel, ragged last block row
+    (36, 52, vs.JBUParams(4, 3, 1.2, 15.0)),
+    (16, 16, vs.JBUParams(4, 0, 1.0, 12.0)),
+    (45, 68, vs.JBUParams(4, 2, 1.0, 12.0)),
 ])
 def test_jbu_and_reproject_small(H, W, jp):
     for smooth in (True, False):
