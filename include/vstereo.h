@@ -54,7 +54,7 @@ typedef struct {
  * min(smooth_slope * |dp - dq|, smooth_trunc); `labels` disparities
  * 0..labels-1 of the left image (IL(x) is compared with IR(x - d));
  * `levels` pyramid levels with `iters` red-black iterations each.
- * Ranges: 2 <= labels <= 128, 1 <= levels <= 8, 1 <= iters <= 1000,
+ * Ranges: w h <= 2^26 pixels, 2 <= labels <= 128, 1 <= levels <= 8, 1 <= iters <= 1000,
  * 0 <= data_trunc <= 127, 0 <= smooth_slope, 0 <= smooth_trunc <= 127, and
  * data_trunc * 4^(levels-1) + 4 * smooth_trunc <= 32767 (messages are kept
  * in 8 bits and sums of a data term and four messages in 16 bits). */
@@ -145,7 +145,8 @@ int vs_bp_stereo_noalloc(const uint8_t *left, const uint8_t *right, int w, int h
 /* Debug read-out after vs_bp_stereo on the same workspace and stream: the
  * final level-0 incoming messages as int32 [4][h][w][labels], directions
  * 0 = from the left neighbour, 1 = right, 2 = up, 3 = down (zero where the
- * neighbour is missing).  out is a device buffer of 16 h w labels bytes. */
+ * neighbour is missing).  out is a device buffer of 16 h w labels bytes;
+ * 4 h w labels must stay below 2^31. */
 int vs_bp_export_messages(const void *workspace, size_t ws_bytes, int w, int h,
                           const vs_bp_params *p, int32_t *out, void *stream);
 

@@ -6,7 +6,8 @@
 //   iteration reads one colour and writes the other, both contiguously:
 //     cost_l[c][y][x >> 1][Lp]     uint8 while data_trunc * 4^l <= 255, else uint16
 //     msg_l [c][k][y][x >> 1][Lp]  uint8 incoming message from direction k
-//   with k = 0 left, 1 right, 2 up, 3 down and Lp = labels rounded up to 16.
+//   with k = 0 left, 1 right, 2 up, 3 down and Lp = labels rounded up to one
+//   of the compiled sizes 16, 32, 48, 64, 96, 128.
 //   Messages live in [0, smooth_trunc] after normalisation, so 8 bits hold
 //   them exactly; all message arithmetic is integer.
 //
@@ -55,7 +56,7 @@ bool params_ok(int w, int h, const vs_bp_params *p)
     const long long coarse = (long long)p->data_trunc << (2 * (p->levels - 1));
     if (coarse + 4LL * p->smooth_trunc > 32767)
         return false;
-    if ((long long)w * h > (1LL << 30))
+    if ((long long)w * h > (1LL << 26))   // keeps every thread index below 2^31
         return false;
     return true;
 }
@@ -64,7 +65,8 @@ BpLayout make_layout(int w, int h, const vs_bp_params *p)
 {
     BpLayout lay;
     lay.L = p->labels;
-    lay.Lp = (p->labels + 15) / 16 * 16;
+    // padded label count: one of the compiled sizes 16, 32, 48, 64, 96, 128
+    lay.Lp = p->labels <= 64 ? (p->labels + 15) / 16 * 16 : (p->labels <= 96 ? 96 : 128);
     lay.levels = p->levels;
     size_t off = 0;
     for (int l = 0; l < p->levels; ++l) {
@@ -98,16 +100,16 @@ struct Cost0Args {
 __global__ void k_cost0(Cost0Args a)
 {
     pdl_begin();
-    const int chunks = a.Lp / 16;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long total = (long long)2 * a.h * a.wh * chunks;
-    if (idx >= total)
+    const unsigned chunks = (unsigned)a.Lp / 16u;
+    const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 2u * a.h * a.wh * chunks)
         return;
     const int j = (int)(idx % chunks);
-    const long long slot = idx / chunks;
-    const int xh = (int)(slot % a.wh);
-    const int y = (int)((slot / a.wh) % a.h);
-    const int c = (int)(slot / ((long long)a.wh * a.h));
+    const unsigned slot = idx / chunks;
+    const unsigned row = slot / (unsigned)a.wh;
+    const int xh = (int)(slot - row * (unsigned)a.wh);
+    const int y = (int)(row % (unsigned)a.h);
+    const int c = (int)(row / (unsigned)a.h);
     const int x = 2 * xh + ((c + y) & 1);
     if (x >= a.w)
         return;
@@ -144,16 +146,16 @@ struct CostDownArgs {
 __global__ void k_cost_down(CostDownArgs a)
 {
     pdl_begin();
-    const int chunks = a.Lp / 8;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long total = (long long)2 * a.hc * a.whc * chunks;
-    if (idx >= total)
+    const unsigned chunks = (unsigned)a.Lp / 8u;
+    const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 2u * a.hc * a.whc * chunks)
         return;
     const int j = (int)(idx % chunks);
-    const long long slot = idx / chunks;
-    const int xh = (int)(slot % a.whc);
-    const int y = (int)((slot / a.whc) % a.hc);
-    const int c = (int)(slot / ((long long)a.whc * a.hc));
+    const unsigned slot = idx / chunks;
+    const unsigned row = slot / (unsigned)a.whc;
+    const int xh = (int)(slot - row * (unsigned)a.whc);
+    const int y = (int)(row % (unsigned)a.hc);
+    const int c = (int)(row / (unsigned)a.hc);
     const int x = 2 * xh + ((c + y) & 1);
     if (x >= a.wc)
         return;
@@ -208,6 +210,8 @@ struct SweepArgs {
     int zero_in;            // incoming = 0 (first iteration of the coarsest level)
     int materialize;        // also store the incoming used into the own slots
     uint32_t c2, ts2;       // (c, c) and (Ts, Ts) packed
+    uint8_t *labels;        // last level-0 iteration: labels of the active colour
+    int labels_pitch;
 };
 
 // Byte i of word a in the low half and byte i of word b in the high half,
@@ -255,17 +259,20 @@ struct CostChunk<uint16_t> {
 // BYTES: level 0 with data_trunc + 4 smooth_trunc <= 255, so the belief sum
 // of four labels fits four byte lanes of one 32-bit add.  FULL: labels == LP,
 // no padding labels to mask.
-template <int LP, typename CostT, bool BYTES, bool FULL>
+// LABELS: the last level-0 iteration also writes the labels of its active
+// pixels (their incoming messages are final): argmin_d of the belief sum S(d)
+// taken as the minimum of S(d) * 256 + d, so ties go to the smallest d.
+template <int LP, typename CostT, bool BYTES, bool FULL, bool LABELS>
 __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
 {
     pdl_begin();
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int pair = (int)(idx & 1);
-    const long long slot = idx >> 1;
-    if (slot >= (long long)a.h * a.wh)
+    const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int pair = (int)(idx & 1u);
+    const unsigned slot = idx >> 1;
+    if (slot >= (unsigned)a.h * (unsigned)a.wh)
         return;
-    const int y = (int)(slot / a.wh);
-    const int xh = (int)(slot - (long long)y * a.wh);
+    const int y = (int)(slot / (unsigned)a.wh);
+    const int xh = (int)(slot - (unsigned)y * (unsigned)a.wh);
     const int x = 2 * xh + ((a.color + y) & 1);
     if (x >= a.w)
         return;
@@ -303,6 +310,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
 
     uint32_t F[LP];
     uint32_t H2 = kBig2;
+    uint32_t best_key = 0xFFFFFFFFu;
 #pragma unroll
     for (int j = 0; j < LP / 16; ++j) {
         uint4 m[4];
@@ -333,6 +341,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int d = 16 * j + 4 * wi + q;
+                    if (LABELS && (FULL || d < a.L))
+                        best_key = min(best_key, (((s4 >> (8 * q)) & 0xFFu) << 8) | (uint32_t)d);
                     uint32_t wv = wq[q];
                     if (!FULL && d >= a.L)
                         wv = kBig2;
@@ -349,6 +359,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
                 const uint32_t pud = pair_bytes((&m[2].x)[wi], (&m[3].x)[wi], i & 3);
                 const uint32_t t = plr + pud;                       // (L+U, R+D), no carry
                 const uint32_t s2 = t + prmt(t, t, 0x1032u) + cc.dup(i);   // (S, S)
+                if (LABELS && (FULL || d < a.L))
+                    best_key = min(best_key, ((s2 & 0xFFFFu) << 8) | (uint32_t)d);
                 uint32_t wv = s2 - (pair ? pud : plr);              // (h_A, h_B)
                 if (!FULL && d >= a.L)
                     wv = kBig2;
@@ -357,6 +369,9 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
             }
         }
     }
+
+    if (LABELS && pair == 0)
+        a.labels[(size_t)y * a.labels_pitch + x] = (uint8_t)(best_key & 0xFFu);
 
     // destinations: A = left / up neighbour, B = right / down neighbour
     const int ncolor = a.color ^ 1;
@@ -409,17 +424,21 @@ struct LabelArgs {
     const uint8_t *msg;    // level 0
     uint8_t *labels;
     int labels_pitch, w, h, wh, L, Lp;
+    int color;             // the colour whose labels are still missing
 };
 
-// d* = argmin_d D0(d) + sum of the in-frame incoming messages, smallest d wins.
+// d* = argmin_d D0(d) + sum of the in-frame incoming messages, smallest d
+// wins, for the pixels of one colour (the other colour's labels come from
+// the last sweep).
 __global__ void k_bp_labels(LabelArgs a)
 {
     pdl_begin();
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int xh = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
+    const int c = a.color;
+    const int x = 2 * xh + ((c + y) & 1);
     if (x >= a.w || y >= a.h)
         return;
-    const int c = (x + y) & 1, xh = x >> 1;
     const bool has[4] = {x > 0, x < a.w - 1, y > 0, y < a.h - 1};
     const uint8_t *cost = a.cost + (((size_t)c * a.h + y) * a.wh + xh) * a.Lp;
     const uint8_t *in[4];
@@ -459,14 +478,14 @@ struct ExportArgs {
 __global__ void k_bp_export(ExportArgs a)
 {
     pdl_begin();
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long total = 4LL * a.h * a.w * a.L;
-    if (idx >= total)
+    const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 4u * a.h * a.w * a.L)
         return;
-    const int d = (int)(idx % a.L);
-    const int x = (int)((idx / a.L) % a.w);
-    const int y = (int)((idx / ((long long)a.L * a.w)) % a.h);
-    const int k = (int)(idx / ((long long)a.L * a.w * a.h));
+    const int d = (int)(idx % (unsigned)a.L);
+    const unsigned px = idx / (unsigned)a.L;
+    const int x = (int)(px % (unsigned)a.w);
+    const int y = (int)((px / (unsigned)a.w) % (unsigned)a.h);
+    const int k = (int)(px / ((unsigned)a.w * (unsigned)a.h));
     const bool has = k == 0 ? x > 0 : k == 1 ? x < a.w - 1 : k == 2 ? y > 0 : y < a.h - 1;
     const int c = (x + y) & 1;
     int v = 0;
@@ -479,19 +498,27 @@ __global__ void k_bp_export(ExportArgs a)
 // host dispatch
 
 // cost8: the level's data term is stored in bytes; bytes: its belief sums
-// fit bytes too (byte-lane arithmetic)
+// fit bytes too (byte-lane arithmetic); labels: the last level-0 iteration
 template <int LP, bool FULL>
 void launch_sweep_lp(const SweepArgs &a, bool cost8, bool bytes, cudaStream_t st)
 {
-    const long long threads = 2LL * a.h * a.wh;
-    const int block = kSweepThreads;
-    const unsigned grid = (unsigned)((threads + block - 1) / block);
-    if (cost8 && bytes)
-        launch_pdl(k_bp_sweep<LP, uint8_t, true, FULL>, dim3(grid), dim3(block), st, a);
-    else if (cost8)
-        launch_pdl(k_bp_sweep<LP, uint8_t, false, FULL>, dim3(grid), dim3(block), st, a);
-    else
-        launch_pdl(k_bp_sweep<LP, uint16_t, false, FULL>, dim3(grid), dim3(block), st, a);
+    const unsigned threads = 2u * (unsigned)a.h * (unsigned)a.wh;
+    const unsigned block = kSweepThreads;
+    const dim3 grid((threads + block - 1) / block);
+    const bool lab = a.labels != nullptr;
+    if (cost8 && bytes) {
+        if (lab)
+            launch_pdl(k_bp_sweep<LP, uint8_t, true, FULL, true>, grid, dim3(block), st, a);
+        else
+            launch_pdl(k_bp_sweep<LP, uint8_t, true, FULL, false>, grid, dim3(block), st, a);
+    } else if (cost8) {
+        if (lab)
+            launch_pdl(k_bp_sweep<LP, uint8_t, false, FULL, true>, grid, dim3(block), st, a);
+        else
+            launch_pdl(k_bp_sweep<LP, uint8_t, false, FULL, false>, grid, dim3(block), st, a);
+    } else {
+        launch_pdl(k_bp_sweep<LP, uint16_t, false, FULL, false>, grid, dim3(block), st, a);
+    }
 }
 
 template <int LP>
@@ -510,9 +537,7 @@ void launch_sweep(int Lp, const SweepArgs &a, bool cost8, bool bytes, cudaStream
     case 32: launch_sweep_full<32>(a, cost8, bytes, st); break;
     case 48: launch_sweep_full<48>(a, cost8, bytes, st); break;
     case 64: launch_sweep_full<64>(a, cost8, bytes, st); break;
-    case 80: launch_sweep_full<80>(a, cost8, bytes, st); break;
     case 96: launch_sweep_full<96>(a, cost8, bytes, st); break;
-    case 112: launch_sweep_full<112>(a, cost8, bytes, st); break;
     default: launch_sweep_full<128>(a, cost8, bytes, st); break;
     }
 }
@@ -597,6 +622,9 @@ extern "C" int vs_bp_stereo(const uint8_t *left, const uint8_t *right, int w, in
             a.from_parent = (t == 0 && l + 1 < lay.levels);
             a.zero_in = (t == 0 && l + 1 == lay.levels);
             a.materialize = (t == 0 && p->iters == 1);
+            const bool last = l == 0 && t == p->iters - 1;
+            a.labels = last ? labels : nullptr;
+            a.labels_pitch = labels_pitch;
             const int slot = prof_begin(l == 0 ? kProfSweepL0 : kProfSweepCoarse, st);
             launch_sweep(lay.Lp, a, lay.cost_u8[l], lay.bytes[l], st);
             prof_end(slot, st);
@@ -604,8 +632,10 @@ extern "C" int vs_bp_stereo(const uint8_t *left, const uint8_t *right, int w, in
         }
     }
     {
-        LabelArgs a{ws + lay.cost_off[0], ws + lay.msg_off[0], labels, labels_pitch, w, h, lay.wh[0], lay.L, lay.Lp};
-        dim3 grid((w + 127) / 128, h);
+        // the last sweep labelled colour (iters - 1) & 1; this pass labels the other
+        LabelArgs a{ws + lay.cost_off[0], ws + lay.msg_off[0], labels, labels_pitch, w, h, lay.wh[0], lay.L, lay.Lp,
+                    (p->iters & 1)};
+        dim3 grid((lay.wh[0] + 127) / 128, h);
         const int slot = prof_begin(kProfBpOther, st);
         launch_pdl(k_bp_labels, dim3(grid), dim3(128), st, a);
         prof_end(slot, st);
@@ -624,8 +654,10 @@ extern "C" int vs_bp_export_messages(const void *workspace, size_t ws_bytes, int
     int rc = check_workspace(lay, workspace, ws_bytes);
     if (rc != VS_OK)
         return rc;
-    ExportArgs a{reinterpret_cast<const uint8_t *>(workspace) + lay.msg_off[0], out, w, h, lay.wh[0], lay.L, lay.Lp};
     const long long n = 4LL * h * w * lay.L;
+    if (n >= (1LL << 31))
+        return VS_EINVAL;
+    ExportArgs a{reinterpret_cast<const uint8_t *>(workspace) + lay.msg_off[0], out, w, h, lay.wh[0], lay.L, lay.Lp};
     launch_pdl(k_bp_export, dim3((unsigned)((n + 255) / 256)), dim3(256), (cudaStream_t)stream, a);
     note_launch();
     return launch_status();

@@ -82,14 +82,28 @@ __global__ void __launch_bounds__(kRemapThreads) k_remap_down(RemapArgs a)
                         const float fx0 = floorf(sx), fy0 = floorf(sy);
                         const int x0 = (int)fx0, y0 = (int)fy0;
                         const float ax = sx - fx0, ay = sy - fy0;
-                        const float w00 = (1.0f - ax) * (1.0f - ay), w10 = ax * (1.0f - ay);
-                        const float w01 = (1.0f - ax) * ay, w11 = ax * ay;
+                        if (x0 >= 0 && y0 >= 0 && x0 + 1 < a.W && y0 + 1 < a.H) {
+                            // all four taps in the frame: one base address, two rows of 6 bytes
+                            const uint8_t *p0 = a.src + (size_t)y0 * a.src_pitch + 3 * x0;
+                            const uint8_t *p1 = p0 + a.src_pitch;
 #pragma unroll
-                        for (int ch = 0; ch < 3; ++ch) {
-                            val[ch] = w00 * tap(a.src, a.src_pitch, a.W, a.H, x0, y0, ch)
-                                    + w10 * tap(a.src, a.src_pitch, a.W, a.H, x0 + 1, y0, ch)
-                                    + w01 * tap(a.src, a.src_pitch, a.W, a.H, x0, y0 + 1, ch)
-                                    + w11 * tap(a.src, a.src_pitch, a.W, a.H, x0 + 1, y0 + 1, ch);
+                            for (int ch = 0; ch < 3; ++ch) {
+                                const float t00 = (float)__ldg(p0 + ch), t10 = (float)__ldg(p0 + 3 + ch);
+                                const float t01 = (float)__ldg(p1 + ch), t11 = (float)__ldg(p1 + 3 + ch);
+                                const float top = fmaf(ax, t10 - t00, t00);
+                                const float bot = fmaf(ax, t11 - t01, t01);
+                                val[ch] = fmaf(ay, bot - top, top);
+                            }
+                        } else {
+                            const float w00 = (1.0f - ax) * (1.0f - ay), w10 = ax * (1.0f - ay);
+                            const float w01 = (1.0f - ax) * ay, w11 = ax * ay;
+#pragma unroll
+                            for (int ch = 0; ch < 3; ++ch) {
+                                val[ch] = w00 * tap(a.src, a.src_pitch, a.W, a.H, x0, y0, ch)
+                                        + w10 * tap(a.src, a.src_pitch, a.W, a.H, x0 + 1, y0, ch)
+                                        + w01 * tap(a.src, a.src_pitch, a.W, a.H, x0, y0 + 1, ch)
+                                        + w11 * tap(a.src, a.src_pitch, a.W, a.H, x0 + 1, y0 + 1, ch);
+                            }
                         }
                     }
                 }
