@@ -231,6 +231,7 @@ struct CostChunk<uint8_t> {
     uint4 v;
     __device__ __forceinline__ void load(const uint8_t *base, int j) { v = reinterpret_cast<const uint4 *>(base)[j]; }
     __device__ __forceinline__ uint32_t word(int wi) const { return (&v.x)[wi]; }
+    __device__ __forceinline__ void zero() { v = make_uint4(0, 0, 0, 0); }
     __device__ __forceinline__ uint32_t dup(int i) const
     {
         // byte i & 3 zero-extended into both 16-bit halves (byte 4 of {0:wv} is 0)
@@ -249,6 +250,11 @@ struct CostChunk<uint16_t> {
         v1 = reinterpret_cast<const uint4 *>(base)[2 * j + 1];
     }
     __device__ __forceinline__ uint32_t word(int) const { return 0u; }   // byte-lane path never uses 16-bit costs
+    __device__ __forceinline__ void zero()
+    {
+        v0 = make_uint4(0, 0, 0, 0);
+        v1 = v0;
+    }
     __device__ __forceinline__ uint32_t dup(int i) const
     {
         const uint32_t wv = i < 8 ? (&v0.x)[i >> 1] : (&v1.x)[(i - 8) >> 1];
@@ -262,7 +268,9 @@ struct CostChunk<uint16_t> {
 // LABELS: the last level-0 iteration also writes the labels of its active
 // pixels (their incoming messages are final): argmin_d of the belief sum S(d)
 // taken as the minimum of S(d) * 256 + d, so ties go to the smallest d.
-template <int LP, typename CostT, bool BYTES, bool FULL, bool LABELS>
+// PRELOAD: issue every load of the pixel before the arithmetic (levels too
+// small to fill the GPU, where one thread's latency is the sweep's time).
+template <int LP, typename CostT, bool BYTES, bool FULL, bool LABELS, bool PRELOAD>
 __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
 {
     pdl_begin();
@@ -308,17 +316,37 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
     uint8_t *own = a.msg + ((((size_t)a.color * 4) * a.h + y) * a.wh + xh) * LP;
     const size_t dir_stride = (size_t)a.h * a.wh * LP;
 
+    constexpr int NPRE = PRELOAD ? LP / 16 : 1;
+    uint4 mpre[NPRE][4];
+    CostChunk<CostT> cpre[NPRE];
+    if (PRELOAD) {
+#pragma unroll
+        for (int j = 0; j < NPRE; ++j) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                mpre[j][k] = use[k] ? reinterpret_cast<const uint4 *>(in[k])[j] : make_uint4(0, 0, 0, 0);
+            cpre[j].load(cost, j);
+        }
+    }
+
     uint32_t F[LP];
     uint32_t H2 = kBig2;
     uint32_t best_key = 0xFFFFFFFFu;
 #pragma unroll
     for (int j = 0; j < LP / 16; ++j) {
         uint4 m[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            m[k] = use[k] ? reinterpret_cast<const uint4 *>(in[k])[j] : make_uint4(0, 0, 0, 0);
         CostChunk<CostT> cc;
-        cc.load(cost, j);
+        if (PRELOAD) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                m[k] = mpre[PRELOAD ? j : 0][k];
+            cc = cpre[PRELOAD ? j : 0];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                m[k] = use[k] ? reinterpret_cast<const uint4 *>(in[k])[j] : make_uint4(0, 0, 0, 0);
+            cc.load(cost, j);
+        }
         if (a.materialize) {
             const size_t k0 = 2 * pair;
             reinterpret_cast<uint4 *>(own + k0 * dir_stride)[j] = pair ? m[2] : m[0];
@@ -417,6 +445,165 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
 }
 
 // ---------------------------------------------------------------------------
+// message sweep, labels split across two lanes (small levels)
+//
+// On the coarse levels there are too few pixels to fill the GPU, so a sweep
+// is as long as one thread's serial label chain.  Here each direction pair
+// is shared by two adjacent lanes, one per half of the labels.  Each lane
+// runs the forward and backward lower-envelope passes over its half; the
+// halves are joined exactly by
+//   F(d) = min(F_half(d), F(d0 - 1) + c (d - d0 + 1))   upper half, forward
+//   G(d) = min(G_half(d), G(d1)     + c (d1 - d))       lower half, backward
+// (d0, d1 = first label of the upper half), with the carries exchanged by
+// one shuffle each and the corrections applied to all labels in parallel.
+// The chain per lane is half as long and the work per lane about half.
+
+template <int LP, typename CostT, bool BYTES, bool FULL>
+__global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_split(SweepArgs a)
+{
+    pdl_begin();
+    constexpr int HL = LP / 2;   // labels per lane
+    constexpr int HC = HL / 16;  // 16-label chunks per lane
+    const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int half = (int)(idx & 1u);
+    const int pair = (int)((idx >> 1) & 1u);
+    const unsigned slot = idx >> 2;
+    int y = 0, xh = 0, x = 0;
+    bool valid = slot < (unsigned)a.h * (unsigned)a.wh;
+    if (valid) {
+        y = (int)(slot / (unsigned)a.wh);
+        xh = (int)(slot - (unsigned)y * (unsigned)a.wh);
+        x = 2 * xh + ((a.color + y) & 1);
+        valid = x < a.w;
+    }
+    const bool has[4] = {x > 0, x < a.w - 1, y > 0, y < a.h - 1};
+    const uint8_t *in[4];
+    if (a.from_parent) {
+        const int px = x >> 1, py = y >> 1, pc = (px + py) & 1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            in[k] = a.pmsg + ((((size_t)pc * 4 + k) * a.ph + py) * a.pwh + (px >> 1)) * LP;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            in[k] = a.msg + ((((size_t)a.color * 4 + k) * a.h + y) * a.wh + xh) * LP;
+    }
+    bool use[4];
+    {
+        const int px = x >> 1, py = y >> 1;
+        const bool phas[4] = {px > 0, px < a.pw - 1, py > 0, py < a.ph - 1};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            use[k] = valid && has[k] && !a.zero_in && (!a.from_parent || phas[k]);
+    }
+    const CostT *cost = reinterpret_cast<const CostT *>(a.cost) + ((size_t)a.color * a.h + y) * a.wh * LP +
+                        (size_t)xh * LP;
+    uint8_t *own = a.msg + ((((size_t)a.color * 4) * a.h + y) * a.wh + xh) * LP;
+    const size_t dir_stride = (size_t)a.h * a.wh * LP;
+
+    uint32_t F[HL];
+    uint32_t H2 = kBig2;
+#pragma unroll
+    for (int jj = 0; jj < HC; ++jj) {
+        const int j = half * HC + jj;   // chunk of the full label range
+        uint4 m[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            m[k] = use[k] ? reinterpret_cast<const uint4 *>(in[k])[j] : make_uint4(0, 0, 0, 0);
+        CostChunk<CostT> cc;
+        if (valid)
+            cc.load(cost, j);
+        else
+            cc.zero();
+        if (valid && a.materialize) {
+            const size_t k0 = 2 * pair;
+            reinterpret_cast<uint4 *>(own + k0 * dir_stride)[j] = pair ? m[2] : m[0];
+            reinterpret_cast<uint4 *>(own + (k0 + 1) * dir_stride)[j] = pair ? m[3] : m[1];
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int k = 16 * jj + i;           // label within the half
+            const int d = half * HL + k;         // label
+            uint32_t wv;
+            if (BYTES) {
+                const int wi = i >> 2, q = i & 3;
+                const uint32_t s4 = cc.word(wi) + (&m[0].x)[wi] + (&m[1].x)[wi] + (&m[2].x)[wi] + (&m[3].x)[wi];
+                const uint32_t a4 = s4 - (pair ? (&m[2].x)[wi] : (&m[0].x)[wi]);
+                const uint32_t b4 = s4 - (pair ? (&m[3].x)[wi] : (&m[1].x)[wi]);
+                // (byte q of a4, byte q of b4) as 16-bit lanes: pick, then clear bytes 1 and 3
+                wv = prmt(a4, b4, (uint32_t)q | ((uint32_t)(4 + q) << 8)) & 0x00FF00FFu;
+            } else {
+                const int wi = i >> 2;
+                const uint32_t plr = pair_bytes((&m[0].x)[wi], (&m[1].x)[wi], i & 3);
+                const uint32_t pud = pair_bytes((&m[2].x)[wi], (&m[3].x)[wi], i & 3);
+                const uint32_t t = plr + pud;
+                const uint32_t s2 = t + prmt(t, t, 0x1032u) + cc.dup(i);
+                wv = s2 - (pair ? pud : plr);
+            }
+            if (!FULL && d >= a.L)
+                wv = kBig2;
+            F[k] = k == 0 ? wv : __viaddmin_u16x2(F[k - 1], a.c2, wv);
+            H2 = min_u16x2(H2, wv);
+        }
+    }
+    // join the halves: global minimum, then the forward carry into the upper half
+    H2 = min_u16x2(H2, __shfl_xor_sync(0xffffffffu, H2, 1));
+    const uint32_t c_lo = __shfl_xor_sync(0xffffffffu, F[HL - 1], 1);
+    if (half == 1) {
+#pragma unroll
+        for (int k = 0; k < HL; ++k)
+            F[k] = min_u16x2(F[k], c_lo + a.c2 * (uint32_t)(k + 1));
+    }
+    // backward pass over the half (G kept in F), then the carry into the lower half
+#pragma unroll
+    for (int k = HL - 2; k >= 0; --k)
+        F[k] = __viaddmin_u16x2(F[k + 1], a.c2, F[k]);
+    const uint32_t c_hi = __shfl_xor_sync(0xffffffffu, F[0], 1);
+    if (half == 0) {
+#pragma unroll
+        for (int k = 0; k < HL; ++k)
+            F[k] = min_u16x2(F[k], c_hi + a.c2 * (uint32_t)(HL - k));
+    }
+    if (!valid)
+        return;
+
+    const int ncolor = a.color ^ 1;
+    uint8_t *dstA = nullptr, *dstB = nullptr;
+    if (pair == 0) {
+        if (has[0])
+            dstA = a.msg + ((((size_t)ncolor * 4 + 1) * a.h + y) * a.wh + ((x - 1) >> 1)) * LP;
+        if (has[1])
+            dstB = a.msg + ((((size_t)ncolor * 4 + 0) * a.h + y) * a.wh + ((x + 1) >> 1)) * LP;
+    } else {
+        if (has[2])
+            dstA = a.msg + ((((size_t)ncolor * 4 + 3) * a.h + (y - 1)) * a.wh + (x >> 1)) * LP;
+        if (has[3])
+            dstB = a.msg + ((((size_t)ncolor * 4 + 2) * a.h + (y + 1)) * a.wh + (x >> 1)) * LP;
+    }
+    const uint32_t negH2 = ((0u - (H2 & 0xFFFFu)) & 0xFFFFu) | ((0u - (H2 >> 16)) << 16);
+#pragma unroll
+    for (int jj = 0; jj < HC; ++jj) {
+        uint32_t o[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            o[i] = __viaddmin_s16x2(F[16 * jj + i], negH2, a.ts2);   // min(G - H, Ts)
+        uint32_t oa[4], ob[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t t01 = prmt(o[4 * q], o[4 * q + 1], 0x6420u);
+            const uint32_t t23 = prmt(o[4 * q + 2], o[4 * q + 3], 0x6420u);
+            oa[q] = prmt(t01, t23, 0x6420u);
+            ob[q] = prmt(t01, t23, 0x7531u);
+        }
+        const int j = half * HC + jj;
+        if (dstA)
+            reinterpret_cast<uint4 *>(dstA)[j] = make_uint4(oa[0], oa[1], oa[2], oa[3]);
+        if (dstB)
+            reinterpret_cast<uint4 *>(dstB)[j] = make_uint4(ob[0], ob[1], ob[2], ob[3]);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // labels and read-out
 
 struct LabelArgs {
@@ -499,6 +686,10 @@ __global__ void k_bp_export(ExportArgs a)
 
 // cost8: the level's data term is stored in bytes; bytes: its belief sums
 // fit bytes too (byte-lane arithmetic); labels: the last level-0 iteration
+// levels with fewer active pixels than this (but too many for the split
+// kernel) preload all inputs
+constexpr unsigned kPreloadMaxPixels = 1u << 16;
+
 template <int LP, bool FULL>
 void launch_sweep_lp(const SweepArgs &a, bool cost8, bool bytes, cudaStream_t st)
 {
@@ -506,28 +697,60 @@ void launch_sweep_lp(const SweepArgs &a, bool cost8, bool bytes, cudaStream_t st
     const unsigned block = kSweepThreads;
     const dim3 grid((threads + block - 1) / block);
     const bool lab = a.labels != nullptr;
+    const bool pre = LP <= 64 && !lab && (unsigned)a.h * (unsigned)a.wh < kPreloadMaxPixels;
     if (cost8 && bytes) {
         if (lab)
-            launch_pdl(k_bp_sweep<LP, uint8_t, true, FULL, true>, grid, dim3(block), st, a);
+            launch_pdl(k_bp_sweep<LP, uint8_t, true, FULL, true, false>, grid, dim3(block), st, a);
+        else if (pre)
+            launch_pdl(k_bp_sweep<LP, uint8_t, true, FULL, false, true>, grid, dim3(block), st, a);
         else
-            launch_pdl(k_bp_sweep<LP, uint8_t, true, FULL, false>, grid, dim3(block), st, a);
+            launch_pdl(k_bp_sweep<LP, uint8_t, true, FULL, false, false>, grid, dim3(block), st, a);
     } else if (cost8) {
         if (lab)
-            launch_pdl(k_bp_sweep<LP, uint8_t, false, FULL, true>, grid, dim3(block), st, a);
+            launch_pdl(k_bp_sweep<LP, uint8_t, false, FULL, true, false>, grid, dim3(block), st, a);
+        else if (pre)
+            launch_pdl(k_bp_sweep<LP, uint8_t, false, FULL, false, true>, grid, dim3(block), st, a);
         else
-            launch_pdl(k_bp_sweep<LP, uint8_t, false, FULL, false>, grid, dim3(block), st, a);
+            launch_pdl(k_bp_sweep<LP, uint8_t, false, FULL, false, false>, grid, dim3(block), st, a);
+    } else if (pre) {
+        launch_pdl(k_bp_sweep<LP, uint16_t, false, FULL, false, true>, grid, dim3(block), st, a);
     } else {
-        launch_pdl(k_bp_sweep<LP, uint16_t, false, FULL, false>, grid, dim3(block), st, a);
+        launch_pdl(k_bp_sweep<LP, uint16_t, false, FULL, false, false>, grid, dim3(block), st, a);
     }
+}
+
+// levels with fewer active pixels than this run the label-split kernel
+constexpr unsigned kSplitMaxPixels = 1u << 14;
+
+template <int LP, bool FULL>
+void launch_sweep_split(const SweepArgs &a, bool cost8, bool bytes, cudaStream_t st)
+{
+    const unsigned threads = 4u * (unsigned)a.h * (unsigned)a.wh;
+    const unsigned block = kSweepThreads;
+    const dim3 grid((threads + block - 1) / block);
+    if (cost8 && bytes)
+        launch_pdl(k_bp_sweep_split<LP, uint8_t, true, FULL>, grid, dim3(block), st, a);
+    else if (cost8)
+        launch_pdl(k_bp_sweep_split<LP, uint8_t, false, FULL>, grid, dim3(block), st, a);
+    else
+        launch_pdl(k_bp_sweep_split<LP, uint16_t, false, FULL>, grid, dim3(block), st, a);
 }
 
 template <int LP>
 void launch_sweep_full(const SweepArgs &a, bool cost8, bool bytes, cudaStream_t st)
 {
-    if (a.L == LP)
+    // the split kernel needs whole 16-label chunks per half and writes no labels
+    const bool split = LP % 32 == 0 && a.labels == nullptr && (unsigned)a.h * (unsigned)a.wh < kSplitMaxPixels;
+    if (split) {
+        if (a.L == LP)
+            launch_sweep_split<LP, true>(a, cost8, bytes, st);
+        else
+            launch_sweep_split<LP, false>(a, cost8, bytes, st);
+    } else if (a.L == LP) {
         launch_sweep_lp<LP, true>(a, cost8, bytes, st);
-    else
+    } else {
         launch_sweep_lp<LP, false>(a, cost8, bytes, st);
+    }
 }
 
 void launch_sweep(int Lp, const SweepArgs &a, bool cost8, bool bytes, cudaStream_t st)
