@@ -7,7 +7,11 @@
 //     cost_l[c][y][x >> 1][Lp]     uint8 while data_trunc * 4^l <= 255, else uint16
 //     msg_l [c][k][y][x >> 1][Lp]  uint8 incoming message from direction k
 //   with k = 0 left, 1 right, 2 up, 3 down and Lp = labels rounded up to one
-//   of the compiled sizes 16, 32, 48, 64, 96, 128.
+//   of the compiled sizes 16, 32, 48, 64, 96, 128.  Within a row the slots
+//   are interleaved in groups of 16: the 16-byte piece p (16 labels in bytes,
+//   8 in uint16) of the 16 slots of a group lies in one 256-byte block, so a
+//   warp reading or writing piece p of 16 consecutive slots touches whole
+//   32-byte sectors (slot_base below).
 //   Messages live in [0, smooth_trunc] after normalisation, so 8 bits hold
 //   them exactly; all message arithmetic is integer.
 //
@@ -36,6 +40,7 @@ constexpr int kSweepThreads = 128;        // 64 pixels x 2 direction pairs per C
 struct BpLayout {
     int L, Lp, levels;
     int w[kMaxLevels], h[kMaxLevels], wh[kMaxLevels];
+    int wg[kMaxLevels];        // 16-slot groups per row
     int cost_u8[kMaxLevels];   // level cost fits a byte: data_trunc * 4^l <= 255
     int bytes[kMaxLevels];     // level belief sums fit a byte: + 4 smooth_trunc <= 255
     size_t cost_off[kMaxLevels], msg_off[kMaxLevels];
@@ -73,7 +78,8 @@ BpLayout make_layout(int w, int h, const vs_bp_params *p)
         lay.w[l] = l == 0 ? w : (lay.w[l - 1] + 1) / 2;
         lay.h[l] = l == 0 ? h : (lay.h[l - 1] + 1) / 2;
         lay.wh[l] = (lay.w[l] + 1) / 2;
-        const size_t slots = (size_t)2 * lay.h[l] * lay.wh[l];
+        lay.wg[l] = (lay.wh[l] + 15) / 16;
+        const size_t slots = (size_t)2 * lay.h[l] * lay.wg[l] * 16;   // both colours, rows padded to groups
         const long long cmax = (long long)p->data_trunc << (2 * l);
         lay.cost_u8[l] = l == 0 || cmax <= 255;
         lay.bytes[l] = lay.cost_u8[l] && cmax + 4LL * p->smooth_trunc <= 255;
@@ -86,12 +92,28 @@ BpLayout make_layout(int w, int h, const vs_bp_params *p)
     return lay;
 }
 
+// Byte offset of piece 0 of slot (row, xh) in an array with wg groups per
+// row and np 16-byte pieces per slot; piece p lies kPieceStride * p further.
+constexpr int kPieceStride = 256;
+__host__ __device__ __forceinline__ size_t slot_base(int row, int xh, int wg, int np)
+{
+    return ((((size_t)row * wg + (xh >> 4)) * np) * 16 + (xh & 15)) * 16;
+}
+__device__ __forceinline__ uint4 ld_piece(const uint8_t *base, int p)
+{
+    return *reinterpret_cast<const uint4 *>(base + (size_t)p * kPieceStride);
+}
+__device__ __forceinline__ void st_piece(uint8_t *base, int p, const uint4 &v)
+{
+    *reinterpret_cast<uint4 *>(base + (size_t)p * kPieceStride) = v;
+}
+
 // ---------------------------------------------------------------------------
 // data term
 
 struct Cost0Args {
     const uint8_t *left, *right;
-    int pitch, w, h, wh, L, Lp, Td;
+    int pitch, w, h, wh, wg, L, Lp, Td;
     uint8_t *cost;
 };
 
@@ -100,16 +122,20 @@ struct Cost0Args {
 __global__ void k_cost0(Cost0Args a)
 {
     pdl_begin();
+    // threads in memory order: (row, group, piece j, slot in group)
     const unsigned chunks = (unsigned)a.Lp / 16u;
     const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= 2u * a.h * a.wh * chunks)
+    if (idx >= 2u * a.h * a.wg * chunks * 16u)
         return;
-    const int j = (int)(idx % chunks);
-    const unsigned slot = idx / chunks;
-    const unsigned row = slot / (unsigned)a.wh;
-    const int xh = (int)(slot - row * (unsigned)a.wh);
+    const int lane = (int)(idx & 15u);
+    unsigned t = idx >> 4;
+    const int j = (int)(t % chunks);
+    t /= chunks;
+    const int g = (int)(t % (unsigned)a.wg);
+    const unsigned row = t / (unsigned)a.wg;
     const int y = (int)(row % (unsigned)a.h);
     const int c = (int)(row / (unsigned)a.h);
+    const int xh = 16 * g + lane;
     const int x = 2 * xh + ((c + y) & 1);
     if (x >= a.w)
         return;
@@ -128,16 +154,15 @@ __global__ void k_cost0(Cost0Args a)
         }
         wv[i >> 2] |= (uint32_t)v << (8 * (i & 3));
     }
-    uint4 *dst = reinterpret_cast<uint4 *>(a.cost + (size_t)slot * a.Lp) + j;
-    *dst = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    st_piece(a.cost + slot_base((int)row, xh, a.wg, (int)chunks), j, make_uint4(wv[0], wv[1], wv[2], wv[3]));
 }
 
 struct CostDownArgs {
     const void *fine;      // level l-1, uint8 or uint16
     void *coarse;          // level l, uint8 (when the sums fit) or uint16
     int fine_is_u8, coarse_is_u8;
-    int wf, hf, whf;       // fine dims
-    int wc, hc, whc;       // coarse dims
+    int wf, hf, wgf;       // fine dims (width, height, slot groups per row)
+    int wc, hc, wgc;       // coarse dims
     int Lp;
 };
 
@@ -146,16 +171,21 @@ struct CostDownArgs {
 __global__ void k_cost_down(CostDownArgs a)
 {
     pdl_begin();
+    // threads in memory order: (row, group, 8-label chunk j, slot in group)
     const unsigned chunks = (unsigned)a.Lp / 8u;
+    const int np16 = a.Lp / 16;
     const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= 2u * a.hc * a.whc * chunks)
+    if (idx >= 2u * a.hc * a.wgc * chunks * 16u)
         return;
-    const int j = (int)(idx % chunks);
-    const unsigned slot = idx / chunks;
-    const unsigned row = slot / (unsigned)a.whc;
-    const int xh = (int)(slot - row * (unsigned)a.whc);
+    const int lane = (int)(idx & 15u);
+    unsigned t = idx >> 4;
+    const int j = (int)(t % chunks);
+    t /= chunks;
+    const int g = (int)(t % (unsigned)a.wgc);
+    const unsigned row = t / (unsigned)a.wgc;
     const int y = (int)(row % (unsigned)a.hc);
     const int c = (int)(row / (unsigned)a.hc);
+    const int xh = 16 * g + lane;
     const int x = 2 * xh + ((c + y) & 1);
     if (x >= a.wc)
         return;
@@ -167,19 +197,19 @@ __global__ void k_cost_down(CostDownArgs a)
             const int xf = 2 * x + ii, yf = 2 * y + jj;
             if (xf >= a.wf || yf >= a.hf)
                 continue;
-            const int cf = (ii + jj) & 1;
-            const size_t fslot = ((size_t)cf * a.hf + yf) * a.whf + x;
+            const int cf = (ii + jj) & 1;   // child slot: row cf*hf + yf, column slot x
+            const int frow = cf * a.hf + yf;
             if (a.fine_is_u8) {
-                const uint2 v = *(reinterpret_cast<const uint2 *>(
-                                    reinterpret_cast<const uint8_t *>(a.fine) + fslot * a.Lp) + j);
+                const uint8_t *b = reinterpret_cast<const uint8_t *>(a.fine) + slot_base(frow, x, a.wgf, np16);
+                const uint2 v = *reinterpret_cast<const uint2 *>(b + (j >> 1) * kPieceStride + (j & 1) * 8);
                 // widen 8 bytes to 8 u16 lanes
                 acc[0] += prmt(v.x, 0, 0x4140);
                 acc[1] += prmt(v.x, 0, 0x4342);
                 acc[2] += prmt(v.y, 0, 0x4140);
                 acc[3] += prmt(v.y, 0, 0x4342);
             } else {
-                const uint4 v = *(reinterpret_cast<const uint4 *>(
-                                    reinterpret_cast<const uint16_t *>(a.fine) + fslot * a.Lp) + j);
+                const uint8_t *b = reinterpret_cast<const uint8_t *>(a.fine) + slot_base(frow, x, a.wgf, 2 * np16);
+                const uint4 v = ld_piece(b, j);
                 acc[0] += v.x;
                 acc[1] += v.y;
                 acc[2] += v.z;
@@ -187,12 +217,13 @@ __global__ void k_cost_down(CostDownArgs a)
             }
         }
     }
+    uint8_t *cb = reinterpret_cast<uint8_t *>(a.coarse);
     if (a.coarse_is_u8) {   // every lane is <= 255 here: narrow back to bytes
-        uint2 *dst = reinterpret_cast<uint2 *>(reinterpret_cast<uint8_t *>(a.coarse) + (size_t)slot * a.Lp) + j;
-        *dst = make_uint2(prmt(acc[0], acc[1], 0x6420u), prmt(acc[2], acc[3], 0x6420u));
+        uint8_t *b = cb + slot_base((int)row, xh, a.wgc, np16);
+        *reinterpret_cast<uint2 *>(b + (j >> 1) * kPieceStride + (j & 1) * 8) =
+            make_uint2(prmt(acc[0], acc[1], 0x6420u), prmt(acc[2], acc[3], 0x6420u));
     } else {
-        uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<uint16_t *>(a.coarse) + (size_t)slot * a.Lp) + j;
-        *dst = make_uint4(acc[0], acc[1], acc[2], acc[3]);
+        st_piece(cb + slot_base((int)row, xh, a.wgc, 2 * np16), j, make_uint4(acc[0], acc[1], acc[2], acc[3]));
     }
 }
 
@@ -203,8 +234,8 @@ struct SweepArgs {
     const void *cost;       // this level
     uint8_t *msg;           // this level
     const uint8_t *pmsg;    // parent level (coarse-to-fine initialisation)
-    int w, h, wh, L;
-    int pw, ph, pwh;
+    int w, h, wh, wg, L;
+    int pw, ph, pwh, pwg;
     int color;              // active colour, = t & 1
     int from_parent;        // incoming = parent's messages (first iteration, not coarsest)
     int zero_in;            // incoming = 0 (first iteration of the coarsest level)
@@ -229,7 +260,7 @@ struct CostChunk;
 template <>
 struct CostChunk<uint8_t> {
     uint4 v;
-    __device__ __forceinline__ void load(const uint8_t *base, int j) { v = reinterpret_cast<const uint4 *>(base)[j]; }
+    __device__ __forceinline__ void load(const uint8_t *base, int j) { v = ld_piece(base, j); }
     __device__ __forceinline__ uint32_t word(int wi) const { return (&v.x)[wi]; }
     __device__ __forceinline__ void zero() { v = make_uint4(0, 0, 0, 0); }
     __device__ __forceinline__ uint32_t dup(int i) const
@@ -244,10 +275,10 @@ struct CostChunk<uint8_t> {
 template <>
 struct CostChunk<uint16_t> {
     uint4 v0, v1;
-    __device__ __forceinline__ void load(const uint16_t *base, int j)
+    __device__ __forceinline__ void load(const uint8_t *base, int j)
     {
-        v0 = reinterpret_cast<const uint4 *>(base)[2 * j];
-        v1 = reinterpret_cast<const uint4 *>(base)[2 * j + 1];
+        v0 = ld_piece(base, 2 * j);
+        v1 = ld_piece(base, 2 * j + 1);
     }
     __device__ __forceinline__ uint32_t word(int) const { return 0u; }   // byte-lane path never uses 16-bit costs
     __device__ __forceinline__ void zero()
@@ -276,11 +307,12 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
     pdl_begin();
     const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
     const int pair = (int)(idx & 1u);
-    const unsigned slot = idx >> 1;
-    if (slot >= (unsigned)a.h * (unsigned)a.wh)
+    const unsigned slot = idx >> 1;   // over rows padded to whole 16-slot groups
+    const unsigned rowslots = 16u * (unsigned)a.wg;
+    if (slot >= (unsigned)a.h * rowslots)
         return;
-    const int y = (int)(slot / (unsigned)a.wh);
-    const int xh = (int)(slot - (unsigned)y * (unsigned)a.wh);
+    const int y = (int)(slot / rowslots);
+    const int xh = (int)(slot - (unsigned)y * rowslots);
     const int x = 2 * xh + ((a.color + y) & 1);
     if (x >= a.w)
         return;
@@ -293,11 +325,11 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
             const int px = x >> 1, py = y >> 1, pc = (px + py) & 1;
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                in[k] = a.pmsg + ((((size_t)pc * 4 + k) * a.ph + py) * a.pwh + (px >> 1)) * LP;
+                in[k] = a.pmsg + slot_base((pc * 4 + k) * a.ph + py, px >> 1, a.pwg, LP / 16);
         } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                in[k] = a.msg + ((((size_t)a.color * 4 + k) * a.h + y) * a.wh + xh) * LP;
+                in[k] = a.msg + slot_base((a.color * 4 + k) * a.h + y, xh, a.wg, LP / 16);
         }
     }
     // a slot is read only if the neighbour exists here and, when the messages
@@ -311,10 +343,10 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
         for (int k = 0; k < 4; ++k)
             use[k] = has[k] && !a.zero_in && (!a.from_parent || phas[k]);
     }
-    const CostT *cost = reinterpret_cast<const CostT *>(a.cost) + ((size_t)a.color * a.h + y) * a.wh * LP +
-                        (size_t)xh * LP;
-    uint8_t *own = a.msg + ((((size_t)a.color * 4) * a.h + y) * a.wh + xh) * LP;
-    const size_t dir_stride = (size_t)a.h * a.wh * LP;
+    const uint8_t *cost = reinterpret_cast<const uint8_t *>(a.cost) +
+                          slot_base(a.color * a.h + y, xh, a.wg, (LP / 16) * (int)sizeof(CostT));
+    uint8_t *own = a.msg + slot_base(a.color * 4 * a.h + y, xh, a.wg, LP / 16);
+    const size_t dir_stride = (size_t)a.h * a.wg * (LP / 16) * kPieceStride;   // bytes between directions
 
     constexpr int NPRE = PRELOAD ? LP / 16 : 1;
     uint4 mpre[NPRE][4];
@@ -324,7 +356,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
         for (int j = 0; j < NPRE; ++j) {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                mpre[j][k] = use[k] ? reinterpret_cast<const uint4 *>(in[k])[j] : make_uint4(0, 0, 0, 0);
+                mpre[j][k] = use[k] ? ld_piece(in[k], j) : make_uint4(0, 0, 0, 0);
             cpre[j].load(cost, j);
         }
     }
@@ -344,13 +376,13 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
         } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                m[k] = use[k] ? reinterpret_cast<const uint4 *>(in[k])[j] : make_uint4(0, 0, 0, 0);
+                m[k] = use[k] ? ld_piece(in[k], j) : make_uint4(0, 0, 0, 0);
             cc.load(cost, j);
         }
         if (a.materialize) {
             const size_t k0 = 2 * pair;
-            reinterpret_cast<uint4 *>(own + k0 * dir_stride)[j] = pair ? m[2] : m[0];
-            reinterpret_cast<uint4 *>(own + (k0 + 1) * dir_stride)[j] = pair ? m[3] : m[1];
+            st_piece(own + k0 * dir_stride, j, pair ? m[2] : m[0]);
+            st_piece(own + (k0 + 1) * dir_stride, j, pair ? m[3] : m[1]);
         }
         if (BYTES) {
             // four labels per word: S = D + L + R + U + D in byte lanes, then
@@ -406,14 +438,14 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
     uint8_t *dstA = nullptr, *dstB = nullptr;
     if (pair == 0) {
         if (has[0])
-            dstA = a.msg + ((((size_t)ncolor * 4 + 1) * a.h + y) * a.wh + ((x - 1) >> 1)) * LP;
+            dstA = a.msg + slot_base((ncolor * 4 + 1) * a.h + y, (x - 1) >> 1, a.wg, LP / 16);
         if (has[1])
-            dstB = a.msg + ((((size_t)ncolor * 4 + 0) * a.h + y) * a.wh + ((x + 1) >> 1)) * LP;
+            dstB = a.msg + slot_base((ncolor * 4 + 0) * a.h + y, (x + 1) >> 1, a.wg, LP / 16);
     } else {
         if (has[2])
-            dstA = a.msg + ((((size_t)ncolor * 4 + 3) * a.h + (y - 1)) * a.wh + (x >> 1)) * LP;
+            dstA = a.msg + slot_base((ncolor * 4 + 3) * a.h + (y - 1), x >> 1, a.wg, LP / 16);
         if (has[3])
-            dstB = a.msg + ((((size_t)ncolor * 4 + 2) * a.h + (y + 1)) * a.wh + (x >> 1)) * LP;
+            dstB = a.msg + slot_base((ncolor * 4 + 2) * a.h + (y + 1), x >> 1, a.wg, LP / 16);
     }
 
     // -H in both 16-bit lanes, for the fused add-min of the output
@@ -438,9 +470,9 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
             ob[q] = prmt(t01, t23, 0x7531u);
         }
         if (dstA)
-            reinterpret_cast<uint4 *>(dstA)[j] = make_uint4(oa[0], oa[1], oa[2], oa[3]);
+            st_piece(dstA, j, make_uint4(oa[0], oa[1], oa[2], oa[3]));
         if (dstB)
-            reinterpret_cast<uint4 *>(dstB)[j] = make_uint4(ob[0], ob[1], ob[2], ob[3]);
+            st_piece(dstB, j, make_uint4(ob[0], ob[1], ob[2], ob[3]));
     }
 }
 
@@ -467,12 +499,13 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_split(SweepArgs a)
     const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
     const int half = (int)(idx & 1u);
     const int pair = (int)((idx >> 1) & 1u);
-    const unsigned slot = idx >> 2;
+    const unsigned slot = idx >> 2;   // over rows padded to whole 16-slot groups
+    const unsigned rowslots = 16u * (unsigned)a.wg;
     int y = 0, xh = 0, x = 0;
-    bool valid = slot < (unsigned)a.h * (unsigned)a.wh;
+    bool valid = slot < (unsigned)a.h * rowslots;
     if (valid) {
-        y = (int)(slot / (unsigned)a.wh);
-        xh = (int)(slot - (unsigned)y * (unsigned)a.wh);
+        y = (int)(slot / rowslots);
+        xh = (int)(slot - (unsigned)y * rowslots);
         x = 2 * xh + ((a.color + y) & 1);
         valid = x < a.w;
     }
@@ -482,11 +515,11 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_split(SweepArgs a)
         const int px = x >> 1, py = y >> 1, pc = (px + py) & 1;
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            in[k] = a.pmsg + ((((size_t)pc * 4 + k) * a.ph + py) * a.pwh + (px >> 1)) * LP;
+            in[k] = a.pmsg + slot_base((pc * 4 + k) * a.ph + py, px >> 1, a.pwg, LP / 16);
     } else {
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            in[k] = a.msg + ((((size_t)a.color * 4 + k) * a.h + y) * a.wh + xh) * LP;
+            in[k] = a.msg + slot_base((a.color * 4 + k) * a.h + y, xh, a.wg, LP / 16);
     }
     bool use[4];
     {
@@ -496,10 +529,10 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_split(SweepArgs a)
         for (int k = 0; k < 4; ++k)
             use[k] = valid && has[k] && !a.zero_in && (!a.from_parent || phas[k]);
     }
-    const CostT *cost = reinterpret_cast<const CostT *>(a.cost) + ((size_t)a.color * a.h + y) * a.wh * LP +
-                        (size_t)xh * LP;
-    uint8_t *own = a.msg + ((((size_t)a.color * 4) * a.h + y) * a.wh + xh) * LP;
-    const size_t dir_stride = (size_t)a.h * a.wh * LP;
+    const uint8_t *cost = reinterpret_cast<const uint8_t *>(a.cost) +
+                          slot_base(a.color * a.h + y, xh, a.wg, (LP / 16) * (int)sizeof(CostT));
+    uint8_t *own = a.msg + slot_base(a.color * 4 * a.h + y, xh, a.wg, LP / 16);
+    const size_t dir_stride = (size_t)a.h * a.wg * (LP / 16) * kPieceStride;   // bytes between directions
 
     uint32_t F[HL];
     uint32_t H2 = kBig2;
@@ -509,7 +542,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_split(SweepArgs a)
         uint4 m[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            m[k] = use[k] ? reinterpret_cast<const uint4 *>(in[k])[j] : make_uint4(0, 0, 0, 0);
+            m[k] = use[k] ? ld_piece(in[k], j) : make_uint4(0, 0, 0, 0);
         CostChunk<CostT> cc;
         if (valid)
             cc.load(cost, j);
@@ -517,8 +550,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_split(SweepArgs a)
             cc.zero();
         if (valid && a.materialize) {
             const size_t k0 = 2 * pair;
-            reinterpret_cast<uint4 *>(own + k0 * dir_stride)[j] = pair ? m[2] : m[0];
-            reinterpret_cast<uint4 *>(own + (k0 + 1) * dir_stride)[j] = pair ? m[3] : m[1];
+            st_piece(own + k0 * dir_stride, j, pair ? m[2] : m[0]);
+            st_piece(own + (k0 + 1) * dir_stride, j, pair ? m[3] : m[1]);
         }
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
@@ -571,14 +604,14 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_split(SweepArgs a)
     uint8_t *dstA = nullptr, *dstB = nullptr;
     if (pair == 0) {
         if (has[0])
-            dstA = a.msg + ((((size_t)ncolor * 4 + 1) * a.h + y) * a.wh + ((x - 1) >> 1)) * LP;
+            dstA = a.msg + slot_base((ncolor * 4 + 1) * a.h + y, (x - 1) >> 1, a.wg, LP / 16);
         if (has[1])
-            dstB = a.msg + ((((size_t)ncolor * 4 + 0) * a.h + y) * a.wh + ((x + 1) >> 1)) * LP;
+            dstB = a.msg + slot_base((ncolor * 4 + 0) * a.h + y, (x + 1) >> 1, a.wg, LP / 16);
     } else {
         if (has[2])
-            dstA = a.msg + ((((size_t)ncolor * 4 + 3) * a.h + (y - 1)) * a.wh + (x >> 1)) * LP;
+            dstA = a.msg + slot_base((ncolor * 4 + 3) * a.h + (y - 1), x >> 1, a.wg, LP / 16);
         if (has[3])
-            dstB = a.msg + ((((size_t)ncolor * 4 + 2) * a.h + (y + 1)) * a.wh + (x >> 1)) * LP;
+            dstB = a.msg + slot_base((ncolor * 4 + 2) * a.h + (y + 1), x >> 1, a.wg, LP / 16);
     }
     const uint32_t negH2 = ((0u - (H2 & 0xFFFFu)) & 0xFFFFu) | ((0u - (H2 >> 16)) << 16);
 #pragma unroll
@@ -597,9 +630,9 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_split(SweepArgs a)
         }
         const int j = half * HC + jj;
         if (dstA)
-            reinterpret_cast<uint4 *>(dstA)[j] = make_uint4(oa[0], oa[1], oa[2], oa[3]);
+            st_piece(dstA, j, make_uint4(oa[0], oa[1], oa[2], oa[3]));
         if (dstB)
-            reinterpret_cast<uint4 *>(dstB)[j] = make_uint4(ob[0], ob[1], ob[2], ob[3]);
+            st_piece(dstB, j, make_uint4(ob[0], ob[1], ob[2], ob[3]));
     }
 }
 
@@ -610,7 +643,7 @@ struct LabelArgs {
     const uint8_t *cost;   // level 0
     const uint8_t *msg;    // level 0
     uint8_t *labels;
-    int labels_pitch, w, h, wh, L, Lp;
+    int labels_pitch, w, h, wh, wg, L, Lp;
     int color;             // the colour whose labels are still missing
 };
 
@@ -627,18 +660,19 @@ __global__ void k_bp_labels(LabelArgs a)
     if (x >= a.w || y >= a.h)
         return;
     const bool has[4] = {x > 0, x < a.w - 1, y > 0, y < a.h - 1};
-    const uint8_t *cost = a.cost + (((size_t)c * a.h + y) * a.wh + xh) * a.Lp;
+    const int np = a.Lp / 16;
+    const uint8_t *cost = a.cost + slot_base(c * a.h + y, xh, a.wg, np);
     const uint8_t *in[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-        in[k] = a.msg + ((((size_t)c * 4 + k) * a.h + y) * a.wh + xh) * a.Lp;
+        in[k] = a.msg + slot_base((c * 4 + k) * a.h + y, xh, a.wg, np);
     int best = 0x7FFFFFFF, bestd = 0;
     for (int j = 0; j < a.Lp / 16; ++j) {
-        uint4 cv = reinterpret_cast<const uint4 *>(cost)[j];
+        uint4 cv = ld_piece(cost, j);
         uint4 m[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            m[k] = has[k] ? reinterpret_cast<const uint4 *>(in[k])[j] : make_uint4(0, 0, 0, 0);
+            m[k] = has[k] ? ld_piece(in[k], j) : make_uint4(0, 0, 0, 0);
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             const int d = 16 * j + i;
@@ -659,7 +693,7 @@ __global__ void k_bp_labels(LabelArgs a)
 struct ExportArgs {
     const uint8_t *msg;
     int32_t *out;
-    int w, h, wh, L, Lp;
+    int w, h, wh, wg, L, Lp;
 };
 
 __global__ void k_bp_export(ExportArgs a)
@@ -677,7 +711,8 @@ __global__ void k_bp_export(ExportArgs a)
     const int c = (x + y) & 1;
     int v = 0;
     if (has)
-        v = a.msg[((((size_t)c * 4 + k) * a.h + y) * a.wh + (x >> 1)) * a.Lp + d];
+        v = a.msg[slot_base((c * 4 + k) * a.h + y, x >> 1, a.wg, a.Lp / 16) + (size_t)(d >> 4) * kPieceStride +
+                  (d & 15)];
     a.out[idx] = v;
 }
 
@@ -693,7 +728,7 @@ constexpr unsigned kPreloadMaxPixels = 1u << 16;
 template <int LP, bool FULL>
 void launch_sweep_lp(const SweepArgs &a, bool cost8, bool bytes, cudaStream_t st)
 {
-    const unsigned threads = 2u * (unsigned)a.h * (unsigned)a.wh;
+    const unsigned threads = 2u * (unsigned)a.h * 16u * (unsigned)a.wg;
     const unsigned block = kSweepThreads;
     const dim3 grid((threads + block - 1) / block);
     const bool lab = a.labels != nullptr;
@@ -725,7 +760,7 @@ constexpr unsigned kSplitMaxPixels = 1u << 14;
 template <int LP, bool FULL>
 void launch_sweep_split(const SweepArgs &a, bool cost8, bool bytes, cudaStream_t st)
 {
-    const unsigned threads = 4u * (unsigned)a.h * (unsigned)a.wh;
+    const unsigned threads = 4u * (unsigned)a.h * 16u * (unsigned)a.wg;
     const unsigned block = kSweepThreads;
     const dim3 grid((threads + block - 1) / block);
     if (cost8 && bytes)
@@ -799,8 +834,8 @@ extern "C" int vs_bp_stereo(const uint8_t *left, const uint8_t *right, int w, in
     const int block = 256;
 
     {   // level-0 data term
-        Cost0Args a{left, right, pitch, w, h, lay.wh[0], lay.L, lay.Lp, p->data_trunc, ws + lay.cost_off[0]};
-        const long long n = 2LL * h * lay.wh[0] * (lay.Lp / 16);
+        Cost0Args a{left, right, pitch, w, h, lay.wh[0], lay.wg[0], lay.L, lay.Lp, p->data_trunc, ws + lay.cost_off[0]};
+        const long long n = 2LL * h * lay.wg[0] * 16 * (lay.Lp / 16);
         const int slot = prof_begin(kProfBpOther, st);
         launch_pdl(k_cost0, dim3((unsigned)((n + block - 1) / block)), dim3(block), st, a);
         prof_end(slot, st);
@@ -814,12 +849,12 @@ extern "C" int vs_bp_stereo(const uint8_t *left, const uint8_t *right, int w, in
         a.coarse_is_u8 = lay.cost_u8[l];
         a.wf = lay.w[l - 1];
         a.hf = lay.h[l - 1];
-        a.whf = lay.wh[l - 1];
+        a.wgf = lay.wg[l - 1];
         a.wc = lay.w[l];
         a.hc = lay.h[l];
-        a.whc = lay.wh[l];
+        a.wgc = lay.wg[l];
         a.Lp = lay.Lp;
-        const long long n = 2LL * a.hc * a.whc * (lay.Lp / 8);
+        const long long n = 2LL * a.hc * a.wgc * 16 * (lay.Lp / 8);
         const int slot = prof_begin(kProfBpOther, st);
         launch_pdl(k_cost_down, dim3((unsigned)((n + block - 1) / block)), dim3(block), st, a);
         prof_end(slot, st);
@@ -834,10 +869,12 @@ extern "C" int vs_bp_stereo(const uint8_t *left, const uint8_t *right, int w, in
         a.w = lay.w[l];
         a.h = lay.h[l];
         a.wh = lay.wh[l];
+        a.wg = lay.wg[l];
         a.L = lay.L;
         a.pw = l + 1 < lay.levels ? lay.w[l + 1] : 0;
         a.ph = l + 1 < lay.levels ? lay.h[l + 1] : 0;
         a.pwh = l + 1 < lay.levels ? lay.wh[l + 1] : 0;
+        a.pwg = l + 1 < lay.levels ? lay.wg[l + 1] : 0;
         a.c2 = (uint32_t)ceff * 0x10001u;
         a.ts2 = (uint32_t)p->smooth_trunc * 0x10001u;
         for (int t = 0; t < p->iters; ++t) {
@@ -856,8 +893,8 @@ extern "C" int vs_bp_stereo(const uint8_t *left, const uint8_t *right, int w, in
     }
     {
         // the last sweep labelled colour (iters - 1) & 1; this pass labels the other
-        LabelArgs a{ws + lay.cost_off[0], ws + lay.msg_off[0], labels, labels_pitch, w, h, lay.wh[0], lay.L, lay.Lp,
-                    (p->iters & 1)};
+        LabelArgs a{ws + lay.cost_off[0], ws + lay.msg_off[0], labels, labels_pitch, w, h, lay.wh[0], lay.wg[0], lay.L,
+                    lay.Lp, (p->iters & 1)};
         dim3 grid((lay.wh[0] + 127) / 128, h);
         const int slot = prof_begin(kProfBpOther, st);
         launch_pdl(k_bp_labels, dim3(grid), dim3(128), st, a);
@@ -880,7 +917,8 @@ extern "C" int vs_bp_export_messages(const void *workspace, size_t ws_bytes, int
     const long long n = 4LL * h * w * lay.L;
     if (n >= (1LL << 31))
         return VS_EINVAL;
-    ExportArgs a{reinterpret_cast<const uint8_t *>(workspace) + lay.msg_off[0], out, w, h, lay.wh[0], lay.L, lay.Lp};
+    ExportArgs a{reinterpret_cast<const uint8_t *>(workspace) + lay.msg_off[0], out, w, h, lay.wh[0], lay.wg[0], lay.L,
+                 lay.Lp};
     launch_pdl(k_bp_export, dim3((unsigned)((n + 255) / 256)), dim3(256), (cudaStream_t)stream, a);
     note_launch();
     return launch_status();
