@@ -108,6 +108,32 @@ __device__ __forceinline__ void st_piece(uint8_t *base, int p, const uint4 &v)
     *reinterpret_cast<uint4 *>(base + (size_t)p * kPieceStride) = v;
 }
 
+// The level being swept reads and rewrites its message arrays every
+// iteration; marking those accesses evict-last keeps more of them in L2
+// (a per-instruction hint, no device setting).
+__device__ __forceinline__ uint64_t l2_evict_last_policy()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint4 ld_piece_keep(const uint8_t *base, int p, uint64_t pol)
+{
+    uint4 v;
+    const uint8_t *ptr = base + (size_t)p * kPieceStride;
+    asm volatile("ld.global.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(ptr), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_piece_keep(uint8_t *base, int p, const uint4 &v, uint64_t pol)
+{
+    uint8_t *ptr = base + (size_t)p * kPieceStride;
+    asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(ptr), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w), "l"(pol)
+                 : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // data term
 
@@ -361,6 +387,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
         }
     }
 
+    const uint64_t pol = l2_evict_last_policy();
     uint32_t F[LP];
     uint32_t H2 = kBig2;
     uint32_t best_key = 0xFFFFFFFFu;
@@ -376,7 +403,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
         } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                m[k] = use[k] ? ld_piece(in[k], j) : make_uint4(0, 0, 0, 0);
+                m[k] = use[k] ? ld_piece_keep(in[k], j, pol) : make_uint4(0, 0, 0, 0);
             cc.load(cost, j);
         }
         if (a.materialize) {
@@ -470,9 +497,9 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
             ob[q] = prmt(t01, t23, 0x7531u);
         }
         if (dstA)
-            st_piece(dstA, j, make_uint4(oa[0], oa[1], oa[2], oa[3]));
+            st_piece_keep(dstA, j, make_uint4(oa[0], oa[1], oa[2], oa[3]), pol);
         if (dstB)
-            st_piece(dstB, j, make_uint4(ob[0], ob[1], ob[2], ob[3]));
+            st_piece_keep(dstB, j, make_uint4(ob[0], ob[1], ob[2], ob[3]), pol);
     }
 }
 

@@ -155,7 +155,7 @@ constexpr int kS4CentresX = 32, kS4CentresY = 4;   // window centres per CTA
 constexpr uint32_t kOffFrameNorm = 1u << 28;
 
 template <int R, bool kXYZ>
-__global__ void __launch_bounds__(kS4CentresX *kS4CentresY) k_jbu_s4(JbuArgs a)
+__global__ void __launch_bounds__(kS4CentresX *kS4CentresY, 4) k_jbu_s4(JbuArgs a)
 {
     pdl_begin();
     constexpr int D = 2 * R + 1;
