@@ -226,6 +226,38 @@ int vs_pair_run_host(const vs_pair_config *cfg, const uint8_t *left_host, const 
                      float *disp_host, float *xyz_host, uint8_t *dev_in, float *dev_disp, float *dev_xyz,
                      void *workspace, size_t ws_bytes, void *stream);
 
+/*
+ * Streaming drivers (overlap of host copies and compute across pairs).
+ * A pipeline owns three CUDA streams (host->device copies, compute,
+ * device->host copies) and `depth` rotating slots of device buffers, all
+ * carved from the caller's workspace (vs_pipeline_workspace_size).  Submit
+ * calls enqueue and return; a slot is reused only after its previous pair
+ * has been copied back, so at most `depth` pairs are in flight and host
+ * buffers handed to a submit must stay valid until that pair completes
+ * (vs_pipeline_flush waits for all).  Host buffers should be page-locked.
+ *  mode 0 (pairs):  vs_pipeline_submit_pair takes both W x H RGB frames of an
+ *                   independent pair; results equal vs_pair_run.
+ *  mode 1 (flight): vs_pipeline_submit_frame takes one new frame; frame f is
+ *                   remapped once (Section 2.1, 2.2) into a ring of k + 1
+ *                   rectified frames, and for f >= k the virtual stereo pair
+ *                   (left = frame f - k, right = frame f, Section 3.2) runs
+ *                   Eq. 1-3; its cloud (left camera) goes to xyz_host, which
+ *                   may be NULL and is ignored while f < k.
+ * vs_pipeline_latencies returns, oldest first, the milliseconds from the
+ * start of each completed pair's input copy to the end of its output copy.
+ * Errors: VS_EINVAL (config, mode, depth 1..16, k 1..64), VS_EWORKSPACE,
+ * VS_ECUDA; after an error a pipeline refuses further submits.
+ */
+typedef struct vs_pipeline vs_pipeline;
+size_t vs_pipeline_workspace_size(const vs_pair_config *cfg, int mode, int depth, int k);
+int vs_pipeline_create(const vs_pair_config *cfg, int mode, int depth, int k, void *workspace, size_t ws_bytes,
+                       vs_pipeline **out);
+int vs_pipeline_submit_pair(vs_pipeline *p, const uint8_t *left_host, const uint8_t *right_host, float *xyz_host);
+int vs_pipeline_submit_frame(vs_pipeline *p, const uint8_t *frame_host, float *xyz_host);
+int vs_pipeline_flush(vs_pipeline *p);
+int vs_pipeline_latencies(vs_pipeline *p, float *ms, int max);
+void vs_pipeline_destroy(vs_pipeline *p);
+
 /* Name of a status code. */
 const char *vs_status_string(int status);
 

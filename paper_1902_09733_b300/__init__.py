@@ -29,7 +29,7 @@ __all__ = [
     "rectify_remap", "bp_workspace_size", "bp_stereo", "bp_export_messages",
     "guided_upsample", "reproject", "guided_upsample_reproject",
     "pair_workspace_size", "pair_run", "pair_run_host", "kernel_launches", "status_string",
-    "profile_enable", "profile_collect",
+    "profile_enable", "profile_collect", "Pipeline",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -153,6 +153,13 @@ def lib() -> ctypes.CDLL:
             "vs_kernel_launches": ([], ctypes.c_uint64),
             "vs_profile_enable": ([I], I),
             "vs_profile_collect": ([P, P, I], I),
+            "vs_pipeline_workspace_size": ([cfg_p, I, I, I], S),
+            "vs_pipeline_create": ([cfg_p, I, I, I, P, S, ctypes.POINTER(P)], I),
+            "vs_pipeline_submit_pair": ([P, P, P, P], I),
+            "vs_pipeline_submit_frame": ([P, P, P], I),
+            "vs_pipeline_flush": ([P], I),
+            "vs_pipeline_latencies": ([P, P, I], I),
+            "vs_pipeline_destroy": ([P], None),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -390,3 +397,65 @@ def pair_run_host(cfg: PairConfig, left_host: torch.Tensor, right_host: torch.Te
         workspace.data_ptr(), workspace.numel(), _stream(stream))
     _check("vs_pair_run_host", rc)
     return xyz_host
+
+
+class Pipeline:
+    """Streaming driver over three CUDA streams (``vs_pipeline_*``).
+
+    ``mode="pairs"``: :meth:`submit_pair` takes both frames of independent
+    pairs.  ``mode="flight"``: :meth:`submit_frame` takes one frame at a time
+    and pairs frame f - k (left) with frame f (right).  Up to ``depth`` pairs
+    are in flight; host tensors passed to a submit must stay alive until the
+    pair completes (:meth:`flush`).  Device memory is one caller-visible
+    workspace tensor; the library allocates none.
+    """
+
+    MODES = {"pairs": 0, "flight": 1}
+
+    def __init__(self, cfg: PairConfig, mode: str = "pairs", depth: int = 3, k: int = 1, device=None):
+        self.cfg = cfg
+        self._c = cfg.c()
+        self.mode = self.MODES[mode]
+        n = int(lib().vs_pipeline_workspace_size(ctypes.byref(self._c), self.mode, depth, k))
+        if n == 0:
+            raise VSError("vs_pipeline_workspace_size", VS_EINVAL)
+        self.workspace = torch.empty(n, dtype=torch.uint8, device=device or "cuda")
+        h = ctypes.c_void_p()
+        _check("vs_pipeline_create", lib().vs_pipeline_create(ctypes.byref(self._c), self.mode, depth, k,
+                                                               self.workspace.data_ptr(), n, ctypes.byref(h)))
+        self._h = h
+        self._keep = []
+
+    def submit_pair(self, left_host: torch.Tensor, right_host: torch.Tensor, xyz_host: torch.Tensor | None):
+        self._keep.append((left_host, right_host, xyz_host))
+        _check("vs_pipeline_submit_pair", lib().vs_pipeline_submit_pair(
+            self._h, left_host.data_ptr(), right_host.data_ptr(),
+            xyz_host.data_ptr() if xyz_host is not None else None))
+
+    def submit_frame(self, frame_host: torch.Tensor, xyz_host: torch.Tensor | None = None):
+        self._keep.append((frame_host, xyz_host))
+        _check("vs_pipeline_submit_frame", lib().vs_pipeline_submit_frame(
+            self._h, frame_host.data_ptr(), xyz_host.data_ptr() if xyz_host is not None else None))
+
+    def flush(self):
+        _check("vs_pipeline_flush", lib().vs_pipeline_flush(self._h))
+        self._keep.clear()
+
+    def latencies(self, max_records: int = 1 << 16):
+        buf = (ctypes.c_float * max_records)()
+        n = lib().vs_pipeline_latencies(self._h, ctypes.cast(buf, ctypes.c_void_p), max_records)
+        if n < 0:
+            raise VSError("vs_pipeline_latencies", n)
+        return [float(buf[i]) for i in range(n)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().vs_pipeline_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -12,6 +12,8 @@ Two workloads:
   Gaussian (sigma 1.5 px), and a right view made by warping it with a seeded
   piecewise-planar disparity field (four planes on the Voronoi cells of four
   seeded points, disparity 0..15).
+* :func:`flight_frames` -- consecutive frames of a straight flight leg at
+  100 m over terrain with box buildings (the streaming workload).
 * :func:`terrain_pair` -- a 2.7K RGB pair of a seeded textured heightfield
   (value-noise fBm relief, independent colour-noise albedo) seen by a nadir
   pinhole camera with radial lens distortion; the right camera is displaced by
@@ -265,6 +267,49 @@ def terrain_pair(seed: int, W: int = 2704, H: int = 1520, cam=TERRAIN_CAMERA,
     if return_depth:
         return left, right, dl, dr
     return left, right
+
+
+def flight_frames(seed: int, n_frames: int, spacing: float = 0.05, altitude: float = 100.0,
+                  W: int = 2704, H: int = 1520, cam=TERRAIN_CAMERA, relief: float = 15.0,
+                  n_buildings: int = 40):
+    """Frames of a straight flight leg over a terrain with box buildings.
+
+    The nadir camera flies along +x at ``altitude`` metres, ``spacing`` metres
+    per frame (3 m/s at 60 fps gives 0.05 m).  The terrain is value-noise fBm
+    (0..``relief`` m); ``n_buildings`` seeded boxes rise 5..30 m above it.
+    Albedo wavelengths scale with the altitude so that texture stays at a few
+    low-resolution pixels.  Yields (H, W, 3) uint8 frames with the radial
+    distortion of ``cam``.
+    """
+    g = _rng(seed)
+    scale = altitude / 20.0
+    leg = spacing * max(n_frames - 1, 0)
+    extent = 2.0 * altitude * 1.4 + leg + 8.0
+    noise = _ValueNoise(g, [40.0 * scale, 20.0 * scale, 10.0 * scale, 5.0 * scale], [1.0, 0.5, 0.25, 0.125],
+                        extent)
+    height = _HeightGrid(noise, extent, 2049)
+    lo, hi = float(height.grid.min()), float(height.grid.max())
+    grid = ((height.grid - lo) * (relief / max(hi - lo, 1e-6))).astype(np.float32)
+    n = grid.shape[0]
+    cells = np.linspace(-extent / 2.0, extent / 2.0, n)
+    for _ in range(n_buildings):
+        cx0, cy0 = g.uniform(-extent / 2 + 10, extent / 2 - 10, size=2)
+        sx, sy = g.uniform(6.0, 25.0, size=2)
+        top = g.uniform(5.0, 30.0)
+        ix = np.where(np.abs(cells - cx0) <= sx / 2)[0]
+        iy = np.where(np.abs(cells - cy0) <= sy / 2)[0]
+        if ix.size and iy.size:
+            block = grid[iy[0]:iy[-1] + 1, ix[0]:ix[-1] + 1]
+            grid[iy[0]:iy[-1] + 1, ix[0]:ix[-1] + 1] = float(block.max()) + top
+    height.grid = grid
+    height.flat = grid.ravel()
+    top_all = float(grid.max())
+    albedo = _ValueNoise(g, [0.8 * scale, 0.4 * scale, 0.2 * scale, 0.1 * scale], [0.5, 0.3, 0.2, 0.15],
+                         extent, channels=3)
+    x0 = -leg / 2.0
+    for i in range(n_frames):
+        frame, _ = _render_view(height, albedo, top_all, W, H, cam, x0 + i * spacing, altitude)
+        yield frame
 
 
 def pair_variants(left: np.ndarray, right: np.ndarray):

@@ -81,3 +81,20 @@ def test_bad_arguments_are_rejected_on_the_host(lib):
     assert lib.vs_guided_upsample(fake, 12, 10, 12, fake, 36, fake, 48, 40, 144, ctypes.byref(jr), fake, None) == vs.VS_EINVAL
     assert lib.vs_reproject(fake, 10, 10, ctypes.byref(cam), 0.0, fake, None) == vs.VS_EINVAL
     assert lib.vs_reproject(fake, 10, 10, ctypes.byref(cam), -1.0, fake, None) == vs.VS_EINVAL
+
+
+def test_pipeline_host_checks(lib):
+    cfg = vs.PairConfig(2704, 1520, vs.Camera(1400, 1400, 1351.5, 759.5, -0.25, 0.07), 0.5,
+                        vs.BPParams(), vs.JBUParams()).c()
+    pairs = lib.vs_pipeline_workspace_size(ctypes.byref(cfg), 0, 3, 1)
+    flight = lib.vs_pipeline_workspace_size(ctypes.byref(cfg), 1, 3, 3)
+    assert pairs > 3 * (2 * 2704 * 1520 * 3 + 2704 * 1520 * 12)
+    assert flight > 4 * 2704 * 1520 * 3
+    for mode, depth, k in ((2, 3, 1), (0, 0, 1), (0, 17, 1), (1, 3, 0), (1, 3, 65)):
+        assert lib.vs_pipeline_workspace_size(ctypes.byref(cfg), mode, depth, k) == 0
+    h = ctypes.c_void_p()
+    # checks fail before any CUDA object is created
+    assert lib.vs_pipeline_create(ctypes.byref(cfg), 0, 3, 1, None, 0, ctypes.byref(h)) == vs.VS_EWORKSPACE
+    assert lib.vs_pipeline_create(ctypes.byref(cfg), 5, 3, 1, None, 0, ctypes.byref(h)) == vs.VS_EINVAL
+    assert lib.vs_pipeline_submit_pair(None, None, None, None) == vs.VS_EINVAL
+    assert lib.vs_pipeline_flush(None) == vs.VS_EINVAL
