@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--stream-frames", type=int, default=1500)
     ap.add_argument("--stream-render", type=int, default=16)
+    ap.add_argument("--batch-pairs", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -230,6 +231,80 @@ def committed_traffic(kernel_src: str):
     return float(m.group(1)) if sh.group(1) == cur else None
 
 
+def run_batched(args, vs, synth, torch, dev, cam):
+    """48 grey pairs: downsample factor 2/4/8 of 2704x1520 and 32/64/96/128
+    labels drawn from a seed, frame offsets 1..5 along a 100 m flight leg."""
+    g = np.random.default_rng(2024)
+    n = args.batch_pairs
+    frames = [torch.from_numpy(f).to(dev) for f in synth.flight_frames(7, 6)]
+    grey = {}
+    for s in (2, 4, 8):
+        for i, f in enumerate(frames):
+            _, _, lg = vs.rectify_remap(f, cam, scale=s, dst=None, low_rgb=None)
+            grey[(s, i)] = lg
+    torch.cuda.synchronize()
+    pairs, shapes = [], []
+    for _ in range(n):
+        s = int(g.choice([2, 4, 8]))
+        L = int(g.choice([32, 64, 96, 128]))
+        off = int(g.integers(1, 6))
+        pairs.append((grey[(s, 0)], grey[(s, off)], vs.BPParams(L, 4, 10, 20, 10, 40)))
+        shapes.append((s, L))
+    # autotune the sweep kernels once per (scale, labels) shape
+    tuned = {}
+    for (s, L) in sorted(set(shapes)):
+        p = vs.BPParams(L, 4, 10, 20, 10, 40)
+        tuned[f"s{s}_L{L}"] = vs.bp_autotune(grey[(s, 0)], grey[(s, 1)], p)
+    labels = [torch.empty(tuple(p[0].shape), dtype=torch.uint8, device=dev) for p in pairs]
+    ws_b = torch.empty(vs.bp_batch_workspace_size(pairs), dtype=torch.uint8, device=dev)
+    ws_s = torch.empty(max(vs.bp_workspace_size(p[0].shape[1], p[0].shape[0], p[2]) for p in pairs),
+                       dtype=torch.uint8, device=dev)
+    st = torch.cuda.Stream(device=dev)
+
+    def batched():
+        vs.bp_stereo_batch(pairs, labels=labels, workspace=ws_b)
+
+    def sequential():
+        for (l, r, p), lab in zip(pairs, labels):
+            vs.bp_stereo(l, r, p, labels=lab, workspace=ws_s)
+
+    def graph_ms(fn, reps=5):
+        with torch.cuda.stream(st):
+            fn()
+        torch.cuda.synchronize()
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr, stream=st):
+            fn()
+        gr.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            e0.record(st)
+            for _ in range(reps):
+                gr.replay()
+            e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    n0 = vs.kernel_launches()
+    sequential()
+    torch.cuda.synchronize()
+    seq_launches = vs.kernel_launches() - n0
+    n0 = vs.kernel_launches()
+    batched()
+    torch.cuda.synchronize()
+    bat_launches = vs.kernel_launches() - n0
+    t_seq = graph_ms(sequential)
+    t_bat = graph_ms(batched)
+    vs.bp_autotune_reset()
+    px = sum(int(p[0].numel()) * p[2].labels for p in pairs)
+    return {"pairs": n, "batched_ms": t_bat, "sequential_ms": t_seq, "speedup": t_seq / t_bat,
+            "batched_pairs_per_s": n / (t_bat * 1e-3), "launches_batched": bat_launches,
+            "launches_sequential": seq_launches, "label_pixels_per_batch": px,
+            "mix": {f"s{s}_L{L}": shapes.count((s, L)) for (s, L) in sorted(set(shapes))},
+            "autotuned_variants": tuned}
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -402,6 +477,13 @@ def run_ours(args):
                      "h2d_bytes_per_pair": W_FULL * H_FULL * 3, "d2h_bytes_per_pair": W_FULL * H_FULL * 12,
                      "input": f"{args.stream_render} rendered frames of a 100 m flight leg with buildings, cycled"}
 
+    # batched BP: 48 pairs of uneven sizes and label counts in lockstep,
+    # against the same 48 pairs as sequential single-pair calls (both as
+    # CUDA-graph replays, after autotuning the sweep kernels on each shape)
+    batched = None
+    if args.batch_pairs > 0 and rank == 0:
+        batched = run_batched(args, vs, synth, torch, dev, cam)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cam_t = synth.TERRAIN_CAMERA
@@ -428,6 +510,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "streaming": streaming,
+            "batched": batched,
             "gpu_launches": launches_per_step * K,
             "clocks": clk,
         }

@@ -142,6 +142,49 @@ int vs_bp_stereo(const uint8_t *left, const uint8_t *right, int w, int h, int pi
 int vs_bp_stereo_noalloc(const uint8_t *left, const uint8_t *right, int w, int h, int pitch,
                          const vs_bp_params *p, uint8_t *labels, int labels_pitch, void *stream);
 
+/* One pair of a batch for vs_bp_stereo_batch (device pointers as in
+ * vs_bp_stereo). */
+typedef struct {
+    const uint8_t *left, *right;
+    int32_t w, h, pitch;
+    vs_bp_params params;
+    uint8_t *labels;
+    int32_t labels_pitch;
+} vs_bp_job;
+
+/* Workspace bytes for a batch (the sum of the pairs' BP workspaces), or 0 if
+ * a job is invalid or the jobs differ in levels or iters. */
+size_t vs_bp_batch_workspace_size(const vs_bp_job *jobs, int n);
+
+/*
+ * Eq. 1 for n independent pairs of any sizes and label counts (1 <= n <=
+ * 4096), exactly as n vs_bp_stereo calls would compute them, but advanced in
+ * lockstep: each level-iteration of all pairs is a handful of batched
+ * launches (one per label count and kernel variant), so small pairs and the
+ * coarse levels fill the GPU together.  All jobs must share `levels` and
+ * `iters`.  `jobs` is a host array read during the call; the pair
+ * descriptors travel in kernel parameters, so the call can be captured in a
+ * CUDA graph and replayed.
+ * Errors: VS_EINVAL, VS_EWORKSPACE, VS_ECUDA.
+ */
+int vs_bp_stereo_batch(const vs_bp_job *jobs, int n, void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * Autotuner for the message sweeps (no counterpart in the paper).  Runs
+ * vs_bp_stereo on the given pair, then times the three sweep kernels (plain,
+ * register preload, labels split over two lanes) on every level and records
+ * the fastest per (padded label count, level size); later vs_bp_stereo and
+ * vs_bp_stereo_batch calls on levels of those sizes use it.  Results are
+ * identical whichever kernel runs.  Ends with a fresh vs_bp_stereo so labels
+ * and workspace hold the pair's result.  Synchronises `stream`; do not call
+ * it while the stream is being captured.  chosen (nullable, `levels` ints)
+ * receives 0 plain, 1 preload, 2 split per level.  vs_bp_autotune_reset
+ * forgets every recorded choice.
+ */
+int vs_bp_autotune(const uint8_t *left, const uint8_t *right, int w, int h, int pitch, const vs_bp_params *p,
+                   uint8_t *labels, int labels_pitch, void *workspace, size_t ws_bytes, void *stream, int *chosen);
+void vs_bp_autotune_reset(void);
+
 /* Debug read-out after vs_bp_stereo on the same workspace and stream: the
  * final level-0 incoming messages as int32 [4][h][w][labels], directions
  * 0 = from the left neighbour, 1 = right, 2 = up, 3 = down (zero where the

@@ -29,7 +29,8 @@ __all__ = [
     "rectify_remap", "bp_workspace_size", "bp_stereo", "bp_export_messages",
     "guided_upsample", "reproject", "guided_upsample_reproject",
     "pair_workspace_size", "pair_run", "pair_run_host", "kernel_launches", "status_string",
-    "profile_enable", "profile_collect", "Pipeline",
+    "profile_enable", "profile_collect", "Pipeline", "bp_stereo_batch", "bp_batch_workspace_size",
+    "bp_autotune", "bp_autotune_reset",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -54,6 +55,12 @@ class _Camera(ctypes.Structure):
 class _BPParams(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in
                 ("labels", "levels", "iters", "data_trunc", "smooth_slope", "smooth_trunc")]
+
+
+class _BPJob(ctypes.Structure):
+    _fields_ = [("left", ctypes.c_void_p), ("right", ctypes.c_void_p), ("w", ctypes.c_int32),
+                ("h", ctypes.c_int32), ("pitch", ctypes.c_int32), ("params", _BPParams),
+                ("labels", ctypes.c_void_p), ("labels_pitch", ctypes.c_int32)]
 
 
 class _JBUParams(ctypes.Structure):
@@ -153,6 +160,10 @@ def lib() -> ctypes.CDLL:
             "vs_kernel_launches": ([], ctypes.c_uint64),
             "vs_profile_enable": ([I], I),
             "vs_profile_collect": ([P, P, I], I),
+            "vs_bp_batch_workspace_size": ([P, I], S),
+            "vs_bp_stereo_batch": ([P, I, P, S, P], I),
+            "vs_bp_autotune": ([P, P, I, I, I, bp_p, P, I, P, S, P, P], I),
+            "vs_bp_autotune_reset": ([], None),
             "vs_pipeline_workspace_size": ([cfg_p, I, I, I], S),
             "vs_pipeline_create": ([cfg_p, I, I, I, P, S, ctypes.POINTER(P)], I),
             "vs_pipeline_submit_pair": ([P, P, P, P], I),
@@ -289,6 +300,68 @@ def bp_stereo(left: torch.Tensor, right: torch.Tensor, params: BPParams, labels=
                             workspace.numel() * workspace.element_size(), _stream(stream))
     _check("vs_bp_stereo", rc)
     return labels
+
+
+def _jobs(pairs, labels):
+    arr = (_BPJob * len(pairs))()
+    for i, ((left, right, params), lab) in enumerate(zip(pairs, labels)):
+        _dev(left, torch.uint8, "left")
+        _dev(right, torch.uint8, "right")
+        if left.shape != right.shape or left.stride() != right.stride():
+            raise ValueError("left and right must have the same shape and strides")
+        h, w = left.shape
+        arr[i] = _BPJob(left.data_ptr(), right.data_ptr(), w, h, _pitched(left, 1, "left"), params.c(),
+                        lab.data_ptr(), _pitched(lab, 1, "labels"))
+    return arr
+
+
+def bp_batch_workspace_size(pairs) -> int:
+    """Workspace bytes for a batch of (left, right, BPParams) grey pairs."""
+    arr = (_BPJob * len(pairs))()
+    for i, (left, right, params) in enumerate(pairs):
+        h, w = left.shape
+        arr[i] = _BPJob(None, None, w, h, w, params.c(), None, w)
+    return int(lib().vs_bp_batch_workspace_size(ctypes.cast(arr, ctypes.c_void_p), len(pairs)))
+
+
+def bp_stereo_batch(pairs, labels=None, workspace=None, stream=None):
+    """Eq. 1 for a list of (left, right, BPParams) pairs advanced in lockstep
+    (all with the same levels and iters); returns the list of label maps."""
+    if labels is None:
+        labels = [torch.empty(tuple(l.shape), dtype=torch.uint8, device=l.device) for l, _, _ in pairs]
+    arr = _jobs(pairs, labels)
+    need = bp_batch_workspace_size(pairs)
+    if need == 0:
+        raise VSError("vs_bp_batch_workspace_size", VS_EINVAL)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=pairs[0][0].device)
+    _check("vs_bp_stereo_batch", lib().vs_bp_stereo_batch(ctypes.cast(arr, ctypes.c_void_p), len(pairs),
+                                                          workspace.data_ptr(), workspace.numel(),
+                                                          _stream(stream)))
+    return labels
+
+
+def bp_autotune(left: torch.Tensor, right: torch.Tensor, params: BPParams, workspace=None, labels=None,
+                stream=None):
+    """Time the three sweep kernels on every level of this pair and keep the
+    fastest for later calls; returns the choice per level (0 plain, 1 preload,
+    2 split) and leaves the pair's labels in ``labels``."""
+    h, w = left.shape
+    if workspace is None:
+        workspace = torch.empty(bp_workspace_size(w, h, params), dtype=torch.uint8, device=left.device)
+    if labels is None:
+        labels = torch.empty((h, w), dtype=torch.uint8, device=left.device)
+    chosen = (ctypes.c_int * params.levels)()
+    p = params.c()
+    _check("vs_bp_autotune", lib().vs_bp_autotune(
+        left.data_ptr(), right.data_ptr(), w, h, _pitched(left, 1, "left"), ctypes.byref(p), labels.data_ptr(),
+        _pitched(labels, 1, "labels"), workspace.data_ptr(), workspace.numel(), _stream(stream),
+        ctypes.cast(chosen, ctypes.c_void_p)))
+    return [int(v) for v in chosen]
+
+
+def bp_autotune_reset() -> None:
+    lib().vs_bp_autotune_reset()
 
 
 def bp_export_messages(workspace: torch.Tensor, w: int, h: int, params: BPParams, stream=None) -> torch.Tensor:

@@ -29,6 +29,8 @@
 #include "vs_common.cuh"
 
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 namespace vs {
 namespace {
@@ -327,11 +329,13 @@ struct CostChunk<uint16_t> {
 // taken as the minimum of S(d) * 256 + d, so ties go to the smallest d.
 // PRELOAD: issue every load of the pixel before the arithmetic (levels too
 // small to fill the GPU, where one thread's latency is the sweep's time).
+// The sweep of one level-iteration for the CTA `block` of a launch; the
+// plain kernel passes blockIdx.x, the batched kernel its position within
+// its job.
 template <int LP, typename CostT, bool BYTES, bool FULL, bool LABELS, bool PRELOAD>
-__global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
+__device__ __forceinline__ void sweep_body(const SweepArgs &a, unsigned block)
 {
-    pdl_begin();
-    const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned idx = block * kSweepThreads + threadIdx.x;
     const int pair = (int)(idx & 1u);
     const unsigned slot = idx >> 1;   // over rows padded to whole 16-slot groups
     const unsigned rowslots = 16u * (unsigned)a.wg;
@@ -518,12 +522,11 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
 // The chain per lane is half as long and the work per lane about half.
 
 template <int LP, typename CostT, bool BYTES, bool FULL>
-__global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_split(SweepArgs a)
+__device__ __forceinline__ void sweep_split_body(const SweepArgs &a, unsigned block)
 {
-    pdl_begin();
     constexpr int HL = LP / 2;   // labels per lane
     constexpr int HC = HL / 16;  // 16-label chunks per lane
-    const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned idx = block * kSweepThreads + threadIdx.x;
     const int half = (int)(idx & 1u);
     const int pair = (int)((idx >> 1) & 1u);
     const unsigned slot = idx >> 2;   // over rows padded to whole 16-slot groups
@@ -663,6 +666,65 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_split(SweepArgs a)
     }
 }
 
+template <int LP, typename CostT, bool BYTES, bool FULL, bool LABELS, bool PRELOAD>
+__global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
+{
+    pdl_begin();
+    sweep_body<LP, CostT, BYTES, FULL, LABELS, PRELOAD>(a, blockIdx.x);
+}
+
+template <int LP, typename CostT, bool BYTES, bool FULL>
+__global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_split(SweepArgs a)
+{
+    pdl_begin();
+    sweep_split_body<LP, CostT, BYTES, FULL>(a, blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// batched sweeps: one launch advances the same level-iteration of many pairs
+//
+// The jobs of a launch (one per pair, same kernel variant) travel in the
+// kernel parameters, so a captured CUDA graph replays them without any
+// host-side table; job j owns the launch's CTAs first_block[j] ..
+// first_block[j + 1] - 1.
+
+constexpr int kMaxBatch = 64;
+
+struct BatchArgs {
+    int njobs;
+    unsigned first_block[kMaxBatch + 1];
+    SweepArgs job[kMaxBatch];
+};
+
+__device__ __forceinline__ int batch_job(const BatchArgs &b, unsigned block)
+{
+    int lo = 0, hi = b.njobs - 1;   // last job whose first block is <= block
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.first_block[mid] <= block)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int LP, typename CostT, bool BYTES, bool FULL, bool LABELS, bool PRELOAD>
+__global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_batch(const __grid_constant__ BatchArgs b)
+{
+    pdl_begin();
+    const int j = batch_job(b, blockIdx.x);
+    sweep_body<LP, CostT, BYTES, FULL, LABELS, PRELOAD>(b.job[j], blockIdx.x - b.first_block[j]);
+}
+
+template <int LP, typename CostT, bool BYTES, bool FULL>
+__global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_split_batch(const __grid_constant__ BatchArgs b)
+{
+    pdl_begin();
+    const int j = batch_job(b, blockIdx.x);
+    sweep_split_body<LP, CostT, BYTES, FULL>(b.job[j], blockIdx.x - b.first_block[j]);
+}
+
 // ---------------------------------------------------------------------------
 // labels and read-out
 
@@ -748,83 +810,174 @@ __global__ void k_bp_export(ExportArgs a)
 
 // cost8: the level's data term is stored in bytes; bytes: its belief sums
 // fit bytes too (byte-lane arithmetic); labels: the last level-0 iteration
-// levels with fewer active pixels than this (but too many for the split
-// kernel) preload all inputs
-constexpr unsigned kPreloadMaxPixels = 1u << 16;
+// ---------------------------------------------------------------------------
+// kernel variant per level: plain, register preload, or labels split over
+// two lanes.  Defaults by level size (active-colour slots h * wh); the
+// autotuner (vs_bp_autotune) measures the three on a given problem and
+// records the fastest per (label count, level size), which then wins.
 
-template <int LP, bool FULL>
-void launch_sweep_lp(const SweepArgs &a, bool cost8, bool bytes, cudaStream_t st)
+enum SweepVariant { kVarPlain = 0, kVarPreload = 1, kVarSplit = 2 };
+
+constexpr unsigned kSplitMaxPixels = 1u << 14;    // smaller levels: split
+constexpr unsigned kPreloadMaxPixels = 1u << 16;  // smaller levels: preload
+
+struct TuneEntry {
+    int Lp;
+    unsigned slots;
+    int variant;
+};
+std::mutex g_tune_mu;
+std::vector<TuneEntry> g_tune;
+
+bool variant_allowed(int Lp, int variant, bool labels)
 {
-    const unsigned threads = 2u * (unsigned)a.h * 16u * (unsigned)a.wg;
-    const unsigned block = kSweepThreads;
-    const dim3 grid((threads + block - 1) / block);
-    const bool lab = a.labels != nullptr;
-    const bool pre = LP <= 64 && !lab && (unsigned)a.h * (unsigned)a.wh < kPreloadMaxPixels;
-    if (cost8 && bytes) {
-        if (lab)
-            launch_pdl(k_bp_sweep<LP, uint8_t, true, FULL, true, false>, grid, dim3(block), st, a);
-        else if (pre)
-            launch_pdl(k_bp_sweep<LP, uint8_t, true, FULL, false, true>, grid, dim3(block), st, a);
-        else
-            launch_pdl(k_bp_sweep<LP, uint8_t, true, FULL, false, false>, grid, dim3(block), st, a);
-    } else if (cost8) {
-        if (lab)
-            launch_pdl(k_bp_sweep<LP, uint8_t, false, FULL, true, false>, grid, dim3(block), st, a);
-        else if (pre)
-            launch_pdl(k_bp_sweep<LP, uint8_t, false, FULL, false, true>, grid, dim3(block), st, a);
-        else
-            launch_pdl(k_bp_sweep<LP, uint8_t, false, FULL, false, false>, grid, dim3(block), st, a);
-    } else if (pre) {
-        launch_pdl(k_bp_sweep<LP, uint16_t, false, FULL, false, true>, grid, dim3(block), st, a);
-    } else {
-        launch_pdl(k_bp_sweep<LP, uint16_t, false, FULL, false, false>, grid, dim3(block), st, a);
-    }
+    if (labels)
+        return variant == kVarPlain;   // only the plain kernel writes labels
+    if (variant == kVarSplit)
+        return Lp % 32 == 0;
+    if (variant == kVarPreload)
+        return Lp <= 64;
+    return true;
 }
 
-// levels with fewer active pixels than this run the label-split kernel
-constexpr unsigned kSplitMaxPixels = 1u << 14;
-
-template <int LP, bool FULL>
-void launch_sweep_split(const SweepArgs &a, bool cost8, bool bytes, cudaStream_t st)
+int choose_variant(int Lp, unsigned slots, bool labels)
 {
-    const unsigned threads = 4u * (unsigned)a.h * 16u * (unsigned)a.wg;
-    const unsigned block = kSweepThreads;
-    const dim3 grid((threads + block - 1) / block);
-    if (cost8 && bytes)
-        launch_pdl(k_bp_sweep_split<LP, uint8_t, true, FULL>, grid, dim3(block), st, a);
-    else if (cost8)
-        launch_pdl(k_bp_sweep_split<LP, uint8_t, false, FULL>, grid, dim3(block), st, a);
-    else
-        launch_pdl(k_bp_sweep_split<LP, uint16_t, false, FULL>, grid, dim3(block), st, a);
+    if (labels)
+        return kVarPlain;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (const TuneEntry &e : g_tune)
+            if (e.Lp == Lp && e.slots == slots && variant_allowed(Lp, e.variant, false))
+                return e.variant;
+    }
+    if (Lp % 32 == 0 && slots < kSplitMaxPixels)
+        return kVarSplit;
+    if (Lp <= 64 && slots < kPreloadMaxPixels)
+        return kVarPreload;
+    return kVarPlain;
+}
+
+unsigned sweep_blocks(const SweepArgs &a, int variant)
+{
+    const unsigned threads = (variant == kVarSplit ? 4u : 2u) * (unsigned)a.h * 16u * (unsigned)a.wg;
+    return (threads + kSweepThreads - 1) / kSweepThreads;
+}
+
+// Launches one sweep kernel: `a` for a single pair, or `b` (njobs >= 1) for
+// a batch; cost8 / bytes / full / labels / variant pick the instantiation.
+template <int LP, bool FULL>
+void launch_sweep_lp(const SweepArgs *a, const BatchArgs *b, unsigned grid, bool cost8, bool bytes, bool labels,
+                     int variant, cudaStream_t st)
+{
+    const dim3 g(grid), blk(kSweepThreads);
+#define VS_SWEEP(...)                                                                                         \
+    do {                                                                                                      \
+        if (b)                                                                                                \
+            launch_pdl(k_bp_sweep_batch<__VA_ARGS__>, g, blk, st, *b);                                        \
+        else                                                                                                  \
+            launch_pdl(k_bp_sweep<__VA_ARGS__>, g, blk, st, *a);                                              \
+    } while (0)
+#define VS_SPLIT(...)                                                                                         \
+    do {                                                                                                      \
+        if (b)                                                                                                \
+            launch_pdl(k_bp_sweep_split_batch<__VA_ARGS__>, g, blk, st, *b);                                  \
+        else                                                                                                  \
+            launch_pdl(k_bp_sweep_split<__VA_ARGS__>, g, blk, st, *a);                                        \
+    } while (0)
+    if (variant == kVarSplit) {
+        if (cost8 && bytes)
+            VS_SPLIT(LP, uint8_t, true, FULL);
+        else if (cost8)
+            VS_SPLIT(LP, uint8_t, false, FULL);
+        else
+            VS_SPLIT(LP, uint16_t, false, FULL);
+        return;
+    }
+    constexpr bool kPre = LP <= 64;   // the preload variant exists up to 64 labels
+    const bool pre = kPre && variant == kVarPreload;
+    if (cost8 && bytes) {
+        if (labels)
+            VS_SWEEP(LP, uint8_t, true, FULL, true, false);
+        else if (pre)
+            VS_SWEEP(LP, uint8_t, true, FULL, false, kPre);
+        else
+            VS_SWEEP(LP, uint8_t, true, FULL, false, false);
+    } else if (cost8) {
+        if (labels)
+            VS_SWEEP(LP, uint8_t, false, FULL, true, false);
+        else if (pre)
+            VS_SWEEP(LP, uint8_t, false, FULL, false, kPre);
+        else
+            VS_SWEEP(LP, uint8_t, false, FULL, false, false);
+    } else if (pre) {
+        VS_SWEEP(LP, uint16_t, false, FULL, false, kPre);
+    } else {
+        VS_SWEEP(LP, uint16_t, false, FULL, false, false);
+    }
+#undef VS_SWEEP
+#undef VS_SPLIT
 }
 
 template <int LP>
-void launch_sweep_full(const SweepArgs &a, bool cost8, bool bytes, cudaStream_t st)
+void launch_sweep_full(const SweepArgs *a, const BatchArgs *b, unsigned grid, bool full, bool cost8, bool bytes,
+                       bool labels, int variant, cudaStream_t st)
 {
-    // the split kernel needs whole 16-label chunks per half and writes no labels
-    const bool split = LP % 32 == 0 && a.labels == nullptr && (unsigned)a.h * (unsigned)a.wh < kSplitMaxPixels;
-    if (split) {
-        if (a.L == LP)
-            launch_sweep_split<LP, true>(a, cost8, bytes, st);
-        else
-            launch_sweep_split<LP, false>(a, cost8, bytes, st);
-    } else if (a.L == LP) {
-        launch_sweep_lp<LP, true>(a, cost8, bytes, st);
-    } else {
-        launch_sweep_lp<LP, false>(a, cost8, bytes, st);
+    if (full)
+        launch_sweep_lp<LP, true>(a, b, grid, cost8, bytes, labels, variant, st);
+    else
+        launch_sweep_lp<LP, false>(a, b, grid, cost8, bytes, labels, variant, st);
+}
+
+void launch_sweep_any(int Lp, const SweepArgs *a, const BatchArgs *b, unsigned grid, bool full, bool cost8,
+                      bool bytes, bool labels, int variant, cudaStream_t st)
+{
+    switch (Lp) {
+    case 16: launch_sweep_full<16>(a, b, grid, full, cost8, bytes, labels, variant, st); break;
+    case 32: launch_sweep_full<32>(a, b, grid, full, cost8, bytes, labels, variant, st); break;
+    case 48: launch_sweep_full<48>(a, b, grid, full, cost8, bytes, labels, variant, st); break;
+    case 64: launch_sweep_full<64>(a, b, grid, full, cost8, bytes, labels, variant, st); break;
+    case 96: launch_sweep_full<96>(a, b, grid, full, cost8, bytes, labels, variant, st); break;
+    default: launch_sweep_full<128>(a, b, grid, full, cost8, bytes, labels, variant, st); break;
     }
 }
 
-void launch_sweep(int Lp, const SweepArgs &a, bool cost8, bool bytes, cudaStream_t st)
+// One pair's sweep with the variant chosen for its level size.
+void launch_sweep(int Lp, const SweepArgs &a, bool cost8, bool bytes, cudaStream_t st, int variant = -1)
 {
-    switch (Lp) {
-    case 16: launch_sweep_full<16>(a, cost8, bytes, st); break;
-    case 32: launch_sweep_full<32>(a, cost8, bytes, st); break;
-    case 48: launch_sweep_full<48>(a, cost8, bytes, st); break;
-    case 64: launch_sweep_full<64>(a, cost8, bytes, st); break;
-    case 96: launch_sweep_full<96>(a, cost8, bytes, st); break;
-    default: launch_sweep_full<128>(a, cost8, bytes, st); break;
-    }
+    const bool labels = a.labels != nullptr;
+    if (variant < 0)
+        variant = choose_variant(Lp, (unsigned)a.h * (unsigned)a.wh, labels);
+    launch_sweep_any(Lp, &a, nullptr, sweep_blocks(a, variant), a.L == Lp, cost8, bytes, labels, variant, st);
+}
+
+// Arguments of the sweep at level l, iteration t of one pair.
+SweepArgs sweep_args(const BpLayout &lay, uint8_t *ws, const vs_bp_params *p, int l, int t, uint8_t *labels,
+                     int labels_pitch)
+{
+    SweepArgs a;
+    a.cost = ws + lay.cost_off[l];
+    a.msg = ws + lay.msg_off[l];
+    a.pmsg = l + 1 < lay.levels ? ws + lay.msg_off[l + 1] : nullptr;
+    a.w = lay.w[l];
+    a.h = lay.h[l];
+    a.wh = lay.wh[l];
+    a.wg = lay.wg[l];
+    a.L = lay.L;
+    a.pw = l + 1 < lay.levels ? lay.w[l + 1] : 0;
+    a.ph = l + 1 < lay.levels ? lay.h[l + 1] : 0;
+    a.pwh = l + 1 < lay.levels ? lay.wh[l + 1] : 0;
+    a.pwg = l + 1 < lay.levels ? lay.wg[l + 1] : 0;
+    const int ceff = std::min(p->smooth_slope, p->smooth_trunc);   // same V for any larger slope
+    a.c2 = (uint32_t)ceff * 0x10001u;
+    a.ts2 = (uint32_t)p->smooth_trunc * 0x10001u;
+    a.color = t & 1;
+    a.from_parent = (t == 0 && l + 1 < lay.levels);
+    a.zero_in = (t == 0 && l + 1 == lay.levels);
+    a.materialize = (t == 0 && p->iters == 1);
+    const bool last = l == 0 && t == p->iters - 1;
+    a.labels = last ? labels : nullptr;
+    a.labels_pitch = labels_pitch;
+    return a;
 }
 
 int check_workspace(const BpLayout &lay, const void *ws, size_t ws_bytes)
@@ -845,30 +998,24 @@ extern "C" size_t vs_bp_workspace_size(int w, int h, const vs_bp_params *p)
     return make_layout(w, h, p).total;
 }
 
-extern "C" int vs_bp_stereo(const uint8_t *left, const uint8_t *right, int w, int h, int pitch,
-                            const vs_bp_params *p, uint8_t *labels, int labels_pitch,
-                            void *workspace, size_t ws_bytes, void *stream)
-{
-    using namespace vs;
-    if (!params_ok(w, h, p) || !left || !right || !labels || pitch < w || labels_pitch < w)
-        return VS_EINVAL;
-    const BpLayout lay = make_layout(w, h, p);
-    int rc = check_workspace(lay, workspace, ws_bytes);
-    if (rc != VS_OK)
-        return rc;
-    cudaStream_t st = (cudaStream_t)stream;
-    uint8_t *ws = reinterpret_cast<uint8_t *>(workspace);
-    const int block = 256;
+namespace vs {
+namespace {
 
-    {   // level-0 data term
-        Cost0Args a{left, right, pitch, w, h, lay.wh[0], lay.wg[0], lay.L, lay.Lp, p->data_trunc, ws + lay.cost_off[0]};
-        const long long n = 2LL * h * lay.wg[0] * 16 * (lay.Lp / 16);
+// Level-0 data term and the coarse pyramid of one pair.
+void launch_costs(const BpLayout &lay, uint8_t *ws, const uint8_t *left, const uint8_t *right, int pitch,
+                  const vs_bp_params *p, cudaStream_t st)
+{
+    const int block = 256;
+    {
+        Cost0Args a{left, right, pitch, lay.w[0], lay.h[0], lay.wh[0], lay.wg[0], lay.L, lay.Lp, p->data_trunc,
+                    ws + lay.cost_off[0]};
+        const long long n = 2LL * lay.h[0] * lay.wg[0] * 16 * (lay.Lp / 16);
         const int slot = prof_begin(kProfBpOther, st);
         launch_pdl(k_cost0, dim3((unsigned)((n + block - 1) / block)), dim3(block), st, a);
         prof_end(slot, st);
         note_launch();
     }
-    for (int l = 1; l < lay.levels; ++l) {   // coarse data terms
+    for (int l = 1; l < lay.levels; ++l) {
         CostDownArgs a;
         a.fine = ws + lay.cost_off[l - 1];
         a.coarse = ws + lay.cost_off[l];
@@ -887,48 +1034,240 @@ extern "C" int vs_bp_stereo(const uint8_t *left, const uint8_t *right, int w, in
         prof_end(slot, st);
         note_launch();
     }
-    const int ceff = std::min(p->smooth_slope, p->smooth_trunc);   // same V for any larger slope
+}
+
+// Labels of the colour the last sweep did not label.
+void launch_labels(const BpLayout &lay, uint8_t *ws, uint8_t *labels, int labels_pitch, const vs_bp_params *p,
+                   cudaStream_t st)
+{
+    // the last sweep labelled colour (iters - 1) & 1; this pass labels the other
+    LabelArgs a{ws + lay.cost_off[0], ws + lay.msg_off[0], labels, labels_pitch, lay.w[0], lay.h[0], lay.wh[0],
+                lay.wg[0], lay.L, lay.Lp, (p->iters & 1)};
+    dim3 grid((lay.wh[0] + 127) / 128, lay.h[0]);
+    const int slot = prof_begin(kProfBpOther, st);
+    launch_pdl(k_bp_labels, dim3(grid), dim3(128), st, a);
+    prof_end(slot, st);
+    note_launch();
+}
+
+}  // namespace
+}  // namespace vs
+
+extern "C" int vs_bp_stereo(const uint8_t *left, const uint8_t *right, int w, int h, int pitch,
+                            const vs_bp_params *p, uint8_t *labels, int labels_pitch,
+                            void *workspace, size_t ws_bytes, void *stream)
+{
+    using namespace vs;
+    if (!params_ok(w, h, p) || !left || !right || !labels || pitch < w || labels_pitch < w)
+        return VS_EINVAL;
+    const BpLayout lay = make_layout(w, h, p);
+    int rc = check_workspace(lay, workspace, ws_bytes);
+    if (rc != VS_OK)
+        return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint8_t *ws = reinterpret_cast<uint8_t *>(workspace);
+    launch_costs(lay, ws, left, right, pitch, p, st);
     for (int l = lay.levels - 1; l >= 0; --l) {
-        SweepArgs a;
-        a.cost = ws + lay.cost_off[l];
-        a.msg = ws + lay.msg_off[l];
-        a.pmsg = l + 1 < lay.levels ? ws + lay.msg_off[l + 1] : nullptr;
-        a.w = lay.w[l];
-        a.h = lay.h[l];
-        a.wh = lay.wh[l];
-        a.wg = lay.wg[l];
-        a.L = lay.L;
-        a.pw = l + 1 < lay.levels ? lay.w[l + 1] : 0;
-        a.ph = l + 1 < lay.levels ? lay.h[l + 1] : 0;
-        a.pwh = l + 1 < lay.levels ? lay.wh[l + 1] : 0;
-        a.pwg = l + 1 < lay.levels ? lay.wg[l + 1] : 0;
-        a.c2 = (uint32_t)ceff * 0x10001u;
-        a.ts2 = (uint32_t)p->smooth_trunc * 0x10001u;
         for (int t = 0; t < p->iters; ++t) {
-            a.color = t & 1;
-            a.from_parent = (t == 0 && l + 1 < lay.levels);
-            a.zero_in = (t == 0 && l + 1 == lay.levels);
-            a.materialize = (t == 0 && p->iters == 1);
-            const bool last = l == 0 && t == p->iters - 1;
-            a.labels = last ? labels : nullptr;
-            a.labels_pitch = labels_pitch;
+            const SweepArgs a = sweep_args(lay, ws, p, l, t, labels, labels_pitch);
             const int slot = prof_begin(l == 0 ? kProfSweepL0 : kProfSweepCoarse, st);
             launch_sweep(lay.Lp, a, lay.cost_u8[l], lay.bytes[l], st);
             prof_end(slot, st);
             note_launch();
         }
     }
-    {
-        // the last sweep labelled colour (iters - 1) & 1; this pass labels the other
-        LabelArgs a{ws + lay.cost_off[0], ws + lay.msg_off[0], labels, labels_pitch, w, h, lay.wh[0], lay.wg[0], lay.L,
-                    lay.Lp, (p->iters & 1)};
-        dim3 grid((lay.wh[0] + 127) / 128, h);
-        const int slot = prof_begin(kProfBpOther, st);
-        launch_pdl(k_bp_labels, dim3(grid), dim3(128), st, a);
-        prof_end(slot, st);
-        note_launch();
-    }
+    launch_labels(lay, ws, labels, labels_pitch, p, st);
     return launch_status();
+}
+
+// ---------------------------------------------------------------------------
+// batch of pairs in lockstep
+
+namespace vs {
+namespace {
+
+bool batch_layouts(const vs_bp_job *jobs, int n, std::vector<BpLayout> &lays, std::vector<size_t> &offs,
+                   size_t &total)
+{
+    if (!jobs || n < 1 || n > 4096)
+        return false;
+    lays.resize(n);
+    offs.resize(n);
+    total = 0;
+    for (int i = 0; i < n; ++i) {
+        const vs_bp_job &j = jobs[i];
+        if (!params_ok(j.w, j.h, &j.params))
+            return false;
+        if (j.params.levels != jobs[0].params.levels || j.params.iters != jobs[0].params.iters)
+            return false;   // the batch advances every pair through the same steps
+        lays[i] = make_layout(j.w, j.h, &j.params);
+        offs[i] = total;
+        total = align_up(total + lays[i].total, 256);
+    }
+    return true;
+}
+
+}  // namespace
+}  // namespace vs
+
+extern "C" size_t vs_bp_batch_workspace_size(const vs_bp_job *jobs, int n)
+{
+    std::vector<vs::BpLayout> lays;
+    std::vector<size_t> offs;
+    size_t total = 0;
+    return vs::batch_layouts(jobs, n, lays, offs, total) ? total : 0;
+}
+
+extern "C" int vs_bp_stereo_batch(const vs_bp_job *jobs, int n, void *workspace, size_t ws_bytes, void *stream)
+{
+    using namespace vs;
+    std::vector<BpLayout> lays;
+    std::vector<size_t> offs;
+    size_t total = 0;
+    if (!batch_layouts(jobs, n, lays, offs, total))
+        return VS_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        const vs_bp_job &j = jobs[i];
+        if (!j.left || !j.right || !j.labels || j.pitch < j.w || j.labels_pitch < j.w)
+            return VS_EINVAL;
+    }
+    if (!workspace || !aligned(workspace, 256) || ws_bytes < total)
+        return VS_EWORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint8_t *base = reinterpret_cast<uint8_t *>(workspace);
+    for (int i = 0; i < n; ++i)
+        launch_costs(lays[i], base + offs[i], jobs[i].left, jobs[i].right, jobs[i].pitch, &jobs[i].params, st);
+
+    const int levels = jobs[0].params.levels, iters = jobs[0].params.iters;
+    struct Group {
+        int Lp, full, cost8, bytes, labels, variant;
+        std::vector<SweepArgs> args;
+    };
+    std::vector<Group> groups;
+    for (int l = levels - 1; l >= 0; --l) {
+        for (int t = 0; t < iters; ++t) {
+            groups.clear();
+            for (int i = 0; i < n; ++i) {
+                const BpLayout &lay = lays[i];
+                const SweepArgs a = sweep_args(lay, base + offs[i], &jobs[i].params, l, t, jobs[i].labels,
+                                               jobs[i].labels_pitch);
+                const int labels = a.labels != nullptr;
+                const int variant = choose_variant(lay.Lp, (unsigned)a.h * (unsigned)a.wh, labels);
+                const int full = a.L == lay.Lp;
+                Group *gp = nullptr;
+                for (Group &g : groups)
+                    if (g.Lp == lay.Lp && g.full == full && g.cost8 == lay.cost_u8[l] && g.bytes == lay.bytes[l] &&
+                        g.labels == labels && g.variant == variant)
+                        gp = &g;
+                if (!gp) {
+                    groups.push_back(Group{lay.Lp, full, lay.cost_u8[l], lay.bytes[l], labels, variant, {}});
+                    gp = &groups.back();
+                }
+                gp->args.push_back(a);
+            }
+            for (const Group &g : groups) {
+                for (size_t first = 0; first < g.args.size(); first += kMaxBatch) {
+                    BatchArgs b;
+                    b.njobs = (int)std::min<size_t>(kMaxBatch, g.args.size() - first);
+                    unsigned blocks = 0;
+                    for (int k = 0; k < b.njobs; ++k) {
+                        b.job[k] = g.args[first + k];
+                        b.first_block[k] = blocks;
+                        blocks += sweep_blocks(b.job[k], g.variant);
+                    }
+                    b.first_block[b.njobs] = blocks;
+                    const int slot = prof_begin(l == 0 ? kProfSweepL0 : kProfSweepCoarse, st);
+                    launch_sweep_any(g.Lp, nullptr, &b, blocks, g.full, g.cost8, g.bytes, g.labels, g.variant, st);
+                    prof_end(slot, st);
+                    note_launch();
+                }
+            }
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        launch_labels(lays[i], base + offs[i], jobs[i].labels, jobs[i].labels_pitch, &jobs[i].params, st);
+    return launch_status();
+}
+
+// ---------------------------------------------------------------------------
+// autotuner
+
+extern "C" int vs_bp_autotune(const uint8_t *left, const uint8_t *right, int w, int h, int pitch,
+                              const vs_bp_params *p, uint8_t *labels, int labels_pitch, void *workspace,
+                              size_t ws_bytes, void *stream, int *chosen)
+{
+    using namespace vs;
+    // a full run first leaves valid state in every level's arrays
+    int rc = vs_bp_stereo(left, right, w, h, pitch, p, labels, labels_pitch, workspace, ws_bytes, stream);
+    if (rc != VS_OK)
+        return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const BpLayout lay = make_layout(w, h, p);
+    uint8_t *ws = reinterpret_cast<uint8_t *>(workspace);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess)
+        return VS_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return VS_ECUDA;
+    }
+    rc = VS_OK;
+    for (int l = 0; l < lay.levels && rc == VS_OK; ++l) {
+        // an interior iteration of the level (t = 2 reads its own arrays)
+        const SweepArgs a = sweep_args(lay, ws, p, l, p->iters > 2 ? 2 : 1, nullptr, 0);
+        const unsigned slots = (unsigned)a.h * (unsigned)a.wh;
+        float best = 3.4e38f;
+        int best_v = kVarPlain;
+        for (int v = kVarPlain; v <= kVarSplit; ++v) {
+            if (!variant_allowed(lay.Lp, v, false))
+                continue;
+            for (int rep = 0; rep < 2; ++rep)   // warm-up
+                launch_sweep(lay.Lp, a, lay.cost_u8[l], lay.bytes[l], st, v);
+            const int reps = 5;
+            cudaEventRecord(e0, st);
+            for (int rep = 0; rep < reps; ++rep)
+                launch_sweep(lay.Lp, a, lay.cost_u8[l], lay.bytes[l], st, v);
+            cudaEventRecord(e1, st);
+            note_launch(reps + 2);
+            float ms = 0.0f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                rc = VS_ECUDA;
+                break;
+            }
+            if (ms < best) {
+                best = ms;
+                best_v = v;
+            }
+        }
+        if (rc != VS_OK)
+            break;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            bool found = false;
+            for (TuneEntry &e : g_tune)
+                if (e.Lp == lay.Lp && e.slots == slots) {
+                    e.variant = best_v;
+                    found = true;
+                }
+            if (!found)
+                g_tune.push_back(TuneEntry{lay.Lp, slots, best_v});
+        }
+        if (chosen)
+            chosen[l] = best_v;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != VS_OK)
+        return rc;
+    // the timing runs changed the message arrays: run once more so that the
+    // workspace and labels hold this problem's result again
+    return vs_bp_stereo(left, right, w, h, pitch, p, labels, labels_pitch, workspace, ws_bytes, stream);
+}
+
+extern "C" void vs_bp_autotune_reset(void)
+{
+    std::lock_guard<std::mutex> lk(vs::g_tune_mu);
+    vs::g_tune.clear();
 }
 
 extern "C" int vs_bp_export_messages(const void *workspace, size_t ws_bytes, int w, int h,

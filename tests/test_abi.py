@@ -98,3 +98,14 @@ def test_pipeline_host_checks(lib):
     assert lib.vs_pipeline_create(ctypes.byref(cfg), 5, 3, 1, None, 0, ctypes.byref(h)) == vs.VS_EINVAL
     assert lib.vs_pipeline_submit_pair(None, None, None, None) == vs.VS_EINVAL
     assert lib.vs_pipeline_flush(None) == vs.VS_EINVAL
+
+
+def test_batch_workspace_is_the_sum_of_the_pairs(lib):
+    import torch
+    shapes = [(120, 160, 16), (61, 97, 64), (45, 33, 128)]
+    pairs = [(torch.empty((h, w), dtype=torch.uint8), None, vs.BPParams(L, 3, 4, 20, 10, 40)) for h, w, L in shapes]
+    total = vs.bp_batch_workspace_size(pairs)
+    singles = sum(vs.bp_workspace_size(w, h, vs.BPParams(L, 3, 4, 20, 10, 40)) for h, w, L in shapes)
+    assert singles <= total <= singles + 256 * len(shapes)
+    pairs[1] = (pairs[1][0], None, vs.BPParams(64, 3, 5, 20, 10, 40))     # different iters
+    assert vs.bp_batch_workspace_size(pairs) == 0

@@ -1,0 +1,91 @@
+"""Batched BP (vs_bp_stereo_batch) and the sweep autotuner (vs_bp_autotune):
+both must reproduce the single-pair results bit for bit."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1902_09733_b300 as vs
+from paper_1902_09733_b300 import build, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    assert torch.cuda.is_available()
+    build.build()
+
+
+def _pair(seed, h, w):
+    left, right, _ = synth.noise_pair(seed, w=w, h=h, max_disp=min(12.0, w / 4))
+    return torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda(), left, right
+
+
+SHAPES = [(120, 160, 16), (61, 97, 64), (45, 33, 32), (150, 200, 128), (17, 23, 48), (90, 70, 96), (33, 40, 5),
+          (64, 64, 64)]
+
+
+def test_batch_matches_single_calls_and_oracle():
+    pairs, hosts = [], []
+    for i, (h, w, L) in enumerate(SHAPES):
+        L_, R_, l, r = _pair(i, h, w)
+        pairs.append((L_, R_, vs.BPParams(L, 3, 4, 20, 10, 40)))
+        hosts.append((l, r))
+    got = vs.bp_stereo_batch(pairs)
+    torch.cuda.synchronize()
+    for (L_, R_, p), lab, (l, r) in zip(pairs, got, hosts):
+        single = vs.bp_stereo(L_, R_, p)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(lab.cpu().numpy(), single.cpu().numpy())
+        if p.labels <= 64:
+            want = oracle.bp(l, r, p.labels, p.levels, p.iters, 20, 10, 40, mode=oracle.MSG_DT)
+            np.testing.assert_array_equal(lab.cpu().numpy(), want)
+
+
+def test_batch_larger_than_one_launch_and_graph_replay():
+    """70 jobs exceed one launch's job table; the batch replays from a graph."""
+    pairs = []
+    for i in range(70):
+        L_, R_, _, _ = _pair(100 + i, 24 + (i % 5), 30 + (i % 7))
+        pairs.append((L_, R_, vs.BPParams(32 if i % 2 else 16, 2, 3, 20, 10, 40)))
+    labels = [torch.empty(tuple(p[0].shape), dtype=torch.uint8, device="cuda") for p in pairs]
+    ws = torch.empty(vs.bp_batch_workspace_size(pairs), dtype=torch.uint8, device="cuda")
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        vs.bp_stereo_batch(pairs, labels=labels, workspace=ws)
+    torch.cuda.synchronize()
+    first = [t.cpu().numpy().copy() for t in labels]
+    for t in labels:
+        t.fill_(255)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        vs.bp_stereo_batch(pairs, labels=labels, workspace=ws)
+    g.replay()
+    torch.cuda.synchronize()
+    for (L_, R_, p), a, b in zip(pairs, first, labels):
+        np.testing.assert_array_equal(b.cpu().numpy(), a)
+        np.testing.assert_array_equal(a, vs.bp_stereo(L_, R_, p).cpu().numpy())
+
+
+def test_batch_rejects_mixed_schedules():
+    L_, R_, _, _ = _pair(0, 20, 30)
+    with pytest.raises(vs.VSError):
+        vs.bp_stereo_batch([(L_, R_, vs.BPParams(16, 3, 4, 20, 10, 40)), (L_, R_, vs.BPParams(16, 2, 4, 20, 10, 40))])
+
+
+def test_autotune_keeps_results_identical():
+    L_, R_, l, r = _pair(7, 190, 338)
+    p = vs.BPParams(64, 4, 10, 20, 10, 40)
+    ws = torch.empty(vs.bp_workspace_size(338, 190, p), dtype=torch.uint8, device="cuda")
+    before = vs.bp_stereo(L_, R_, p, workspace=ws).cpu().numpy()
+    msg_before = vs.bp_export_messages(ws, 338, 190, p).cpu().numpy()
+    try:
+        chosen = vs.bp_autotune(L_, R_, p, workspace=ws)
+        assert len(chosen) == 4 and all(c in (0, 1, 2) for c in chosen)
+        after = vs.bp_stereo(L_, R_, p, workspace=ws).cpu().numpy()
+        np.testing.assert_array_equal(after, before)
+        np.testing.assert_array_equal(vs.bp_export_messages(ws, 338, 190, p).cpu().numpy(), msg_before)
+    finally:
+        vs.bp_autotune_reset()
+    np.testing.assert_array_equal(before, oracle.bp(l, r, 64, 4, 10, 20, 10, 40, mode=oracle.MSG_DT))
