@@ -14,6 +14,9 @@ Functions, each following one step of the method:
 * :func:`bp`                -- Eq. 1 hierarchical loopy min-sum BP + labels
 * :func:`guided_upsample`   -- Eq. 2 joint bilateral upsampling
 * :func:`reproject`         -- Eq. 3 reprojection to (x, y, z)
+* :func:`sp_message`, :func:`sp_forward`, :func:`sp_backward` -- the
+  temperature-smoothed (log-domain sum-product) relaxation of the Eq. 1
+  messages and its reverse-mode derivative (``vsref_smooth.c``)
 """
 from __future__ import annotations
 
@@ -25,7 +28,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "vsref.c")
+_SRCS = [os.path.join(_HERE, "vsref.c"), os.path.join(_HERE, "vsref_smooth.c")]
 _BUILD_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD_DIR, "libvsref.so")
 
@@ -37,14 +40,14 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile ``vsref.c`` into ``oracle/_build/libvsref.so`` with gcc."""
+    """Compile ``vsref.c`` and ``vsref_smooth.c`` into ``oracle/_build/libvsref.so`` with gcc."""
     os.makedirs(_BUILD_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f) for f in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-           "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+           "-shared", "-fPIC", "-o", tmp, *_SRCS, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -75,6 +78,12 @@ def _load():
         lib.vsref_guided_upsample.restype = I
         lib.vsref_reproject.argtypes = [P, I, I, P, D, P]
         lib.vsref_reproject.restype = None
+        lib.vsref_sp_message.argtypes = [P, I, D, D, D, P, P]
+        lib.vsref_sp_message.restype = None
+        lib.vsref_sp_forward.argtypes = [P, I, I, I, I, D, D, D, P, P]
+        lib.vsref_sp_forward.restype = I
+        lib.vsref_sp_backward.argtypes = [P, I, I, I, I, D, D, D, P, P, P, P]
+        lib.vsref_sp_backward.restype = I
         _lib = lib
         return lib
 
@@ -187,3 +196,50 @@ def reproject(disp: np.ndarray, cam, baseline: float) -> np.ndarray:
     xyz = np.zeros((H, W, 3), np.float64)
     _load().vsref_reproject(_ptr(disp), W, H, _ptr(cam_a), float(baseline), _ptr(xyz))
     return xyz
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def sp_message(hv, lam: float, T: float, tau: float, return_unnormalised: bool = False):
+    """Smoothed message -tau log sum_d' exp(-(h(d') + min(lam|d-d'|, T))/tau), mean-normalised."""
+    hv = _f64(hv)
+    out = np.zeros_like(hv)
+    mt = np.zeros_like(hv)
+    _load().vsref_sp_message(_ptr(hv), hv.shape[0], float(lam), float(T), float(tau),
+                             _ptr(out), _ptr(mt))
+    return (out, mt) if return_unnormalised else out
+
+
+def sp_forward(D, lam: float, T: float, tau: float, iters: int, return_states: bool = False):
+    """Synchronous smoothed BP on an (h, w, L) data term; returns (h, w, L) beliefs.
+
+    With ``return_states`` also returns every iteration's incoming messages,
+    (iters + 1, 4, h, w, L), slots 0 left, 1 right, 2 up, 3 down.
+    """
+    D = _f64(D)
+    h, w, L = D.shape
+    states = np.zeros((iters + 1, 4, h, w, L), np.float64)
+    bel = np.zeros((h, w, L), np.float64)
+    rc = _load().vsref_sp_forward(_ptr(D), w, h, L, iters, float(lam), float(T), float(tau),
+                                  _ptr(states), _ptr(bel))
+    _check(rc, "sp_forward")
+    return (bel, states) if return_states else bel
+
+
+def sp_backward(D, lam: float, T: float, tau: float, iters: int, gbel, states=None):
+    """Reverse mode of :func:`sp_forward`: returns (dL/dD, dL/dlam, dL/dT, dL/dtau)."""
+    D = _f64(D)
+    h, w, L = D.shape
+    if states is None:
+        _, states = sp_forward(D, lam, T, tau, iters, return_states=True)
+    states = _f64(states)
+    gbel = _f64(gbel)
+    assert gbel.shape == D.shape and states.shape == (iters + 1, 4, h, w, L)
+    gD = np.zeros_like(D)
+    gpar = np.zeros(3, np.float64)
+    rc = _load().vsref_sp_backward(_ptr(D), w, h, L, iters, float(lam), float(T), float(tau),
+                                   _ptr(states), _ptr(gbel), _ptr(gD), _ptr(gpar))
+    _check(rc, "sp_backward")
+    return gD, float(gpar[0]), float(gpar[1]), float(gpar[2])
