@@ -301,6 +301,63 @@ int vs_pipeline_flush(vs_pipeline *p);
 int vs_pipeline_latencies(vs_pipeline *p, float *ms, int max);
 void vs_pipeline_destroy(vs_pipeline *p);
 
+/*
+ * Temperature-smoothed BP and its adjoint (a differentiable relaxation of
+ * Eq. 1; the paper itself only runs min-sum).  The minimum in the Eq. 1
+ * message becomes the soft minimum at temperature tau:
+ *   m_{r->p}(d) = -tau log sum_d' exp(-(h(d') + V(d, d')) / tau) - (its mean
+ *                 over d),  h = D_r + the messages r received from its other
+ *                 in-frame neighbours,  V(d, d') = min(lambda |d - d'|, trunc),
+ * on one level, every message of iteration t computed from those of t - 1
+ * (synchronous; all zero before the first), a missing neighbour sending
+ * nothing.  Output after `iters` iterations: beliefs b_p(d) = D_p(d) + the
+ * sum of p's incoming messages.  FP32 throughout; as tau -> 0 the messages
+ * tend to the min-sum ones.
+ *   cost          D, h x w x labels floats, label fastest (device, 16-byte
+ *                 aligned).  Any finite values.
+ *   beliefs       h x w x labels floats out (device, 16-byte aligned).
+ *   labels        16, 32, 48 or 64.  iters 1..64.  w, h >= 1, w h <= 2^22.
+ *   ckpt_every    k, 1..iters: the forward pass keeps the messages of every
+ *                 k-th iteration in the workspace; the adjoint recomputes the
+ *                 k - 1 iterations in between from them.
+ *   lambda >= 0, trunc >= 0, tau > 0, trunc / tau <= 50 (keeps every
+ *   exp(-V/tau) a normal FP32 number).
+ * vs_sp_workspace_size gives the workspace bytes (0 for invalid arguments):
+ * (floor((iters-1)/k) + min(k, iters) + 1) message states of 16 w h labels
+ * bytes, plus 24 bytes per 32 pixels.  The workspace is 256-byte aligned
+ * device memory owned by the caller.
+ */
+typedef struct {
+    int32_t labels;
+    int32_t iters;
+    int32_t ckpt_every;
+    float lambda;
+    float trunc;
+    float tau;
+} vs_sp_params;
+
+size_t vs_sp_workspace_size(int w, int h, const vs_sp_params *p);
+
+/* Forward pass: beliefs, and the checkpoints the adjoint needs, in the
+ * workspace.  Errors: VS_EINVAL, VS_EALIGN, VS_EWORKSPACE, VS_ECUDA. */
+int vs_sp_forward(const float *cost, int w, int h, const vs_sp_params *p, float *beliefs,
+                  void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * Adjoint: given grad_beliefs = dLoss/db (h x w x labels floats), writes
+ * grad_cost = dLoss/dD (same shape, overwritten) and grad_params = device
+ * array of 3 floats {dLoss/dlambda, dLoss/dtrunc, dLoss/dtau}.  The workspace
+ * must hold the checkpoints of a vs_sp_forward with the same cost, sizes and
+ * parameters, enqueued earlier (stream order); the adjoint overwrites all but
+ * those checkpoints, so it may be run several times after one forward.  At a
+ * kink lambda |d - d'| == trunc, V is taken as trunc (its derivative in
+ * lambda is 0 there).  grad_params is summed in double in a fixed order, so
+ * results are bit-identical from run to run.
+ * Errors: VS_EINVAL, VS_EALIGN, VS_EWORKSPACE, VS_ECUDA.
+ */
+int vs_sp_backward(const float *cost, int w, int h, const vs_sp_params *p, const float *grad_beliefs,
+                   float *grad_cost, float *grad_params, void *workspace, size_t ws_bytes, void *stream);
+
 /* Name of a status code. */
 const char *vs_status_string(int status);
 
@@ -316,7 +373,7 @@ uint64_t vs_kernel_launches(void);
  * time (recorded during capture of a graph that has not run); it returns the
  * count.  Tags: 0 level-0 message sweep, 1 coarser-level sweep,
  * 2 remap, 3 upsample (+ reprojection), 4 other BP kernels (cost, pyramid,
- * labels).  Slots are reused round-robin, so collect before n more launches. */
+ * labels), 5 smoothed-BP forward iteration, 6 smoothed-BP adjoint iteration.  Slots are reused round-robin, so collect before n more launches. */
 int vs_profile_enable(int capacity);
 int vs_profile_collect(int *tags, float *ms, int max);
 

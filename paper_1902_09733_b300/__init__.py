@@ -14,6 +14,9 @@ Steps of the method (arXiv 1902.09733):
 * :func:`reproject`                   Eq. 3 point cloud
 * :func:`guided_upsample_reproject`   Eq. 2 + Eq. 3 fused
 * :func:`pair_run`, :func:`pair_run_host`  a whole pair (device / host buffers)
+* :func:`sp_forward`, :func:`sp_backward`, :func:`smooth_bp`  the temperature-
+  smoothed (log-domain sum-product) relaxation of the Eq. 1 messages, its
+  adjoint, and a ``torch.autograd.Function`` over the two
 """
 from __future__ import annotations
 
@@ -30,7 +33,8 @@ __all__ = [
     "guided_upsample", "reproject", "guided_upsample_reproject",
     "pair_workspace_size", "pair_run", "pair_run_host", "kernel_launches", "status_string",
     "profile_enable", "profile_collect", "Pipeline", "bp_stereo_batch", "bp_batch_workspace_size",
-    "bp_autotune", "bp_autotune_reset",
+    "bp_autotune", "bp_autotune_reset", "SPParams", "sp_workspace_size", "sp_forward", "sp_backward",
+    "smooth_bp", "SmoothBP",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -61,6 +65,11 @@ class _BPJob(ctypes.Structure):
     _fields_ = [("left", ctypes.c_void_p), ("right", ctypes.c_void_p), ("w", ctypes.c_int32),
                 ("h", ctypes.c_int32), ("pitch", ctypes.c_int32), ("params", _BPParams),
                 ("labels", ctypes.c_void_p), ("labels_pitch", ctypes.c_int32)]
+
+
+class _SPParams(ctypes.Structure):
+    _fields_ = [("labels", ctypes.c_int32), ("iters", ctypes.c_int32), ("ckpt_every", ctypes.c_int32),
+                ("lam", ctypes.c_float), ("trunc", ctypes.c_float), ("tau", ctypes.c_float)]
 
 
 class _JBUParams(ctypes.Structure):
@@ -98,6 +107,20 @@ class BPParams:
     def c(self) -> _BPParams:
         return _BPParams(self.labels, self.levels, self.iters, self.data_trunc,
                          self.smooth_slope, self.smooth_trunc)
+
+
+@dataclass(frozen=True)
+class SPParams:
+    """Smoothed BP: V(d, d') = min(lam |d - d'|, trunc), temperature tau."""
+    labels: int = 48
+    iters: int = 8
+    ckpt_every: int = 2
+    lam: float = 2.5
+    trunc: float = 13.7
+    tau: float = 2.0
+
+    def c(self) -> _SPParams:
+        return _SPParams(self.labels, self.iters, self.ckpt_every, self.lam, self.trunc, self.tau)
 
 
 @dataclass(frozen=True)
@@ -144,6 +167,7 @@ def lib() -> ctypes.CDLL:
         L = ctypes.CDLL(library_path)
         P, I, F, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_size_t
         cam_p, bp_p = ctypes.POINTER(_Camera), ctypes.POINTER(_BPParams)
+        sp_p = ctypes.POINTER(_SPParams)
         jbu_p, cfg_p = ctypes.POINTER(_JBUParams), ctypes.POINTER(_PairConfig)
         sig = {
             "vs_rectify_remap": ([P, I, I, I, cam_p, P, P, I, I, P, I, P, I, P], I),
@@ -171,6 +195,9 @@ def lib() -> ctypes.CDLL:
             "vs_pipeline_flush": ([P], I),
             "vs_pipeline_latencies": ([P, P, I], I),
             "vs_pipeline_destroy": ([P], None),
+            "vs_sp_workspace_size": ([I, I, sp_p], S),
+            "vs_sp_forward": ([P, I, I, sp_p, P, P, S, P], I),
+            "vs_sp_backward": ([P, I, I, sp_p, P, P, P, P, S, P], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -191,7 +218,8 @@ def kernel_launches() -> int:
     return int(lib().vs_kernel_launches())
 
 
-PROFILE_TAGS = {0: "sweep_level0", 1: "sweep_coarse", 2: "remap", 3: "upsample", 4: "bp_other"}
+PROFILE_TAGS = {0: "sweep_level0", 1: "sweep_coarse", 2: "remap", 3: "upsample", 4: "bp_other",
+                5: "smooth_fwd", 6: "smooth_adj"}
 
 
 def profile_enable(capacity: int) -> None:
@@ -532,3 +560,103 @@ class Pipeline:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# temperature-smoothed BP (differentiable relaxation of Eq. 1)
+
+
+def _cost_volume(cost: torch.Tensor, name: str) -> tuple[int, int, int]:
+    _dev(cost, torch.float32, name)
+    if cost.dim() != 3 or not cost.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous (h, w, labels) float32 tensor")
+    h, w, L = cost.shape
+    return h, w, L
+
+
+def sp_workspace_size(w: int, h: int, params: SPParams) -> int:
+    c = params.c()
+    return int(lib().vs_sp_workspace_size(w, h, ctypes.byref(c)))
+
+
+def sp_forward(cost: torch.Tensor, params: SPParams, beliefs=None, workspace=None, stream=None):
+    """Beliefs of the smoothed BP on an (h, w, L) cost volume; returns
+    (beliefs, workspace), the workspace holding the adjoint's checkpoints."""
+    h, w, L = _cost_volume(cost, "cost")
+    if L != params.labels:
+        raise ValueError(f"cost has {L} labels, params.labels is {params.labels}")
+    need = sp_workspace_size(w, h, params)
+    if need == 0:
+        raise VSError("vs_sp_workspace_size", VS_EINVAL)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=cost.device)
+    if beliefs is None:
+        beliefs = torch.empty_like(cost)
+    c = params.c()
+    _check("vs_sp_forward", lib().vs_sp_forward(cost.data_ptr(), w, h, ctypes.byref(c),
+                                                _dev(beliefs, torch.float32, "beliefs").data_ptr(),
+                                                workspace.data_ptr(), workspace.numel(), _stream(stream)))
+    return beliefs, workspace
+
+
+def sp_backward(cost: torch.Tensor, params: SPParams, grad_beliefs: torch.Tensor, workspace: torch.Tensor,
+                grad_cost=None, grad_params=None, stream=None):
+    """Adjoint after :func:`sp_forward` on the same workspace: returns
+    (dL/dcost, tensor([dL/dlam, dL/dtrunc, dL/dtau]))."""
+    h, w, L = _cost_volume(cost, "cost")
+    grad_beliefs = grad_beliefs.contiguous()
+    _cost_volume(grad_beliefs, "grad_beliefs")
+    if grad_cost is None:
+        grad_cost = torch.empty_like(cost)
+    if grad_params is None:
+        grad_params = torch.empty(3, dtype=torch.float32, device=cost.device)
+    c = params.c()
+    _check("vs_sp_backward", lib().vs_sp_backward(
+        cost.data_ptr(), w, h, ctypes.byref(c), grad_beliefs.data_ptr(),
+        _dev(grad_cost, torch.float32, "grad_cost").data_ptr(),
+        _dev(grad_params, torch.float32, "grad_params").data_ptr(),
+        workspace.data_ptr(), workspace.numel(), _stream(stream)))
+    return grad_cost, grad_params
+
+
+def _scalar(v) -> float:
+    return float(v.detach().item()) if isinstance(v, torch.Tensor) else float(v)
+
+
+class SmoothBP(torch.autograd.Function):
+    """beliefs = smoothed BP(cost; lam, trunc, tau), differentiable in all four.
+
+    Forward and backward are the library's kernels (``vs_sp_forward``,
+    ``vs_sp_backward``); the workspace with the message checkpoints lives in
+    the autograd context until the graph is freed.  The three scalars are read
+    on the host (one synchronisation each when they are CUDA tensors).
+    """
+
+    @staticmethod
+    def forward(ctx, cost, lam, trunc, tau, iters: int = 8, ckpt_every: int = 2):
+        cost = cost.contiguous()
+        params = SPParams(labels=cost.shape[-1], iters=int(iters), ckpt_every=int(ckpt_every),
+                          lam=_scalar(lam), trunc=_scalar(trunc), tau=_scalar(tau))
+        beliefs, ws = sp_forward(cost, params)
+        ctx.save_for_backward(cost)
+        ctx.params = params
+        ctx.ws = ws
+        ctx.scalar_like = [v if isinstance(v, torch.Tensor) else None for v in (lam, trunc, tau)]
+        return beliefs
+
+    @staticmethod
+    def backward(ctx, grad_beliefs):
+        (cost,) = ctx.saved_tensors
+        g_cost, g_par = sp_backward(cost, ctx.params, grad_beliefs.to(torch.float32), ctx.ws)
+        outs = []
+        for i, like in enumerate(ctx.scalar_like):
+            if like is None or not ctx.needs_input_grad[1 + i]:
+                outs.append(None)
+            else:
+                outs.append(g_par[i].to(like.dtype).to(like.device).reshape(like.shape))
+        return (g_cost if ctx.needs_input_grad[0] else None, *outs, None, None)
+
+
+def smooth_bp(cost: torch.Tensor, lam, trunc, tau, iters: int = 8, ckpt_every: int = 2) -> torch.Tensor:
+    """Differentiable beliefs of the smoothed BP on an (h, w, L) float32 CUDA cost volume."""
+    return SmoothBP.apply(cost, lam, trunc, tau, iters, ckpt_every)

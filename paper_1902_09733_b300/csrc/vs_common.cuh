@@ -20,7 +20,15 @@ int launch_status();
 // Optional CUDA-event timing of selected launches (vs_profile_enable).
 // prof_begin returns a slot (or -1 when timing is off) and records its start
 // event on `st`; prof_end records the matching stop event.
-enum ProfTag { kProfSweepL0 = 0, kProfSweepCoarse = 1, kProfRemap = 2, kProfJbu = 3, kProfBpOther = 4 };
+enum ProfTag {
+    kProfSweepL0 = 0,
+    kProfSweepCoarse = 1,
+    kProfRemap = 2,
+    kProfJbu = 3,
+    kProfBpOther = 4,
+    kProfSmoothFwd = 5,
+    kProfSmoothAdj = 6
+};
 int prof_begin(int tag, cudaStream_t st);
 void prof_end(int slot, cudaStream_t st);
 

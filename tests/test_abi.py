@@ -109,3 +109,34 @@ def test_batch_workspace_is_the_sum_of_the_pairs(lib):
     assert singles <= total <= singles + 256 * len(shapes)
     pairs[1] = (pairs[1][0], None, vs.BPParams(64, 3, 5, 20, 10, 40))     # different iters
     assert vs.bp_batch_workspace_size(pairs) == 0
+
+
+def test_smooth_bp_workspace_and_host_checks(lib):
+    ok = vs.SPParams(labels=48, iters=8, ckpt_every=2, lam=2.5, trunc=13.7, tau=2.0)
+    n = vs.sp_workspace_size(338, 190, ok)
+    state = 16 * 338 * 190 * 48
+    # checkpoints of iterations 2, 4, 6 + one recompute state + two adjoint states
+    assert 6 * state <= n < 6 * state + 6 * 256 + (4 * 338 * 190 // 128 + 1) * 32 + 256
+    # every ckpt interval gives floor((iters-1)/k) + min(k, iters) + 1 states
+    for k in range(1, 9):
+        p = vs.SPParams(**{**ok.__dict__, "ckpt_every": k})
+        states = (8 - 1) // k + min(k, 8) + 1
+        assert states * state <= vs.sp_workspace_size(338, 190, p) < (states + 1) * state
+    bad = [dict(labels=40), dict(labels=8), dict(labels=128), dict(iters=0), dict(iters=65),
+           dict(ckpt_every=0), dict(ckpt_every=9), dict(tau=0.0), dict(tau=-1.0), dict(lam=-0.5),
+           dict(trunc=-1.0), dict(trunc=101.0, tau=2.0), dict(lam=float("nan")), dict(tau=float("inf"))]
+    for b in bad:
+        p = vs.SPParams(**{**ok.__dict__, **b})
+        assert vs.sp_workspace_size(338, 190, p) == 0, b
+    assert vs.sp_workspace_size(0, 190, ok) == 0
+    assert vs.sp_workspace_size(4096, 1025, ok) == 0          # more than 2^22 pixels
+    c = ok.c()
+    bad_p = vs.SPParams(**{**ok.__dict__, "labels": 40}).c()
+    assert lib.vs_sp_forward(None, 338, 190, ctypes.byref(c), None, None, 0, None) == vs.VS_EINVAL
+    assert lib.vs_sp_forward(16, 338, 190, ctypes.byref(bad_p), 16, 256, 1 << 30, None) == vs.VS_EINVAL
+    assert lib.vs_sp_forward(20, 338, 190, ctypes.byref(c), 16, 256, 1 << 30, None) == vs.VS_EALIGN
+    assert lib.vs_sp_forward(16, 338, 190, ctypes.byref(c), 16, 256, 1024, None) == vs.VS_EWORKSPACE
+    assert lib.vs_sp_forward(16, 338, 190, ctypes.byref(c), 16, 100, 1 << 30, None) == vs.VS_EWORKSPACE
+    assert lib.vs_sp_backward(16, 338, 190, ctypes.byref(c), 16, 16, None, 256, 1 << 30, None) == vs.VS_EINVAL
+    assert lib.vs_sp_backward(16, 338, 190, ctypes.byref(c), 16, 24, 16, 256, 1 << 30, None) == vs.VS_EALIGN
+    assert lib.vs_sp_backward(16, 338, 190, ctypes.byref(c), 16, 16, 16, 256, 64, None) == vs.VS_EWORKSPACE
