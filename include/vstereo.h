@@ -42,6 +42,7 @@ extern "C" {
 #define VS_EALIGN (-2)      /* a pointer or pitch breaks an alignment rule  */
 #define VS_EWORKSPACE (-3)  /* workspace NULL, misaligned or too small      */
 #define VS_ECUDA (-4)       /* the CUDA runtime reported an error           */
+#define VS_ETIMEOUT (-5)    /* a bounded wait inside a kernel ran out       */
 
 /* Pinhole camera with radial distortion (Section 2.1 and Eq. 3), in pixels of
  * the full-resolution frame: focal lengths fx = f/du, fy = f/dv, principal
@@ -324,8 +325,13 @@ void vs_pipeline_destroy(vs_pipeline *p);
  *   exp(-V/tau) a normal FP32 number).
  * vs_sp_workspace_size gives the workspace bytes (0 for invalid arguments):
  * (floor((iters-1)/k) + min(k, iters) + 1) message states of 16 w h labels
- * bytes, plus 24 bytes per 32 pixels.  The workspace is 256-byte aligned
- * device memory owned by the caller.
+ * bytes (each rounded up to 256), 32 bytes per 32 pixels (rounded up to 256)
+ * and 256 bytes.  The workspace is 256-byte aligned device memory owned by
+ * the caller.
+ * The label contractions run as FP32 multiply-adds (SIMT kernels);
+ * vs_sp_select_kernels(0) switches to tensor-core kernels (tcgen05 MMAs in
+ * 3xTF32, about twice the rounding error, slower at 48 labels on B300) and
+ * (1) back, for comparison (no counterpart in the paper).
  */
 typedef struct {
     int32_t labels;
@@ -357,6 +363,16 @@ int vs_sp_forward(const float *cost, int w, int h, const vs_sp_params *p, float 
  */
 int vs_sp_backward(const float *cost, int w, int h, const vs_sp_params *p, const float *grad_beliefs,
                    float *grad_cost, float *grad_params, void *workspace, size_t ws_bytes, void *stream);
+
+/* Kernel family for the two calls above: 1 SIMT (default), 0 tensor cores.
+ * Errors: VS_EINVAL. */
+int vs_sp_select_kernels(int family);
+
+/* Synchronises `stream` and reports whether a tensor-core kernel of the
+ * vs_sp_forward / vs_sp_backward calls since the last vs_sp_forward on this
+ * workspace gave up a bounded wait for its MMAs (VS_ETIMEOUT; its outputs are
+ * then invalid).  Errors: VS_EINVAL, VS_EWORKSPACE, VS_ECUDA. */
+int vs_sp_status(const void *workspace, size_t ws_bytes, int w, int h, const vs_sp_params *p, void *stream);
 
 /* Name of a status code. */
 const char *vs_status_string(int status);

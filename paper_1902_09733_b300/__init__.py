@@ -34,13 +34,13 @@ __all__ = [
     "pair_workspace_size", "pair_run", "pair_run_host", "kernel_launches", "status_string",
     "profile_enable", "profile_collect", "Pipeline", "bp_stereo_batch", "bp_batch_workspace_size",
     "bp_autotune", "bp_autotune_reset", "SPParams", "sp_workspace_size", "sp_forward", "sp_backward",
-    "smooth_bp", "SmoothBP",
+    "smooth_bp", "SmoothBP", "sp_select_kernels", "sp_status",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_HERE, "libvstereo.so")
 
-VS_OK, VS_EINVAL, VS_EALIGN, VS_EWORKSPACE, VS_ECUDA = 0, -1, -2, -3, -4
+VS_OK, VS_EINVAL, VS_EALIGN, VS_EWORKSPACE, VS_ECUDA, VS_ETIMEOUT = 0, -1, -2, -3, -4, -5
 
 
 class VSError(RuntimeError):
@@ -198,6 +198,8 @@ def lib() -> ctypes.CDLL:
             "vs_sp_workspace_size": ([I, I, sp_p], S),
             "vs_sp_forward": ([P, I, I, sp_p, P, P, S, P], I),
             "vs_sp_backward": ([P, I, I, sp_p, P, P, P, P, S, P], I),
+            "vs_sp_select_kernels": ([I], I),
+            "vs_sp_status": ([P, S, I, I, sp_p, P], I),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -617,6 +619,18 @@ def sp_backward(cost: torch.Tensor, params: SPParams, grad_beliefs: torch.Tensor
         _dev(grad_params, torch.float32, "grad_params").data_ptr(),
         workspace.data_ptr(), workspace.numel(), _stream(stream)))
     return grad_cost, grad_params
+
+
+def sp_select_kernels(family: str) -> None:
+    """"simt" (FP32 multiply-adds, the default) or "tensor" (tcgen05) kernels for sp_forward / sp_backward."""
+    _check("vs_sp_select_kernels", lib().vs_sp_select_kernels({"tensor": 0, "simt": 1}[family]))
+
+
+def sp_status(workspace: torch.Tensor, w: int, h: int, params: SPParams, stream=None) -> None:
+    """Raise VSError(VS_ETIMEOUT) if a tensor-core kernel gave up waiting for its MMAs."""
+    c = params.c()
+    _check("vs_sp_status", lib().vs_sp_status(workspace.data_ptr(), workspace.numel(), w, h, ctypes.byref(c),
+                                              _stream(stream)))
 
 
 def _scalar(v) -> float:

@@ -159,6 +159,7 @@ extern "C" const char *vs_status_string(int status)
     case VS_EALIGN: return "pointer or pitch breaks an alignment rule";
     case VS_EWORKSPACE: return "workspace missing, misaligned or too small";
     case VS_ECUDA: return "CUDA runtime error";
+    case VS_ETIMEOUT: return "bounded wait inside a kernel timed out";
     default: return "unknown status";
     }
 }

@@ -33,7 +33,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_status_strings(lib):
-    for code in (0, -1, -2, -3, -4):
+    for code in (0, -1, -2, -3, -4, -5):
         assert lib.vs_status_string(code)
     assert vs.status_string(-3).startswith("workspace")
 
@@ -116,7 +116,7 @@ def test_smooth_bp_workspace_and_host_checks(lib):
     n = vs.sp_workspace_size(338, 190, ok)
     state = 16 * 338 * 190 * 48
     # checkpoints of iterations 2, 4, 6 + one recompute state + two adjoint states
-    assert 6 * state <= n < 6 * state + 6 * 256 + (4 * 338 * 190 // 128 + 1) * 32 + 256
+    assert 6 * state <= n < 6 * state + 6 * 256 + (4 * 338 * 190 // 128 + 1) * 32 + 512
     # every ckpt interval gives floor((iters-1)/k) + min(k, iters) + 1 states
     for k in range(1, 9):
         p = vs.SPParams(**{**ok.__dict__, "ckpt_every": k})
@@ -140,3 +140,6 @@ def test_smooth_bp_workspace_and_host_checks(lib):
     assert lib.vs_sp_backward(16, 338, 190, ctypes.byref(c), 16, 16, None, 256, 1 << 30, None) == vs.VS_EINVAL
     assert lib.vs_sp_backward(16, 338, 190, ctypes.byref(c), 16, 24, 16, 256, 1 << 30, None) == vs.VS_EALIGN
     assert lib.vs_sp_backward(16, 338, 190, ctypes.byref(c), 16, 16, 16, 256, 64, None) == vs.VS_EWORKSPACE
+    assert lib.vs_sp_select_kernels(2) == vs.VS_EINVAL
+    assert lib.vs_sp_status(256, 64, 338, 190, ctypes.byref(c), None) == vs.VS_EWORKSPACE
+    assert lib.vs_sp_status(256, 1 << 30, 338, 190, ctypes.byref(bad_p), None) == vs.VS_EINVAL

@@ -1,12 +1,15 @@
 """GPU parity of the temperature-smoothed BP (forward and adjoint) against the
 FP64 oracle, through the C ABI.
 
-Tolerances (FP32 kernels against FP64): beliefs within 2e-4 * max(|b|, 1) of
-the oracle, element by element; the adjoint dL/dD within 1e-3 of max |dL/dD|
+Tolerances (FP32 kernels against FP64).  A message is tau times a difference
+of logs of sums of positive terms, so its rounding error is absolute, about
+tau x 1e-6 per iteration (FP32 sums; the tensor-core MMAs truncate and give
+about twice that), and the sums of three incoming messages carry it on, so
+after 8 iterations beliefs are off by up to ~5e-4 in absolute terms whatever
+their own size.  Hence beliefs within 2e-5 of the volume's belief scale
+max |b| (about 60 here), element by element; dL/dD within 1e-3 of max |dL/dD|
 element by element and the three scalar gradients within 1e-3 relative --
-the bar set for the adjoint against finite differences.  Messages are sums of
-positive terms (no cancellation), so FP32 rounding stays near 1e-6 relative
-per message and grows slowly over the iterations.
+the bar set for the adjoint against finite differences.
 """
 import numpy as np
 import pytest
@@ -17,8 +20,16 @@ import paper_1902_09733_b300 as vs
 
 pytestmark = pytest.mark.gpu
 
-B_RTOL = 2e-4
+B_TOL = 2e-5
 G_RTOL = 1e-3
+
+
+@pytest.fixture(params=["simt", "tensor"])
+def kernels(request):
+    """Both kernel families must meet the same bar."""
+    vs.sp_select_kernels(request.param)
+    yield request.param
+    vs.sp_select_kernels("simt")
 
 
 def _cost(seed, h, w, L, hi=20.0):
@@ -34,13 +45,14 @@ def _run(D, params, gb=None):
         gcost, gpar = vs.sp_backward(cost, params, torch.from_numpy(gb).cuda(), ws)
         out += [gcost.cpu().numpy(), gpar.cpu().numpy()]
     torch.cuda.synchronize()
+    vs.sp_status(ws, D.shape[1], D.shape[0], params)
     return out
 
 
-def _check_beliefs(got, ref):
+def _check_beliefs(got, ref, scale=None):
     err = np.abs(got.astype(np.float64) - ref)
-    tol = B_RTOL * np.maximum(np.abs(ref), 1.0)
-    assert np.all(err <= tol), f"max err {err.max():.3g}, worst ratio {(err / tol).max():.3g}"
+    tol = B_TOL * (np.abs(ref).max() if scale is None else scale)
+    assert err.max() <= tol, f"max err {err.max():.3g} > {tol:.3g}"
 
 
 def _check_grads(gD, gpar, ref):
@@ -68,7 +80,7 @@ CASES = [
 
 
 @pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}x{c[1]}x{c[2]}_i{c[3]}k{c[4]}" for c in CASES])
-def test_forward_and_adjoint_match_oracle(case):
+def test_forward_and_adjoint_match_oracle(case, kernels):
     w, h, L, iters, k, lam, T, tau = case
     # the library takes float parameters: give the oracle the same values
     lam, T, tau = (float(np.float32(v)) for v in (lam, T, tau))
@@ -82,7 +94,7 @@ def test_forward_and_adjoint_match_oracle(case):
     _check_grads(gD, gpar, oracle.sp_backward(D64, lam, T, tau, iters, gb.astype(np.float64), states))
 
 
-def test_checkpoint_interval_does_not_change_results():
+def test_checkpoint_interval_does_not_change_results(kernels):
     """Recomputation from checkpoints repeats the same arithmetic: every interval
     gives the same bits."""
     D = _cost(5, 31, 45, 48)
@@ -97,7 +109,7 @@ def test_checkpoint_interval_does_not_change_results():
                 assert np.array_equal(a, b), k
 
 
-def test_runs_are_bit_identical_and_backward_repeats():
+def test_runs_are_bit_identical_and_backward_repeats(kernels):
     D = _cost(6, 40, 50, 32)
     gb = np.random.default_rng(6).normal(size=D.shape).astype(np.float32)
     p = vs.SPParams(labels=32, iters=6, ckpt_every=2, lam=1.5, trunc=9.1, tau=1.3)
@@ -113,7 +125,7 @@ def test_runs_are_bit_identical_and_backward_repeats():
     assert torch.equal(g1[0], g2[0]) and torch.equal(g1[1], g2[1])
 
 
-def test_no_smoothness_and_constant_shift():
+def test_no_smoothness_and_constant_shift(kernels):
     D = _cost(8, 20, 30, 16)
     gb = np.random.default_rng(8).normal(size=D.shape).astype(np.float32)
     bel, gD, gpar = _run(D, vs.SPParams(labels=16, iters=4, ckpt_every=2, lam=0.0, trunc=5.0, tau=1.0), gb)
@@ -164,10 +176,11 @@ def test_full_size_sampled_beliefs(full_case):
     """A belief after 8 iterations depends on the data within L1 distance 8;
     the oracle on a crop of radius 9 reproduces it exactly."""
     D, _, bel, _, _ = full_case
+    scale = np.abs(bel).max()
     for x, y in SAMPLES:
         x0, x1, y0, y1 = _crop(x, y, ITERS + 1)
         ref = oracle.sp_forward(D[y0:y1, x0:x1].astype(np.float64), FULL.lam, FULL.trunc, FULL.tau, ITERS)
-        _check_beliefs(bel[y, x][None], ref[y - y0, x - x0][None])
+        _check_beliefs(bel[y, x][None], ref[y - y0, x - x0][None], scale)
 
 
 def test_full_size_sampled_adjoint(full_case):
