@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--stream-frames", type=int, default=1500)
     ap.add_argument("--stream-render", type=int, default=16)
     ap.add_argument("--batch-pairs", type=int, default=48)
+    ap.add_argument("--smooth-reps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -305,6 +306,76 @@ def run_batched(args, vs, synth, torch, dev, cam):
             "autotuned_variants": tuned}
 
 
+def run_smooth(args, vs, synth, torch, dev):
+    """Smoothed (sum-product) BP and its adjoint on a 338x190x48 FP32 cost
+    volume (truncated absolute differences of a seeded noise pair with
+    disparities up to 40 px), 8 synchronous iterations, checkpoint every 2.
+    Times one forward call and one adjoint call (which recomputes 4 of the 8
+    iterations) per kernel family, with CUDA events, and relates the SIMT
+    kernels to the FP32 FMA peak: per directed edge, L^2 FMAs per forward
+    message and 3 L^2 per adjoint message (K u, the correlation, K r)."""
+    W, H, L = 338, 190, 48
+    left, right, _ = synth.noise_pair(11, w=W, h=H, max_disp=40.0)
+    IL = torch.from_numpy(left.astype(np.float32)).to(dev)
+    IR = torch.from_numpy(right.astype(np.float32)).to(dev)
+    cost = torch.full((H, W, L), 20.0, device=dev)
+    for d in range(L):
+        cost[:, d:, d] = torch.clamp((IL[:, d:] - IR[:, :W - d]).abs(), max=20.0)
+    cost = cost.contiguous()
+    p = vs.SPParams(labels=L, iters=8, ckpt_every=2, lam=2.5, trunc=13.75, tau=2.0)
+    g = torch.Generator(device=dev).manual_seed(5)
+    gb = torch.randn((H, W, L), device=dev, generator=g)
+    edges = 2 * (W - 1) * H + 2 * W * (H - 1)
+    sm_mhz = 2032.0
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        sm_mhz = float(json.load(open(pk_path)).get("sm_max_mhz", sm_mhz))
+    fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s, FMA = 2 flops
+    out = {"workload": f"{W}x{H}x{L} FP32 cost volume, 8 synchronous iterations, checkpoint every 2, "
+                       "lambda 2.5, trunc 13.75, tau 2", "reps": args.smooth_reps}
+    for fam in ("simt", "tensor"):
+        vs.sp_select_kernels(fam)
+        bel, ws = vs.sp_forward(cost, p)
+        gc, gp = vs.sp_backward(cost, p, gb, ws)
+        for _ in range(3):
+            vs.sp_forward(cost, p, beliefs=bel, workspace=ws)
+            vs.sp_backward(cost, p, gb, ws, grad_cost=gc, grad_params=gp)
+        torch.cuda.synchronize()
+        vs.profile_enable(4096)
+        vs.profile_collect()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        for _ in range(args.smooth_reps):
+            vs.sp_forward(cost, p, beliefs=bel, workspace=ws)
+        e[1].record()
+        for _ in range(args.smooth_reps):
+            vs.sp_backward(cost, p, gb, ws, grad_cost=gc, grad_params=gp)
+        e[2].record()
+        torch.cuda.synchronize()
+        vs.sp_status(ws, W, H, p)
+        by = {}
+        for tag, ms in vs.profile_collect():
+            by.setdefault(tag, []).append(ms)
+        vs.profile_enable(0)
+        fwd_us = 1e3 * statistics.median(by["smooth_fwd"])
+        adj_us = 1e3 * statistics.median(by["smooth_adj"])
+        r = {"forward_ms": e[0].elapsed_time(e[1]) / args.smooth_reps,
+             "adjoint_ms": e[1].elapsed_time(e[2]) / args.smooth_reps,
+             "forward_iteration_us": fwd_us, "adjoint_iteration_us": adj_us}
+        if fam == "simt":
+            fl_f, fl_a = 2.0 * edges * L * L, 6.0 * edges * L * L
+            r["alu"] = {"bound": "alu", "unit": "TFLOP/s", "peak": fp32_peak,
+                        "peak_source": f"148 SMs x 128 FP32 FMA lanes x 2 x {sm_mhz:.0f} MHz",
+                        "forward_achieved": fl_f / (fwd_us * 1e-6) / 1e12,
+                        "adjoint_achieved": fl_a / (adj_us * 1e-6) / 1e12}
+            r["alu"]["forward_frac"] = r["alu"]["forward_achieved"] / fp32_peak
+            r["alu"]["adjoint_frac"] = r["alu"]["adjoint_achieved"] / fp32_peak
+        out[fam] = r
+    vs.sp_select_kernels("simt")
+    out["default_kernels"] = "simt"
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -484,6 +555,11 @@ def run_ours(args):
     if args.batch_pairs > 0 and rank == 0:
         batched = run_batched(args, vs, synth, torch, dev, cam)
 
+    # smoothed BP + adjoint (the differentiable relaxation of Eq. 1)
+    smooth = None
+    if args.smooth_reps > 0 and rank == 0:
+        smooth = run_smooth(args, vs, synth, torch, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cam_t = synth.TERRAIN_CAMERA
@@ -511,6 +587,7 @@ def run_ours(args):
             "e2e": e2e,
             "streaming": streaming,
             "batched": batched,
+            "smooth_bp": smooth,
             "gpu_launches": launches_per_step * K,
             "clocks": clk,
         }

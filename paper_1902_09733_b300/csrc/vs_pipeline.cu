@@ -72,6 +72,18 @@ int launch_status()
     return cudaGetLastError() == cudaSuccess ? VS_OK : VS_ECUDA;
 }
 
+// Inside stream capture a plain cudaEventRecord only orders the capture; the
+// external flag makes it an event-record node of the graph, so the pair
+// times every replay of the captured kernel.
+static void prof_record(cudaEvent_t ev, cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(ev, st);
+}
+
 int prof_begin(int tag, cudaStream_t st)
 {
     std::lock_guard<std::mutex> lk(g_prof.mu);
@@ -81,7 +93,7 @@ int prof_begin(int tag, cudaStream_t st)
     g_prof.next = (g_prof.next + 1) % (int)g_prof.start.size();
     g_prof.tag[slot] = tag;
     g_prof.pending.push_back(slot);
-    cudaEventRecord(g_prof.start[slot], st);
+    prof_record(g_prof.start[slot], st);
     return slot;
 }
 
@@ -90,7 +102,7 @@ void prof_end(int slot, cudaStream_t st)
     if (slot < 0)
         return;
     std::lock_guard<std::mutex> lk(g_prof.mu);
-    cudaEventRecord(g_prof.stop[slot], st);
+    prof_record(g_prof.stop[slot], st);
 }
 
 }  // namespace vs
