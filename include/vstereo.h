@@ -172,18 +172,29 @@ int vs_bp_stereo_batch(const vs_bp_job *jobs, int n, void *workspace, size_t ws_
 
 /*
  * Autotuner for the message sweeps (no counterpart in the paper).  Runs
- * vs_bp_stereo on the given pair, then times the three sweep kernels (plain,
- * register preload, labels split over two lanes) on every level and records
+ * vs_bp_stereo on the given pair, then times the sweep kernels (plain,
+ * register preload, labels split over two lanes, over four lanes when the
+ * padded label count is a multiple of 64) on every level and records
  * the fastest per (padded label count, level size); later vs_bp_stereo and
  * vs_bp_stereo_batch calls on levels of those sizes use it.  Results are
  * identical whichever kernel runs.  Ends with a fresh vs_bp_stereo so labels
  * and workspace hold the pair's result.  Synchronises `stream`; do not call
  * it while the stream is being captured.  chosen (nullable, `levels` ints)
- * receives 0 plain, 1 preload, 2 split per level.  vs_bp_autotune_reset
+ * receives 0 plain, 1 preload, 2 split in two, 3 split in four per level.
+ * vs_bp_autotune_reset
  * forgets every recorded choice.
  */
 int vs_bp_autotune(const uint8_t *left, const uint8_t *right, int w, int h, int pitch, const vs_bp_params *p,
                    uint8_t *labels, int labels_pitch, void *workspace, size_t ws_bytes, void *stream, int *chosen);
+/* The timings behind the last vs_bp_autotune: milliseconds per launch as
+ * [level][variant] (4 per level, -1 where a variant does not apply), up to
+ * `max` values written; returns the count. */
+int vs_bp_autotune_times(float *ms, int max);
+/* Test and measurement aid: run sweep variant `variant` (0 plain, 1 preload,
+ * 2 split in two, 3 split in four) on every level where it applies, ahead of
+ * any autotuned choice; -1 restores the automatic choice.  Results are
+ * identical either way.  Errors: VS_EINVAL. */
+int vs_bp_select_sweep(int variant);
 void vs_bp_autotune_reset(void);
 
 /* Debug read-out after vs_bp_stereo on the same workspace and stream: the

@@ -33,7 +33,7 @@ __all__ = [
     "guided_upsample", "reproject", "guided_upsample_reproject",
     "pair_workspace_size", "pair_run", "pair_run_host", "kernel_launches", "status_string",
     "profile_enable", "profile_collect", "Pipeline", "bp_stereo_batch", "bp_batch_workspace_size",
-    "bp_autotune", "bp_autotune_reset", "SPParams", "sp_workspace_size", "sp_forward", "sp_backward",
+    "bp_autotune", "bp_autotune_reset", "bp_autotune_times", "bp_select_sweep", "SPParams", "sp_workspace_size", "sp_forward", "sp_backward",
     "smooth_bp", "SmoothBP", "sp_select_kernels", "sp_status",
 ]
 
@@ -188,6 +188,8 @@ def lib() -> ctypes.CDLL:
             "vs_bp_stereo_batch": ([P, I, P, S, P], I),
             "vs_bp_autotune": ([P, P, I, I, I, bp_p, P, I, P, S, P, P], I),
             "vs_bp_autotune_reset": ([], None),
+            "vs_bp_autotune_times": ([P, I], I),
+            "vs_bp_select_sweep": ([I], I),
             "vs_pipeline_workspace_size": ([cfg_p, I, I, I], S),
             "vs_pipeline_create": ([cfg_p, I, I, I, P, S, ctypes.POINTER(P)], I),
             "vs_pipeline_submit_pair": ([P, P, P, P], I),
@@ -373,9 +375,9 @@ def bp_stereo_batch(pairs, labels=None, workspace=None, stream=None):
 
 def bp_autotune(left: torch.Tensor, right: torch.Tensor, params: BPParams, workspace=None, labels=None,
                 stream=None):
-    """Time the three sweep kernels on every level of this pair and keep the
+    """Time the sweep kernels on every level of this pair and keep the
     fastest for later calls; returns the choice per level (0 plain, 1 preload,
-    2 split) and leaves the pair's labels in ``labels``."""
+    2 labels split in two, 3 in four) and leaves the pair's labels in ``labels``."""
     h, w = left.shape
     if workspace is None:
         workspace = torch.empty(bp_workspace_size(w, h, params), dtype=torch.uint8, device=left.device)
@@ -388,6 +390,18 @@ def bp_autotune(left: torch.Tensor, right: torch.Tensor, params: BPParams, works
         _pitched(labels, 1, "labels"), workspace.data_ptr(), workspace.numel(), _stream(stream),
         ctypes.cast(chosen, ctypes.c_void_p)))
     return [int(v) for v in chosen]
+
+
+def bp_autotune_times():
+    """[[ms per launch of variants 0..3] per level] of the last bp_autotune (-1: not applicable)."""
+    buf = (ctypes.c_float * 64)()
+    n = lib().vs_bp_autotune_times(ctypes.cast(buf, ctypes.c_void_p), 64)
+    return [[float(buf[i + v]) for v in range(4)] for i in range(0, n, 4)]
+
+
+def bp_select_sweep(variant: int) -> None:
+    """Force sweep variant 0..3 on every level where it applies (-1: automatic)."""
+    _check("vs_bp_select_sweep", lib().vs_bp_select_sweep(int(variant)))
 
 
 def bp_autotune_reset() -> None:

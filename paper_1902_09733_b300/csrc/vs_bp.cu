@@ -508,28 +508,32 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, unsigned block)
 }
 
 // ---------------------------------------------------------------------------
-// message sweep, labels split across two lanes (small levels)
+// message sweep, labels split across NS = 2 or 4 lanes (small levels)
 //
 // On the coarse levels there are too few pixels to fill the GPU, so a sweep
 // is as long as one thread's serial label chain.  Here each direction pair
-// is shared by two adjacent lanes, one per half of the labels.  Each lane
-// runs the forward and backward lower-envelope passes over its half; the
-// halves are joined exactly by
-//   F(d) = min(F_half(d), F(d0 - 1) + c (d - d0 + 1))   upper half, forward
-//   G(d) = min(G_half(d), G(d1)     + c (d1 - d))       lower half, backward
-// (d0, d1 = first label of the upper half), with the carries exchanged by
-// one shuffle each and the corrections applied to all labels in parallel.
-// The chain per lane is half as long and the work per lane about half.
+// is shared by NS adjacent lanes, one per block of HL = LP / NS labels.  Each
+// lane runs the forward and backward lower-envelope passes over its block;
+// the blocks are joined exactly by
+//   F(d) = min(F_blk(d), F(s_j - 1) + c (d - s_j + 1))   forward, block j > 0
+//   G(d) = min(G_blk(d), G(s_{j+1}) + c (s_{j+1} - d))    backward, block j < NS-1
+// (s_j = first label of block j).  The carries are min-plus scans over the
+// lane group: F(end of block j) = min over i <= j of (E_i + c HL (j - i)),
+// E_i the block's own end value, and the mirror image backwards -- one
+// shuffle step for two lanes, two for four.  The chain per lane is NS times
+// shorter; the corrections touch all labels in parallel.
 
-template <int LP, typename CostT, bool BYTES, bool FULL>
+template <int LP, typename CostT, bool BYTES, bool FULL, int NS>
 __device__ __forceinline__ void sweep_split_body(const SweepArgs &a, unsigned block)
 {
-    constexpr int HL = LP / 2;   // labels per lane
+    static_assert(NS == 2 || NS == 4, "label blocks per direction pair");
+    constexpr int HL = LP / NS;  // labels per lane
     constexpr int HC = HL / 16;  // 16-label chunks per lane
+    static_assert(HC >= 1 && HL % 16 == 0, "whole 16-label chunks per lane");
     const unsigned idx = block * kSweepThreads + threadIdx.x;
-    const int half = (int)(idx & 1u);
-    const int pair = (int)((idx >> 1) & 1u);
-    const unsigned slot = idx >> 2;   // over rows padded to whole 16-slot groups
+    const int half = (int)(idx % NS);   // label block of this lane
+    const int pair = (int)((idx / NS) & 1u);
+    const unsigned slot = idx / (2 * NS);   // over rows padded to whole 16-slot groups
     const unsigned rowslots = 16u * (unsigned)a.wg;
     int y = 0, xh = 0, x = 0;
     bool valid = slot < (unsigned)a.h * rowslots;
@@ -609,20 +613,37 @@ __device__ __forceinline__ void sweep_split_body(const SweepArgs &a, unsigned bl
             H2 = min_u16x2(H2, wv);
         }
     }
-    // join the halves: global minimum, then the forward carry into the upper half
-    H2 = min_u16x2(H2, __shfl_xor_sync(0xffffffffu, H2, 1));
-    const uint32_t c_lo = __shfl_xor_sync(0xffffffffu, F[HL - 1], 1);
-    if (half == 1) {
+    // join the blocks: global minimum over the lane group
+#pragma unroll
+    for (int o = 1; o < NS; o <<= 1)
+        H2 = min_u16x2(H2, __shfl_xor_sync(0xffffffffu, H2, o));
+    // forward carry: inclusive min-plus scan of the blocks' end values
+    uint32_t A = F[HL - 1];
+#pragma unroll
+    for (int o = 1; o < NS; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, A, o, NS);
+        if (half >= o)
+            A = min_u16x2(A, t + a.c2 * (uint32_t)(HL * o));
+    }
+    const uint32_t c_lo = __shfl_up_sync(0xffffffffu, A, 1, NS);   // F at the end of the previous block
+    if (half > 0) {
 #pragma unroll
         for (int k = 0; k < HL; ++k)
             F[k] = min_u16x2(F[k], c_lo + a.c2 * (uint32_t)(k + 1));
     }
-    // backward pass over the half (G kept in F), then the carry into the lower half
+    // backward pass over the block (G kept in F), then the carry from the right
 #pragma unroll
     for (int k = HL - 2; k >= 0; --k)
         F[k] = __viaddmin_u16x2(F[k + 1], a.c2, F[k]);
-    const uint32_t c_hi = __shfl_xor_sync(0xffffffffu, F[0], 1);
-    if (half == 0) {
+    uint32_t B = F[0];
+#pragma unroll
+    for (int o = 1; o < NS; o <<= 1) {
+        const uint32_t t = __shfl_down_sync(0xffffffffu, B, o, NS);
+        if (half + o < NS)
+            B = min_u16x2(B, t + a.c2 * (uint32_t)(HL * o));
+    }
+    const uint32_t c_hi = __shfl_down_sync(0xffffffffu, B, 1, NS);   // G at the start of the next block
+    if (half < NS - 1) {
 #pragma unroll
         for (int k = 0; k < HL; ++k)
             F[k] = min_u16x2(F[k], c_hi + a.c2 * (uint32_t)(HL - k));
@@ -673,11 +694,11 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
     sweep_body<LP, CostT, BYTES, FULL, LABELS, PRELOAD>(a, blockIdx.x);
 }
 
-template <int LP, typename CostT, bool BYTES, bool FULL>
+template <int LP, typename CostT, bool BYTES, bool FULL, int NS>
 __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_split(SweepArgs a)
 {
     pdl_begin();
-    sweep_split_body<LP, CostT, BYTES, FULL>(a, blockIdx.x);
+    sweep_split_body<LP, CostT, BYTES, FULL, NS>(a, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -717,12 +738,12 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_batch(const __grid_c
     sweep_body<LP, CostT, BYTES, FULL, LABELS, PRELOAD>(b.job[j], blockIdx.x - b.first_block[j]);
 }
 
-template <int LP, typename CostT, bool BYTES, bool FULL>
+template <int LP, typename CostT, bool BYTES, bool FULL, int NS>
 __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_split_batch(const __grid_constant__ BatchArgs b)
 {
     pdl_begin();
     const int j = batch_job(b, blockIdx.x);
-    sweep_split_body<LP, CostT, BYTES, FULL>(b.job[j], blockIdx.x - b.first_block[j]);
+    sweep_split_body<LP, CostT, BYTES, FULL, NS>(b.job[j], blockIdx.x - b.first_block[j]);
 }
 
 // ---------------------------------------------------------------------------
@@ -812,14 +833,22 @@ __global__ void k_bp_export(ExportArgs a)
 // fit bytes too (byte-lane arithmetic); labels: the last level-0 iteration
 // ---------------------------------------------------------------------------
 // kernel variant per level: plain, register preload, or labels split over
-// two lanes.  Defaults by level size (active-colour slots h * wh); the
-// autotuner (vs_bp_autotune) measures the three on a given problem and
-// records the fastest per (label count, level size), which then wins.
+// two or four lanes.  Defaults by level size (active-colour slots h * wh);
+// the autotuner (vs_bp_autotune) measures the variants on a given problem
+// and records the fastest per (label count, level size), which then wins.
 
-enum SweepVariant { kVarPlain = 0, kVarPreload = 1, kVarSplit = 2 };
+enum SweepVariant { kVarPlain = 0, kVarPreload = 1, kVarSplit = 2, kVarSplit4 = 3 };
 
-constexpr unsigned kSplitMaxPixels = 1u << 14;    // smaller levels: split
-constexpr unsigned kPreloadMaxPixels = 1u << 16;  // smaller levels: preload
+// Defaults measured on B300 (vs_bp_autotune_times, eager launches, 2.7K
+// flight frames at s = 2, 4, 8, 64 and 128 labels): with up to 64 labels the
+// register preload wins at every level size (level 0 at 676x380: 12.5 us vs
+// 13.1 plain; at 1352x760: 51.8 vs 64.7) except the smallest levels, where
+// four lanes per direction pair shorten the serial chain (85x48: 3.07 vs
+// 3.28 us); with 96 / 128 labels two lanes win on the largest levels (141.9
+// vs 150.1 us at 1352x760), plain in between, four lanes on the smallest.
+constexpr unsigned kSplit4MaxSlots = 1u << 12;    // smaller levels: four lanes
+constexpr unsigned kSplitMaxSlots = 1u << 14;     // 32 labels, smaller levels: two lanes
+constexpr unsigned kWideSplitMinSlots = 1u << 16; // 96 / 128 labels, larger levels: two lanes
 
 struct TuneEntry {
     int Lp;
@@ -828,6 +857,8 @@ struct TuneEntry {
 };
 std::mutex g_tune_mu;
 std::vector<TuneEntry> g_tune;
+std::vector<float> g_tune_last;   // ms per launch of the last vs_bp_autotune, [level][variant]
+int g_force_variant = -1;         // vs_bp_select_sweep: one variant on every level where allowed
 
 bool variant_allowed(int Lp, int variant, bool labels)
 {
@@ -835,6 +866,8 @@ bool variant_allowed(int Lp, int variant, bool labels)
         return variant == kVarPlain;   // only the plain kernel writes labels
     if (variant == kVarSplit)
         return Lp % 32 == 0;
+    if (variant == kVarSplit4)
+        return Lp % 64 == 0;
     if (variant == kVarPreload)
         return Lp <= 64;
     return true;
@@ -846,20 +879,25 @@ int choose_variant(int Lp, unsigned slots, bool labels)
         return kVarPlain;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
+        if (g_force_variant >= 0 && variant_allowed(Lp, g_force_variant, false))
+            return g_force_variant;
         for (const TuneEntry &e : g_tune)
             if (e.Lp == Lp && e.slots == slots && variant_allowed(Lp, e.variant, false))
                 return e.variant;
     }
-    if (Lp % 32 == 0 && slots < kSplitMaxPixels)
+    if (Lp % 64 == 0 && slots < kSplit4MaxSlots)
+        return kVarSplit4;
+    if (Lp <= 64)
+        return (Lp == 32 && slots < kSplitMaxSlots) ? kVarSplit : kVarPreload;
+    if (slots >= kWideSplitMinSlots || slots < kSplit4MaxSlots)
         return kVarSplit;
-    if (Lp <= 64 && slots < kPreloadMaxPixels)
-        return kVarPreload;
     return kVarPlain;
 }
 
 unsigned sweep_blocks(const SweepArgs &a, int variant)
 {
-    const unsigned threads = (variant == kVarSplit ? 4u : 2u) * (unsigned)a.h * 16u * (unsigned)a.wg;
+    const unsigned lanes = variant == kVarSplit4 ? 8u : (variant == kVarSplit ? 4u : 2u);
+    const unsigned threads = lanes * (unsigned)a.h * 16u * (unsigned)a.wg;
     return (threads + kSweepThreads - 1) / kSweepThreads;
 }
 
@@ -884,14 +922,27 @@ void launch_sweep_lp(const SweepArgs *a, const BatchArgs *b, unsigned grid, bool
         else                                                                                                  \
             launch_pdl(k_bp_sweep_split<__VA_ARGS__>, g, blk, st, *a);                                        \
     } while (0)
-    if (variant == kVarSplit) {
-        if (cost8 && bytes)
-            VS_SPLIT(LP, uint8_t, true, FULL);
-        else if (cost8)
-            VS_SPLIT(LP, uint8_t, false, FULL);
-        else
-            VS_SPLIT(LP, uint16_t, false, FULL);
-        return;
+    if constexpr (LP % 32 == 0) {
+        if (variant == kVarSplit) {
+            if (cost8 && bytes)
+                VS_SPLIT(LP, uint8_t, true, FULL, 2);
+            else if (cost8)
+                VS_SPLIT(LP, uint8_t, false, FULL, 2);
+            else
+                VS_SPLIT(LP, uint16_t, false, FULL, 2);
+            return;
+        }
+    }
+    if constexpr (LP % 64 == 0) {
+        if (variant == kVarSplit4) {
+            if (cost8 && bytes)
+                VS_SPLIT(LP, uint8_t, true, FULL, 4);
+            else if (cost8)
+                VS_SPLIT(LP, uint8_t, false, FULL, 4);
+            else
+                VS_SPLIT(LP, uint16_t, false, FULL, 4);
+            return;
+        }
     }
     constexpr bool kPre = LP <= 64;   // the preload variant exists up to 64 labels
     const bool pre = kPre && variant == kVarPreload;
@@ -1212,13 +1263,14 @@ extern "C" int vs_bp_autotune(const uint8_t *left, const uint8_t *right, int w, 
         return VS_ECUDA;
     }
     rc = VS_OK;
+    std::vector<float> times((size_t)lay.levels * 4, -1.0f);
     for (int l = 0; l < lay.levels && rc == VS_OK; ++l) {
         // an interior iteration of the level (t = 2 reads its own arrays)
         const SweepArgs a = sweep_args(lay, ws, p, l, p->iters > 2 ? 2 : 1, nullptr, 0);
         const unsigned slots = (unsigned)a.h * (unsigned)a.wh;
         float best = 3.4e38f;
         int best_v = kVarPlain;
-        for (int v = kVarPlain; v <= kVarSplit; ++v) {
+        for (int v = kVarPlain; v <= kVarSplit4; ++v) {
             if (!variant_allowed(lay.Lp, v, false))
                 continue;
             for (int rep = 0; rep < 2; ++rep)   // warm-up
@@ -1234,6 +1286,7 @@ extern "C" int vs_bp_autotune(const uint8_t *left, const uint8_t *right, int w, 
                 rc = VS_ECUDA;
                 break;
             }
+            times[(size_t)l * 4 + v] = ms / reps;
             if (ms < best) {
                 best = ms;
                 best_v = v;
@@ -1255,6 +1308,10 @@ extern "C" int vs_bp_autotune(const uint8_t *left, const uint8_t *right, int w, 
         if (chosen)
             chosen[l] = best_v;
     }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_last = times;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != VS_OK)
@@ -1262,6 +1319,24 @@ extern "C" int vs_bp_autotune(const uint8_t *left, const uint8_t *right, int w, 
     // the timing runs changed the message arrays: run once more so that the
     // workspace and labels hold this problem's result again
     return vs_bp_stereo(left, right, w, h, pitch, p, labels, labels_pitch, workspace, ws_bytes, stream);
+}
+
+extern "C" int vs_bp_autotune_times(float *ms, int max)
+{
+    std::lock_guard<std::mutex> lk(vs::g_tune_mu);
+    const int n = (int)vs::g_tune_last.size() < max ? (int)vs::g_tune_last.size() : max;
+    for (int i = 0; i < n; ++i)
+        ms[i] = vs::g_tune_last[i];
+    return n;
+}
+
+extern "C" int vs_bp_select_sweep(int variant)
+{
+    if (variant < -1 || variant > 3)
+        return VS_EINVAL;
+    std::lock_guard<std::mutex> lk(vs::g_tune_mu);
+    vs::g_force_variant = variant;
+    return VS_OK;
 }
 
 extern "C" void vs_bp_autotune_reset(void)

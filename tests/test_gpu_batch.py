@@ -82,10 +82,34 @@ def test_autotune_keeps_results_identical():
     msg_before = vs.bp_export_messages(ws, 338, 190, p).cpu().numpy()
     try:
         chosen = vs.bp_autotune(L_, R_, p, workspace=ws)
-        assert len(chosen) == 4 and all(c in (0, 1, 2) for c in chosen)
+        assert len(chosen) == 4 and all(c in (0, 1, 2, 3) for c in chosen)
+        times = vs.bp_autotune_times()
+        assert len(times) == 4 and all(row[c] > 0 and row[c] == min(t for t in row if t > 0)
+                                       for row, c in zip(times, chosen))
         after = vs.bp_stereo(L_, R_, p, workspace=ws).cpu().numpy()
         np.testing.assert_array_equal(after, before)
         np.testing.assert_array_equal(vs.bp_export_messages(ws, 338, 190, p).cpu().numpy(), msg_before)
     finally:
         vs.bp_autotune_reset()
     np.testing.assert_array_equal(before, oracle.bp(l, r, 64, 4, 10, 20, 10, 40, mode=oracle.MSG_DT))
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("shape", [(190, 338, 64), (61, 97, 128), (33, 70, 96)])
+def test_every_sweep_variant_matches_the_oracle(variant, shape):
+    """Each sweep kernel (plain, preload, labels split over two or four lanes)
+    forced on every level where it applies gives the oracle's labels and final
+    level-0 messages bit for bit."""
+    h, w, L = shape
+    L_, R_, l, r = _pair(11 + variant, h, w)
+    p = vs.BPParams(L, 4, 6, 20, 10, 40)
+    try:
+        vs.bp_select_sweep(variant)
+        ws = torch.empty(vs.bp_workspace_size(w, h, p), dtype=torch.uint8, device="cuda")
+        got = vs.bp_stereo(L_, R_, p, workspace=ws).cpu().numpy()
+        msg = vs.bp_export_messages(ws, w, h, p).cpu().numpy()
+    finally:
+        vs.bp_select_sweep(-1)
+    want, wmsg = oracle.bp(l, r, L, 4, 6, 20, 10, 40, mode=oracle.MSG_DT, return_messages=True)
+    np.testing.assert_array_equal(got, want)
+    np.testing.assert_array_equal(msg, wmsg)
