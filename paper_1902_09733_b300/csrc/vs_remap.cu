@@ -27,6 +27,7 @@ struct RemapArgs {
     float fx, fy, cx, cy, k1, k2;
     float inv_fx, inv_fy;   // 1/fx, 1/fy rounded once on the host
     int dst_vec;            // dst rows allow 4-byte stores of 4-pixel groups
+    int src_words;          // src rows start on 4-byte boundaries (aligned word gathers)
     float R[9];
     int has_R;
 };
@@ -82,7 +83,35 @@ __global__ void __launch_bounds__(kRemapThreads) k_remap_down(RemapArgs a)
                         const float fx0 = floorf(sx), fy0 = floorf(sy);
                         const int x0 = (int)fx0, y0 = (int)fy0;
                         const float ax = sx - fx0, ay = sy - fy0;
-                        if (x0 >= 0 && y0 >= 0 && x0 + 1 < a.W && y0 + 1 < a.H) {
+                        if (x0 >= 0 && y0 >= 0 && x0 + 2 < a.W && y0 + 1 < a.H && a.src_words) {
+                            // all four taps in the frame, and the aligned words that
+                            // cover each row's 6 bytes end inside that row: 4 to 6 loads
+                            const uint8_t *p0 = a.src + (size_t)y0 * a.src_pitch + 3 * x0;
+                            const uint32_t o = (uint32_t)(reinterpret_cast<uintptr_t>(p0) & 3u);
+                            const uint32_t *q0 = reinterpret_cast<const uint32_t *>(p0 - o);
+                            const uint32_t *q1 = reinterpret_cast<const uint32_t *>(p0 - o + a.src_pitch);
+                            const uint32_t a0 = __ldg(q0), a1 = __ldg(q0 + 1), b0 = __ldg(q1), b1 = __ldg(q1 + 1);
+                            // byte o + 5 lies in a third word only for o = 3 (it is then
+                            // byte 3x0 + 5 of the row, inside it since x0 + 3 <= W)
+                            const uint32_t a2 = o == 3 ? __ldg(q0 + 2) : 0u, b2 = o == 3 ? __ldg(q1 + 2) : 0u;
+                            // bytes o .. o+5 of each row: (R0 G0 B0 R1) from {a1:a0}, (G1 B1) from {a2:a1}
+                            const uint32_t s_lo = o | ((o + 1) << 4) | ((o + 2) << 8) | ((o + 3) << 12);
+                            const uint32_t s_hi = o | ((o + 1) << 4);
+                            const uint32_t r0a = prmt(a0, a1, s_lo), r0b = prmt(a1, a2, s_hi);
+                            const uint32_t r1a = prmt(b0, b1, s_lo), r1b = prmt(b1, b2, s_hi);
+                            const uint32_t top6[2] = {r0a, r0b}, bot6[2] = {r1a, r1b};
+#pragma unroll
+                            for (int ch = 0; ch < 3; ++ch) {
+                                const int k0 = ch, k1 = ch + 3;   // byte of the left / right tap
+                                const float t00 = (float)((top6[k0 >> 2] >> (8 * (k0 & 3))) & 0xFFu);
+                                const float t10 = (float)((top6[k1 >> 2] >> (8 * (k1 & 3))) & 0xFFu);
+                                const float t01 = (float)((bot6[k0 >> 2] >> (8 * (k0 & 3))) & 0xFFu);
+                                const float t11 = (float)((bot6[k1 >> 2] >> (8 * (k1 & 3))) & 0xFFu);
+                                const float top = fmaf(ax, t10 - t00, t00);
+                                const float bot = fmaf(ax, t11 - t01, t01);
+                                val[ch] = fmaf(ay, bot - top, top);
+                            }
+                        } else if (x0 >= 0 && y0 >= 0 && x0 + 1 < a.W && y0 + 1 < a.H) {
                             // all four taps in the frame: one base address, two rows of 6 bytes
                             const uint8_t *p0 = a.src + (size_t)y0 * a.src_pitch + 3 * x0;
                             const uint8_t *p1 = p0 + a.src_pitch;
@@ -243,6 +272,7 @@ extern "C" int vs_rectify_remap(const uint8_t *src, int W, int H, int src_pitch,
     a.inv_fy = (float)(1.0 / (double)cam->fy);
     // 4-pixel groups start at multiples of 4 pixels (12 bytes) of the row
     a.dst_vec = dst != nullptr && aligned(dst, 4) && dst_pitch % 4 == 0;
+    a.src_words = aligned(src, 4) && src_pitch % 4 == 0;
     a.has_R = R9 != nullptr;
     for (int i = 0; i < 9; ++i)
         a.R[i] = R9 ? R9[i] : (i % 4 == 0 ? 1.0f : 0.0f);
