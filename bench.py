@@ -3,15 +3,18 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-One step is one frame pair of 2704 x 1520 RGB through the whole hot path:
-radial undistort/rectify remap of both frames fused with the x4 downsample
-(Section 2.1, 2.2), hierarchical min-sum BP with 64 labels, 4 levels x 10
-iterations on 676 x 380 (Eq. 1), joint bilateral upsampling of the labels to
-2704 x 1520 fused with the reprojection to an FP32 point cloud (Eq. 2, 3).
-Inputs are seeded synthetic terrain pairs rendered on the host; eight distinct
-pairs (197 MB, more than the 126 MB L2) are resident in HBM and rotated so no
-step reads its inputs from L2.  Each step is one CUDA-graph replay of the
-library's kernels.
+One step is a batch of P independent frame pairs of 2704 x 1520 RGB (P =
+--pairs-in-flight, default 4) through the whole hot path: radial
+undistort/rectify remap of both frames fused with the x4 downsample (Section
+2.1, 2.2), hierarchical min-sum BP with 64 labels, 4 levels x 10 iterations
+on 676 x 380 (Eq. 1), joint bilateral upsampling of the labels to 2704 x 1520
+fused with the reprojection to an FP32 point cloud (Eq. 2, 3).  Each step is
+one CUDA-graph replay in which the P pairs run on P streams, so one pair's
+latency-bound coarse BP levels overlap another's bandwidth-bound kernels;
+the line also reports the plain rate (one pair per replay).  Inputs are
+seeded synthetic terrain pairs rendered on the host; eight distinct pairs
+(197 MB, more than the 126 MB L2) are resident in HBM and rotated so no step
+reads its inputs from L2.
 
 Prints ONE JSON line (rank 0).  Pairs are independent, so N GPUs run N
 replicas ("scaling": "weak") and the value is all pairs over the slowest rank.
@@ -46,7 +49,9 @@ WORKLOAD = ("2704x1520 RGB pair: remap+downsample x4 -> 676x380 min-sum BP 64 la
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=8000)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--pairs-in-flight", type=int, default=4)
+    ap.add_argument("--plain-steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=40)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=200)
@@ -399,28 +404,59 @@ def run_ours(args):
         l, r = synth.terrain_pair(seed)
         host_pairs.extend(synth.pair_variants(l, r))
     pairs = [(torch.from_numpy(l).to(dev), torch.from_numpy(r).to(dev)) for l, r in host_pairs]
-    ws = torch.empty(vs.pair_workspace_size(cfg), dtype=torch.uint8, device=dev)
-    xyz = [torch.empty((H_FULL, W_FULL, 3), dtype=torch.float32, device=dev) for _ in range(2)]
+    P = max(1, args.pairs_in_flight)
+    ws = [torch.empty(vs.pair_workspace_size(cfg), dtype=torch.uint8, device=dev) for _ in range(P)]
+    xyz = [torch.empty((H_FULL, W_FULL, 3), dtype=torch.float32, device=dev) for _ in range(P)]
 
     stream = torch.cuda.Stream(device=dev)
+    side = [torch.cuda.Stream(device=dev) for _ in range(P)]
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
-        vs.pair_run(cfg, *pairs[0], xyz=xyz[0], workspace=ws)   # load every kernel once
+        vs.pair_run(cfg, *pairs[0], xyz=xyz[0], workspace=ws[0])   # load every kernel once
     torch.cuda.synchronize()
 
-    def capture(i):
+    def capture(first, n):
+        """A graph that runs pairs first .. first+n-1 (mod 8) on n streams."""
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
-            vs.pair_run(cfg, *pairs[i], xyz=xyz[i % 2], workspace=ws)
+            if n == 1:
+                vs.pair_run(cfg, *pairs[first % len(pairs)], xyz=xyz[0], workspace=ws[0], stream=stream)
+            else:
+                fork = torch.cuda.Event()
+                fork.record(stream)
+                joins = []
+                for k in range(n):
+                    side[k].wait_event(fork)
+                    vs.pair_run(cfg, *pairs[(first + k) % len(pairs)], xyz=xyz[k], workspace=ws[k],
+                                stream=side[k])
+                    e = torch.cuda.Event()
+                    e.record(side[k])
+                    joins.append(e)
+                for e in joins:
+                    stream.wait_event(e)
         return g
 
     n0 = vs.kernel_launches()
-    graphs = [capture(i) for i in range(len(pairs))]
+    graphs = [capture(P * i, P) for i in range(len(pairs))]
     launches_per_step = (vs.kernel_launches() - n0) // len(pairs)
-    # a second set of graphs whose launches are bracketed by CUDA events
+    plain_graphs = [capture(i, 1) for i in range(len(pairs))]
+    # single-pair graphs whose launches are bracketed by CUDA events
+    # (profiling stays on until these have been replayed and collected: the
+    # graphs record into its events)
     vs.profile_enable(4096)
-    prof_graphs = [capture(i) for i in range(len(pairs))]
+    prof_graphs = [capture(i, 1) for i in range(len(pairs))]
     torch.cuda.synchronize()
+
+    def timed(gs, steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for k in range(steps):
+                gs[k % len(gs)].replay()
+            e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
 
     # warm-up
     for k in range(args.warmup):
@@ -433,38 +469,32 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
     K = args.steps
-    n_prof = min(len(graphs), K)
-    with torch.cuda.stream(stream):
-        ev0.record(stream)
-        for k in range(K):
-            # the last steps replay the event-bracketed copies of the graphs
-            (prof_graphs if k >= K - n_prof else graphs)[k % len(graphs)].replay()
-        ev1.record(stream)
-    ev1.synchronize()
+    elapsed_ms = timed(graphs, K)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    elapsed_ms = ev0.elapsed_time(ev1)
     slowest_ms = elapsed_ms
     if world > 1:
         t = torch.tensor([elapsed_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         slowest_ms = float(t.item())
+
+    # plain rate (one pair per replay) and the per-kernel event times of
+    # single-pair replays, right after the timed region
+    plain = None
+    if args.plain_steps > 0:
+        for k in range(args.warmup):
+            plain_graphs[k % len(plain_graphs)].replay()
+        t_plain = timed(plain_graphs, args.plain_steps)
+        plain = {"value": args.plain_steps / (t_plain * 1e-3), "unit": UNIT, "steps": args.plain_steps,
+                 "ms_per_pair": t_plain / args.plain_steps}
+    timed(prof_graphs, len(prof_graphs))
     recs = vs.profile_collect()
-    timing_src = "CUDA events around each launch inside the last graph replays of the timed region"
-    if not any(t == "sweep_level0" for t, _ in recs):
-        # event nodes inside graphs gave no times: time a few eager steps instead
-        with torch.cuda.stream(stream):
-            for i in range(len(pairs)):
-                vs.pair_run(cfg, *pairs[i], xyz=xyz[i % 2], workspace=ws)
-        torch.cuda.synchronize()
-        recs = vs.profile_collect()
-        timing_src = "CUDA events around each launch of eager steps after the timed region"
     vs.profile_enable(0)
+    del prof_graphs
+    timing_src = "CUDA events around each launch in single-pair graph replays right after the timed region"
 
     # per-kernel durations from the event pairs of the last replays
     by_tag = {}
@@ -569,14 +599,15 @@ def run_ours(args):
                          f"DT messages), single thread, {tsec:.1f} s"}
 
     if rank == 0:
-        value = world * K / (slowest_ms * 1e-3)
+        value = world * K * P / (slowest_ms * 1e-3)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": slowest_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int16+f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}",
+            "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}", "pairs_in_flight": P,
                        "l2": "8 distinct input pairs (197 MB) rotated per step, larger than L2",
-                       "launch": "one CUDA graph replay per step"},
+                       "launch": f"one CUDA graph replay per step, {P} pairs on {P} streams"},
+            "plain": plain,
             "roofline": {"bound": "hbm", "kernel": "k_bp_sweep (level 0)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak if achieved else None, "traffic": traffic,
@@ -589,6 +620,7 @@ def run_ours(args):
             "batched": batched,
             "smooth_bp": smooth,
             "gpu_launches": launches_per_step * K,
+            "pairs_per_step": P,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
