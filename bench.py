@@ -70,6 +70,29 @@ def dist_env():
     return rank, world, local
 
 
+def slowest_over_ranks(value, device):
+    """The largest of every rank's `value` (a time), via all-reduce MAX; the
+    value itself on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(world, units_per_rank, slowest_s):
+    """Whole-job rate of `world` independent replicas: every rank's units over
+    the slowest rank's time."""
+    return world * units_per_rank / slowest_s
+
+
+def replica_seeds(rank):
+    """Scene seeds of a rank: each replica renders its own two terrain pairs."""
+    return (2 * rank, 2 * rank + 1)
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle pipeline (the reference arm and the cpu_baseline leg only)
 
@@ -400,7 +423,7 @@ def run_ours(args):
 
     # eight distinct resident pairs (197 MB > L2)
     host_pairs = []
-    for seed in (2 * rank, 2 * rank + 1):
+    for seed in replica_seeds(rank):
         l, r = synth.terrain_pair(seed)
         host_pairs.extend(synth.pair_variants(l, r))
     pairs = [(torch.from_numpy(l).to(dev), torch.from_numpy(r).to(dev)) for l, r in host_pairs]
@@ -475,11 +498,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    slowest_ms = elapsed_ms
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        slowest_ms = float(t.item())
+    slowest_ms = slowest_over_ranks(elapsed_ms, dev)
 
     # plain rate (one pair per replay) and the per-kernel event times of
     # single-pair replays, right after the timed region
@@ -539,11 +558,8 @@ def run_ours(args):
         t_e2e = time.perf_counter() - t0
         lat = sorted(pipe.latencies())
         pipe.close()
-        if world > 1:
-            t = torch.tensor([t_e2e], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        e2e = {"value": world * args.e2e_steps / t_e2e, "unit": UNIT,
+        t_e2e = slowest_over_ranks(t_e2e, dev)
+        e2e = {"value": replica_rate(world, args.e2e_steps, t_e2e), "unit": UNIT,
                "h2d_bytes_per_step": 2 * W_FULL * H_FULL * 3, "d2h_bytes_per_step": W_FULL * H_FULL * 3 * 4,
                "steps": args.e2e_steps, "api": "vs_pipeline_submit_pair (3 streams, depth 3)",
                "latency_ms_p50": lat[len(lat) // 2] if lat else None}
@@ -599,7 +615,7 @@ def run_ours(args):
                          f"DT messages), single thread, {tsec:.1f} s"}
 
     if rank == 0:
-        value = world * K * P / (slowest_ms * 1e-3)
+        value = replica_rate(world, K * P, slowest_ms * 1e-3)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": slowest_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
