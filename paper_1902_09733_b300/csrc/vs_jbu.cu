@@ -30,6 +30,11 @@ struct JbuArgs {
     float a_r;       // log2(e) / (2 sigma_r^2)
     float *disp, *xyz;
     float fx, cx, cy, fx_over_fy, baseline;
+    // scale 4: the spatial exponent of tap t (window radius <= 3, up to 49
+    // taps) for the pixel at (px, py) of its 4 x 4 block, (|p-q|^2 - |p-c|^2) a_s,
+    // at [(4 py + px) 49 + t]; in the kernel parameters, so each tap's
+    // multiply-add reads it from the constant bank
+    float sp_as[16 * 49];
 };
 
 __device__ __forceinline__ float ex2(float x)
@@ -88,10 +93,10 @@ __global__ void __launch_bounds__(kTileW *kThreadsY) k_jbu(JbuArgs a)
             for (int qx = qxa; qx <= qxb; ++qx) {
                 const uchar4 q = stage[qy - qy0][qx - qx0];
                 const float dx = pxd - (float)qx;
-                const float ds = dx * dx + dy * dy;
+                const float ds = fmaf(dx, dx, dy * dy);
                 const int dR = R - q.x, dG = Gc - q.y, dB = B - q.z;
                 const int dr = dR * dR + dG * dG + dB * dB;
-                const float k = ds * a.a_s + (float)dr * a.a_r;
+                const float k = fmaf((float)dr, a.a_r, ds * a.a_s);
                 if (k < kmin) {
                     kmin = k;
                     ds_m = ds;
@@ -106,10 +111,11 @@ __global__ void __launch_bounds__(kTileW *kThreadsY) k_jbu(JbuArgs a)
             for (int qx = qxa; qx <= qxb; ++qx) {
                 const uchar4 q = stage[qy - qy0][qx - qx0];
                 const float dx = pxd - (float)qx;
-                const float ds = dx * dx + dy * dy;
+                const float ds = fmaf(dx, dx, dy * dy);
                 const int dR = R - q.x, dG = Gc - q.y, dB = B - q.z;
                 const int dr = dR * dR + dG * dG + dB * dB;
-                const float e = (ds - ds_m) * a.a_s + (float)(dr - dr_m) * a.a_r;
+                // explicit fmaf: every instantiation rounds the same way
+                const float e = fmaf((float)(dr - dr_m), a.a_r, (ds - ds_m) * a.a_s);
                 const float wgt = ex2(-e);
                 num = fmaf(wgt, (float)q.w, num);
                 den += wgt;
@@ -219,11 +225,8 @@ __global__ void __launch_bounds__(kS4CentresX *kS4CentresY, 4) k_jbu_s4(JbuArgs 
             for (int j = 0; j < D; ++j) {
 #pragma unroll
                 for (int i = 0; i < D; ++i) {
-                    const float ox = (px + 0.5f) * 0.25f - 0.5f, oy = (py + 0.5f) * 0.25f - 0.5f;
-                    const float dx = ox - (float)(i - R), dy = oy - (float)(j - R);
-                    const float sp = (dx * dx + dy * dy) - (ox * ox + oy * oy);   // exact, compile time
                     const int t = j * D + i;
-                    const float e = fmaf((float)(v[t] - vmin), a.a_r, sp * a.a_s);
+                    const float e = fmaf((float)(v[t] - vmin), a.a_r, a.sp_as[(4 * py + px) * 49 + t]);
                     const float wgt = ex2(-e);
                     num = fmaf(wgt, tl[t], num);
                     den += wgt;
@@ -351,6 +354,23 @@ int jbu_common(const uint8_t *labels, int w, int h, int labels_pitch, const uint
     a.cy = cam ? cam->cy : 0.0f;
     a.fx_over_fy = cam ? cam->fx / cam->fy : 0.0f;
     a.baseline = baseline;
+    // spatial exponents of the scale-4 windows: p_down - q = (ox - (i - r), oy - (j - r)),
+    // (ox, oy) = ((px + 0.5) / 4 - 0.5, (py + 0.5) / 4 - 0.5); the squared distances are
+    // exact in FP32 and the product with a_s rounds as it would on the device
+    for (int k = 0; k < 16 * 49; ++k)
+        a.sp_as[k] = 0.0f;
+    if (s == 4 && a.r <= 3) {
+        const int D = 2 * a.r + 1;
+        for (int py = 0; py < 4; ++py)
+            for (int px = 0; px < 4; ++px)
+                for (int j = 0; j < D; ++j)
+                    for (int i = 0; i < D; ++i) {
+                        const float ox = (px + 0.5f) * 0.25f - 0.5f, oy = (py + 0.5f) * 0.25f - 0.5f;
+                        const float dx = ox - (float)(i - a.r), dy = oy - (float)(j - a.r);
+                        const float sp = (dx * dx + dy * dy) - (ox * ox + oy * oy);
+                        a.sp_as[(4 * py + px) * 49 + j * D + i] = sp * a.a_s;
+                    }
+    }
     dim3 grid((W + kTileW - 1) / kTileW, (H + kTileH - 1) / kTileH);
     dim3 block(kTileW, kThreadsY);
     // the scale-4 kernel needs whole 4-pixel groups on every row and
