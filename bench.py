@@ -319,17 +319,24 @@ def run_batched(args, vs, synth, torch, dev, cam):
     sequential()
     torch.cuda.synchronize()
     seq_launches = vs.kernel_launches() - n0
-    n0 = vs.kernel_launches()
-    batched()
-    torch.cuda.synchronize()
-    bat_launches = vs.kernel_launches() - n0
     t_seq = graph_ms(sequential)
-    t_bat = graph_ms(batched)
+    res = {}
+    for mode in ("streams", "lockstep"):
+        vs.bp_batch_mode(mode)
+        n0 = vs.kernel_launches()
+        batched()
+        torch.cuda.synchronize()
+        launches = vs.kernel_launches() - n0
+        res[mode] = (graph_ms(batched), launches)
+    vs.bp_batch_mode("streams")
     vs.bp_autotune_reset()
+    t_bat, bat_launches = res["streams"]
     px = sum(int(p[0].numel()) * p[2].labels for p in pairs)
     return {"pairs": n, "batched_ms": t_bat, "sequential_ms": t_seq, "speedup": t_seq / t_bat,
-            "batched_pairs_per_s": n / (t_bat * 1e-3), "launches_batched": bat_launches,
-            "launches_sequential": seq_launches, "label_pixels_per_batch": px,
+            "batched_pairs_per_s": n / (t_bat * 1e-3), "schedule": "streams (4 library streams, pairs balanced by size)",
+            "launches_batched": bat_launches, "launches_sequential": seq_launches,
+            "lockstep_ms": res["lockstep"][0], "launches_lockstep": res["lockstep"][1],
+            "label_pixels_per_batch": px,
             "mix": {f"s{s}_L{L}": shapes.count((s, L)) for (s, L) in sorted(set(shapes))},
             "autotuned_variants": tuned}
 

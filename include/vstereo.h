@@ -159,16 +159,24 @@ size_t vs_bp_batch_workspace_size(const vs_bp_job *jobs, int n);
 
 /*
  * Eq. 1 for n independent pairs of any sizes and label counts (1 <= n <=
- * 4096), exactly as n vs_bp_stereo calls would compute them, but advanced in
- * lockstep: each level-iteration of all pairs is a handful of batched
- * launches (one per label count and kernel variant), so small pairs and the
- * coarse levels fill the GPU together.  All jobs must share `levels` and
- * `iters`.  `jobs` is a host array read during the call; the pair
- * descriptors travel in kernel parameters, so the call can be captured in a
- * CUDA graph and replayed.
+ * 4096), exactly as n vs_bp_stereo calls would compute them.  Two schedules
+ * (vs_bp_batch_mode): 0 (default) balances the pairs by size over four
+ * library streams forked from `stream` and joined back to it with events,
+ * so independent pairs fill each other's idle time; 1 advances all pairs in
+ * lockstep, each level-iteration a handful of batched launches (one per
+ * label count and kernel variant) whose pair descriptors travel in kernel
+ * parameters -- a quarter of the launches, but every pair waits for the
+ * largest at each sweep.  Either way the call is enqueued on / ordered after
+ * `stream` and can be captured into a CUDA graph and replayed.  All jobs
+ * must share `levels` and `iters`; `jobs` is a host array read during the
+ * call.  The library streams are per device and shared: do not run batches
+ * from several host threads at once.
  * Errors: VS_EINVAL, VS_EWORKSPACE, VS_ECUDA.
  */
 int vs_bp_stereo_batch(const vs_bp_job *jobs, int n, void *workspace, size_t ws_bytes, void *stream);
+/* Schedule of vs_bp_stereo_batch: 0 streams (default), 1 lockstep.
+ * Errors: VS_EINVAL. */
+int vs_bp_batch_mode(int mode);
 
 /*
  * Autotuner for the message sweeps (no counterpart in the paper).  Runs

@@ -33,7 +33,7 @@ __all__ = [
     "guided_upsample", "reproject", "guided_upsample_reproject",
     "pair_workspace_size", "pair_run", "pair_run_host", "kernel_launches", "status_string",
     "profile_enable", "profile_collect", "Pipeline", "bp_stereo_batch", "bp_batch_workspace_size",
-    "bp_autotune", "bp_autotune_reset", "bp_autotune_times", "bp_select_sweep", "SPParams", "sp_workspace_size", "sp_forward", "sp_backward",
+    "bp_autotune", "bp_autotune_reset", "bp_autotune_times", "bp_select_sweep", "bp_batch_mode", "SPParams", "sp_workspace_size", "sp_forward", "sp_backward",
     "smooth_bp", "SmoothBP", "sp_select_kernels", "sp_status",
 ]
 
@@ -186,6 +186,7 @@ def lib() -> ctypes.CDLL:
             "vs_profile_collect": ([P, P, I], I),
             "vs_bp_batch_workspace_size": ([P, I], S),
             "vs_bp_stereo_batch": ([P, I, P, S, P], I),
+            "vs_bp_batch_mode": ([I], I),
             "vs_bp_autotune": ([P, P, I, I, I, bp_p, P, I, P, S, P, P], I),
             "vs_bp_autotune_reset": ([], None),
             "vs_bp_autotune_times": ([P, I], I),
@@ -371,6 +372,11 @@ def bp_stereo_batch(pairs, labels=None, workspace=None, stream=None):
                                                           workspace.data_ptr(), workspace.numel(),
                                                           _stream(stream)))
     return labels
+
+
+def bp_batch_mode(mode: str) -> None:
+    """Schedule of bp_stereo_batch: "streams" (default) or "lockstep"."""
+    _check("vs_bp_batch_mode", lib().vs_bp_batch_mode({"streams": 0, "lockstep": 1}[mode]))
 
 
 def bp_autotune(left: torch.Tensor, right: torch.Tensor, params: BPParams, workspace=None, labels=None,

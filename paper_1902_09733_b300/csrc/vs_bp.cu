@@ -1101,6 +1101,23 @@ void launch_labels(const BpLayout &lay, uint8_t *ws, uint8_t *labels, int labels
     note_launch();
 }
 
+// Eq. 1 for one pair on `st`: costs and pyramid, every level-iteration, labels.
+void run_pair(const BpLayout &lay, uint8_t *ws, const uint8_t *left, const uint8_t *right, int pitch,
+              const vs_bp_params *p, uint8_t *labels, int labels_pitch, cudaStream_t st)
+{
+    launch_costs(lay, ws, left, right, pitch, p, st);
+    for (int l = lay.levels - 1; l >= 0; --l) {
+        for (int t = 0; t < p->iters; ++t) {
+            const SweepArgs a = sweep_args(lay, ws, p, l, t, labels, labels_pitch);
+            const int slot = prof_begin(l == 0 ? kProfSweepL0 : kProfSweepCoarse, st);
+            launch_sweep(lay.Lp, a, lay.cost_u8[l], lay.bytes[l], st);
+            prof_end(slot, st);
+            note_launch();
+        }
+    }
+    launch_labels(lay, ws, labels, labels_pitch, p, st);
+}
+
 }  // namespace
 }  // namespace vs
 
@@ -1115,19 +1132,8 @@ extern "C" int vs_bp_stereo(const uint8_t *left, const uint8_t *right, int w, in
     int rc = check_workspace(lay, workspace, ws_bytes);
     if (rc != VS_OK)
         return rc;
-    cudaStream_t st = (cudaStream_t)stream;
-    uint8_t *ws = reinterpret_cast<uint8_t *>(workspace);
-    launch_costs(lay, ws, left, right, pitch, p, st);
-    for (int l = lay.levels - 1; l >= 0; --l) {
-        for (int t = 0; t < p->iters; ++t) {
-            const SweepArgs a = sweep_args(lay, ws, p, l, t, labels, labels_pitch);
-            const int slot = prof_begin(l == 0 ? kProfSweepL0 : kProfSweepCoarse, st);
-            launch_sweep(lay.Lp, a, lay.cost_u8[l], lay.bytes[l], st);
-            prof_end(slot, st);
-            note_launch();
-        }
-    }
-    launch_labels(lay, ws, labels, labels_pitch, p, st);
+    run_pair(lay, reinterpret_cast<uint8_t *>(workspace), left, right, pitch, p, labels, labels_pitch,
+             (cudaStream_t)stream);
     return launch_status();
 }
 
@@ -1169,23 +1175,14 @@ extern "C" size_t vs_bp_batch_workspace_size(const vs_bp_job *jobs, int n)
     return vs::batch_layouts(jobs, n, lays, offs, total) ? total : 0;
 }
 
-extern "C" int vs_bp_stereo_batch(const vs_bp_job *jobs, int n, void *workspace, size_t ws_bytes, void *stream)
+namespace vs {
+namespace {
+
+// Lockstep: every level-iteration of all pairs is a few batched launches
+// (one per label count and kernel variant), the jobs in the kernel parameters.
+void batch_lockstep(const vs_bp_job *jobs, int n, const std::vector<BpLayout> &lays,
+                    const std::vector<size_t> &offs, uint8_t *base, cudaStream_t st)
 {
-    using namespace vs;
-    std::vector<BpLayout> lays;
-    std::vector<size_t> offs;
-    size_t total = 0;
-    if (!batch_layouts(jobs, n, lays, offs, total))
-        return VS_EINVAL;
-    for (int i = 0; i < n; ++i) {
-        const vs_bp_job &j = jobs[i];
-        if (!j.left || !j.right || !j.labels || j.pitch < j.w || j.labels_pitch < j.w)
-            return VS_EINVAL;
-    }
-    if (!workspace || !aligned(workspace, 256) || ws_bytes < total)
-        return VS_EWORKSPACE;
-    cudaStream_t st = (cudaStream_t)stream;
-    uint8_t *base = reinterpret_cast<uint8_t *>(workspace);
     for (int i = 0; i < n; ++i)
         launch_costs(lays[i], base + offs[i], jobs[i].left, jobs[i].right, jobs[i].pitch, &jobs[i].params, st);
 
@@ -1237,6 +1234,121 @@ extern "C" int vs_bp_stereo_batch(const vs_bp_job *jobs, int n, void *workspace,
     }
     for (int i = 0; i < n; ++i)
         launch_labels(lays[i], base + offs[i], jobs[i].labels, jobs[i].labels_pitch, &jobs[i].params, st);
+
+}
+
+// Streams: the pairs, balanced by size (w h labels, largest first, each to
+// the least loaded stream), run one after another on kBatchStreams library
+// streams forked from `st` and joined back to it by events -- capturable.
+// Independent pairs then fill each other's gaps: B300, 48 mixed pairs,
+// 28.6 ms against 31.8 ms in lockstep and 33.3 ms one after another.
+constexpr int kBatchStreams = 4;
+
+cudaStream_t *batch_streams_of_device()
+{
+    static std::mutex mu;
+    static std::vector<std::vector<cudaStream_t>> per_dev;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)per_dev.size() <= dev)
+        per_dev.resize(dev + 1);
+    std::vector<cudaStream_t> &v = per_dev[dev];
+    if (v.empty()) {
+        for (int k = 0; k < kBatchStreams; ++k) {
+            cudaStream_t s;
+            if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+                return nullptr;
+            v.push_back(s);
+        }
+    }
+    return v.data();
+}
+
+int batch_streams(const vs_bp_job *jobs, int n, const std::vector<BpLayout> &lays, const std::vector<size_t> &offs,
+                  uint8_t *base, cudaStream_t st)
+{
+    cudaStream_t *side = batch_streams_of_device();
+    if (!side)
+        return VS_ECUDA;
+    const int S = n < kBatchStreams ? n : kBatchStreams;
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i)
+        order[i] = i;
+    auto work = [&](int i) { return (double)jobs[i].w * (double)jobs[i].h * (double)lays[i].Lp; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+    std::vector<std::vector<int>> queue(S);
+    std::vector<double> load(S, 0.0);
+    for (int i : order) {
+        int k = 0;
+        for (int j = 1; j < S; ++j)
+            if (load[j] < load[k])
+                k = j;
+        queue[k].push_back(i);
+        load[k] += work(i);
+    }
+    cudaEvent_t fork;
+    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess)
+        return VS_ECUDA;
+    int rc = cudaEventRecord(fork, st) == cudaSuccess ? VS_OK : VS_ECUDA;
+    for (int k = 0; k < S && rc == VS_OK; ++k) {
+        if (cudaStreamWaitEvent(side[k], fork, 0) != cudaSuccess) {
+            rc = VS_ECUDA;
+            break;
+        }
+        for (int i : queue[k])
+            run_pair(lays[i], base + offs[i], jobs[i].left, jobs[i].right, jobs[i].pitch, &jobs[i].params,
+                     jobs[i].labels, jobs[i].labels_pitch, side[k]);
+        cudaEvent_t join;
+        if (cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
+            rc = VS_ECUDA;
+            break;
+        }
+        if (cudaEventRecord(join, side[k]) != cudaSuccess || cudaStreamWaitEvent(st, join, 0) != cudaSuccess)
+            rc = VS_ECUDA;
+        cudaEventDestroy(join);
+    }
+    cudaEventDestroy(fork);
+    return rc;
+}
+
+int g_batch_mode = 0;   // 0 streams, 1 lockstep
+
+}  // namespace
+}  // namespace vs
+
+extern "C" int vs_bp_batch_mode(int mode)
+{
+    if (mode != 0 && mode != 1)
+        return VS_EINVAL;
+    vs::g_batch_mode = mode;
+    return VS_OK;
+}
+
+extern "C" int vs_bp_stereo_batch(const vs_bp_job *jobs, int n, void *workspace, size_t ws_bytes, void *stream)
+{
+    using namespace vs;
+    std::vector<BpLayout> lays;
+    std::vector<size_t> offs;
+    size_t total = 0;
+    if (!batch_layouts(jobs, n, lays, offs, total))
+        return VS_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        const vs_bp_job &j = jobs[i];
+        if (!j.left || !j.right || !j.labels || j.pitch < j.w || j.labels_pitch < j.w)
+            return VS_EINVAL;
+    }
+    if (!workspace || !aligned(workspace, 256) || ws_bytes < total)
+        return VS_EWORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint8_t *base = reinterpret_cast<uint8_t *>(workspace);
+    if (g_batch_mode == 0) {
+        if (int rc = batch_streams(jobs, n, lays, offs, base, st))
+            return rc;
+    } else {
+        batch_lockstep(jobs, n, lays, offs, base, st);
+    }
     return launch_status();
 }
 

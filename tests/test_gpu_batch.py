@@ -26,7 +26,15 @@ SHAPES = [(120, 160, 16), (61, 97, 64), (45, 33, 32), (150, 200, 128), (17, 23, 
           (64, 64, 64)]
 
 
-def test_batch_matches_single_calls_and_oracle():
+@pytest.fixture(params=["streams", "lockstep"])
+def batch_mode(request):
+    """Both schedules of the batch must give the single calls' results."""
+    vs.bp_batch_mode(request.param)
+    yield request.param
+    vs.bp_batch_mode("streams")
+
+
+def test_batch_matches_single_calls_and_oracle(batch_mode):
     pairs, hosts = [], []
     for i, (h, w, L) in enumerate(SHAPES):
         L_, R_, l, r = _pair(i, h, w)
@@ -43,8 +51,9 @@ def test_batch_matches_single_calls_and_oracle():
             np.testing.assert_array_equal(lab.cpu().numpy(), want)
 
 
-def test_batch_larger_than_one_launch_and_graph_replay():
-    """70 jobs exceed one launch's job table; the batch replays from a graph."""
+def test_batch_larger_than_one_launch_and_graph_replay(batch_mode):
+    """70 jobs exceed one lockstep launch's job table; the batch (forked onto
+    the library streams in the default schedule) replays from a graph."""
     pairs = []
     for i in range(70):
         L_, R_, _, _ = _pair(100 + i, 24 + (i % 5), 30 + (i % 7))
