@@ -77,7 +77,9 @@ typedef struct {
  * (R9 = row-major 3x3 rectifying rotation, host pointer, NULL = identity, as
  * when the extrinsics are ignored), distorted by 1 + k1 r^2 + k2 r^4 and
  * mapped back through (fx, fy, cx, cy); the source is sampled bilinearly per
- * channel (taps outside the frame read 0), rounded half to even and clamped.
+ * channel (taps outside the frame read 0) with the weights quantised to
+ * 1/4096, rounded half up and clamped: within 0.06 of the exact bilinear
+ * value before rounding, so within 1 of the exactly rounded byte.
  * Rays with a non-positive depth after the rotation give 0.  Arithmetic is
  * FP32.  Optionally the same kernel writes the low-resolution RGB
  * (ceil(W/s) x ceil(H/s), mean of the in-frame pixels of each s x s block,

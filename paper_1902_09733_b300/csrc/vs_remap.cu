@@ -3,9 +3,11 @@
 // One CTA owns a tile of TLW x TLH low-resolution pixels, i.e. an aligned
 // block of (TLW s) x (TLH s) full-resolution pixels.  Each thread maps its
 // destination pixels through the radial lens model (FP32), samples the
-// source bilinearly, rounds, writes the full-resolution RGB and keeps a copy
-// in shared memory; the CTA then reduces every s x s block to the low-res RGB
-// mean and its grey.  One launch per frame, no intermediate buffers.
+// source bilinearly in fixed point (weights in 1/4096: a two-term dot
+// product per row and channel, no byte-to-float conversions), rounds, writes
+// the full-resolution RGB and keeps a copy in shared memory; the CTA then
+// reduces every s x s block to the low-res RGB mean and its grey.  One
+// launch per frame, no intermediate buffers.
 #include "vs_common.cuh"
 
 namespace vs {
@@ -58,7 +60,7 @@ __global__ void __launch_bounds__(kRemapThreads) k_remap_down(RemapArgs a)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int lu = lu0 + q, u = u0 + lu;
-            float val[3] = {0.0f, 0.0f, 0.0f};
+            int ival[3] = {0, 0, 0};   // rounded sample; 0 for rays that miss the frame
             if (lu < tfw && u < a.W && v < a.H) {
                 float xn = ((float)u - a.cx) * a.inv_fx;
                 float yn = ((float)v - a.cy) * a.inv_fy;
@@ -83,6 +85,9 @@ __global__ void __launch_bounds__(kRemapThreads) k_remap_down(RemapArgs a)
                         const float fx0 = floorf(sx), fy0 = floorf(sy);
                         const int x0 = (int)fx0, y0 = (int)fy0;
                         const float ax = sx - fx0, ay = sy - fy0;
+                        // the two taps of each row per channel, packed as (R0 R1 G0 G1) and
+                        // (B0 B1 . .), top row t_*, bottom row b_*; taps outside the frame are 0
+                        uint32_t t_rg, t_b, b_rg, b_b;
                         if (x0 >= 0 && y0 >= 0 && x0 + 2 < a.W && y0 + 1 < a.H && a.src_words) {
                             // all four taps in the frame, and the aligned words that
                             // cover each row's 6 bytes end inside that row: 4 to 6 loads
@@ -99,49 +104,44 @@ __global__ void __launch_bounds__(kRemapThreads) k_remap_down(RemapArgs a)
                             const uint32_t s_hi = o | ((o + 1) << 4);
                             const uint32_t r0a = prmt(a0, a1, s_lo), r0b = prmt(a1, a2, s_hi);
                             const uint32_t r1a = prmt(b0, b1, s_lo), r1b = prmt(b1, b2, s_hi);
-                            const uint32_t top6[2] = {r0a, r0b}, bot6[2] = {r1a, r1b};
-#pragma unroll
-                            for (int ch = 0; ch < 3; ++ch) {
-                                const int k0 = ch, k1 = ch + 3;   // byte of the left / right tap
-                                const float t00 = (float)((top6[k0 >> 2] >> (8 * (k0 & 3))) & 0xFFu);
-                                const float t10 = (float)((top6[k1 >> 2] >> (8 * (k1 & 3))) & 0xFFu);
-                                const float t01 = (float)((bot6[k0 >> 2] >> (8 * (k0 & 3))) & 0xFFu);
-                                const float t11 = (float)((bot6[k1 >> 2] >> (8 * (k1 & 3))) & 0xFFu);
-                                const float top = fmaf(ax, t10 - t00, t00);
-                                const float bot = fmaf(ax, t11 - t01, t01);
-                                val[ch] = fmaf(ay, bot - top, top);
-                            }
-                        } else if (x0 >= 0 && y0 >= 0 && x0 + 1 < a.W && y0 + 1 < a.H) {
-                            // all four taps in the frame: one base address, two rows of 6 bytes
-                            const uint8_t *p0 = a.src + (size_t)y0 * a.src_pitch + 3 * x0;
-                            const uint8_t *p1 = p0 + a.src_pitch;
-#pragma unroll
-                            for (int ch = 0; ch < 3; ++ch) {
-                                const float t00 = (float)__ldg(p0 + ch), t10 = (float)__ldg(p0 + 3 + ch);
-                                const float t01 = (float)__ldg(p1 + ch), t11 = (float)__ldg(p1 + 3 + ch);
-                                const float top = fmaf(ax, t10 - t00, t00);
-                                const float bot = fmaf(ax, t11 - t01, t01);
-                                val[ch] = fmaf(ay, bot - top, top);
-                            }
+                            t_rg = prmt(r0a, r0b, 0x4130u), t_b = prmt(r0a, r0b, 0x0052u);
+                            b_rg = prmt(r1a, r1b, 0x4130u), b_b = prmt(r1a, r1b, 0x0052u);
                         } else {
-                            const float w00 = (1.0f - ax) * (1.0f - ay), w10 = ax * (1.0f - ay);
-                            const float w01 = (1.0f - ax) * ay, w11 = ax * ay;
+                            // byte loads, with frame checks where a tap may be outside
+                            uint32_t tq[2][2][3];   // [row][column][channel]
 #pragma unroll
-                            for (int ch = 0; ch < 3; ++ch) {
-                                val[ch] = w00 * tap(a.src, a.src_pitch, a.W, a.H, x0, y0, ch)
-                                        + w10 * tap(a.src, a.src_pitch, a.W, a.H, x0 + 1, y0, ch)
-                                        + w01 * tap(a.src, a.src_pitch, a.W, a.H, x0, y0 + 1, ch)
-                                        + w11 * tap(a.src, a.src_pitch, a.W, a.H, x0 + 1, y0 + 1, ch);
-                            }
+                            for (int jy = 0; jy < 2; ++jy)
+#pragma unroll
+                                for (int jx = 0; jx < 2; ++jx)
+#pragma unroll
+                                    for (int ch = 0; ch < 3; ++ch)
+                                        tq[jy][jx][ch] = (uint32_t)tap(a.src, a.src_pitch, a.W, a.H, x0 + jx, y0 + jy, ch);
+                            t_rg = tq[0][0][0] | (tq[0][1][0] << 8) | (tq[0][0][1] << 16) | (tq[0][1][1] << 24);
+                            t_b = tq[0][0][2] | (tq[0][1][2] << 8);
+                            b_rg = tq[1][0][0] | (tq[1][1][0] << 8) | (tq[1][0][1] << 16) | (tq[1][1][1] << 24);
+                            b_b = tq[1][0][2] | (tq[1][1][2] << 8);
+                        }
+                        // fixed-point bilinear blend: weights in 1/4096, each row's two taps
+                        // per channel in one 16 x 8-bit two-term dot product, the rows in
+                        // 32-bit integers; within 0.06 of the exact value before rounding
+                        const uint32_t axq = (uint32_t)__float2int_rn(ax * 4096.0f);
+                        const uint32_t ayq = (uint32_t)__float2int_rn(ay * 4096.0f);
+                        const uint32_t wx = (axq << 16) | (4096u - axq);   // (left, right) tap weights
+                        const uint32_t top[3] = {__dp2a_lo(wx, t_rg, 0u), __dp2a_hi(wx, t_rg, 0u),
+                                                 __dp2a_lo(wx, t_b, 0u)};
+                        const uint32_t bot[3] = {__dp2a_lo(wx, b_rg, 0u), __dp2a_hi(wx, b_rg, 0u),
+                                                 __dp2a_lo(wx, b_b, 0u)};
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) {
+                            const uint32_t vv = top[ch] * (4096u - ayq) + bot[ch] * ayq;   // < 2^32
+                            ival[ch] = (int)((vv + (1u << 23)) >> 24);   // round half up
                         }
                     }
                 }
             }
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                const int r = __float2int_rn(val[ch]);   // round half to even
-                out[3 * q + ch] = (uint8_t)min(max(r, 0), 255);
-            }
+            for (int ch = 0; ch < 3; ++ch)
+                out[3 * q + ch] = (uint8_t)min(max(ival[ch], 0), 255);
         }
         if (v >= a.H)
             continue;
