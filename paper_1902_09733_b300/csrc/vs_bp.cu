@@ -15,8 +15,9 @@
 //   Messages live in [0, smooth_trunc] after normalisation, so 8 bits hold
 //   them exactly; all message arithmetic is integer.
 //
-// Kernels per call: k_cost0 (level-0 data term), k_cost_down per coarse
-// level, one k_bp_sweep per iteration and level, k_bp_labels.
+// Kernels per call: k_cost01 (level-0 data term and its level-1 sums),
+// k_cost_down per further coarse level, one k_bp_sweep per iteration and
+// level, k_bp_labels.
 //
 // k_bp_sweep: two threads per active pixel, each owning a pair of outgoing
 // directions (left/right or up/down).  A thread packs the pair into the two
@@ -139,36 +140,23 @@ __device__ __forceinline__ void st_piece_keep(uint8_t *base, int p, const uint4 
 // ---------------------------------------------------------------------------
 // data term
 
-struct Cost0Args {
+struct Cost01Args {
     const uint8_t *left, *right;
-    int pitch, w, h, wh, wg, L, Lp, Td;
-    uint8_t *cost;
+    int pitch, L, Lp, Td;
+    int w0, h0, wg0;        // level 0
+    int w1, h1, wg1;        // level 1 (its size even when levels == 1)
+    uint8_t *cost0;
+    uint8_t *cost1;         // null when there is no level 1
+    int cost1_u8;
 };
 
-// D0(x, y, d) = min(|IL(x,y) - IR(x-d,y)|, Td), Td where x - d < 0; 16 labels
-// per thread, padding labels hold 0.
-__global__ void k_cost0(Cost0Args a)
+// D0(x, y, d) = min(|IL(x,y) - IR(x-d,y)|, Td), Td where x - d < 0, 0 on
+// padding labels, for labels 16 j .. 16 j + 15 of pixel (x, y); also added
+// into acc (8 words of 2 x u16, label k in half k & 1 of word k >> 1).
+// Byte loads: the left edge, the right edge, the last label chunk.
+__device__ __forceinline__ uint4 cost0_chunk_slow(const Cost01Args &a, const uint8_t *rowL, const uint8_t *rowR,
+                                                  int x, int j, uint32_t (&acc)[8])
 {
-    pdl_begin();
-    // threads in memory order: (row, group, piece j, slot in group)
-    const unsigned chunks = (unsigned)a.Lp / 16u;
-    const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= 2u * a.h * a.wg * chunks * 16u)
-        return;
-    const int lane = (int)(idx & 15u);
-    unsigned t = idx >> 4;
-    const int j = (int)(t % chunks);
-    t /= chunks;
-    const int g = (int)(t % (unsigned)a.wg);
-    const unsigned row = t / (unsigned)a.wg;
-    const int y = (int)(row % (unsigned)a.h);
-    const int c = (int)(row / (unsigned)a.h);
-    const int xh = 16 * g + lane;
-    const int x = 2 * xh + ((c + y) & 1);
-    if (x >= a.w)
-        return;
-    const uint8_t *rowL = a.left + (size_t)y * a.pitch;
-    const uint8_t *rowR = a.right + (size_t)y * a.pitch;
     const int il = __ldg(rowL + x);
     uint32_t wv[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -181,8 +169,101 @@ __global__ void k_cost0(Cost0Args a)
                 v = min(abs(il - (int)__ldg(rowR + x - d)), a.Td);
         }
         wv[i >> 2] |= (uint32_t)v << (8 * (i & 3));
+        acc[i >> 1] += (uint32_t)v << (16 * (i & 1));
     }
-    st_piece(a.cost + slot_base((int)row, xh, a.wg, (int)chunks), j, make_uint4(wv[0], wv[1], wv[2], wv[3]));
+    return make_uint4(wv[0], wv[1], wv[2], wv[3]);
+}
+
+// Level-0 data term and its level-1 2x2 sums in one pass.  A thread owns the
+// level-1 pixel (X, Y) and 16 labels; its children (2X+i, 2Y+j) have colour
+// (i+j) & 1 and level-0 column slot X, so a warp of 32 consecutive X writes
+// whole 256-byte blocks on both levels.  Inside the frame the 17 right-image
+// bytes that the two children of a row need are 5 aligned words, shifted into
+// place with funnel shifts; per 4 labels one byte permute reverses them, one
+// SIMD absolute difference forms |IL - IR|, and the truncation runs on 2 x u16
+// lanes (no byte-lane minimum in hardware).
+__global__ void __launch_bounds__(128) k_cost01(Cost01Args a)
+{
+    pdl_begin();
+    const int chunks = a.Lp / 16;
+    const int nxb = (a.w1 + 31) / 32;
+    const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned t = idx >> 5;
+    const int j = (int)(t % (unsigned)chunks);
+    t /= (unsigned)chunks;
+    const int X = 32 * (int)(t % (unsigned)nxb) + (int)(idx & 31u);
+    const int Y = (int)(t / (unsigned)nxb);
+    if (Y >= a.h1 || X >= a.w1)
+        return;
+    uint32_t acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const uint32_t td2 = (uint32_t)a.Td * 0x00010001u;
+    const int s0 = 2 * X - 16 * j - 15;   // first right-image column of the row window
+    // fast: both children in the frame, a full label chunk, and the 20 bytes
+    // of the aligned words inside the row
+    const bool fast = 2 * X + 1 < a.w0 && 16 * j + 15 < a.L && s0 >= 3 && s0 + 20 <= a.w0;
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
+        const int yf = 2 * Y + jj;
+        if (yf >= a.h0)
+            break;
+        const uint8_t *rowL = a.left + (size_t)yf * a.pitch;
+        const uint8_t *rowR = a.right + (size_t)yf * a.pitch;
+        uint4 out[2];
+        if (fast) {
+            // bytes s0 .. s0 + 16 of the row: W[k] = bytes s0 + 4k .. s0 + 4k + 3
+            const uintptr_t addr = reinterpret_cast<uintptr_t>(rowR + s0);
+            const uint32_t *q = reinterpret_cast<const uint32_t *>(addr & ~(uintptr_t)3);
+            const uint32_t sh = 8u * (uint32_t)(addr & 3u);
+            uint32_t w[5], W[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k)
+                w[k] = __ldg(q + k);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                W[k] = __funnelshift_r(w[k], w[k + 1], sh);
+            W[4] = w[4] >> sh;
+            const uint32_t il2 = (uint32_t)__ldg(reinterpret_cast<const uint8_t *>(rowL + 2 * X)) |
+                                 ((uint32_t)__ldg(rowL + 2 * X + 1) << 8);
+#pragma unroll
+            for (int ii = 0; ii < 2; ++ii) {
+                const uint32_t il4 = ((il2 >> (8 * ii)) & 0xFFu) * 0x01010101u;
+                uint32_t wv[4];
+#pragma unroll
+                for (int qd = 0; qd < 4; ++qd) {
+                    // labels 16j + 4qd + r sit at window offsets 15 + ii - 4qd - r
+                    const uint32_t rev = ii == 0 ? prmt(W[3 - qd], 0u, 0x0123u) : prmt(W[3 - qd], W[4 - qd], 0x1234u);
+                    const uint32_t ad = __vabsdiffu4(il4, rev);
+                    const uint32_t lo = min_u16x2(prmt(ad, 0u, 0x4140u), td2);
+                    const uint32_t hi = min_u16x2(prmt(ad, 0u, 0x4342u), td2);
+                    wv[qd] = prmt(lo, hi, 0x6420u);
+                    acc[2 * qd] += lo;
+                    acc[2 * qd + 1] += hi;
+                }
+                out[ii] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+            }
+        } else {
+#pragma unroll
+            for (int ii = 0; ii < 2; ++ii)
+                if (2 * X + ii < a.w0)
+                    out[ii] = cost0_chunk_slow(a, rowL, rowR, 2 * X + ii, j, acc);
+        }
+#pragma unroll
+        for (int ii = 0; ii < 2; ++ii)
+            if (2 * X + ii < a.w0)
+                st_piece(a.cost0 + slot_base(((ii + jj) & 1) * a.h0 + yf, X, a.wg0, chunks), j, out[ii]);
+    }
+    if (!a.cost1)
+        return;
+    const int row1 = ((X + Y) & 1) * a.h1 + Y;
+    if (a.cost1_u8) {   // every sum is <= 4 Td <= 255 here
+        st_piece(a.cost1 + slot_base(row1, X >> 1, a.wg1, chunks), j,
+                 make_uint4(prmt(acc[0], acc[1], 0x6420u), prmt(acc[2], acc[3], 0x6420u),
+                            prmt(acc[4], acc[5], 0x6420u), prmt(acc[6], acc[7], 0x6420u)));
+    } else {
+        uint8_t *b = a.cost1 + slot_base(row1, X >> 1, a.wg1, 2 * chunks);
+        st_piece(b, 2 * j, make_uint4(acc[0], acc[1], acc[2], acc[3]));
+        st_piece(b, 2 * j + 1, make_uint4(acc[4], acc[5], acc[6], acc[7]));
+    }
 }
 
 struct CostDownArgs {
@@ -1056,17 +1137,31 @@ namespace {
 void launch_costs(const BpLayout &lay, uint8_t *ws, const uint8_t *left, const uint8_t *right, int pitch,
                   const vs_bp_params *p, cudaStream_t st)
 {
-    const int block = 256;
     {
-        Cost0Args a{left, right, pitch, lay.w[0], lay.h[0], lay.wh[0], lay.wg[0], lay.L, lay.Lp, p->data_trunc,
-                    ws + lay.cost_off[0]};
-        const long long n = 2LL * lay.h[0] * lay.wg[0] * 16 * (lay.Lp / 16);
+        Cost01Args a;
+        a.left = left;
+        a.right = right;
+        a.pitch = pitch;
+        a.L = lay.L;
+        a.Lp = lay.Lp;
+        a.Td = p->data_trunc;
+        a.w0 = lay.w[0];
+        a.h0 = lay.h[0];
+        a.wg0 = lay.wg[0];
+        a.w1 = (lay.w[0] + 1) / 2;
+        a.h1 = (lay.h[0] + 1) / 2;
+        a.wg1 = lay.levels > 1 ? lay.wg[1] : 0;
+        a.cost0 = ws + lay.cost_off[0];
+        a.cost1 = lay.levels > 1 ? ws + lay.cost_off[1] : nullptr;
+        a.cost1_u8 = lay.levels > 1 ? lay.cost_u8[1] : 1;
+        const long long n = (long long)a.h1 * ((a.w1 + 31) / 32) * (lay.Lp / 16) * 32;
         const int slot = prof_begin(kProfBpOther, st);
-        launch_pdl(k_cost0, dim3((unsigned)((n + block - 1) / block)), dim3(block), st, a);
+        launch_pdl(k_cost01, dim3((unsigned)((n + 127) / 128)), dim3(128), st, a);
         prof_end(slot, st);
         note_launch();
     }
-    for (int l = 1; l < lay.levels; ++l) {
+    const int block = 256;
+    for (int l = 2; l < lay.levels; ++l) {
         CostDownArgs a;
         a.fine = ws + lay.cost_off[l - 1];
         a.coarse = ws + lay.cost_off[l];

@@ -37,6 +37,14 @@ struct JbuArgs {
     float sp_as[16 * 49];
 };
 
+// 0 <= n < 2^23 as a float: n added into the mantissa of 2^23, minus 2^23
+// (exact; an integer add and a float add instead of a quarter-rate
+// conversion)
+__device__ __forceinline__ float exact_float(int n)
+{
+    return __int_as_float(0x4B000000 + n) - 8388608.0f;
+}
+
 __device__ __forceinline__ float ex2(float x)
 {
     float y;
@@ -96,7 +104,7 @@ __global__ void __launch_bounds__(kTileW *kThreadsY) k_jbu(JbuArgs a)
                 const float ds = fmaf(dx, dx, dy * dy);
                 const int dR = R - q.x, dG = Gc - q.y, dB = B - q.z;
                 const int dr = dR * dR + dG * dG + dB * dB;
-                const float k = fmaf((float)dr, a.a_r, ds * a.a_s);
+                const float k = fmaf(exact_float(dr), a.a_r, ds * a.a_s);
                 if (k < kmin) {
                     kmin = k;
                     ds_m = ds;
@@ -115,7 +123,7 @@ __global__ void __launch_bounds__(kTileW *kThreadsY) k_jbu(JbuArgs a)
                 const int dR = R - q.x, dG = Gc - q.y, dB = B - q.z;
                 const int dr = dR * dR + dG * dG + dB * dB;
                 // explicit fmaf: every instantiation rounds the same way
-                const float e = fmaf((float)(dr - dr_m), a.a_r, (ds - ds_m) * a.a_s);
+                const float e = fmaf(exact_float(dr) - exact_float(dr_m), a.a_r, (ds - ds_m) * a.a_s);
                 const float wgt = ex2(-e);
                 num = fmaf(wgt, (float)q.w, num);
                 den += wgt;
@@ -153,12 +161,22 @@ __global__ void __launch_bounds__(kTileW *kThreadsY) k_jbu(JbuArgs a)
 // spatial offsets relative to the window centre (the nearest tap) are
 // compile-time constants of the pixel's position in its 4 x 4 block, so
 //   exponent = (v_q - v_min) * a_r + (|p-q|^2 - |p-c|^2) * a_s >= 0
-// and the window always holds a tap of weight >= 2^-(spatial spread).
-// Taps outside the low-res frame are staged with |I_q|^2 = 2^28, which
-// gives them weight exactly 0 (skipped, as in the definition).
+// and the window always holds a tap of weight >= 2^-(spatial spread); the
+// host takes this kernel only while that spread is <= 100, so the
+// normaliser stays a normal float.
+// v_q is formed directly as the bit pattern of the float 2^23 + kVBias + v_q
+// (|v_q| <= 2 * 195075 = kVBias keeps it in [2^23, 2^24), where floats are
+// the integers), so v_q - v_min is one exact float subtraction instead of an
+// integer-to-float conversion (a quarter-rate operation).  Taps outside the
+// low-res frame are staged with the pattern of 2^127 (and colour 0), whose
+// exponent is >= 2^127 a_r >= 2^27 with a_r >= 2^-100: weight exactly 0,
+// skipped as in the definition.
 
 constexpr int kS4CentresX = 32, kS4CentresY = 4;   // window centres per CTA
-constexpr uint32_t kOffFrameNorm = 1u << 28;
+constexpr uint32_t kVBias = 2u * 195075u;            // 2 * 3 * 255^2
+constexpr uint32_t kVMagic = 0x4B000000u + kVBias;   // float bits of 2^23 + kVBias
+constexpr uint32_t kOffFrameBits = 0x7F000000u;      // float bits of 2^127
+constexpr float kMinAr = 0x1p-100f;                  // floor of a_r on this path
 
 template <int R, bool kXYZ>
 __global__ void __launch_bounds__(kS4CentresX *kS4CentresY, 4) k_jbu_s4(JbuArgs a)
@@ -166,17 +184,18 @@ __global__ void __launch_bounds__(kS4CentresX *kS4CentresY, 4) k_jbu_s4(JbuArgs 
     pdl_begin();
     constexpr int D = 2 * R + 1;
     constexpr int SW = kS4CentresX + 2 * R, SH = kS4CentresY + 2 * R;
-    __shared__ uint2 stage[SH][SW];   // (R | G<<8 | B<<16 | label<<24, R^2+G^2+B^2)
+    // (R | G<<8 | B<<16 | label<<24, bits of 2^23 + kVBias + R^2+G^2+B^2)
+    __shared__ uint2 stage[SH][SW];
     const int k0 = blockIdx.x * kS4CentresX, l0 = blockIdx.y * kS4CentresY;
     for (int i = threadIdx.x; i < SW * SH; i += kS4CentresX * kS4CentresY) {
         const int sx = i % SW, sy = i / SW;
         const int qx = k0 - R + sx, qy = l0 - R + sy;
-        uint2 v = make_uint2(0u, kOffFrameNorm);
+        uint2 v = make_uint2(0u, kOffFrameBits);
         if (qx >= 0 && qy >= 0 && qx < a.w && qy < a.h) {
             const uint8_t *g = a.guide_low + (size_t)qy * a.guide_low_pitch + (size_t)qx * 3;
             const uint32_t r = g[0], gg = g[1], b = g[2];
             const uint32_t lab = a.labels[(size_t)qy * a.labels_pitch + qx];
-            v = make_uint2(r | (gg << 8) | (b << 16) | (lab << 24), r * r + gg * gg + b * b);
+            v = make_uint2(r | (gg << 8) | (b << 16) | (lab << 24), kVMagic + r * r + gg * gg + b * b);
         }
         stage[sy][sx] = v;
     }
@@ -202,8 +221,8 @@ __global__ void __launch_bounds__(kS4CentresX *kS4CentresY, 4) k_jbu_s4(JbuArgs 
 #pragma unroll
     for (int py = 0; py < 4; ++py) {
         const int y = 4 * l + py;
-        if (y >= a.H)
-            break;
+        if (y >= a.H)   // the last block row of a frame whose height is not a multiple of 4
+            continue;
         const uint32_t *gp = reinterpret_cast<const uint32_t *>(a.guide_full + (size_t)y * a.guide_full_pitch +
                                                                  (size_t)k * 12);
         const uint32_t g0 = gp[0], g1 = gp[1], g2 = gp[2];
@@ -212,13 +231,14 @@ __global__ void __launch_bounds__(kS4CentresX *kS4CentresY, 4) k_jbu_s4(JbuArgs 
         float dres[4];
 #pragma unroll
         for (int px = 0; px < 4; ++px) {
-            int v[D * D];
+            int v[D * D];   // float bits of 2^23 + kVBias + v_q (2^127 off the frame)
             int vmin = 0x7FFFFFFF;
 #pragma unroll
             for (int t = 0; t < D * D; ++t) {
                 v[t] = tn[t] - 2 * (int)__dp4a(ip[px], tq[t], 0u);
                 vmin = min(vmin, v[t]);
             }
+            const float fmin = __int_as_float(vmin);
             float num = 0.0f, den = 0.0f;
             // spatial terms: p_down - q = ((px + 0.5)/4 - 0.5 - i, (py + 0.5)/4 - 0.5 - j)
 #pragma unroll
@@ -226,13 +246,15 @@ __global__ void __launch_bounds__(kS4CentresX *kS4CentresY, 4) k_jbu_s4(JbuArgs 
 #pragma unroll
                 for (int i = 0; i < D; ++i) {
                     const int t = j * D + i;
-                    const float e = fmaf((float)(v[t] - vmin), a.a_r, a.sp_as[(4 * py + px) * 49 + t]);
+                    const float e = fmaf(__int_as_float(v[t]) - fmin, a.a_r, a.sp_as[(4 * py + px) * 49 + t]);
                     const float wgt = ex2(-e);
                     num = fmaf(wgt, tl[t], num);
                     den += wgt;
                 }
             }
-            dres[px] = 4.0f * num / den;
+            // den >= 2^-100 (the reference tap) and <= 49: the fast reciprocal
+            // division is within 2 ulp here
+            dres[px] = __fdividef(4.0f * num, den);
         }
         const size_t p = (size_t)y * a.W + (size_t)4 * k;
         if (a.disp)
@@ -243,7 +265,7 @@ __global__ void __launch_bounds__(kS4CentresX *kS4CentresY, 4) k_jbu_s4(JbuArgs 
             for (int px = 0; px < 4; ++px) {
                 float X = __int_as_float(0x7fc00000), Y = X, Z = X;
                 if (dres[px] > 0.0f) {
-                    const float bd = a.baseline / dres[px];
+                    const float bd = __fdividef(a.baseline, dres[px]);   // dres <= 4 * 255
                     X = ((float)(4 * k + px) - a.cx) * bd;
                     Y = ((float)y - a.cy) * a.fx_over_fy * bd;
                     Z = a.fx * bd;
@@ -359,6 +381,7 @@ int jbu_common(const uint8_t *labels, int w, int h, int labels_pitch, const uint
     // exact in FP32 and the product with a_s rounds as it would on the device
     for (int k = 0; k < 16 * 49; ++k)
         a.sp_as[k] = 0.0f;
+    float sp_spread = 0.0f;   // largest spatial exponent of a scale-4 window
     if (s == 4 && a.r <= 3) {
         const int D = 2 * a.r + 1;
         for (int py = 0; py < 4; ++py)
@@ -369,16 +392,21 @@ int jbu_common(const uint8_t *labels, int w, int h, int labels_pitch, const uint
                         const float dx = ox - (float)(i - a.r), dy = oy - (float)(j - a.r);
                         const float sp = (dx * dx + dy * dy) - (ox * ox + oy * oy);
                         a.sp_as[(4 * py + px) * 49 + j * D + i] = sp * a.a_s;
+                        sp_spread = fmaxf(sp_spread, sp * a.a_s);
                     }
     }
     dim3 grid((W + kTileW - 1) / kTileW, (H + kTileH - 1) / kTileH);
     dim3 block(kTileW, kThreadsY);
     // the scale-4 kernel needs whole 4-pixel groups on every row and
     // 4/16-byte aligned rows for its vector loads and stores
+    // and a spatial spread that keeps the reference tap's weight >= 2^-100
     const bool s4 = s == 4 && W % 4 == 0 && guide_full_pitch % 4 == 0 && aligned(guide_full, 4) &&
-                    (!disp || aligned(disp, 16)) && (!xyz || aligned(xyz, 16));
+                    (!disp || aligned(disp, 16)) && (!xyz || aligned(xyz, 16)) && sp_spread <= 100.0f;
     const int slot = prof_begin(kProfJbu, st);
     if (s4) {
+        // a_r below 2^-100 makes every in-frame range term < 2^-80, which
+        // changes no weight; the floor keeps off-frame taps at weight 0
+        a.a_r = fmaxf(a.a_r, kMinAr);
         if (xyz)
             launch_jbu_s4<true>(a, st);
         else

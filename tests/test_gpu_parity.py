@@ -149,6 +149,29 @@ def test_bp_pitched_rows():
     assert not got[:, 50:].any()
 
 
+@pytest.mark.parametrize("p", [
+    vs.BPParams(64, 3, 2, 20, 10, 40),    # level-1 costs in bytes
+    vs.BPParams(40, 2, 2, 70, 6, 50),     # level-1 costs in 16 bits, a partial label chunk
+    vs.BPParams(17, 1, 3, 20, 10, 40),    # one level: no level-1 sums
+])
+def test_bp_wide_rows_at_odd_addresses(p):
+    """Rows of 150 bytes at an odd start and an odd pitch: the data term reads
+    the right image in aligned words whatever the row alignment, and falls back
+    to byte loads at both edges and on padding labels."""
+    left, right, _ = synth.noise_pair(21, w=150, h=37, max_disp=30.0)
+    big_l = np.zeros((37, 203), np.uint8)
+    big_r = np.zeros((37, 203), np.uint8)
+    big_l[:, 1:151], big_r[:, 1:151] = left, right
+    L, R = dev(big_l)[:, 1:151], dev(big_r)[:, 1:151]
+    n = vs.bp_workspace_size(150, 37, p)
+    ws = torch.randint(0, 256, (n,), dtype=torch.uint8, device="cuda")
+    lab = vs.bp_stereo(L, R, p, workspace=ws)
+    msg = vs.bp_export_messages(ws, 150, 37, p)
+    olab, omsg = oracle_bp(left, right, p, mode=oracle.MSG_DT)
+    np.testing.assert_array_equal(host(msg), omsg)
+    np.testing.assert_array_equal(host(lab), olab)
+
+
 def test_bp_rejects_small_workspace():
     left, right, _ = synth.noise_pair(0, w=32, h=24)
     ws = torch.empty(100, dtype=torch.uint8, device="cuda")
@@ -264,6 +287,9 @@ def _assert_xyz_close(a, b, disp_ref):
     (36, 52, vs.JBUParams(4, 3, 1.2, 15.0)),
     (16, 16, vs.JBUParams(4, 0, 1.0, 12.0)),
     (45, 68, vs.JBUParams(4, 2, 1.0, 12.0)),
+    (40, 64, vs.JBUParams(4, 2, 1.0, 5000.0)),  # flat range term: frame-edge taps must stay out
+    (30, 62, vs.JBUParams(2, 2, 1.0, 5000.0)),
+    (44, 60, vs.JBUParams(4, 3, 0.25, 12.0)),   # spatial spread beyond the scale-4 kernel's range
 ])
 def test_jbu_and_reproject_small(H, W, jp):
     for smooth in (True, False):
