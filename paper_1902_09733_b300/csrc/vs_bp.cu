@@ -881,6 +881,55 @@ __global__ void k_bp_labels(LabelArgs a)
     a.labels[(size_t)y * a.labels_pitch + x] = (uint8_t)bestd;
 }
 
+// k_bp_labels where the belief sum of every label fits a byte (level-0
+// costs in bytes, data_trunc + 4 smooth_trunc <= 255): one 32-bit add sums
+// four labels, and the argmin runs on 16-bit keys S(d) * 256 + d, two labels
+// per packed minimum, so ties still go to the smallest d.  LP labels at
+// compile time; FULL: no padding labels to mask.
+template <int LP, bool FULL>
+__global__ void __launch_bounds__(128) k_bp_labels_bytes(LabelArgs a)
+{
+    pdl_begin();
+    const int xh = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    const int c = a.color;
+    const int x = 2 * xh + ((c + y) & 1);
+    if (x >= a.w || y >= a.h)
+        return;
+    const bool has[4] = {x > 0, x < a.w - 1, y > 0, y < a.h - 1};
+    constexpr int NP = LP / 16;
+    const uint8_t *cost = a.cost + slot_base(c * a.h + y, xh, a.wg, NP);
+    const uint8_t *in[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        in[k] = a.msg + slot_base((c * 4 + k) * a.h + y, xh, a.wg, NP);
+    uint32_t best2 = 0xFFFFFFFFu;   // smallest key of the even / odd labels of each pair
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        const uint4 cv = ld_piece(cost, j);
+        uint4 m[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            m[k] = has[k] ? ld_piece(in[k], j) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int wi = 0; wi < 4; ++wi) {
+            const uint32_t s4 = (&cv.x)[wi] + (&m[0].x)[wi] + (&m[1].x)[wi] + (&m[2].x)[wi] + (&m[3].x)[wi];
+            const uint32_t d0 = (uint32_t)(16 * j + 4 * wi);
+            const uint32_t dd = d0 * 0x01010101u + 0x03020100u;   // the four labels as bytes
+            uint32_t k01 = prmt(s4, dd, 0x1504u);                 // (S0 << 8 | d0, S1 << 8 | d1)
+            uint32_t k23 = prmt(s4, dd, 0x3726u);                 // (S2 << 8 | d2, S3 << 8 | d3)
+            if (!FULL && (int)d0 + 3 >= a.L) {
+                const int L = a.L - (int)d0;   // labels of this word that exist
+                k01 |= (L <= 0 ? 0xFFFFu : 0u) | (L <= 1 ? 0xFFFF0000u : 0u);
+                k23 |= (L <= 2 ? 0xFFFFu : 0u) | (L <= 3 ? 0xFFFF0000u : 0u);
+            }
+            best2 = min_u16x2(best2, min_u16x2(k01, k23));
+        }
+    }
+    const uint32_t best = min(best2 & 0xFFFFu, best2 >> 16);
+    a.labels[(size_t)y * a.labels_pitch + x] = (uint8_t)(best & 0xFFu);
+}
+
 struct ExportArgs {
     const uint8_t *msg;
     int32_t *out;
@@ -1191,7 +1240,27 @@ void launch_labels(const BpLayout &lay, uint8_t *ws, uint8_t *labels, int labels
                 lay.wg[0], lay.L, lay.Lp, (p->iters & 1)};
     dim3 grid((lay.wh[0] + 127) / 128, lay.h[0]);
     const int slot = prof_begin(kProfBpOther, st);
-    launch_pdl(k_bp_labels, dim3(grid), dim3(128), st, a);
+    if (lay.bytes[0]) {
+        const bool full = lay.L == lay.Lp;
+#define VS_LABELS(LP)                                                                                         \
+    do {                                                                                                      \
+        if (full)                                                                                             \
+            launch_pdl(k_bp_labels_bytes<LP, true>, dim3(grid), dim3(128), st, a);                           \
+        else                                                                                                  \
+            launch_pdl(k_bp_labels_bytes<LP, false>, dim3(grid), dim3(128), st, a);                          \
+    } while (0)
+        switch (lay.Lp) {
+        case 16: VS_LABELS(16); break;
+        case 32: VS_LABELS(32); break;
+        case 48: VS_LABELS(48); break;
+        case 64: VS_LABELS(64); break;
+        case 96: VS_LABELS(96); break;
+        default: VS_LABELS(128); break;
+        }
+#undef VS_LABELS
+    } else {
+        launch_pdl(k_bp_labels, dim3(grid), dim3(128), st, a);
+    }
     prof_end(slot, st);
     note_launch();
 }

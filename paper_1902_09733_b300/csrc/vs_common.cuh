@@ -71,6 +71,14 @@ __device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b)
     return d;
 }
 
+// 0 <= n < 2^23 as a float: n added into the mantissa of 2^23, minus 2^23
+// (exact; an integer add and a float add instead of a quarter-rate
+// conversion)
+__device__ __forceinline__ float exact_float(int n)
+{
+    return __int_as_float(0x4B000000 + n) - 8388608.0f;
+}
+
 // Byte permute: result byte i = byte sel[i] of {b:a} (a = bytes 0..3); a
 // selector nibble with bit 3 set replicates the sign bit of that byte.
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)

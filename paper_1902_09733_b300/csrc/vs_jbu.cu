@@ -37,14 +37,6 @@ struct JbuArgs {
     float sp_as[16 * 49];
 };
 
-// 0 <= n < 2^23 as a float: n added into the mantissa of 2^23, minus 2^23
-// (exact; an integer add and a float add instead of a quarter-rate
-// conversion)
-__device__ __forceinline__ float exact_float(int n)
-{
-    return __int_as_float(0x4B000000 + n) - 8388608.0f;
-}
-
 __device__ __forceinline__ float ex2(float x)
 {
     float y;

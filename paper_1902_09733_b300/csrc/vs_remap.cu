@@ -1,13 +1,13 @@
 // Section 2.1 undistort/rectify remap fused with the Section 2.2 downsample.
 //
-// One CTA owns a tile of TLW x TLH low-resolution pixels, i.e. an aligned
-// block of (TLW s) x (TLH s) full-resolution pixels.  Each thread maps its
-// destination pixels through the radial lens model (FP32), samples the
-// source bilinearly in fixed point (weights in 1/4096: a two-term dot
-// product per row and channel, no byte-to-float conversions), rounds, writes
-// the full-resolution RGB and keeps a copy in shared memory; the CTA then
-// reduces every s x s block to the low-res RGB mean and its grey.  One
-// launch per frame, no intermediate buffers.
+// Each destination pixel is mapped through the radial lens model (FP32) and
+// the source sampled bilinearly in fixed point (weights in 1/4096: a two-term
+// dot product per row and channel, no byte-to-float conversions), rounded
+// half up; the kernel writes the full-resolution RGB and reduces every s x s
+// block to the low-res RGB mean and its grey.  One launch per frame, no
+// intermediate buffers.  k_remap_s4 serves scale 4 without rotation (the
+// pair pipeline); k_remap_down everything else, staging its tile in shared
+// memory for the block means.
 #include "vs_common.cuh"
 
 namespace vs {
@@ -34,16 +34,122 @@ struct RemapArgs {
     int has_R;
 };
 
-__device__ __forceinline__ float tap(const uint8_t *src, int pitch, int W, int H, int x, int y, int ch)
+__device__ __forceinline__ uint32_t tap(const uint8_t *src, int pitch, int W, int H, int x, int y, int ch)
 {
     if (x < 0 || y < 0 || x >= W || y >= H)
-        return 0.0f;
-    return (float)__ldg(src + (size_t)y * pitch + (size_t)x * 3 + ch);
+        return 0u;
+    return (uint32_t)__ldg(src + (size_t)y * pitch + (size_t)x * 3 + ch);
 }
 
-// Destination pixels are processed four consecutive ones per thread, so the
-// 48 tap loads of a thread are all in flight together and its 12 output
-// bytes leave as three 32-bit stores when the row allows it.
+// The normalised ray of destination pixel (u, v), rotated by R^T when a
+// rotation is given; false for a ray with non-positive depth.
+__device__ __forceinline__ bool ray(const RemapArgs &a, int u, int v, float &xn, float &yn)
+{
+    xn = __fmul_rn(__fsub_rn((float)u, a.cx), a.inv_fx);
+    yn = __fmul_rn(__fsub_rn((float)v, a.cy), a.inv_fy);
+    if (!a.has_R)
+        return true;
+    const float X = a.R[0] * xn + a.R[3] * yn + a.R[6];
+    const float Y = a.R[1] * xn + a.R[4] * yn + a.R[7];
+    const float Z = a.R[2] * xn + a.R[5] * yn + a.R[8];
+    if (!(Z > 0.0f))
+        return false;
+    xn = X / Z;
+    yn = Y / Z;
+    return true;
+}
+
+// Radial distortion 1 + k1 r^2 + k2 r^4 and the pinhole back to source
+// pixels; explicit fused multiply-adds, so every kernel rounds alike.
+__device__ __forceinline__ void distort(const RemapArgs &a, float xn, float yn, float &sx, float &sy)
+{
+    const float r2 = fmaf(xn, xn, __fmul_rn(yn, yn));
+    const float radial = fmaf(fmaf(a.k2, r2, a.k1), r2, 1.0f);
+    sx = fmaf(a.fx, __fmul_rn(xn, radial), a.cx);
+    sy = fmaf(a.fy, __fmul_rn(yn, radial), a.cy);
+}
+
+// Fixed-point bilinear blend: weights in 1/4096, each row's two taps per
+// channel in one 16 x 8-bit two-term dot product, the rows in 32-bit
+// integers.  t_rg / b_rg = (R0 R1 G0 G1) of the top / bottom row, t_b / b_b
+// = (B0 B1 . .).  Returns value * 2^24 + 2^23 per channel: the rounded-half-up
+// byte is bits 24..31 (the value is within 0.06 of the exact bilinear one).
+__device__ __forceinline__ void blend(uint32_t t_rg, uint32_t t_b, uint32_t b_rg, uint32_t b_b, uint32_t axq,
+                                      uint32_t ayq, uint32_t (&vv)[3])
+{
+    const uint32_t wx = axq * 0xFFFFu + 4096u;   // (4096 - axq, axq) as 2 x u16
+    const uint32_t top[3] = {__dp2a_lo(wx, t_rg, 0u), __dp2a_hi(wx, t_rg, 0u), __dp2a_lo(wx, t_b, 0u)};
+    const uint32_t bot[3] = {__dp2a_lo(wx, b_rg, 0u), __dp2a_hi(wx, b_rg, 0u), __dp2a_lo(wx, b_b, 0u)};
+    const uint32_t ayc = 4096u - ayq;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch)
+        vv[ch] = bot[ch] * ayq + (top[ch] * ayc + (1u << 23));   // < 2^32
+}
+
+// Taps of the 2 x 2 footprint at (x0, y0) from aligned words: needs x0 >= 0,
+// y0 >= 0, x0 + 2 < W, y0 + 1 < H and word-aligned rows; q0 = the word that
+// holds byte 3 x0 of row y0, o = that byte's position in it.  The words that
+// cover a row's 6 bytes end inside that row: 4 to 6 loads.
+__device__ __forceinline__ void taps_words(const uint32_t *q0, int pitch32, uint32_t o, uint32_t &t_rg,
+                                           uint32_t &t_b, uint32_t &b_rg, uint32_t &b_b)
+{
+    const uint32_t *q1 = q0 + pitch32;
+    const uint32_t a0 = __ldg(q0), a1 = __ldg(q0 + 1), b0 = __ldg(q1), b1 = __ldg(q1 + 1);
+    // byte o + 5 lies in a third word only for o = 3 (it is then byte
+    // 3 x0 + 5 of the row, inside it since x0 + 3 <= W)
+    const uint32_t a2 = o == 3 ? __ldg(q0 + 2) : 0u, b2 = o == 3 ? __ldg(q1 + 2) : 0u;
+    // bytes o .. o+5 of each row: (R0 G0 B0 R1) from {a1:a0}, (G1 B1) from {a2:a1}
+    const uint32_t s_lo = o * 0x1111u + 0x3210u;
+    const uint32_t s_hi = o * 0x11u + 0x10u;
+    const uint32_t r0a = prmt(a0, a1, s_lo), r0b = prmt(a1, a2, s_hi);
+    const uint32_t r1a = prmt(b0, b1, s_lo), r1b = prmt(b1, b2, s_hi);
+    t_rg = prmt(r0a, r0b, 0x4130u), t_b = prmt(r0a, r0b, 0x0052u);
+    b_rg = prmt(r1a, r1b, 0x4130u), b_b = prmt(r1a, r1b, 0x0052u);
+}
+
+// One destination pixel anywhere in the frame: blend accumulators as
+// blend() returns them, 2^23 (byte 0) for rays that miss the frame.
+__device__ __forceinline__ void sample_px(const RemapArgs &a, int u, int v, uint32_t (&vv)[3])
+{
+    vv[0] = vv[1] = vv[2] = 1u << 23;
+    float xn, yn;
+    if (!ray(a, u, v, xn, yn))
+        return;
+    float sx, sy;
+    distort(a, xn, yn, sx, sy);
+    if (!(sx > -1.0f && sx < (float)a.W && sy > -1.0f && sy < (float)a.H))
+        return;
+    const float fx0 = floorf(sx), fy0 = floorf(sy);
+    const int x0 = (int)fx0, y0 = (int)fy0;
+    const uint32_t axq = (uint32_t)__float2int_rn((sx - fx0) * 4096.0f);
+    const uint32_t ayq = (uint32_t)__float2int_rn((sy - fy0) * 4096.0f);
+    uint32_t t_rg, t_b, b_rg, b_b;
+    if (x0 >= 0 && y0 >= 0 && x0 + 2 < a.W && y0 + 1 < a.H && a.src_words) {
+        const uint8_t *p0 = a.src + (size_t)y0 * a.src_pitch + 3 * x0;
+        const uint32_t o = (uint32_t)(reinterpret_cast<uintptr_t>(p0) & 3u);
+        taps_words(reinterpret_cast<const uint32_t *>(p0 - o), a.src_pitch >> 2, o, t_rg, t_b, b_rg, b_b);
+    } else {
+        // byte loads, with frame checks where a tap may be outside
+        uint32_t tq[2][2][3];   // [row][column][channel]
+#pragma unroll
+        for (int jy = 0; jy < 2; ++jy)
+#pragma unroll
+            for (int jx = 0; jx < 2; ++jx)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch)
+                    tq[jy][jx][ch] = tap(a.src, a.src_pitch, a.W, a.H, x0 + jx, y0 + jy, ch);
+        t_rg = tq[0][0][0] | (tq[0][1][0] << 8) | (tq[0][0][1] << 16) | (tq[0][1][1] << 24);
+        t_b = tq[0][0][2] | (tq[0][1][2] << 8);
+        b_rg = tq[1][0][0] | (tq[1][1][0] << 8) | (tq[1][0][1] << 16) | (tq[1][1][1] << 24);
+        b_b = tq[1][0][2] | (tq[1][1][2] << 8);
+    }
+    blend(t_rg, t_b, b_rg, b_b, axq, ayq, vv);
+}
+
+// General kernel: any scale, rotation, alignment and frame size.  Destination
+// pixels are processed four consecutive ones per thread, so the tap loads of
+// a thread are in flight together and its 12 output bytes leave as three
+// 32-bit stores when the row allows it.
 __global__ void __launch_bounds__(kRemapThreads) k_remap_down(RemapArgs a)
 {
     pdl_begin();
@@ -60,88 +166,12 @@ __global__ void __launch_bounds__(kRemapThreads) k_remap_down(RemapArgs a)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int lu = lu0 + q, u = u0 + lu;
-            int ival[3] = {0, 0, 0};   // rounded sample; 0 for rays that miss the frame
-            if (lu < tfw && u < a.W && v < a.H) {
-                float xn = ((float)u - a.cx) * a.inv_fx;
-                float yn = ((float)v - a.cy) * a.inv_fy;
-                bool valid = true;
-                if (a.has_R) {
-                    const float X = a.R[0] * xn + a.R[3] * yn + a.R[6];
-                    const float Y = a.R[1] * xn + a.R[4] * yn + a.R[7];
-                    const float Z = a.R[2] * xn + a.R[5] * yn + a.R[8];
-                    if (Z <= 0.0f) {
-                        valid = false;
-                    } else {
-                        xn = X / Z;
-                        yn = Y / Z;
-                    }
-                }
-                if (valid) {
-                    const float r2 = xn * xn + yn * yn;
-                    const float radial = 1.0f + a.k1 * r2 + a.k2 * r2 * r2;
-                    const float sx = a.fx * (xn * radial) + a.cx;
-                    const float sy = a.fy * (yn * radial) + a.cy;
-                    if (sx > -1.0f && sx < (float)a.W && sy > -1.0f && sy < (float)a.H) {
-                        const float fx0 = floorf(sx), fy0 = floorf(sy);
-                        const int x0 = (int)fx0, y0 = (int)fy0;
-                        const float ax = sx - fx0, ay = sy - fy0;
-                        // the two taps of each row per channel, packed as (R0 R1 G0 G1) and
-                        // (B0 B1 . .), top row t_*, bottom row b_*; taps outside the frame are 0
-                        uint32_t t_rg, t_b, b_rg, b_b;
-                        if (x0 >= 0 && y0 >= 0 && x0 + 2 < a.W && y0 + 1 < a.H && a.src_words) {
-                            // all four taps in the frame, and the aligned words that
-                            // cover each row's 6 bytes end inside that row: 4 to 6 loads
-                            const uint8_t *p0 = a.src + (size_t)y0 * a.src_pitch + 3 * x0;
-                            const uint32_t o = (uint32_t)(reinterpret_cast<uintptr_t>(p0) & 3u);
-                            const uint32_t *q0 = reinterpret_cast<const uint32_t *>(p0 - o);
-                            const uint32_t *q1 = reinterpret_cast<const uint32_t *>(p0 - o + a.src_pitch);
-                            const uint32_t a0 = __ldg(q0), a1 = __ldg(q0 + 1), b0 = __ldg(q1), b1 = __ldg(q1 + 1);
-                            // byte o + 5 lies in a third word only for o = 3 (it is then
-                            // byte 3x0 + 5 of the row, inside it since x0 + 3 <= W)
-                            const uint32_t a2 = o == 3 ? __ldg(q0 + 2) : 0u, b2 = o == 3 ? __ldg(q1 + 2) : 0u;
-                            // bytes o .. o+5 of each row: (R0 G0 B0 R1) from {a1:a0}, (G1 B1) from {a2:a1}
-                            const uint32_t s_lo = o | ((o + 1) << 4) | ((o + 2) << 8) | ((o + 3) << 12);
-                            const uint32_t s_hi = o | ((o + 1) << 4);
-                            const uint32_t r0a = prmt(a0, a1, s_lo), r0b = prmt(a1, a2, s_hi);
-                            const uint32_t r1a = prmt(b0, b1, s_lo), r1b = prmt(b1, b2, s_hi);
-                            t_rg = prmt(r0a, r0b, 0x4130u), t_b = prmt(r0a, r0b, 0x0052u);
-                            b_rg = prmt(r1a, r1b, 0x4130u), b_b = prmt(r1a, r1b, 0x0052u);
-                        } else {
-                            // byte loads, with frame checks where a tap may be outside
-                            uint32_t tq[2][2][3];   // [row][column][channel]
-#pragma unroll
-                            for (int jy = 0; jy < 2; ++jy)
-#pragma unroll
-                                for (int jx = 0; jx < 2; ++jx)
-#pragma unroll
-                                    for (int ch = 0; ch < 3; ++ch)
-                                        tq[jy][jx][ch] = (uint32_t)tap(a.src, a.src_pitch, a.W, a.H, x0 + jx, y0 + jy, ch);
-                            t_rg = tq[0][0][0] | (tq[0][1][0] << 8) | (tq[0][0][1] << 16) | (tq[0][1][1] << 24);
-                            t_b = tq[0][0][2] | (tq[0][1][2] << 8);
-                            b_rg = tq[1][0][0] | (tq[1][1][0] << 8) | (tq[1][0][1] << 16) | (tq[1][1][1] << 24);
-                            b_b = tq[1][0][2] | (tq[1][1][2] << 8);
-                        }
-                        // fixed-point bilinear blend: weights in 1/4096, each row's two taps
-                        // per channel in one 16 x 8-bit two-term dot product, the rows in
-                        // 32-bit integers; within 0.06 of the exact value before rounding
-                        const uint32_t axq = (uint32_t)__float2int_rn(ax * 4096.0f);
-                        const uint32_t ayq = (uint32_t)__float2int_rn(ay * 4096.0f);
-                        const uint32_t wx = (axq << 16) | (4096u - axq);   // (left, right) tap weights
-                        const uint32_t top[3] = {__dp2a_lo(wx, t_rg, 0u), __dp2a_hi(wx, t_rg, 0u),
-                                                 __dp2a_lo(wx, t_b, 0u)};
-                        const uint32_t bot[3] = {__dp2a_lo(wx, b_rg, 0u), __dp2a_hi(wx, b_rg, 0u),
-                                                 __dp2a_lo(wx, b_b, 0u)};
-#pragma unroll
-                        for (int ch = 0; ch < 3; ++ch) {
-                            const uint32_t vv = top[ch] * (4096u - ayq) + bot[ch] * ayq;   // < 2^32
-                            ival[ch] = (int)((vv + (1u << 23)) >> 24);   // round half up
-                        }
-                    }
-                }
-            }
+            uint32_t vv[3] = {1u << 23, 1u << 23, 1u << 23};
+            if (lu < tfw && u < a.W && v < a.H)
+                sample_px(a, u, v, vv);
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch)
-                out[3 * q + ch] = (uint8_t)min(max(ival[ch], 0), 255);
+                out[3 * q + ch] = (uint8_t)(vv[ch] >> 24);
         }
         if (v >= a.H)
             continue;
@@ -214,6 +244,102 @@ __global__ void __launch_bounds__(kRemapThreads) k_remap_down(RemapArgs a)
     }
 }
 
+// Scale-4 kernel for the common case: no rotation, W and H multiples of 4
+// and below 2^22, word-aligned source and destination rows, frame offsets
+// below 2^31.  A CTA
+// covers 64 x 16 destination pixels; warp w takes block row w >> 1 and half
+// w & 1 of the tile, lane (r, i) = (lane >> 3, lane & 7) the 4 pixels of row
+// r of 4 x 4 block i.  Per quad, pixel coordinates come from exact float
+// arithmetic (integer-valued floats via the 2^23 mantissa, floors by a
+// round-down add of 1.5 x 2^23) instead of conversions; a quad whose four
+// footprints are inside the frame takes the word gathers with no further
+// checks, any other quad the general per-pixel sampler.  The 4 x 4 block
+// means are summed across the four lanes of a block with two shuffles.
+constexpr float kFloorMagic = 12582912.0f;        // 1.5 x 2^23
+constexpr uint32_t kFloorMagicBits = 0x4B400000u;
+
+__global__ void __launch_bounds__(256) k_remap_s4(RemapArgs a)
+{
+    pdl_begin();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = lane >> 3, qi = lane & 7;
+    const int yl = blockIdx.y * 4 + (warp >> 1);       // low-res row = block row
+    if (4 * yl >= a.H)                                 // the whole warp (H is a multiple of 4)
+        return;
+    const int xl = blockIdx.x * 16 + 8 * (warp & 1) + qi;   // low-res column = quad of the row
+    const int v = 4 * yl + r, u0 = 4 * xl;
+    const bool inside = u0 < a.W;                      // whole quad (W is a multiple of 4)
+    uint32_t w[3] = {0u, 0u, 0u};
+    if (inside) {
+        uint32_t vv[4][3];
+        float yn = __fmul_rn(__fsub_rn(exact_float(v), a.cy), a.inv_fy);
+        uint32_t off[4], axq[4], ayq[4];
+        bool fast = true;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float xn = __fmul_rn(__fsub_rn(exact_float(u0 + q), a.cx), a.inv_fx);
+            float sx, sy;
+            distort(a, xn, yn, sx, sy);
+            // floors as integer-valued floats in [2^23, 2^24), exact for |s| < 2^22;
+            // any other s (NaN and infinities too) gives an x0 / y0 that fails the
+            // interior test below, since W and H are below 2^22
+            const float bx = __fadd_rd(sx, kFloorMagic), by = __fadd_rd(sy, kFloorMagic);
+            const int x0 = (int)(__float_as_uint(bx) - kFloorMagicBits);
+            const int y0 = (int)(__float_as_uint(by) - kFloorMagicBits);
+            fast = fast && (unsigned)x0 < (unsigned)(a.W - 2) && (unsigned)y0 < (unsigned)(a.H - 1);
+            // round(frac * 4096) as the low bits of an integer-valued float
+            axq[q] = __float_as_uint(fmaf(sx - (bx - kFloorMagic), 4096.0f, kFloorMagic)) - kFloorMagicBits;
+            ayq[q] = __float_as_uint(fmaf(sy - (by - kFloorMagic), 4096.0f, kFloorMagic)) - kFloorMagicBits;
+            off[q] = (uint32_t)y0 * (uint32_t)a.src_pitch + 3u * (uint32_t)x0;   // used only when fast
+        }
+        if (fast) {
+            const uint32_t *src32 = reinterpret_cast<const uint32_t *>(a.src);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t t_rg, t_b, b_rg, b_b;
+                taps_words(src32 + (off[q] >> 2), a.src_pitch >> 2, off[q] & 3u, t_rg, t_b, b_rg, b_b);
+                blend(t_rg, t_b, b_rg, b_b, axq[q], ayq[q], vv[q]);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                sample_px(a, u0 + q, v, vv[q]);
+        }
+        // the rounded bytes (bits 24..31) packed as R0 G0 B0 R1 | G1 B1 R2 G2 | B2 R3 G3 B3
+        w[0] = prmt(prmt(vv[0][0], vv[0][1], 0x0073u), prmt(vv[0][2], vv[1][0], 0x0073u), 0x5410u);
+        w[1] = prmt(prmt(vv[1][1], vv[1][2], 0x0073u), prmt(vv[2][0], vv[2][1], 0x0073u), 0x5410u);
+        w[2] = prmt(prmt(vv[2][2], vv[3][0], 0x0073u), prmt(vv[3][1], vv[3][2], 0x0073u), 0x5410u);
+        if (a.dst) {
+            uint32_t *d32 = reinterpret_cast<uint32_t *>(a.dst + (size_t)v * a.dst_pitch + (size_t)u0 * 3);
+            d32[0] = w[0];
+            d32[1] = w[1];
+            d32[2] = w[2];
+        }
+    }
+    if (!a.low_rgb && !a.low_gray)
+        return;
+    // row sums of the quad per channel, then the block's four rows
+    const uint32_t sr = __dp4a(w[0], 0x01000001u, __dp4a(w[1], 0x00010000u, __dp4a(w[2], 0x00000100u, 0u)));
+    const uint32_t sg = __dp4a(w[0], 0x00000100u, __dp4a(w[1], 0x01000001u, __dp4a(w[2], 0x00010000u, 0u)));
+    const uint32_t sb = __dp4a(w[0], 0x00010000u, __dp4a(w[1], 0x00000100u, __dp4a(w[2], 0x01000001u, 0u)));
+    uint32_t rg = sr | (sg << 16), b = sb;   // each sum <= 16 x 255 < 2^16
+    rg += __shfl_xor_sync(0xFFFFFFFFu, rg, 8);
+    b += __shfl_xor_sync(0xFFFFFFFFu, b, 8);
+    rg += __shfl_xor_sync(0xFFFFFFFFu, rg, 16);
+    b += __shfl_xor_sync(0xFFFFFFFFu, b, 16);
+    if (r != 0 || !inside)
+        return;
+    const uint32_t R = ((rg & 0xFFFFu) + 8u) >> 4, G = ((rg >> 16) + 8u) >> 4, B = (b + 8u) >> 4;
+    if (a.low_rgb) {
+        uint8_t *d = a.low_rgb + (size_t)yl * a.low_rgb_pitch + (size_t)xl * 3;
+        d[0] = (uint8_t)R;
+        d[1] = (uint8_t)G;
+        d[2] = (uint8_t)B;
+    }
+    if (a.low_gray)
+        a.low_gray[(size_t)yl * a.low_gray_pitch + xl] = (uint8_t)((77u * R + 150u * G + 29u * B + 128u) >> 8);
+}
+
 }  // namespace
 }  // namespace vs
 
@@ -276,10 +402,20 @@ extern "C" int vs_rectify_remap(const uint8_t *src, int W, int H, int src_pitch,
     a.has_R = R9 != nullptr;
     for (int i = 0; i < 9; ++i)
         a.R[i] = R9 ? R9[i] : (i % 4 == 0 ? 1.0f : 0.0f);
-    const int tfw = a.tlw * s, tfh = a.tlh * s;
-    dim3 grid((W + tfw - 1) / tfw, (H + tfh - 1) / tfh);
+    // the scale-4 kernel: whole 4 x 4 blocks, word-aligned rows both ways,
+    // no rotation, 32-bit source offsets, and the low-res output wanted
+    const bool s4 = want_low && s == 4 && !a.has_R && W % 4 == 0 && H % 4 == 0 && W < (1 << 22) &&
+                    H < (1 << 22) && a.src_words && (dst == nullptr || a.dst_vec) &&
+                    (long long)H * src_pitch < (1LL << 31);
     const int slot = prof_begin(kProfRemap, (cudaStream_t)stream);
-    launch_pdl(k_remap_down, dim3(grid), dim3(kRemapThreads), (cudaStream_t)stream, a);
+    if (s4) {
+        dim3 grid((W + 63) / 64, (H + 15) / 16);
+        launch_pdl(k_remap_s4, dim3(grid), dim3(256), (cudaStream_t)stream, a);
+    } else {
+        const int tfw = a.tlw * s, tfh = a.tlh * s;
+        dim3 grid((W + tfw - 1) / tfw, (H + tfh - 1) / tfh);
+        launch_pdl(k_remap_down, dim3(grid), dim3(kRemapThreads), (cudaStream_t)stream, a);
+    }
     prof_end(slot, (cudaStream_t)stream);
     note_launch();
     return launch_status();
