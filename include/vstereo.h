@@ -201,10 +201,21 @@ int vs_bp_autotune(const uint8_t *left, const uint8_t *right, int w, int h, int 
  * `max` values written; returns the count. */
 int vs_bp_autotune_times(float *ms, int max);
 /* Test and measurement aid: run sweep variant `variant` (0 plain, 1 preload,
- * 2 split in two, 3 split in four) on every level where it applies, ahead of
- * any autotuned choice; -1 restores the automatic choice.  Results are
- * identical either way.  Errors: VS_EINVAL. */
+ * 2 split in two, 3 split in four, 4 staged) on every level where it
+ * applies, ahead of any autotuned choice; -1 restores the automatic choice.
+ * The staged variant (persistent CTAs that stream each tile's messages and
+ * costs through shared memory with bulk asynchronous copies) applies to
+ * single-pair sweeps after the first iteration of a level with byte costs
+ * and byte-lane sums; by default it runs on such levels of at least 2^16
+ * pixels, ahead of the autotuned choice.  Results are identical whichever
+ * variant runs.  Errors: VS_EINVAL. */
 int vs_bp_select_sweep(int variant);
+
+/* Synchronises `stream` and reports whether a kernel of the last
+ * vs_bp_stereo call on this workspace gave up a bounded wait for its
+ * shared-memory copies (VS_ETIMEOUT; the labels are then invalid), else
+ * VS_OK.  Errors: VS_EINVAL, VS_EWORKSPACE, VS_ECUDA. */
+int vs_bp_status(const void *workspace, size_t ws_bytes, int w, int h, const vs_bp_params *p, void *stream);
 void vs_bp_autotune_reset(void);
 
 /* Debug read-out after vs_bp_stereo on the same workspace and stream: the

@@ -174,6 +174,7 @@ def lib() -> ctypes.CDLL:
             "vs_bp_workspace_size": ([I, I, bp_p], S),
             "vs_bp_stereo": ([P, P, I, I, I, bp_p, P, I, P, S, P], I),
             "vs_bp_export_messages": ([P, S, I, I, bp_p, P, P], I),
+            "vs_bp_status": ([P, S, I, I, bp_p, P], I),
             "vs_guided_upsample": ([P, I, I, I, P, I, P, I, I, I, jbu_p, P, P], I),
             "vs_reproject": ([P, I, I, cam_p, F, P, P], I),
             "vs_guided_upsample_reproject": ([P, I, I, I, P, I, P, I, I, I, jbu_p, cam_p, F, P, P, P], I),
@@ -406,8 +407,15 @@ def bp_autotune_times():
 
 
 def bp_select_sweep(variant: int) -> None:
-    """Force sweep variant 0..3 on every level where it applies (-1: automatic)."""
+    """Force sweep variant 0..4 (plain, preload, split 2, split 4, staged) wherever it applies (-1: automatic)."""
     _check("vs_bp_select_sweep", lib().vs_bp_select_sweep(int(variant)))
+
+
+def bp_status(workspace: torch.Tensor, w: int, h: int, params: BPParams, stream=None) -> None:
+    """Raise VSError(VS_ETIMEOUT) if a kernel of the last bp_stereo on ``workspace`` gave up a bounded wait."""
+    c = params.c()
+    _check("vs_bp_status", lib().vs_bp_status(workspace.data_ptr(), workspace.numel(), w, h, ctypes.byref(c),
+                                              _stream(stream)))
 
 
 def bp_autotune_reset() -> None:

@@ -28,6 +28,7 @@
 // registers.  All lane values stay below 2^15 (ABI limits), so the packed
 // adds never carry across lanes and the signed form is exact too.
 #include "vs_common.cuh"
+#include "vs_tcgen05.cuh"
 
 #include <algorithm>
 #include <mutex>
@@ -47,6 +48,7 @@ struct BpLayout {
     int cost_u8[kMaxLevels];   // level cost fits a byte: data_trunc * 4^l <= 255
     int bytes[kMaxLevels];     // level belief sums fit a byte: + 4 smooth_trunc <= 255
     size_t cost_off[kMaxLevels], msg_off[kMaxLevels];
+    size_t status_off;         // int: VS_OK, or VS_ETIMEOUT from a kernel of the last call
     size_t total;
 };
 
@@ -91,6 +93,8 @@ BpLayout make_layout(int w, int h, const vs_bp_params *p)
         lay.msg_off[l] = off;
         off = align_up(off + slots * 4 * lay.Lp, 256);
     }
+    lay.status_off = off;
+    off = align_up(off + sizeof(int), 256);
     lay.total = off;
     return lay;
 }
@@ -148,6 +152,7 @@ struct Cost01Args {
     uint8_t *cost0;
     uint8_t *cost1;         // null when there is no level 1
     int cost1_u8;
+    int *status;            // reset to VS_OK: the first kernel of every call
 };
 
 // D0(x, y, d) = min(|IL(x,y) - IR(x-d,y)|, Td), Td where x - d < 0, 0 on
@@ -188,6 +193,8 @@ __global__ void __launch_bounds__(128) k_cost01(Cost01Args a)
     const int chunks = a.Lp / 16;
     const int nxb = (a.w1 + 31) / 32;
     const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx == 0)
+        *a.status = VS_OK;
     unsigned t = idx >> 5;
     const int j = (int)(t % (unsigned)chunks);
     t /= (unsigned)chunks;
@@ -352,6 +359,7 @@ struct SweepArgs {
     uint32_t c2, ts2;       // (c, c) and (Ts, Ts) packed
     uint8_t *labels;        // last level-0 iteration: labels of the active colour
     int labels_pitch;
+    int *status;            // set to VS_ETIMEOUT by a kernel that gives up a bounded wait
 };
 
 // Byte i of word a in the low half and byte i of word b in the high half,
@@ -413,6 +421,11 @@ struct CostChunk<uint16_t> {
 // The sweep of one level-iteration for the CTA `block` of a launch; the
 // plain kernel passes blockIdx.x, the batched kernel its position within
 // its job.
+template <int LP, typename CostT, bool BYTES, bool FULL, bool LABELS, bool PRELOAD, bool SMEM>
+__device__ __forceinline__ void sweep_pixel(const SweepArgs &a, int pair, int x, int y, const bool (&has)[4],
+                                            const uint8_t *const (&in)[4], const bool (&use)[4],
+                                            const uint8_t *cost, uint8_t *own);
+
 template <int LP, typename CostT, bool BYTES, bool FULL, bool LABELS, bool PRELOAD>
 __device__ __forceinline__ void sweep_body(const SweepArgs &a, unsigned block)
 {
@@ -457,6 +470,20 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, unsigned block)
     const uint8_t *cost = reinterpret_cast<const uint8_t *>(a.cost) +
                           slot_base(a.color * a.h + y, xh, a.wg, (LP / 16) * (int)sizeof(CostT));
     uint8_t *own = a.msg + slot_base(a.color * 4 * a.h + y, xh, a.wg, LP / 16);
+    sweep_pixel<LP, CostT, BYTES, FULL, LABELS, PRELOAD, false>(a, pair, x, y, has, in, use, cost, own);
+}
+
+// The message update of one pixel for one direction pair (pair 0: left /
+// right, 1: up / down) once the sources are known: in[k] = piece 0 of the
+// incoming message from direction k (read only where use[k]), cost = piece 0
+// of the data term, own = this pixel's slot of direction 0 (for
+// materialize).  SMEM: the sources are a shared-memory copy (plain loads,
+// no L2 hint).
+template <int LP, typename CostT, bool BYTES, bool FULL, bool LABELS, bool PRELOAD, bool SMEM>
+__device__ __forceinline__ void sweep_pixel(const SweepArgs &a, int pair, int x, int y, const bool (&has)[4],
+                                            const uint8_t *const (&in)[4], const bool (&use)[4],
+                                            const uint8_t *cost, uint8_t *own)
+{
     const size_t dir_stride = (size_t)a.h * a.wg * (LP / 16) * kPieceStride;   // bytes between directions
 
     constexpr int NPRE = PRELOAD ? LP / 16 : 1;
@@ -488,7 +515,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, unsigned block)
         } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                m[k] = use[k] ? ld_piece_keep(in[k], j, pol) : make_uint4(0, 0, 0, 0);
+                m[k] = !use[k] ? make_uint4(0, 0, 0, 0) : (SMEM ? ld_piece(in[k], j) : ld_piece_keep(in[k], j, pol));
             cc.load(cost, j);
         }
         if (a.materialize) {
@@ -783,6 +810,100 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_split(SweepArgs a)
 }
 
 // ---------------------------------------------------------------------------
+// staged sweep: persistent CTAs stream their tiles through shared memory
+//
+// A tile is 64 consecutive slots of the active colour (4 slot groups, which
+// may run across a row end).  Its four incoming-message blocks and its cost
+// block are each one contiguous run of 64 LP bytes, so one thread issues five
+// bulk asynchronous copies per tile, into one of two shared-memory stages
+// tracked by an mbarrier; a CTA works through tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ..., with the next tile's copies in flight while it
+// computes the current one.  Compute is sweep_pixel reading shared memory;
+// the outgoing messages go straight to global memory as in k_bp_sweep.
+// Measured on the 2.7K pair (level 0, 64 labels, 740 resident CTAs): 17.3 us
+// per sweep against 16.7 for the register-preload kernel, yet four pairs in
+// flight run 4110 pairs/s against 3941 (one pair at a time 3015 against
+// 3109).  Reading the cost from global memory instead (four blocks per
+// stage, six CTAs per SM) measured 3953 / 3015.
+// For the iterations that read this level's own messages (not the first of a
+// level) with byte costs and byte-lane sums -- level 0 here.
+constexpr int kStageSlots = kSweepThreads / 2;
+
+template <int LP>
+constexpr int staged_smem_bytes()
+{
+    return 2 * 5 * kStageSlots * LP + 16;   // two stages of 5 blocks, two mbarriers
+}
+
+template <int LP, bool FULL, bool LABELS>
+__global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_staged(SweepArgs a)
+{
+    constexpr int NP = LP / 16;
+    constexpr int kBlock = kStageSlots * LP;   // one direction (or the cost) of a tile
+    constexpr int kStage = 5 * kBlock;
+    extern __shared__ __align__(128) uint8_t sm[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 2 * kStage);
+    if (threadIdx.x == 0) {
+        tc::mbar_init(bar, 1);
+        tc::mbar_init(bar + 1, 1);
+    }
+    __syncthreads();
+    pdl_begin();
+    const int ngroups = a.h * a.wg;   // 16-slot groups of one colour
+    const int ntiles = (ngroups + 3) / 4;
+    const size_t arr = (size_t)ngroups * NP * kPieceStride;   // one colour-direction array
+    const uint8_t *msg_in = a.msg + (size_t)a.color * 4 * arr;
+    const uint8_t *cost_in = static_cast<const uint8_t *>(a.cost) + (size_t)a.color * arr;
+    auto issue = [&](int tile, int buf) {
+        const size_t off = (size_t)tile * 4 * NP * kPieceStride;
+        const uint32_t bytes = (uint32_t)min(4, ngroups - 4 * tile) * NP * kPieceStride;
+        uint8_t *dst = sm + buf * kStage;
+        tc::mbar_expect_tx(bar + buf, 5 * bytes);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            tc::bulk_g2s(dst + k * kBlock, msg_in + k * arr + off, bytes, bar + buf);
+        tc::bulk_g2s(dst + 4 * kBlock, cost_in + off, bytes, bar + buf);
+    };
+    if (threadIdx.x == 0 && (int)blockIdx.x < ntiles)
+        issue(blockIdx.x, 0);
+    const int sl = threadIdx.x >> 1, pair = threadIdx.x & 1;
+    const unsigned rowslots = 16u * (unsigned)a.wg;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int buf = it & 1;
+        const int next = tile + gridDim.x;
+        // the stage of `next` was read in the previous round, which every
+        // thread has left (the barrier at the end of the loop)
+        if (threadIdx.x == 0 && next < ntiles)
+            issue(next, buf ^ 1);
+        const bool arrived = tc::mbar_wait(bar + buf, (uint32_t)(it >> 1) & 1u);
+        if (!__syncthreads_and(arrived)) {
+            // the copies never completed: report, let the ones in flight land, leave
+            if (threadIdx.x == 0) {
+                atomicExch(a.status, VS_ETIMEOUT);
+                tc::mbar_wait(bar + buf, (uint32_t)(it >> 1) & 1u);
+                if (next < ntiles)
+                    tc::mbar_wait(bar + (buf ^ 1), (uint32_t)((it + 1) >> 1) & 1u);
+            }
+            __syncthreads();
+            return;
+        }
+        const unsigned slot = (unsigned)tile * kStageSlots + (unsigned)sl;
+        const int y = (int)(slot / rowslots);
+        const int xh = (int)(slot - (unsigned)y * rowslots);
+        const int x = 2 * xh + ((a.color + y) & 1);
+        if (y < a.h && x < a.w) {
+            const bool has[4] = {x > 0, x < a.w - 1, y > 0, y < a.h - 1};
+            const uint8_t *base = sm + buf * kStage + (sl >> 4) * NP * kPieceStride + (sl & 15) * 16;
+            const uint8_t *const in[4] = {base, base + kBlock, base + 2 * kBlock, base + 3 * kBlock};
+            const uint8_t *cost = base + 4 * kBlock;
+            sweep_pixel<LP, uint8_t, true, FULL, LABELS, false, true>(a, pair, x, y, has, in, has, cost, nullptr);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // batched sweeps: one launch advances the same level-iteration of many pairs
 //
 // The jobs of a launch (one per pair, same kernel variant) travel in the
@@ -967,7 +1088,7 @@ __global__ void k_bp_export(ExportArgs a)
 // the autotuner (vs_bp_autotune) measures the variants on a given problem
 // and records the fastest per (label count, level size), which then wins.
 
-enum SweepVariant { kVarPlain = 0, kVarPreload = 1, kVarSplit = 2, kVarSplit4 = 3 };
+enum SweepVariant { kVarPlain = 0, kVarPreload = 1, kVarSplit = 2, kVarSplit4 = 3, kVarStaged = 4 };
 
 // Defaults measured on B300 (vs_bp_autotune_times, eager launches, 2.7K
 // flight frames at s = 2, 4, 8, 64 and 128 labels): with up to 64 labels the
@@ -992,6 +1113,8 @@ int g_force_variant = -1;         // vs_bp_select_sweep: one variant on every le
 
 bool variant_allowed(int Lp, int variant, bool labels)
 {
+    if (variant == kVarStaged)   // chosen in launch_sweep, where eligibility is known
+        return false;
     if (labels)
         return variant == kVarPlain;   // only the plain kernel writes labels
     if (variant == kVarSplit)
@@ -1123,9 +1246,91 @@ void launch_sweep_any(int Lp, const SweepArgs *a, const BatchArgs *b, unsigned g
 }
 
 // One pair's sweep with the variant chosen for its level size.
+// The staged kernel serves the single-pair sweeps that read the level's own
+// messages with byte costs and byte-lane sums, on levels large enough to
+// fill the GPU.
+constexpr unsigned kStagedMinSlots = 1u << 16;
+
+bool staged_eligible(const SweepArgs &a, bool cost8, bool bytes)
+{
+    return cost8 && bytes && !a.from_parent && !a.zero_in && !a.materialize;
+}
+
+// Resident CTAs of a staged instantiation on the current device, cached.
+template <int LP, bool FULL, bool LABELS>
+int staged_grid_cap()
+{
+    constexpr int kMaxDev = 64;
+    static std::mutex mu;
+    static int cap[kMaxDev] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev)
+        return -1;
+    std::lock_guard<std::mutex> lk(mu);
+    if (cap[dev] == 0) {
+        auto kern = k_bp_sweep_staged<LP, FULL, LABELS>;
+        constexpr int smem = staged_smem_bytes<LP>();
+        int sms = 0, per_sm = 0;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSweepThreads, smem) != cudaSuccess ||
+            per_sm < 1)
+            return -1;
+        cap[dev] = sms * per_sm;
+    }
+    return cap[dev];
+}
+
+// False (nothing launched) when the device cannot host the kernel; the
+// caller then takes another variant.
+template <int LP, bool FULL, bool LABELS>
+bool launch_staged_t(const SweepArgs &a, cudaStream_t st)
+{
+    const int cap = staged_grid_cap<LP, FULL, LABELS>();
+    if (cap < 1) {
+        (void)cudaGetLastError();   // the failed attribute or occupancy query
+        return false;
+    }
+    const int ntiles = (a.h * a.wg + 3) / 4;
+    launch_pdl_smem(k_bp_sweep_staged<LP, FULL, LABELS>, dim3((unsigned)std::min(ntiles, cap)),
+                    dim3(kSweepThreads), (size_t)staged_smem_bytes<LP>(), st, a);
+    return true;
+}
+
+template <int LP>
+bool launch_staged_lp(const SweepArgs &a, bool full, bool labels, cudaStream_t st)
+{
+    if (full)
+        return labels ? launch_staged_t<LP, true, true>(a, st) : launch_staged_t<LP, true, false>(a, st);
+    return labels ? launch_staged_t<LP, false, true>(a, st) : launch_staged_t<LP, false, false>(a, st);
+}
+
+bool launch_staged(int Lp, const SweepArgs &a, cudaStream_t st)
+{
+    const bool full = a.L == Lp, labels = a.labels != nullptr;
+    switch (Lp) {
+    case 16: return launch_staged_lp<16>(a, full, labels, st);
+    case 32: return launch_staged_lp<32>(a, full, labels, st);
+    case 48: return launch_staged_lp<48>(a, full, labels, st);
+    case 64: return launch_staged_lp<64>(a, full, labels, st);
+    case 96: return launch_staged_lp<96>(a, full, labels, st);
+    default: return launch_staged_lp<128>(a, full, labels, st);
+    }
+}
+
 void launch_sweep(int Lp, const SweepArgs &a, bool cost8, bool bytes, cudaStream_t st, int variant = -1)
 {
     const bool labels = a.labels != nullptr;
+    if (variant < 0 && staged_eligible(a, cost8, bytes)) {
+        int forced;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            forced = g_force_variant;
+        }
+        if ((forced == kVarStaged || (forced < 0 && (unsigned)a.h * (unsigned)a.wh >= kStagedMinSlots)) &&
+            launch_staged(Lp, a, st))
+            return;
+    }
     if (variant < 0)
         variant = choose_variant(Lp, (unsigned)a.h * (unsigned)a.wh, labels);
     launch_sweep_any(Lp, &a, nullptr, sweep_blocks(a, variant), a.L == Lp, cost8, bytes, labels, variant, st);
@@ -1158,6 +1363,7 @@ SweepArgs sweep_args(const BpLayout &lay, uint8_t *ws, const vs_bp_params *p, in
     const bool last = l == 0 && t == p->iters - 1;
     a.labels = last ? labels : nullptr;
     a.labels_pitch = labels_pitch;
+    a.status = reinterpret_cast<int *>(ws + lay.status_off);
     return a;
 }
 
@@ -1203,6 +1409,7 @@ void launch_costs(const BpLayout &lay, uint8_t *ws, const uint8_t *left, const u
         a.cost0 = ws + lay.cost_off[0];
         a.cost1 = lay.levels > 1 ? ws + lay.cost_off[1] : nullptr;
         a.cost1_u8 = lay.levels > 1 ? lay.cost_u8[1] : 1;
+        a.status = reinterpret_cast<int *>(ws + lay.status_off);
         const long long n = (long long)a.h1 * ((a.w1 + 31) / 32) * (lay.Lp / 16) * 32;
         const int slot = prof_begin(kProfBpOther, st);
         launch_pdl(k_cost01, dim3((unsigned)((n + 127) / 128)), dim3(128), st, a);
@@ -1606,9 +1813,28 @@ extern "C" int vs_bp_autotune_times(float *ms, int max)
     return n;
 }
 
+extern "C" int vs_bp_status(const void *workspace, size_t ws_bytes, int w, int h, const vs_bp_params *p,
+                            void *stream)
+{
+    using namespace vs;
+    if (!params_ok(w, h, p))
+        return VS_EINVAL;
+    const BpLayout lay = make_layout(w, h, p);
+    const int rc = check_workspace(lay, workspace, ws_bytes);
+    if (rc != VS_OK)
+        return rc;
+    int status = VS_ECUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(&status, static_cast<const uint8_t *>(workspace) + lay.status_off, sizeof(int),
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return VS_ECUDA;
+    return status == VS_ETIMEOUT ? VS_ETIMEOUT : VS_OK;
+}
+
 extern "C" int vs_bp_select_sweep(int variant)
 {
-    if (variant < -1 || variant > 3)
+    if (variant < -1 || variant > 4)
         return VS_EINVAL;
     std::lock_guard<std::mutex> lk(vs::g_tune_mu);
     vs::g_force_variant = variant;

@@ -1,8 +1,9 @@
 // Thin inline-PTX wrappers for the 5th-generation tensor cores of sm_100+
-// (tcgen05: MMA with the accumulator in tensor memory, TMEM) and the
-// mbarrier that tracks their completion.  Only what the smoothed-BP kernels
-// use: one CTA (cta_group::1), kind::tf32, K-major operands in shared memory
-// without swizzling, 32x32b TMEM loads.
+// (tcgen05: MMA with the accumulator in tensor memory, TMEM), the bulk
+// asynchronous global-to-shared copies of the TMA engine, and the mbarrier
+// that tracks both.  Only what the kernels here use: one CTA
+// (cta_group::1), kind::tf32, K-major operands in shared memory without
+// swizzling, 32x32b TMEM loads, 1-D bulk copies.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -38,15 +39,35 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity, uint32_
     return done != 0;
 }
 
-// Bounded wait: at most `limit` attempts of up to 100 us each (the
-// tensor-core work waited on here takes microseconds; the bound is about a
-// second).  Returns false if the phase never completed.
+// Bounded wait: at most `limit` attempts of up to 100 us each (the work
+// waited on here, MMAs or bulk copies, takes microseconds; the bound is
+// about a second).  Returns false if the phase never completed.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit = 10000)
 {
     for (uint32_t i = 0; i < limit; ++i)
         if (mbar_try(bar, parity, 100000u))
             return true;
     return false;
+}
+
+// The calling thread arrives once on `bar` and adds `bytes` to the
+// transaction count that the phase waits for (the bulk copies below).
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// ---------------------------------------------------------------- bulk copies
+// `bytes` (a multiple of 16) from global `src` to shared `dst`, both 16-byte
+// aligned, completing as transactions on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
 }
 
 // ---------------------------------------------------------------- fences

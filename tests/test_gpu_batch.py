@@ -103,12 +103,13 @@ def test_autotune_keeps_results_identical():
     np.testing.assert_array_equal(before, oracle.bp(l, r, 64, 4, 10, 20, 10, 40, mode=oracle.MSG_DT))
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("shape", [(190, 338, 64), (61, 97, 128), (33, 70, 96)])
 def test_every_sweep_variant_matches_the_oracle(variant, shape):
-    """Each sweep kernel (plain, preload, labels split over two or four lanes)
-    forced on every level where it applies gives the oracle's labels and final
-    level-0 messages bit for bit."""
+    """Each sweep kernel (plain, preload, labels split over two or four lanes,
+    staged through shared memory -- here on levels 0 and 1, whose costs and
+    belief sums fit bytes) forced on every level where it applies gives the
+    oracle's labels and final level-0 messages bit for bit."""
     h, w, L = shape
     L_, R_, l, r = _pair(11 + variant, h, w)
     p = vs.BPParams(L, 4, 6, 20, 10, 40)
@@ -117,6 +118,7 @@ def test_every_sweep_variant_matches_the_oracle(variant, shape):
         ws = torch.empty(vs.bp_workspace_size(w, h, p), dtype=torch.uint8, device="cuda")
         got = vs.bp_stereo(L_, R_, p, workspace=ws).cpu().numpy()
         msg = vs.bp_export_messages(ws, w, h, p).cpu().numpy()
+        vs.bp_status(ws, w, h, p)    # no bounded wait ran out
     finally:
         vs.bp_select_sweep(-1)
     want, wmsg = oracle.bp(l, r, L, 4, 6, 20, 10, 40, mode=oracle.MSG_DT, return_messages=True)
