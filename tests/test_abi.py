@@ -81,6 +81,15 @@ def test_bad_arguments_are_rejected_on_the_host(lib):
     assert lib.vs_guided_upsample(fake, 12, 10, 12, fake, 36, fake, 48, 40, 144, ctypes.byref(jr), fake, None) == vs.VS_EINVAL
     assert lib.vs_reproject(fake, 10, 10, ctypes.byref(cam), 0.0, fake, None) == vs.VS_EINVAL
     assert lib.vs_reproject(fake, 10, 10, ctypes.byref(cam), -1.0, fake, None) == vs.VS_EINVAL
+    # the BP status read-out checks its workspace before touching the device
+    bad_bp = vs._BPParams(1, 3, 5, 20, 10, 40)
+    assert lib.vs_bp_status(fake, 1 << 30, 160, 120, ctypes.byref(bad_bp), None) == vs.VS_EINVAL
+    assert lib.vs_bp_status(None, 1 << 30, 160, 120, ctypes.byref(p), None) == vs.VS_EWORKSPACE
+    assert lib.vs_bp_status(fake, 100, 160, 120, ctypes.byref(p), None) == vs.VS_EWORKSPACE
+    assert lib.vs_bp_status(fake + 16, 1 << 30, 160, 120, ctypes.byref(p), None) == vs.VS_EWORKSPACE
+    # sweep variants: -1 (automatic) .. 4 (staged)
+    assert lib.vs_bp_select_sweep(5) == vs.VS_EINVAL
+    assert lib.vs_bp_select_sweep(-2) == vs.VS_EINVAL
 
 
 def test_pipeline_host_checks(lib):

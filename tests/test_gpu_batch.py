@@ -104,7 +104,7 @@ def test_autotune_keeps_results_identical():
 
 
 @pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
-@pytest.mark.parametrize("shape", [(190, 338, 64), (61, 97, 128), (33, 70, 96)])
+@pytest.mark.parametrize("shape", [(190, 338, 64), (61, 97, 128), (33, 70, 96), (29, 45, 37), (36, 52, 16)])
 def test_every_sweep_variant_matches_the_oracle(variant, shape):
     """Each sweep kernel (plain, preload, labels split over two or four lanes,
     staged through shared memory -- here on levels 0 and 1, whose costs and
