@@ -153,6 +153,8 @@ struct Cost01Args {
     uint8_t *cost1;         // null when there is no level 1
     int cost1_u8;
     int *status;            // reset to VS_OK: the first kernel of every call
+    uint8_t *msg0, *msg1;   // levels 0 and 1 (msg1 null without level 1): the incoming
+                            // slots no neighbour ever writes are zeroed
 };
 
 // D0(x, y, d) = min(|IL(x,y) - IR(x-d,y)|, Td), Td where x - d < 0, 0 on
@@ -255,12 +257,30 @@ __global__ void __launch_bounds__(128) k_cost01(Cost01Args a)
                     out[ii] = cost0_chunk_slow(a, rowL, rowR, 2 * X + ii, j, acc);
         }
 #pragma unroll
-        for (int ii = 0; ii < 2; ++ii)
-            if (2 * X + ii < a.w0)
-                st_piece(a.cost0 + slot_base(((ii + jj) & 1) * a.h0 + yf, X, a.wg0, chunks), j, out[ii]);
+        for (int ii = 0; ii < 2; ++ii) {
+            const int xf = 2 * X + ii, cf = (ii + jj) & 1;
+            if (xf >= a.w0)
+                continue;
+            st_piece(a.cost0 + slot_base(cf * a.h0 + yf, X, a.wg0, chunks), j, out[ii]);
+            // incoming slots of a missing neighbour (frame border) read as 0
+            const uint4 z = make_uint4(0, 0, 0, 0);
+            const bool border[4] = {xf == 0, xf == a.w0 - 1, yf == 0, yf == a.h0 - 1};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (border[k])
+                    st_piece(a.msg0 + slot_base((cf * 4 + k) * a.h0 + yf, X, a.wg0, chunks), j, z);
+        }
     }
     if (!a.cost1)
         return;
+    {
+        const uint4 z = make_uint4(0, 0, 0, 0);
+        const bool border[4] = {X == 0, X == a.w1 - 1, Y == 0, Y == a.h1 - 1};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (border[k])
+                st_piece(a.msg1 + slot_base((((X + Y) & 1) * 4 + k) * a.h1 + Y, X >> 1, a.wg1, chunks), j, z);
+    }
     const int row1 = ((X + Y) & 1) * a.h1 + Y;
     if (a.cost1_u8) {   // every sum is <= 4 Td <= 255 here
         st_piece(a.cost1 + slot_base(row1, X >> 1, a.wg1, chunks), j,
@@ -360,6 +380,7 @@ struct SweepArgs {
     uint8_t *labels;        // last level-0 iteration: labels of the active colour
     int labels_pitch;
     int *status;            // set to VS_ETIMEOUT by a kernel that gives up a bounded wait
+    int zero_border;        // this level's never-written incoming slots hold 0 (levels 0, 1)
 };
 
 // Byte i of word a in the low half and byte i of word b in the high half,
@@ -826,7 +847,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_split(SweepArgs a)
 // 3109).  Reading the cost from global memory instead (four blocks per
 // stage, six CTAs per SM) measured 3953 / 3015.
 // For the iterations that read this level's own messages (not the first of a
-// level) with byte costs and byte-lane sums -- level 0 here.
+// level) with byte costs and byte-lane sums, on levels 0 and 1, whose
+// never-written border slots k_cost01 zeroes -- level 0 by default.
 constexpr int kStageSlots = kSweepThreads / 2;
 
 template <int LP>
@@ -897,7 +919,10 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_staged(SweepArgs a)
             const uint8_t *base = sm + buf * kStage + (sl >> 4) * NP * kPieceStride + (sl & 15) * 16;
             const uint8_t *const in[4] = {base, base + kBlock, base + 2 * kBlock, base + 3 * kBlock};
             const uint8_t *cost = base + 4 * kBlock;
-            sweep_pixel<LP, uint8_t, true, FULL, LABELS, false, true>(a, pair, x, y, has, in, has, cost, nullptr);
+            // the slots of missing neighbours hold 0 (k_cost01 of this call), so
+            // all four directions are read as they are
+            const bool all[4] = {true, true, true, true};
+            sweep_pixel<LP, uint8_t, true, FULL, LABELS, false, true>(a, pair, x, y, has, in, all, cost, nullptr);
         }
         __syncthreads();
     }
@@ -1253,7 +1278,7 @@ constexpr unsigned kStagedMinSlots = 1u << 16;
 
 bool staged_eligible(const SweepArgs &a, bool cost8, bool bytes)
 {
-    return cost8 && bytes && !a.from_parent && !a.zero_in && !a.materialize;
+    return cost8 && bytes && !a.from_parent && !a.zero_in && !a.materialize && a.zero_border;
 }
 
 // Resident CTAs of a staged instantiation on the current device, cached.
@@ -1364,6 +1389,7 @@ SweepArgs sweep_args(const BpLayout &lay, uint8_t *ws, const vs_bp_params *p, in
     a.labels = last ? labels : nullptr;
     a.labels_pitch = labels_pitch;
     a.status = reinterpret_cast<int *>(ws + lay.status_off);
+    a.zero_border = l <= 1;
     return a;
 }
 
@@ -1410,6 +1436,8 @@ void launch_costs(const BpLayout &lay, uint8_t *ws, const uint8_t *left, const u
         a.cost1 = lay.levels > 1 ? ws + lay.cost_off[1] : nullptr;
         a.cost1_u8 = lay.levels > 1 ? lay.cost_u8[1] : 1;
         a.status = reinterpret_cast<int *>(ws + lay.status_off);
+        a.msg0 = ws + lay.msg_off[0];
+        a.msg1 = lay.levels > 1 ? ws + lay.msg_off[1] : nullptr;
         const long long n = (long long)a.h1 * ((a.w1 + 31) / 32) * (lay.Lp / 16) * 32;
         const int slot = prof_begin(kProfBpOther, st);
         launch_pdl(k_cost01, dim3((unsigned)((n + 127) / 128)), dim3(128), st, a);
