@@ -61,7 +61,16 @@ struct SpArgs {
     float k[kSpMaxLabels];
     float kl[kSpMaxLabels];
     float kt[kSpMaxLabels];
+    // banded form: K(delta) = kinf = exp(-T / tau) for every delta >= band
+    // (lambda delta >= T); kd = K - kinf, zero from the band on
+    int band;
+    float kinf;
+    float kd[kSpMaxLabels];
 };
+
+// Band width of the banded kernels: used when the band of K (labels closer
+// than T / lambda) is at most this wide.
+constexpr int kSpBand = 8;
 
 __device__ __forceinline__ int neighbour(int p, int dir, int w, int h)
 {
@@ -120,18 +129,39 @@ __device__ __forceinline__ float shift_to_min(float (&e)[L])
     return m;
 }
 
-// s(d) = sum_d' K(|d - d'|) u(d').
-template <int L>
+// s(d) = sum_d' K(|d - d'|) u(d').  BW = 0: the whole L x L product.  BW > 0
+// (K constant = kinf from distance BW on): the same sum regrouped exactly as
+// kinf sum_d' u(d') + sum over |d - d'| < BW of (K - kinf) u(d'), 2 BW - 1
+// multiply-adds per label instead of L; for u >= 0 every term is
+// non-negative.
+template <int L, int BW>
 __device__ __forceinline__ void matvec_k(const SpArgs &a, const float (&u)[L], float (&s)[L])
 {
-#pragma unroll
-    for (int d = 0; d < L; ++d)
-        s[d] = 0.f;
-#pragma unroll
-    for (int dd = 0; dd < L; ++dd)
+    if constexpr (BW == 0) {
 #pragma unroll
         for (int d = 0; d < L; ++d)
-            s[d] = fmaf(a.k[d > dd ? d - dd : dd - d], u[dd], s[d]);
+            s[d] = 0.f;
+#pragma unroll
+        for (int dd = 0; dd < L; ++dd)
+#pragma unroll
+            for (int d = 0; d < L; ++d)
+                s[d] = fmaf(a.k[d > dd ? d - dd : dd - d], u[dd], s[d]);
+    } else {
+        float U = 0.f;
+#pragma unroll
+        for (int d = 0; d < L; ++d)
+            U += u[d];
+        const float base = a.kinf * U;
+#pragma unroll
+        for (int d = 0; d < L; ++d) {
+            float acc = base;
+#pragma unroll
+            for (int del = -(BW - 1); del < BW; ++del)
+                if (d + del >= 0 && d + del < L)
+                    acc = fmaf(a.kd[del < 0 ? -del : del], u[d + del], acc);
+            s[d] = acc;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -139,7 +169,7 @@ __device__ __forceinline__ void matvec_k(const SpArgs &a, const float (&u)[L], f
 // receives in slot k, from r = p + off(k), out of state t - 1.  In the last
 // iteration the four lanes of p add their messages to D_p and write the
 // beliefs instead of a state.
-template <int L, bool BELIEF>
+template <int L, bool BELIEF, int BW>
 __global__ void __launch_bounds__(kSpThreads, L <= 48 ? 4 : 3) k_sp_fwd(const __grid_constant__ SpArgs a)
 {
     pdl_begin();
@@ -155,7 +185,7 @@ __global__ void __launch_bounds__(kSpThreads, L <= 48 ? 4 : 3) k_sp_fwd(const __
         for (int d = 0; d < L; ++d)
             m[d] = exp2f(m[d] * a.nc);   // u
         float s[L];
-        matvec_k<L>(a, m, s);
+        matvec_k<L, BW>(a, m, s);
         float lsum = 0.f;
 #pragma unroll
         for (int d = 0; d < L; ++d) {
@@ -205,7 +235,7 @@ __global__ void __launch_bounds__(kSpThreads, L <= 48 ? 4 : 3) k_sp_fwd(const __
 //   dL/d(slot j of p, state t - 1) = sum over q != j of dL/dh_q
 //   dL/dD_p                       += sum over q of dL/dh_q
 // and the scalar parts are summed per CTA in double.
-template <int L>
+template <int L, int BW>
 __global__ void __launch_bounds__(kSpThreads, L <= 32 ? 4 : (L == 48 ? 3 : 2)) k_sp_adj(const __grid_constant__ SpArgs a)
 {
     pdl_begin();
@@ -223,7 +253,7 @@ __global__ void __launch_bounds__(kSpThreads, L <= 32 ? 4 : (L == 48 ? 3 : 2)) k
         for (int d = 0; d < L; ++d)
             e[d] = exp2f(e[d] * a.nc);   // u
         float s[L];
-        matvec_k<L>(a, e, s);             // S = K u
+        matvec_k<L, BW>(a, e, s);         // S = K u
         const float *g = a.from_belief ? a.gin + (size_t)nb * L : a.gin + (size_t)(q ^ 1) * plane + (size_t)nb * L;
         float gsum = 0.f;
 #pragma unroll
@@ -246,9 +276,13 @@ __global__ void __launch_bounds__(kSpThreads, L <= 32 ? 4 : (L == 48 ? 3 : 2)) k
             }
         }
         // r^T Kl u and r^T Kt u from the correlation C(delta) = sum over
-        // |d - d'| = delta of r(d) u(d')
+        // |d - d'| = delta of r(d) u(d'); banded, Kl vanishes from the band on
+        // and Kt equals kinf there, so the tail is kinf sum over |d - d'| >= BW
+        // of r(d) u(d') = kinf sum_d r(d) (P(d - BW) + Q(d + BW)), with P / Q the
+        // prefix / suffix sums of u taken as running sums
+        constexpr int NDEL = BW == 0 ? L : BW;
 #pragma unroll
-        for (int del = 0; del < L; ++del) {
+        for (int del = 0; del < NDEL; ++del) {
             float cr = 0.f;
 #pragma unroll
             for (int d = 0; d + del < L; ++d) {
@@ -259,18 +293,53 @@ __global__ void __launch_bounds__(kSpThreads, L <= 32 ? 4 : (L == 48 ? 3 : 2)) k
             s_lam = fmaf(a.kl[del], cr, s_lam);
             s_T = fmaf(a.kt[del], cr, s_T);
         }
+        if constexpr (BW > 0) {
+            float run = 0.f, tail = 0.f;
+#pragma unroll
+            for (int d = BW; d < L; ++d) {
+                run += e[d - BW];
+                tail = fmaf(s[d], run, tail);
+            }
+            run = 0.f;
+#pragma unroll
+            for (int d = L - 1 - BW; d >= 0; --d) {
+                run += e[d + BW];
+                tail = fmaf(s[d], run, tail);
+            }
+            s_T = fmaf(a.kinf, tail, s_T);
+        }
         // dL/dh(d') = u(d') (K r)(d'), and sum_d' log2 u(d') dL/dh(d'), where
         // h - a = -tau ln2 log2 u (u = 0 contributes nothing)
         float s_lu = 0.f;
+        if constexpr (BW == 0) {
 #pragma unroll
-        for (int dd = 0; dd < L; ++dd) {
-            float V = 0.f;
+            for (int dd = 0; dd < L; ++dd) {
+                float V = 0.f;
+#pragma unroll
+                for (int d = 0; d < L; ++d)
+                    V = fmaf(a.k[d > dd ? d - dd : dd - d], s[d], V);
+                const float hb = e[dd] * V;
+                s_lu = fmaf(__log2f(fmaxf(e[dd], 1e-30f)), hb, s_lu);
+                e[dd] = hb;
+            }
+        } else {
+            // (K r)(d') = kinf sum_d r(d) + sum over the band of (K - kinf) r(d)
+            float R = 0.f;
 #pragma unroll
             for (int d = 0; d < L; ++d)
-                V = fmaf(a.k[d > dd ? d - dd : dd - d], s[d], V);
-            const float hb = e[dd] * V;
-            s_lu = fmaf(__log2f(fmaxf(e[dd], 1e-30f)), hb, s_lu);
-            e[dd] = hb;
+                R += s[d];
+            const float base = a.kinf * R;
+#pragma unroll
+            for (int dd = 0; dd < L; ++dd) {
+                float V = base;
+#pragma unroll
+                for (int del = -(BW - 1); del < BW; ++del)
+                    if (dd + del >= 0 && dd + del < L)
+                        V = fmaf(a.kd[del < 0 ? -del : del], s[dd + del], V);
+                const float hb = e[dd] * V;
+                s_lu = fmaf(__log2f(fmaxf(e[dd], 1e-30f)), hb, s_lu);
+                e[dd] = hb;
+            }
         }
         // tau dL/dtau = sum_d gt mt - sum_d' (h - a) dL/dh - lambda (.) - T (.),
         // sum_d gt mt = -tau ln2 sum_d gt log2 S
@@ -904,6 +973,13 @@ void fill_tables(SpArgs &a, const vs_sp_params *p)
         a.kl[del] = lin ? (float)(k * del) : 0.f;
         a.kt[del] = lin ? 0.f : (float)k;
     }
+    const double kinf = std::exp(-T / tau);
+    a.band = 0;
+    while (a.band < kSpMaxLabels && lam * a.band < T)   // the same test as `lin` above
+        ++a.band;
+    a.kinf = (float)kinf;
+    for (int del = 0; del < kSpMaxLabels; ++del)
+        a.kd[del] = lam * del < T ? (float)(std::exp(-lam * del / tau) - kinf) : 0.f;
     a.nc = (float)(-1.0 / (tau * std::log(2.0)));
     a.tau_ln2 = (float)(tau * std::log(2.0));
     a.lambda = p->lambda;
@@ -954,6 +1030,14 @@ inline cudaLaunchConfig_t pdl_config(dim3 grid, dim3 block, size_t smem, cudaStr
     return cfg;
 }
 
+// The banded SIMT kernels serve a band of at most kSpBand labels when that is
+// well under L (the full product is as cheap for 16 labels).
+template <int L>
+bool sp_banded(const SpArgs &a)
+{
+    return L >= 32 && a.band <= kSpBand;
+}
+
 // One forward iteration (pull form); with belief = true the last one, which
 // writes the beliefs instead of a message state.
 template <int L>
@@ -977,7 +1061,12 @@ int launch_fwd(const SpArgs &a, bool belief, cudaStream_t st)
     } else {
         const int nblocks = (int)(((size_t)4 * a.npix + kSpThreads - 1) / kSpThreads);
         cudaLaunchConfig_t cfg = pdl_config(dim3(nblocks), dim3(kSpThreads), 0, st, attr);
-        err = belief ? cudaLaunchKernelEx(&cfg, k_sp_fwd<L, true>, a) : cudaLaunchKernelEx(&cfg, k_sp_fwd<L, false>, a);
+        if (sp_banded<L>(a))
+            err = belief ? cudaLaunchKernelEx(&cfg, k_sp_fwd<L, true, kSpBand>, a)
+                         : cudaLaunchKernelEx(&cfg, k_sp_fwd<L, false, kSpBand>, a);
+        else
+            err = belief ? cudaLaunchKernelEx(&cfg, k_sp_fwd<L, true, 0>, a)
+                         : cudaLaunchKernelEx(&cfg, k_sp_fwd<L, false, 0>, a);
     }
     prof_end(slot, st);
     note_launch();
@@ -1007,7 +1096,8 @@ int launch_adj(const SpArgs &a, int grid, cudaStream_t st)
         err = cudaLaunchKernelEx(&cfg, k_sp_adj_tc<L>, a);
     } else {
         cudaLaunchConfig_t cfg = pdl_config(dim3(grid), dim3(kSpThreads), 0, st, attr);
-        err = cudaLaunchKernelEx(&cfg, k_sp_adj<L>, a);
+        err = sp_banded<L>(a) ? cudaLaunchKernelEx(&cfg, k_sp_adj<L, kSpBand>, a)
+                              : cudaLaunchKernelEx(&cfg, k_sp_adj<L, 0>, a);
     }
     prof_end(slot, st);
     note_launch();
