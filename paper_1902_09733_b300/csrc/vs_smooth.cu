@@ -165,10 +165,14 @@ __device__ __forceinline__ void matvec_k(const SpArgs &a, const float (&u)[L], f
 }
 
 // ---------------------------------------------------------------------------
-// Forward iteration, pull form: thread (p, k) computes the message that p
-// receives in slot k, from r = p + off(k), out of state t - 1.  In the last
-// iteration the four lanes of p add their messages to D_p and write the
-// beliefs instead of a state.
+// Forward iteration.  State t: thread (r, q) sends the message of r to its
+// neighbour nb = r + off(q), which receives it in slot q ^ 1, out of state
+// t - 1 (h = D_r + the slots of r other than q); the four lanes of r read the
+// same rows, so each gather serves four messages.  A lane whose neighbour is
+// missing writes the zero message of r's own slot q instead.  In the last
+// iteration (BELIEF) the pull form is used: thread (p, k) computes the
+// message p receives in slot k, from r = p + off(k), and the four lanes of p
+// add their messages to D_p to write the beliefs.
 template <int L, bool BELIEF, int BW>
 __global__ void __launch_bounds__(kSpThreads, L <= 48 ? 4 : 3) k_sp_fwd(const __grid_constant__ SpArgs a)
 {
@@ -176,10 +180,14 @@ __global__ void __launch_bounds__(kSpThreads, L <= 48 ? 4 : 3) k_sp_fwd(const __
     const int gid = blockIdx.x * kSpThreads + threadIdx.x;
     const int p = gid >> 2, k = gid & 3;
     const bool valid = p < a.npix;
+    // BELIEF: r sends to p; otherwise p sends to r
     const int r = valid ? neighbour(p, k, a.w, a.h) : -1;
     float m[L];
     if (r >= 0) {
-        gather_h<L>(a, r, k ^ 1, m);   // r's slot k^1 holds what p sent it
+        if (BELIEF)
+            gather_h<L>(a, r, k ^ 1, m);   // r's slot k^1 holds what p sent it
+        else
+            gather_h<L>(a, p, k, m);       // p's slot k holds what r sent it
         shift_to_min<L>(m);
 #pragma unroll
         for (int d = 0; d < L; ++d)
@@ -203,7 +211,9 @@ __global__ void __launch_bounds__(kSpThreads, L <= 48 ? 4 : 3) k_sp_fwd(const __
     }
     if constexpr (!BELIEF) {
         if (valid) {
-            float *o = a.mout + (size_t)k * a.npix * L + (size_t)p * L;
+            // to slot k^1 of the receiver, or a zero into p's own slot k
+            float *o = r >= 0 ? a.mout + (size_t)(k ^ 1) * a.npix * L + (size_t)r * L
+                              : a.mout + (size_t)k * a.npix * L + (size_t)p * L;
 #pragma unroll
             for (int c = 0; c < L / 4; ++c)
                 st4(o + 4 * c, m[4 * c], m[4 * c + 1], m[4 * c + 2], m[4 * c + 3]);
