@@ -91,7 +91,11 @@ __device__ __forceinline__ void st4(float *p, float a, float b, float c, float d
 }
 
 // h = D_q + the three slots of q other than `skip` (state may be nullptr).
-template <int L>
+// SAME_ROWS: the four lanes of a pixel call this for the same q (sender
+// form), so every lane reads all four slots in the same order, the skipped
+// one with weight 0: each load instruction then touches one row per pixel
+// instead of four.  Otherwise only the three slots are read.
+template <int L, bool SAME_ROWS>
 __device__ __forceinline__ void gather_h(const SpArgs &a, int q, int skip, float (&h)[L])
 {
     const float *dq = a.cost + (size_t)q * L;
@@ -103,13 +107,17 @@ __device__ __forceinline__ void gather_h(const SpArgs &a, int q, int skip, float
     if (a.min_ != nullptr) {
         const size_t plane = (size_t)a.npix * L;
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const int j = (skip + 1 + i) & 3;
+        for (int i = 0; i < (SAME_ROWS ? 4 : 3); ++i) {
+            const int j = SAME_ROWS ? i : (skip + 1 + i) & 3;
+            const float f = SAME_ROWS && j == skip ? 0.f : 1.f;
             const float *s = a.min_ + (size_t)j * plane + (size_t)q * L;
 #pragma unroll
             for (int c = 0; c < L / 4; ++c) {
                 const float4 v = ld4(s + 4 * c);
-                h[4 * c] += v.x, h[4 * c + 1] += v.y, h[4 * c + 2] += v.z, h[4 * c + 3] += v.w;
+                h[4 * c] = fmaf(f, v.x, h[4 * c]);
+                h[4 * c + 1] = fmaf(f, v.y, h[4 * c + 1]);
+                h[4 * c + 2] = fmaf(f, v.z, h[4 * c + 2]);
+                h[4 * c + 3] = fmaf(f, v.w, h[4 * c + 3]);
             }
         }
     }
@@ -185,9 +193,9 @@ __global__ void __launch_bounds__(kSpThreads, L <= 48 ? 4 : 3) k_sp_fwd(const __
     float m[L];
     if (r >= 0) {
         if (BELIEF)
-            gather_h<L>(a, r, k ^ 1, m);   // r's slot k^1 holds what p sent it
+            gather_h<L, false>(a, r, k ^ 1, m);   // r's slot k^1 holds what p sent it
         else
-            gather_h<L>(a, p, k, m);       // p's slot k holds what r sent it
+            gather_h<L, true>(a, p, k, m);        // p's slot k holds what r sent it
         shift_to_min<L>(m);
 #pragma unroll
         for (int d = 0; d < L; ++d)
@@ -257,7 +265,7 @@ __global__ void __launch_bounds__(kSpThreads, L <= 32 ? 4 : (L == 48 ? 3 : 2)) k
     float e[L];   // h - min h, then u, then dL/dh
     float s_lam = 0.f, s_T = 0.f, s_tau = 0.f;
     if (nb >= 0) {
-        gather_h<L>(a, p, q, e);
+        gather_h<L, true>(a, p, q, e);
         shift_to_min<L>(e);
 #pragma unroll
         for (int d = 0; d < L; ++d)
@@ -622,7 +630,7 @@ __global__ void __launch_bounds__(TcPlan<L, false>::kThreads, 1) k_sp_fwd_tc(con
         const int r = valid ? neighbour(p, k, a.w, a.h) : -1;
         float m[L];
         if (r >= 0) {
-            gather_h<L>(a, r, k ^ 1, m);
+            gather_h<L, false>(a, r, k ^ 1, m);
             shift_to_min<L>(m);
 #pragma unroll
             for (int d = 0; d < L; ++d)
@@ -729,7 +737,7 @@ __global__ void __launch_bounds__(TcPlan<L, true>::kThreads, 1) k_sp_adj_tc(cons
         const int nb = valid ? neighbour(p, q, a.w, a.h) : -1;
         float u[L];
         if (nb >= 0) {
-            gather_h<L>(a, p, q, u);
+            gather_h<L, false>(a, p, q, u);
             shift_to_min<L>(u);
 #pragma unroll
             for (int d = 0; d < L; ++d)
