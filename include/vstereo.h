@@ -211,6 +211,13 @@ int vs_bp_autotune_times(float *ms, int max);
  * variant runs.  Errors: VS_EINVAL. */
 int vs_bp_select_sweep(int variant);
 
+/* Test aid for the bounded waits: with on = 1, staged sweeps launched from
+ * then on announce their tile bytes to the mbarrier but issue no copy, so
+ * each wait runs out (about a second per wait) and the call's status becomes
+ * VS_ETIMEOUT, its labels invalid; on = 0 restores normal operation.  No
+ * fault and no unbounded wait results.  Errors: VS_EINVAL. */
+int vs_bp_test_withhold_copies(int on);
+
 /* Synchronises `stream` and reports whether a kernel of the last
  * vs_bp_stereo call on this workspace gave up a bounded wait for its
  * shared-memory copies (VS_ETIMEOUT; the labels are then invalid), else

@@ -175,6 +175,7 @@ def lib() -> ctypes.CDLL:
             "vs_bp_stereo": ([P, P, I, I, I, bp_p, P, I, P, S, P], I),
             "vs_bp_export_messages": ([P, S, I, I, bp_p, P, P], I),
             "vs_bp_status": ([P, S, I, I, bp_p, P], I),
+            "vs_bp_test_withhold_copies": ([I], I),
             "vs_guided_upsample": ([P, I, I, I, P, I, P, I, I, I, jbu_p, P, P], I),
             "vs_reproject": ([P, I, I, cam_p, F, P, P], I),
             "vs_guided_upsample_reproject": ([P, I, I, I, P, I, P, I, I, I, jbu_p, cam_p, F, P, P, P], I),
@@ -409,6 +410,11 @@ def bp_autotune_times():
 def bp_select_sweep(variant: int) -> None:
     """Force sweep variant 0..4 (plain, preload, split 2, split 4, staged) wherever it applies (-1: automatic)."""
     _check("vs_bp_select_sweep", lib().vs_bp_select_sweep(int(variant)))
+
+
+def bp_test_withhold_copies(on: bool) -> None:
+    """Test aid: staged sweeps issue no copies, so their bounded waits run out (status VS_ETIMEOUT)."""
+    _check("vs_bp_test_withhold_copies", lib().vs_bp_test_withhold_copies(1 if on else 0))
 
 
 def bp_status(workspace: torch.Tensor, w: int, h: int, params: BPParams, stream=None) -> None:

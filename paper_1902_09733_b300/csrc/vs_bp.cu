@@ -31,6 +31,7 @@
 #include "vs_tcgen05.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -381,6 +382,7 @@ struct SweepArgs {
     int labels_pitch;
     int *status;            // set to VS_ETIMEOUT by a kernel that gives up a bounded wait
     int zero_border;        // this level's never-written incoming slots hold 0 (levels 0, 1)
+    int withhold_copies;    // test aid: the staged sweep expects its tile bytes but issues no copy
 };
 
 // Byte i of word a in the low half and byte i of word b in the high half,
@@ -881,6 +883,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_staged(SweepArgs a)
         const uint32_t bytes = (uint32_t)min(4, ngroups - 4 * tile) * NP * kPieceStride;
         uint8_t *dst = sm + buf * kStage;
         tc::mbar_expect_tx(bar + buf, 5 * bytes);
+        if (a.withhold_copies)   // nothing completes the phase: the bounded wait runs out
+            return;
 #pragma unroll
         for (int k = 0; k < 4; ++k)
             tc::bulk_g2s(dst + k * kBlock, msg_in + k * arr + off, bytes, bar + buf);
@@ -1135,6 +1139,7 @@ std::mutex g_tune_mu;
 std::vector<TuneEntry> g_tune;
 std::vector<float> g_tune_last;   // ms per launch of the last vs_bp_autotune, [level][variant]
 int g_force_variant = -1;         // vs_bp_select_sweep: one variant on every level where allowed
+std::atomic<int> g_withhold_copies{0};   // vs_bp_test_withhold_copies
 
 bool variant_allowed(int Lp, int variant, bool labels)
 {
@@ -1390,6 +1395,7 @@ SweepArgs sweep_args(const BpLayout &lay, uint8_t *ws, const vs_bp_params *p, in
     a.labels_pitch = labels_pitch;
     a.status = reinterpret_cast<int *>(ws + lay.status_off);
     a.zero_border = l <= 1;
+    a.withhold_copies = g_withhold_copies.load(std::memory_order_relaxed);
     return a;
 }
 
@@ -1858,6 +1864,14 @@ extern "C" int vs_bp_status(const void *workspace, size_t ws_bytes, int w, int h
         cudaStreamSynchronize(st) != cudaSuccess)
         return VS_ECUDA;
     return status == VS_ETIMEOUT ? VS_ETIMEOUT : VS_OK;
+}
+
+extern "C" int vs_bp_test_withhold_copies(int on)
+{
+    if (on != 0 && on != 1)
+        return VS_EINVAL;
+    vs::g_withhold_copies.store(on, std::memory_order_relaxed);
+    return VS_OK;
 }
 
 extern "C" int vs_bp_select_sweep(int variant)

@@ -90,6 +90,7 @@ def test_bad_arguments_are_rejected_on_the_host(lib):
     # sweep variants: -1 (automatic) .. 4 (staged)
     assert lib.vs_bp_select_sweep(5) == vs.VS_EINVAL
     assert lib.vs_bp_select_sweep(-2) == vs.VS_EINVAL
+    assert lib.vs_bp_test_withhold_copies(2) == vs.VS_EINVAL
 
 
 def test_pipeline_host_checks(lib):

@@ -1,0 +1,46 @@
+"""The bounded waits of the staged BP sweep: when the bulk copies a CTA waits
+for never arrive, each wait gives up after about a second, the call reports
+VS_ETIMEOUT through vs_bp_status, and the GPU context stays usable.  The
+missing copies are made on purpose by a test aid that announces the bytes to
+the mbarrier but issues no copy (no fault, no unbounded wait)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1902_09733_b300 as vs
+from paper_1902_09733_b300 import build, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    assert torch.cuda.is_available()
+    build.build()
+
+
+def test_staged_sweep_wait_runs_out_and_is_reported():
+    # one level, three iterations: iterations 1 and 2 read the level's own
+    # messages, so the forced staged variant runs them
+    p = vs.BPParams(16, 1, 3, 20, 10, 40)
+    left, right, _ = synth.noise_pair(3, w=64, h=48)
+    L, R = torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()
+    ws = torch.empty(vs.bp_workspace_size(64, 48, p), dtype=torch.uint8, device="cuda")
+    vs.bp_select_sweep(4)
+    try:
+        vs.bp_test_withhold_copies(True)
+        try:
+            vs.bp_stereo(L, R, p, workspace=ws)
+            with pytest.raises(vs.VSError) as e:
+                vs.bp_status(ws, 64, 48, p)
+            assert e.value.code == vs.VS_ETIMEOUT
+        finally:
+            vs.bp_test_withhold_copies(False)
+        # the same workspace and context serve the next call normally
+        lab = vs.bp_stereo(L, R, p, workspace=ws)
+        vs.bp_status(ws, 64, 48, p)
+    finally:
+        vs.bp_select_sweep(-1)
+    want = oracle.bp(left, right, 16, 1, 3, 20, 10, 40)
+    np.testing.assert_array_equal(lab.cpu().numpy(), want)
