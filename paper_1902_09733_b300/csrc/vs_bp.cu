@@ -15,9 +15,12 @@
 //   Messages live in [0, smooth_trunc] after normalisation, so 8 bits hold
 //   them exactly; all message arithmetic is integer.
 //
-// Kernels per call: k_cost01 (level-0 data term and its level-1 sums),
-// k_cost_down per further coarse level, one k_bp_sweep per iteration and
-// level, k_bp_labels.
+// Kernels per call: k_cost01 (level-0 data term and its level-1 sums; it
+// also resets the call's status word and zeroes the border message slots
+// of levels 0 and 1), k_cost_down per further coarse level, one sweep per
+// iteration and level (k_bp_sweep, k_bp_sweep_split on small levels,
+// k_bp_sweep_staged on large byte-lane levels), and k_bp_labels_bytes /
+// k_bp_labels for the colour the last sweep did not label.
 //
 // k_bp_sweep: two threads per active pixel, each owning a pair of outgoing
 // directions (left/right or up/down).  A thread packs the pair into the two
