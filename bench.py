@@ -245,19 +245,27 @@ def sweep_bytes_per_launch(w, h, L):
     return 0.5 * (per[col == 0].sum() + per[col == 1].sum())
 
 
+def code_sha256(path: str) -> str:
+    """SHA-256 of a source file's code: comments and blank lines removed, so
+    edits to comments do not retire a capture of the same kernels."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
+    return hashlib.sha256("\n".join(ln for ln in lines if ln.strip()).encode()).hexdigest()
+
+
 def committed_traffic(kernel_src: str):
     """DRAM bytes per launch of the level-0 sweep from the committed ncu
-    summary, if it was taken on the current kernel source."""
+    summary, if it was taken on the current kernel code."""
     path = os.path.join(ROOT, "profiles", "k_bp_sweep_level0_2704x1520.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    sh = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
+    sh = re.search(r"kernel_code_sha256:\s*([0-9a-f]+)", text)
     if not m or not sh:
         return None
-    cur = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-    return float(m.group(1)) if sh.group(1) == cur else None
+    return float(m.group(1)) if sh.group(1) == code_sha256(kernel_src) else None
 
 
 def run_batched(args, vs, synth, torch, dev, cam):
