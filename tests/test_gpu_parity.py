@@ -315,6 +315,7 @@ def _assert_xyz_close(a, b, disp_ref):
     (40, 64, vs.JBUParams(4, 2, 1.0, 5000.0)),  # flat range term: frame-edge taps must stay out
     (30, 62, vs.JBUParams(2, 2, 1.0, 5000.0)),
     (44, 60, vs.JBUParams(4, 3, 0.25, 12.0)),   # spatial spread beyond the scale-4 kernel's range
+    (40, 64, vs.JBUParams(4, 2, 1.0, 2.0)),     # narrow range term: many pixels' weights underflow
 ])
 def test_jbu_and_reproject_small(H, W, jp):
     for smooth in (True, False):
