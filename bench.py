@@ -349,7 +349,15 @@ def run_batched(args, vs, synth, torch, dev, cam):
             "autotuned_variants": tuned}
 
 
-SP_BAND = 8   # band width of the library's banded smoothed-BP kernels
+def sp_kernel_band(L, lam, T):
+    """Band of the library's SIMT smoothed-BP kernels: the smallest of 4, 6, 8
+    holding the labels closer than T / lambda, 0 (dense) beyond or at 16 labels."""
+    b = 0
+    while b < 64 and lam * b < T:
+        b += 1
+    if L < 32 or b > 8:
+        return 0
+    return 4 if b <= 4 else (6 if b <= 6 else 8)
 
 
 def sp_flops(L, band):
@@ -424,13 +432,13 @@ def run_smooth(args, vs, synth, torch, dev):
              "adjoint_ms": e[1].elapsed_time(e[2]) / args.smooth_reps,
              "forward_iteration_us": fwd_us, "adjoint_iteration_us": adj_us}
         if fam == "simt":
-            # lambda 2.5, T 13.75: K is constant from distance 6 on, within the banded kernels' 8
-            f_msg, a_msg = sp_flops(L, SP_BAND)
+            band = sp_kernel_band(L, p.lam, p.trunc)   # lambda 2.5, T 13.75: 6
+            f_msg, a_msg = sp_flops(L, band)
             fl_f, fl_a = edges * f_msg, edges * a_msg
             d_f, d_a = sp_flops(L, 0)
             r["alu"] = {"bound": "alu", "unit": "TFLOP/s", "peak": fp32_peak,
                         "peak_source": f"148 SMs x 128 FP32 FMA lanes x 2 x {sm_mhz:.0f} MHz",
-                        "kernels": f"banded (K constant beyond {SP_BAND} labels): {f_msg:.0f} / {a_msg:.0f} "
+                        "kernels": f"banded (K constant beyond {band} labels): {f_msg:.0f} / {a_msg:.0f} "
                                    f"flops per forward / adjoint message, against {d_f:.0f} / {d_a:.0f} dense",
                         "forward_achieved": fl_f / (fwd_us * 1e-6) / 1e12,
                         "adjoint_achieved": fl_a / (adj_us * 1e-6) / 1e12}

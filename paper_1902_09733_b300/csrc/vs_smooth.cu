@@ -68,8 +68,8 @@ struct SpArgs {
     float kd[kSpMaxLabels];
 };
 
-// Band width of the banded kernels: used when the band of K (labels closer
-// than T / lambda) is at most this wide.
+// Widest band of the banded kernels: used when the band of K (labels closer
+// than T / lambda) is at most this wide; they come in bands of 4, 6 and 8.
 constexpr int kSpBand = 8;
 
 __device__ __forceinline__ int neighbour(int p, int dir, int w, int h)
@@ -1048,12 +1048,15 @@ inline cudaLaunchConfig_t pdl_config(dim3 grid, dim3 block, size_t smem, cudaStr
     return cfg;
 }
 
-// The banded SIMT kernels serve a band of at most kSpBand labels when that is
-// well under L (the full product is as cheap for 16 labels).
+// Band of the SIMT kernels for these parameters: the smallest compiled band
+// (4, 6, 8) that holds the band of K, or 0 (the full product) for a wider
+// band or 16 labels, where the full product is as cheap.
 template <int L>
-bool sp_banded(const SpArgs &a)
+int sp_band(const SpArgs &a)
 {
-    return L >= 32 && a.band <= kSpBand;
+    if (L < 32 || a.band > kSpBand)
+        return 0;
+    return a.band <= 4 ? 4 : (a.band <= 6 ? 6 : 8);
 }
 
 // One forward iteration (pull form); with belief = true the last one, which
@@ -1079,12 +1082,23 @@ int launch_fwd(const SpArgs &a, bool belief, cudaStream_t st)
     } else {
         const int nblocks = (int)(((size_t)4 * a.npix + kSpThreads - 1) / kSpThreads);
         cudaLaunchConfig_t cfg = pdl_config(dim3(nblocks), dim3(kSpThreads), 0, st, attr);
-        if (sp_banded<L>(a))
-            err = belief ? cudaLaunchKernelEx(&cfg, k_sp_fwd<L, true, kSpBand>, a)
-                         : cudaLaunchKernelEx(&cfg, k_sp_fwd<L, false, kSpBand>, a);
-        else
+        switch (sp_band<L>(a)) {
+        case 4:
+            err = belief ? cudaLaunchKernelEx(&cfg, k_sp_fwd<L, true, 4>, a)
+                         : cudaLaunchKernelEx(&cfg, k_sp_fwd<L, false, 4>, a);
+            break;
+        case 6:
+            err = belief ? cudaLaunchKernelEx(&cfg, k_sp_fwd<L, true, 6>, a)
+                         : cudaLaunchKernelEx(&cfg, k_sp_fwd<L, false, 6>, a);
+            break;
+        case 8:
+            err = belief ? cudaLaunchKernelEx(&cfg, k_sp_fwd<L, true, 8>, a)
+                         : cudaLaunchKernelEx(&cfg, k_sp_fwd<L, false, 8>, a);
+            break;
+        default:
             err = belief ? cudaLaunchKernelEx(&cfg, k_sp_fwd<L, true, 0>, a)
                          : cudaLaunchKernelEx(&cfg, k_sp_fwd<L, false, 0>, a);
+        }
     }
     prof_end(slot, st);
     note_launch();
@@ -1114,8 +1128,12 @@ int launch_adj(const SpArgs &a, int grid, cudaStream_t st)
         err = cudaLaunchKernelEx(&cfg, k_sp_adj_tc<L>, a);
     } else {
         cudaLaunchConfig_t cfg = pdl_config(dim3(grid), dim3(kSpThreads), 0, st, attr);
-        err = sp_banded<L>(a) ? cudaLaunchKernelEx(&cfg, k_sp_adj<L, kSpBand>, a)
-                              : cudaLaunchKernelEx(&cfg, k_sp_adj<L, 0>, a);
+        switch (sp_band<L>(a)) {
+        case 4: err = cudaLaunchKernelEx(&cfg, k_sp_adj<L, 4>, a); break;
+        case 6: err = cudaLaunchKernelEx(&cfg, k_sp_adj<L, 6>, a); break;
+        case 8: err = cudaLaunchKernelEx(&cfg, k_sp_adj<L, 8>, a); break;
+        default: err = cudaLaunchKernelEx(&cfg, k_sp_adj<L, 0>, a);
+        }
     }
     prof_end(slot, st);
     note_launch();
