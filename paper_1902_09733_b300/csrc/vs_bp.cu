@@ -849,8 +849,10 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_split(SweepArgs a)
 // Measured on the 2.7K pair (level 0, 64 labels, 740 resident CTAs): 17.3 us
 // per sweep against 16.7 for the register-preload kernel, yet four pairs in
 // flight run 4110 pairs/s against 3941 (one pair at a time 3015 against
-// 3109).  Reading the cost from global memory instead (four blocks per
-// stage, six CTAs per SM) measured 3953 / 3015.
+// 3109); since the border slots are zeroed and all four directions are read
+// without selects, 16.5 us per sweep and 4107 / 3070-3090 pairs/s.  Reading
+// the cost from global memory instead (four blocks per stage, six CTAs per
+// SM) measured 3953 / 3015.
 // For the iterations that read this level's own messages (not the first of a
 // level) with byte costs and byte-lane sums, on levels 0 and 1, whose
 // never-written border slots k_cost01 zeroes -- level 0 by default.
