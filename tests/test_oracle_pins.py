@@ -434,6 +434,37 @@ def test_jbu_range_kernel_uses_full_res_detail():
     np.testing.assert_allclose(d[:, 20:22], 9 * s, rtol=1e-9)
 
 
+def test_jbu_hand_worked_weights(golden):
+    """Eq. 2 values worked by hand, exponent by exponent, at a clipped corner,
+    an interior window and a second clipped corner (tests/golden/jbu_hand.txt).
+    These fix the numeric scale of both Gaussians: the factor 2 in 2 sigma^2,
+    sigma_s in low-res pixels and the Euclidean RGB distance."""
+    g = golden("jbu_hand.txt")
+    w, h, W, H = (int(v) for v in g["size"][0][0])
+    s, r, sig_s, sig_r = g["params"][0][0]
+    lab = np.array(g["lab"][0], np.uint8)
+    gl = np.array(g["glow"][0], np.uint8).reshape(h, w, 3)
+    gf = np.zeros((H, W, 3), np.uint8)
+    pix = [row[0] for row in g["pixel"]]
+    for x, y, R, G, B, _ in pix:
+        gf[int(y), int(x)] = (int(R), int(G), int(B))
+    d = oracle.guided_upsample(lab, gl, gf, int(s), int(r), sig_s, sig_r)
+    for x, y, _, _, _, want in pix:
+        assert abs(d[int(y), int(x)] - want) <= 1e-12 * want, (x, y, d[int(y), int(x)], want)
+
+
+def test_jbu_two_taps_closed_form(golden):
+    """Two taps on a flat guide: D_p = s (w1 d1 + w2 d2) / (w1 + w2) with
+    w = exp(-ds2 / 2), the decimal values of tests/golden/jbu_hand.txt."""
+    g = golden("jbu_hand.txt")
+    lab = np.array([[0, 10]], np.uint8)
+    gl = np.full((1, 2, 3), 77, np.uint8)
+    gf = np.full((2, 4, 3), 77, np.uint8)
+    d = oracle.guided_upsample(lab, gl, gf, 2, 1, 1.0, 12.0)
+    for x, y, want in (row[0] for row in g["two"]):
+        assert abs(d[int(y), int(x)] - want) <= 1e-12 * want
+
+
 # ---------------------------------------------------------------------------
 # Eq. 3 -- reprojection
 
