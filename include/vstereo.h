@@ -58,9 +58,19 @@ typedef struct {
  * Ranges: w h <= 2^26 pixels, 2 <= labels <= 128, 1 <= levels <= 8, 1 <= iters <= 1000,
  * 0 <= data_trunc <= 127, 0 <= smooth_slope, 0 <= smooth_trunc <= 127, and
  * data_trunc * 4^(levels-1) + 4 * smooth_trunc <= 32767 (messages are kept
- * in 8 bits and sums of a data term and four messages in 16 bits). */
+ * in 8 bits and sums of a data term and four messages in 16 bits).
+ * `iters_per_tile` (0..64) chooses how the iterations are launched, never
+ * what they compute: 1 runs one kernel per iteration everywhere; k >= 2
+ * runs up to k iterations per kernel on every level, each CTA iterating a
+ * tile of the level in shared memory with a halo that shrinks by one pixel
+ * per iteration (fewer than k where tile and halo would not fit shared
+ * memory); 0 (automatic) runs fused tiles on the coarse levels where
+ * vs_bp_autotune measured them faster for levels of that size, one kernel
+ * per iteration elsewhere.  The workspace of k != 1 holds one more message
+ * buffer (the largest level that may be fused). */
 typedef struct {
     int32_t labels, levels, iters, data_trunc, smooth_slope, smooth_trunc;
+    int32_t iters_per_tile;
 } vs_bp_params;
 
 /* Eq. 2 parameters: `scale` s between the full-res and the low-res grid
@@ -135,15 +145,25 @@ int vs_bp_stereo(const uint8_t *left, const uint8_t *right, int w, int h, int pi
  * the process exits.  That fits, for example, 320 x 180 with 16 labels and 3
  * levels (the paper's own setting) or 160 x 120 with up to 48 labels; a pair
  * whose vs_bp_workspace_size() exceeds it is rejected with VS_EWORKSPACE
- * before anything is enqueued.  The call allocates nothing.  Its first call
- * on a device looks up the scratch address for that device (the device must
- * be current), so make that first call before any stream capture.  All calls
- * share the one scratch and it keeps the last call's contents (nothing needs
- * clearing between calls); calls whose work overlaps on the GPU -- other
- * streams, other host threads -- race on it. */
+ * before anything is enqueued.  The call allocates nothing.  Each call made
+ * outside stream capture looks up the scratch address for the current device
+ * (so a module the runtime loads again, e.g. after cudaDeviceReset, is
+ * followed); a call during capture reuses the device's last address, so make
+ * a device's first call before any stream capture.  All calls share the one
+ * scratch and it keeps the last call's contents (nothing needs clearing
+ * between calls); calls whose work overlaps on the GPU -- other streams,
+ * other host threads -- race on it. */
 #define VS_BP_NOALLOC_SCRATCH_BYTES (8u << 20)
 int vs_bp_stereo_noalloc(const uint8_t *left, const uint8_t *right, int w, int h, int pitch,
                          const vs_bp_params *p, uint8_t *labels, int labels_pitch, void *stream);
+
+/* vs_bp_status for vs_bp_stereo_noalloc, whose caller never sees the scratch:
+ * synchronises `stream` and reports VS_ETIMEOUT if a kernel of the last
+ * vs_bp_stereo_noalloc call (with the same w, h and parameters) gave up a
+ * bounded wait (its labels are then invalid), else VS_OK.  No counterpart in
+ * the paper.  Errors: VS_EINVAL, VS_EWORKSPACE (pair too large for the
+ * scratch), VS_ECUDA. */
+int vs_bp_noalloc_status(int w, int h, const vs_bp_params *p, void *stream);
 
 /* One pair of a batch for vs_bp_stereo_batch (device pointers as in
  * vs_bp_stereo). */
@@ -200,6 +220,20 @@ int vs_bp_autotune(const uint8_t *left, const uint8_t *right, int w, int h, int 
  * [level][variant] (4 per level, -1 where a variant does not apply), up to
  * `max` values written; returns the count. */
 int vs_bp_autotune_times(float *ms, int max);
+/* With p->iters_per_tile == 0 (automatic), vs_bp_autotune also times every
+ * coarse level (level 0 stays one kernel per iteration in the automatic
+ * mode), replayed from CUDA graphs, as one kernel per iteration against
+ * fused launches of K = 2..10 iterations per tile on several tile shapes
+ * and lane counts, and records
+ * the fastest for levels of that size, labels and iterations; the
+ * automatic mode then uses it.  This reports the last choices as
+ * [level][4] = {K, tile_w, tile_h, lanes} (K = 0: one kernel per
+ * iteration), up to `max` ints; returns the count. */
+int vs_bp_autotune_plans(int *out, int max);
+/* The level timings behind those choices, graph replays: [level][2] =
+ * {ms of one kernel per iteration, ms of the fastest fused plan} (-1 where
+ * not timed), up to `max` floats; returns the count. */
+int vs_bp_autotune_level_times(float *ms, int max);
 /* Test and measurement aid: run sweep variant `variant` (0 plain, 1 preload,
  * 2 split in two, 3 split in four, 4 staged) on every level where it
  * applies, ahead of any autotuned choice; -1 restores the automatic choice.
@@ -210,6 +244,14 @@ int vs_bp_autotune_times(float *ms, int max);
  * pixels, ahead of the autotuned choice.  Results are identical whichever
  * variant runs.  Errors: VS_EINVAL. */
 int vs_bp_select_sweep(int variant);
+
+/* Test and measurement aid for the fused sweeps (iters_per_tile != 1): every
+ * fused launch from then on uses cores of tile_w x tile_h pixels (where tile
+ * and halo fit shared memory) and `lanes` (1, 2 or 4) threads per direction
+ * pair, each running the distance transform over labels / lanes labels;
+ * 0, 0, 0 restores the library's own choice.  Results are identical for
+ * every tile and lane count.  Errors: VS_EINVAL. */
+int vs_bp_select_fused(int tile_w, int tile_h, int lanes);
 
 /* Test aid for the bounded waits: with on = 1, staged sweeps launched from
  * then on announce their tile bytes to the mbarrier but issue no copy, so

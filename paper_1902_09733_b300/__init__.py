@@ -33,7 +33,7 @@ __all__ = [
     "guided_upsample", "reproject", "guided_upsample_reproject",
     "pair_workspace_size", "pair_run", "pair_run_host", "kernel_launches", "status_string",
     "profile_enable", "profile_collect", "Pipeline", "bp_stereo_batch", "bp_batch_workspace_size",
-    "bp_autotune", "bp_autotune_reset", "bp_autotune_times", "bp_select_sweep", "bp_batch_mode", "SPParams", "sp_workspace_size", "sp_forward", "sp_backward",
+    "bp_autotune", "bp_autotune_reset", "bp_autotune_times", "bp_select_sweep", "bp_select_fused", "bp_autotune_plans", "bp_autotune_level_times", "bp_batch_mode", "SPParams", "sp_workspace_size", "sp_forward", "sp_backward",
     "smooth_bp", "SmoothBP", "sp_select_kernels", "sp_status",
 ]
 
@@ -58,7 +58,7 @@ class _Camera(ctypes.Structure):
 
 class _BPParams(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in
-                ("labels", "levels", "iters", "data_trunc", "smooth_slope", "smooth_trunc")]
+                ("labels", "levels", "iters", "data_trunc", "smooth_slope", "smooth_trunc", "iters_per_tile")]
 
 
 class _BPJob(ctypes.Structure):
@@ -103,10 +103,11 @@ class BPParams:
     data_trunc: int = 20
     smooth_slope: int = 10
     smooth_trunc: int = 40
+    iters_per_tile: int = 0     # 0 automatic, 1 one kernel per iteration, k >= 2 up to k per fused tile launch
 
     def c(self) -> _BPParams:
         return _BPParams(self.labels, self.levels, self.iters, self.data_trunc,
-                         self.smooth_slope, self.smooth_trunc)
+                         self.smooth_slope, self.smooth_trunc, self.iters_per_tile)
 
 
 @dataclass(frozen=True)
@@ -193,6 +194,9 @@ def lib() -> ctypes.CDLL:
             "vs_bp_autotune_reset": ([], None),
             "vs_bp_autotune_times": ([P, I], I),
             "vs_bp_select_sweep": ([I], I),
+            "vs_bp_select_fused": ([I, I, I], I),
+            "vs_bp_autotune_plans": ([P, I], I),
+            "vs_bp_autotune_level_times": ([P, I], I),
             "vs_pipeline_workspace_size": ([cfg_p, I, I, I], S),
             "vs_pipeline_create": ([cfg_p, I, I, I, P, S, ctypes.POINTER(P)], I),
             "vs_pipeline_submit_pair": ([P, P, P, P], I),
@@ -407,9 +411,28 @@ def bp_autotune_times():
     return [[float(buf[i + v]) for v in range(4)] for i in range(0, n, 4)]
 
 
+def bp_autotune_plans():
+    """[(K, tile_w, tile_h, lanes)] per level chosen by the last bp_autotune (K = 0: unfused)."""
+    buf = (ctypes.c_int * 64)()
+    n = lib().vs_bp_autotune_plans(ctypes.cast(buf, ctypes.c_void_p), 64)
+    return [tuple(buf[i:i + 4]) for i in range(0, n, 4)]
+
+
+def bp_autotune_level_times():
+    """[(ms unfused, ms best fused)] per level behind the last bp_autotune (-1: not timed)."""
+    buf = (ctypes.c_float * 64)()
+    n = lib().vs_bp_autotune_level_times(ctypes.cast(buf, ctypes.c_void_p), 64)
+    return [(buf[i], buf[i + 1]) for i in range(0, n, 2)]
+
+
 def bp_select_sweep(variant: int) -> None:
     """Force sweep variant 0..4 (plain, preload, split 2, split 4, staged) wherever it applies (-1: automatic)."""
     _check("vs_bp_select_sweep", lib().vs_bp_select_sweep(int(variant)))
+
+
+def bp_select_fused(tile_w: int = 0, tile_h: int = 0, lanes: int = 0) -> None:
+    """Force the core tile and lanes per direction pair of fused sweeps (0, 0, 0: automatic)."""
+    _check("vs_bp_select_fused", lib().vs_bp_select_fused(int(tile_w), int(tile_h), int(lanes)))
 
 
 def bp_test_withhold_copies(on: bool) -> None:

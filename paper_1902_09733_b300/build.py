@@ -2,12 +2,13 @@
 
     python -m paper_1902_09733_b300.build [--force]
 
-Every ``csrc/*.cu`` is compiled by nvcc for ``compute_103a/sm_103a`` and
+Every ``csrc/*.cu`` is compiled by nvcc (one process per file, in parallel) for ``compute_103a/sm_103a`` and
 linked into ``paper_1902_09733_b300/libvstereo.so`` next to this file, so the
 built library travels with the source tree.  No GPU is needed to build.
 """
 from __future__ import annotations
 
+import concurrent.futures
 import glob
 import os
 import shutil
@@ -48,16 +49,21 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
     os.makedirs(OBJ_DIR, exist_ok=True)
-    objs = []
+    srcs = sources()
+    objs = [os.path.join(OBJ_DIR, os.path.basename(src)[:-3] + ".o") for src in srcs]
+
+    def compile_one(i):
+        cmd = [nvcc(), *ARCH, *NVCC_FLAGS, "-I", INCLUDE, "-c", srcs[i], "-o", objs[i]]
+        return subprocess.run(cmd, capture_output=True, text=True)
+
+    # one nvcc per source file, in parallel
+    with concurrent.futures.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
+        results = list(ex.map(compile_one, range(len(srcs))))
     log = []
-    for src in sources():
-        obj = os.path.join(OBJ_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc(), *ARCH, *NVCC_FLAGS, "-I", INCLUDE, "-dc" if False else "-c", src, "-o", obj]
-        r = subprocess.run(cmd, capture_output=True, text=True)
+    for src, r in zip(srcs, results):
         log.append(r.stdout + r.stderr)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
-        objs.append(obj)
     tmp = LIB + f".{os.getpid()}.tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs, "-lcudart_static", "-lrt",
            "-lpthread", "-ldl"]

@@ -19,7 +19,9 @@
 // also resets the call's status word and zeroes the border message slots
 // of levels 0 and 1), k_cost_down per further coarse level, one sweep per
 // iteration and level (k_bp_sweep, k_bp_sweep_split on small levels,
-// k_bp_sweep_staged on large byte-lane levels), and k_bp_labels_bytes /
+// k_bp_sweep_staged on large byte-lane levels) or, where iters_per_tile
+// asks for it or the autotuner measured it faster, k_bp_fused launches of
+// several iterations each on shared-memory tiles, and k_bp_labels_bytes /
 // k_bp_labels for the colour the last sweep did not label.
 //
 // k_bp_sweep: two threads per active pixel, each owning a pair of outgoing
@@ -52,6 +54,10 @@ struct BpLayout {
     int cost_u8[kMaxLevels];   // level cost fits a byte: data_trunc * 4^l <= 255
     int bytes[kMaxLevels];     // level belief sums fit a byte: + 4 smooth_trunc <= 255
     size_t cost_off[kMaxLevels], msg_off[kMaxLevels];
+    size_t msg_bytes[kMaxLevels];
+    size_t fused_off;          // second message buffer of the fused sweeps (0 bytes when none)
+    size_t fused_bytes;
+    int fused_min_level;       // levels >= this one may run fused sweeps (levels: none)
     size_t status_off;         // int: VS_OK, or VS_ETIMEOUT from a kernel of the last call
     size_t total;
 };
@@ -63,6 +69,8 @@ bool params_ok(int w, int h, const vs_bp_params *p)
     if (p->labels < 2 || p->labels > 128 || p->levels < 1 || p->levels > kMaxLevels)
         return false;
     if (p->iters < 1 || p->iters > 1000)
+        return false;
+    if (p->iters_per_tile < 0 || p->iters_per_tile > 64)
         return false;
     if (p->data_trunc < 0 || p->data_trunc > 127 || p->smooth_slope < 0 || p->smooth_trunc < 0 ||
         p->smooth_trunc > 127)
@@ -95,8 +103,17 @@ BpLayout make_layout(int w, int h, const vs_bp_params *p)
         lay.cost_off[l] = off;
         off = align_up(off + slots * lay.Lp * (lay.cost_u8[l] ? 1 : 2), 256);
         lay.msg_off[l] = off;
-        off = align_up(off + slots * 4 * lay.Lp, 256);
+        lay.msg_bytes[l] = slots * 4 * lay.Lp;
+        off = align_up(off + lay.msg_bytes[l], 256);
     }
+    // iters_per_tile 1: every sweep unfused; >= 2: fused on every level; 0
+    // (automatic): fused only where chosen, on the coarse levels
+    lay.fused_min_level = p->iters_per_tile == 1 ? p->levels : (p->iters_per_tile >= 2 ? 0 : 1);
+    lay.fused_bytes = 0;
+    for (int l = lay.fused_min_level; l < p->levels; ++l)
+        lay.fused_bytes = std::max(lay.fused_bytes, lay.msg_bytes[l]);
+    lay.fused_off = off;
+    off = align_up(off + lay.fused_bytes, 256);
     lay.status_off = off;
     off = align_up(off + sizeof(int), 256);
     lay.total = off;
@@ -404,6 +421,8 @@ template <>
 struct CostChunk<uint8_t> {
     uint4 v;
     __device__ __forceinline__ void load(const uint8_t *base, int j) { v = ld_piece(base, j); }
+    // shared-memory copy with `ps` pieces between consecutive pieces of a slot
+    __device__ __forceinline__ void load_s(const uint4 *base, int j, int ps) { v = base[j * ps]; }
     __device__ __forceinline__ uint32_t word(int wi) const { return (&v.x)[wi]; }
     __device__ __forceinline__ void zero() { v = make_uint4(0, 0, 0, 0); }
     __device__ __forceinline__ uint32_t dup(int i) const
@@ -422,6 +441,11 @@ struct CostChunk<uint16_t> {
     {
         v0 = ld_piece(base, 2 * j);
         v1 = ld_piece(base, 2 * j + 1);
+    }
+    __device__ __forceinline__ void load_s(const uint4 *base, int j, int ps)
+    {
+        v0 = base[2 * j * ps];
+        v1 = base[(2 * j + 1) * ps];
     }
     __device__ __forceinline__ uint32_t word(int) const { return 0u; }   // byte-lane path never uses 16-bit costs
     __device__ __forceinline__ void zero()
@@ -909,12 +933,21 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_staged(SweepArgs a)
             issue(next, buf ^ 1);
         const bool arrived = tc::mbar_wait(bar + buf, (uint32_t)(it >> 1) & 1u);
         if (!__syncthreads_and(arrived)) {
-            // the copies never completed: report, let the ones in flight land, leave
+            // The copies did not complete within the bound: report it and issue
+            // nothing more.  A CTA must not leave while a bulk copy still
+            // writes its shared memory, so thread 0 first waits once more
+            // (four seconds each) for the stages whose copies it did issue:
+            // this tile's and, if issued above, the next one's.  (The test aid
+            // issues none, so nothing is in flight and the CTA leaves at
+            // once.)  Only a copy that never lands at all, which no input can
+            // cause, would still be pending when that second bound runs out.
             if (threadIdx.x == 0) {
                 atomicExch(a.status, VS_ETIMEOUT);
-                tc::mbar_wait(bar + buf, (uint32_t)(it >> 1) & 1u);
-                if (next < ntiles)
-                    tc::mbar_wait(bar + (buf ^ 1), (uint32_t)((it + 1) >> 1) & 1u);
+                if (!a.withhold_copies) {
+                    tc::mbar_wait(bar + buf, (uint32_t)(it >> 1) & 1u, 4000000000ull);
+                    if (next < ntiles)
+                        tc::mbar_wait(bar + (buf ^ 1), (uint32_t)((it + 1) >> 1) & 1u, 4000000000ull);
+                }
             }
             __syncthreads();
             return;
@@ -934,6 +967,339 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_staged(SweepArgs a)
             sweep_pixel<LP, uint8_t, true, FULL, LABELS, false, true>(a, pair, x, y, has, in, all, cost, nullptr);
         }
         __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// fused sweeps: K iterations per launch on shared-memory tiles with a halo
+//
+// A CTA owns a core tile of TW x TH pixels of the level.  It copies into
+// shared memory the data term and the incoming messages (both colours, all
+// four directions) of its region -- the core grown by K pixels on every side
+// that is not a frame edge -- and runs iterations t0 .. t0 + K - 1 of the
+// red-black schedule there, with the global parity ((x + y + t) even), in
+// place: an iteration reads the active colour's slots and writes the other
+// colour's, as in the global layout.  At fused iteration i only the active
+// pixels of the region shrunk by i on its cut sides compute.  Their incoming
+// messages are exact: a slot whose sender lies outside the region is never
+// refreshed, and each iteration spreads that staleness by at most one pixel
+// inward, so the computed set is a trapezoid over the K iterations that ends
+// on the core, whose state after K iterations is exact.  The CTA writes the
+// core's messages to the level's other message buffer (no CTA reads
+// another's results within a launch).  The launch that ends the last
+// level-0 iteration also writes every core pixel's label.
+//
+// Shared memory, 16-byte pieces in planes of rh x rwh slots (row ry of the
+// region; slot sx = (x >> 1) - (rx0 >> 1), the global colour split):
+//   messages [c][k][j][rh][rwh]    j  < LP / 16
+//   cost     [c][jc][rh][rwh]      jc < LP / 16 * sizeof(CostT)
+// The lanes of a pixel are 2 NS consecutive threads: direction pair (left /
+// right, up / down) times NS blocks of the labels, joined by shuffles as in
+// the split sweep; one thread per lane, up to 512 per CTA.
+
+constexpr int kFusedThreads = 512;   // most threads of a fused CTA (a launch may use fewer)
+
+struct FusedArgs {
+    const uint8_t *cost;    // this level's data term
+    const uint8_t *src;     // incoming messages before iteration t0: this level's, or the parent's
+    uint8_t *dst;           // this level's incoming messages after iteration t0 + K - 1
+    int w, h, wg, L;
+    int pw, ph, pwg;        // parent level (from_parent)
+    int t0, K;              // first iteration of the launch, iterations fused
+    int TW, TH, tiles_x;    // core tile, tiles per row
+    int from_parent;        // t0 == 0 below the coarsest level: start from the parent's messages
+    int zero_in;            // t0 == 0 on the coarsest level: start from zero messages
+    uint32_t c2, ts2;       // (c, c) and (Ts, Ts) packed
+    uint8_t *labels;        // non-null: write the core's labels at the end
+    int labels_pitch;
+};
+
+__host__ __device__ constexpr int fused_region_rows(int TH, int K) { return TH + 2 * K; }
+__host__ __device__ constexpr int fused_region_slots(int TW, int K) { return ((TW + 2 * K + 1) >> 1) + 1; }
+
+// One direction pair (or one label block of it) of one active pixel, its
+// sources and destinations in shared memory (`ps` pieces between the pieces
+// of a slot).  Every lane of the warp calls this (the label blocks are joined
+// by shuffles); lanes with valid == false read zeros and store nothing.
+template <int LP, typename CostT, bool BYTES, bool FULL, int NS>
+__device__ __forceinline__ void fused_pixel(const FusedArgs &a, int pair, int half, bool valid,
+                                            const uint4 *const (&in)[4], const uint4 *cost, int ps, uint4 *dstA,
+                                            uint4 *dstB)
+{
+    constexpr int HL = LP / NS;   // labels per lane
+    constexpr int HC = HL / 16;   // 16-label chunks per lane
+    static_assert(NS == 1 || NS == 2 || NS == 4, "label blocks per direction pair");
+    static_assert(HL % 16 == 0, "whole 16-label chunks per lane");
+    uint32_t F[HL];
+    uint32_t H2 = kBig2;
+#pragma unroll
+    for (int jj = 0; jj < HC; ++jj) {
+        const int j = half * HC + jj;
+        uint4 m[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            m[k] = valid ? in[k][j * ps] : make_uint4(0, 0, 0, 0);
+        CostChunk<CostT> cc;
+        if (valid)
+            cc.load_s(cost, j, ps);
+        else
+            cc.zero();
+        if (BYTES) {
+#pragma unroll
+            for (int wi = 0; wi < 4; ++wi) {
+                const uint32_t s4 = cc.word(wi) + (&m[0].x)[wi] + (&m[1].x)[wi] + (&m[2].x)[wi] + (&m[3].x)[wi];
+                const uint32_t a4 = s4 - (pair ? (&m[2].x)[wi] : (&m[0].x)[wi]);
+                const uint32_t b4 = s4 - (pair ? (&m[3].x)[wi] : (&m[1].x)[wi]);
+                const uint32_t x01 = prmt(a4, b4, 0x5140u);   // A0 B0 A1 B1
+                const uint32_t x23 = prmt(a4, b4, 0x7362u);   // A2 B2 A3 B3
+                const uint32_t wq[4] = {prmt(x01, 0u, 0x4140u), prmt(x01, 0u, 0x4342u), prmt(x23, 0u, 0x4140u),
+                                        prmt(x23, 0u, 0x4342u)};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int kk = 16 * jj + 4 * wi + q;   // label within the lane's block
+                    uint32_t wv = wq[q];
+                    if (!FULL && half * HL + kk >= a.L)
+                        wv = kBig2;
+                    F[kk] = kk == 0 ? wv : __viaddmin_u16x2(F[kk - 1], a.c2, wv);   // min(F + c, h)
+                    H2 = min_u16x2(H2, wv);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int kk = 16 * jj + i;
+                const int wi = i >> 2;
+                const uint32_t plr = pair_bytes((&m[0].x)[wi], (&m[1].x)[wi], i & 3);
+                const uint32_t pud = pair_bytes((&m[2].x)[wi], (&m[3].x)[wi], i & 3);
+                const uint32_t t = plr + pud;                                  // (L+U, R+D), no carry
+                const uint32_t s2 = t + prmt(t, t, 0x1032u) + cc.dup(i);      // (S, S)
+                uint32_t wv = s2 - (pair ? pud : plr);                         // (h_A, h_B)
+                if (!FULL && half * HL + kk >= a.L)
+                    wv = kBig2;
+                F[kk] = kk == 0 ? wv : __viaddmin_u16x2(F[kk - 1], a.c2, wv);
+                H2 = min_u16x2(H2, wv);
+            }
+        }
+    }
+    if (NS > 1) {
+        // the label blocks of a direction pair are NS consecutive lanes:
+        // global minimum, then the forward carry from the blocks to the left
+#pragma unroll
+        for (int o = 1; o < NS; o <<= 1)
+            H2 = min_u16x2(H2, __shfl_xor_sync(0xffffffffu, H2, o));
+        uint32_t A = F[HL - 1];
+#pragma unroll
+        for (int o = 1; o < NS; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, A, o, NS);
+            if (half >= o)
+                A = min_u16x2(A, t + a.c2 * (uint32_t)(HL * o));
+        }
+        const uint32_t c_lo = __shfl_up_sync(0xffffffffu, A, 1, NS);
+        if (half > 0) {
+#pragma unroll
+            for (int k = 0; k < HL; ++k)
+                F[k] = min_u16x2(F[k], c_lo + a.c2 * (uint32_t)(k + 1));
+        }
+    }
+    // backward pass (G kept in F)
+#pragma unroll
+    for (int k = HL - 2; k >= 0; --k)
+        F[k] = __viaddmin_u16x2(F[k + 1], a.c2, F[k]);
+    if (NS > 1) {
+        uint32_t B = F[0];
+#pragma unroll
+        for (int o = 1; o < NS; o <<= 1) {
+            const uint32_t t = __shfl_down_sync(0xffffffffu, B, o, NS);
+            if (half + o < NS)
+                B = min_u16x2(B, t + a.c2 * (uint32_t)(HL * o));
+        }
+        const uint32_t c_hi = __shfl_down_sync(0xffffffffu, B, 1, NS);
+        if (half < NS - 1) {
+#pragma unroll
+            for (int k = 0; k < HL; ++k)
+                F[k] = min_u16x2(F[k], c_hi + a.c2 * (uint32_t)(HL - k));
+        }
+    }
+    if (!valid)
+        return;
+    const uint32_t negH2 = ((0u - (H2 & 0xFFFFu)) & 0xFFFFu) | ((0u - (H2 >> 16)) << 16);
+#pragma unroll
+    for (int jj = 0; jj < HC; ++jj) {
+        uint32_t o[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            o[i] = __viaddmin_s16x2(F[16 * jj + i], negH2, a.ts2);   // min(G - H, Ts)
+        uint32_t oa[4], ob[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t t01 = prmt(o[4 * q], o[4 * q + 1], 0x6420u);
+            const uint32_t t23 = prmt(o[4 * q + 2], o[4 * q + 3], 0x6420u);
+            oa[q] = prmt(t01, t23, 0x6420u);
+            ob[q] = prmt(t01, t23, 0x7531u);
+        }
+        const int j = half * HC + jj;
+        if (dstA)
+            dstA[j * ps] = make_uint4(oa[0], oa[1], oa[2], oa[3]);
+        if (dstB)
+            dstB[j * ps] = make_uint4(ob[0], ob[1], ob[2], ob[3]);
+    }
+}
+
+// 16 bytes from global to shared memory without a register round trip
+// (zeros when `valid` is false: no byte is read then).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid)
+{
+    const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+template <int LP, typename CostT, bool BYTES, bool FULL, int NS>
+__global__ void __launch_bounds__(kFusedThreads, 1) k_bp_fused(FusedArgs a)
+{
+    constexpr int NP = LP / 16;                     // pieces of a message
+    constexpr int NPC = NP * (int)sizeof(CostT);    // pieces of a data term
+    extern __shared__ __align__(16) uint4 fsm[];
+    pdl_begin();
+    const int by = (int)(blockIdx.x / (unsigned)a.tiles_x);
+    const int bx = (int)blockIdx.x - by * a.tiles_x;
+    const int x0 = bx * a.TW, y0 = by * a.TH;
+    const int x1 = min(x0 + a.TW, a.w), y1 = min(y0 + a.TH, a.h);
+    const int rx0 = max(x0 - a.K, 0), ry0 = max(y0 - a.K, 0);
+    const int rx1 = min(x1 + a.K, a.w), ry1 = min(y1 + a.K, a.h);
+    const int sx0 = rx0 >> 1;
+    const int rwh = ((rx1 - 1) >> 1) - sx0 + 1;
+    const int ps = (ry1 - ry0) * rwh;   // slots of a plane = pieces between planes
+    uint4 *msg_s = fsm;                 // planes (c * 4 + k) * NP + j
+    uint4 *cost_s = fsm + 8 * NP * ps;  // planes c * NPC + jc
+
+    // 1. the region's state, one (colour, direction or data term, slot) per
+    //    work item: a slot outside the region, or from a missing neighbour
+    //    (or one the parent level lacked), reads 0
+    for (int u = threadIdx.x; u < 10 * ps; u += blockDim.x) {
+        const int grp = u / ps, r = u - grp * ps;
+        const int c = grp >= 5, g = grp - 5 * c;   // g: direction 0..3, or 4 for the data term
+        const int ry = r / rwh;
+        const int y = ry0 + ry, xh = sx0 + (r - ry * rwh);
+        const int x = 2 * xh + ((c + y) & 1);
+        const bool in = x >= rx0 && x < rx1;
+        if (g < 4) {
+            const int k = g;
+            const int px = x >> 1, py = y >> 1;
+            const bool has = k == 0 ? x > 0 : k == 1 ? x < a.w - 1 : k == 2 ? y > 0 : y < a.h - 1;
+            const bool phas = k == 0 ? px > 0 : k == 1 ? px < a.pw - 1 : k == 2 ? py > 0 : py < a.ph - 1;
+            const bool use = in && has && !a.zero_in && (!a.from_parent || phas);
+            const uint8_t *g0 = !use ? a.cost
+                                : a.from_parent
+                                    ? a.src + slot_base((((px + py) & 1) * 4 + k) * a.ph + py, px >> 1, a.pwg, NP)
+                                    : a.src + slot_base((c * 4 + k) * a.h + y, xh, a.wg, NP);
+#pragma unroll
+            for (int j = 0; j < NP; ++j)
+                cp_async16(msg_s + ((c * 4 + k) * NP + j) * ps + r, use ? g0 + (size_t)j * kPieceStride : g0, use);
+        } else {
+            const uint8_t *g0 = in ? a.cost + slot_base(c * a.h + y, xh, a.wg, NPC) : a.cost;
+#pragma unroll
+            for (int jc = 0; jc < NPC; ++jc)
+                cp_async16(cost_s + (c * NPC + jc) * ps + r, in ? g0 + (size_t)jc * kPieceStride : g0, in);
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+
+    // 2. K iterations on the shrinking region
+    for (int i = 0; i < a.K; ++i) {
+        const int c = (a.t0 + i) & 1;
+        const int ex0 = rx0 + (rx0 > 0 ? i : 0), ex1 = rx1 - (rx1 < a.w ? i : 0);
+        const int ey0 = ry0 + (ry0 > 0 ? i : 0), ey1 = ry1 - (ry1 < a.h ? i : 0);
+        const int es0 = ex0 >> 1, ens = ((ex1 - 1) >> 1) - es0 + 1;
+        const int items = (ey1 - ey0) * ens * (2 * NS);
+        for (int base = 0; base < items; base += blockDim.x) {
+            const int u = base + (int)threadIdx.x;
+            const int pix = u / (2 * NS), sub = u - pix * (2 * NS);
+            const int half = sub % NS, pair = sub / NS;
+            const int row = pix / ens;
+            const int y = ey0 + row, xh = es0 + (pix - row * ens);
+            const int x = 2 * xh + ((c + y) & 1);
+            const bool valid = u < items && x >= ex0 && x < ex1;
+            const int slot = (y - ry0) * rwh + (xh - sx0);
+            const uint4 *in[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                in[k] = msg_s + (c * 4 + k) * NP * ps + slot;
+            const uint4 *cost = cost_s + c * NPC * ps + slot;
+            // destinations: A = left / up neighbour, B = right / down, inside the region
+            uint4 *dstA = nullptr, *dstB = nullptr;
+            if (valid) {
+                uint4 *o = msg_s + (c ^ 1) * 4 * NP * ps;
+                if (pair == 0) {
+                    if (x - 1 >= rx0)
+                        dstA = o + 1 * NP * ps + (y - ry0) * rwh + ((x - 1) >> 1) - sx0;
+                    if (x + 1 < rx1)
+                        dstB = o + 0 * NP * ps + (y - ry0) * rwh + ((x + 1) >> 1) - sx0;
+                } else {
+                    if (y - 1 >= ry0)
+                        dstA = o + 3 * NP * ps + slot - rwh;
+                    if (y + 1 < ry1)
+                        dstB = o + 2 * NP * ps + slot + rwh;
+                }
+            }
+            fused_pixel<LP, CostT, BYTES, FULL, NS>(a, pair, half, valid, in, cost, ps, dstA, dstB);
+        }
+        __syncthreads();
+    }
+
+    // 3. the core's messages out, one (colour, direction, slot) per work item
+    const int cs0 = x0 >> 1, cns = ((x1 - 1) >> 1) - cs0 + 1;
+    const int n = (y1 - y0) * cns;
+    for (int u = threadIdx.x; u < 8 * n; u += blockDim.x) {
+        const int plane = u / n, r = u - plane * n;   // plane = c * 4 + k
+        const int c = plane >> 2, k = plane & 3;
+        const int row = r / cns;
+        const int y = y0 + row, xh = cs0 + (r - row * cns);
+        const int x = 2 * xh + ((c + y) & 1);
+        if (x < x0 || x >= x1)
+            continue;
+        const int slot = (y - ry0) * rwh + (xh - sx0);
+        uint8_t *g = a.dst + slot_base((c * 4 + k) * a.h + y, xh, a.wg, NP);
+#pragma unroll
+        for (int j = 0; j < NP; ++j)
+            st_piece(g, j, msg_s[((c * 4 + k) * NP + j) * ps + slot]);
+    }
+    if (!a.labels)
+        return;
+    // labels of the core (the launch that ends level 0): d* = argmin_d D(d)
+    // + the four incoming messages (0 from a missing neighbour), the
+    // smallest d on ties
+    for (int u = threadIdx.x; u < 2 * n; u += blockDim.x) {
+        const int c = u >= n, r = u - c * n;
+        const int row = r / cns;
+        const int y = y0 + row, xh = cs0 + (r - row * cns);
+        const int x = 2 * xh + ((c + y) & 1);
+        if (x < x0 || x >= x1)
+            continue;
+        const int slot = (y - ry0) * rwh + (xh - sx0);
+        int best = 0x7FFFFFFF, bestd = 0;
+        for (int j = 0; j < NP; ++j) {
+            uint4 m[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                m[k] = msg_s[((c * 4 + k) * NP + j) * ps + slot];
+            CostChunk<CostT> cc;
+            cc.load_s(cost_s + c * NPC * ps + slot, j, ps);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int sh = 8 * (i & 3);
+                int b = (int)(cc.dup(i) & 0xFFFFu);
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    b += (int)(((&m[k].x)[i >> 2] >> sh) & 0xFFu);
+                if (16 * j + i < a.L && b < best) {
+                    best = b;
+                    bestd = 16 * j + i;
+                }
+            }
+        }
+        a.labels[(size_t)y * a.labels_pitch + x] = (uint8_t)bestd;
     }
 }
 
@@ -1371,6 +1737,244 @@ void launch_sweep(int Lp, const SweepArgs &a, bool cost8, bool bytes, cudaStream
     launch_sweep_any(Lp, &a, nullptr, sweep_blocks(a, variant), a.L == Lp, cost8, bytes, labels, variant, st);
 }
 
+// ---------------------------------------------------------------------------
+// fused sweeps: plans and launches
+
+struct FusedPlan {
+    int K;        // iterations per launch; 0: the level runs one kernel per iteration
+    int TW, TH;   // core tile
+    int NS;       // lanes per direction pair: 1, 2 (padded labels % 32 == 0) or 4 (% 64)
+};
+
+int fused_smem_bytes(int Lp, int cost_bytes, int TW, int TH, int K)
+{
+    const int NP = Lp / 16;
+    return 16 * (8 * NP + 2 * NP * cost_bytes) * fused_region_rows(TH, K) * fused_region_slots(TW, K);
+}
+
+// One lane per direction pair keeps the whole label range in registers:
+// compiled up to 64 labels (the register budget of 512 threads per CTA).
+bool fused_ns_ok(int Lp, int NS)
+{
+    return (NS == 1 && Lp <= 64) || (NS == 2 && Lp % 32 == 0) || (NS == 4 && Lp % 64 == 0);
+}
+
+// Threads of a fused launch: one per lane of the first iteration's active
+// pixels (about half the region, two direction pairs, NS lanes each), whole
+// warps, at most kFusedThreads.
+int fused_threads(int TW, int TH, int K, int NS)
+{
+    const int items = fused_region_rows(TH, K) * fused_region_slots(TW, K) * 2 * NS;
+    return std::min(kFusedThreads, std::max(64, (items + 31) / 32 * 32));
+}
+
+struct DeviceInfo {
+    int sms = 0, smem_optin = 0, smem_per_sm = 0;
+};
+
+// Multiprocessors and shared-memory limits of the current device, cached.
+const DeviceInfo *device_info()
+{
+    constexpr int kMaxDev = 64;
+    static std::mutex mu;
+    static DeviceInfo info[kMaxDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    DeviceInfo &d = info[dev];
+    if (d.sms == 0) {
+        if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&d.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+                cudaSuccess) {
+            (void)cudaGetLastError();
+            d.sms = 0;
+            return nullptr;
+        }
+    }
+    return &d;
+}
+
+// Tile shape for K fused iterations on level l, from a model of the launch:
+// ceil(CTAs / SMs) x the pixel updates of one CTA's trapezoid, tiles that
+// fit the shared memory of one CTA.  K is lowered while no 4 x 4 core fits.
+// Lanes per direction pair: enough to give every thread work when the
+// region is small.  Returns K = 0 if nothing fits.
+FusedPlan fused_default(const BpLayout &lay, int l, int K)
+{
+    const DeviceInfo *dv = device_info();
+    if (!dv)
+        return FusedPlan{0, 0, 0, 0};
+    const int cb = lay.cost_u8[l] ? 1 : 2;
+    const int w = lay.w[l], h = lay.h[l];
+    K = std::max(1, std::min(K, 64));
+    while (K > 1 && fused_smem_bytes(lay.Lp, cb, 4, 4, K) > dv->smem_optin)
+        --K;
+    if (fused_smem_bytes(lay.Lp, cb, 4, 4, K) > dv->smem_optin)
+        return FusedPlan{0, 0, 0, 0};
+    double best = 1e300;
+    FusedPlan plan{K, 4, 4, 1};
+    for (int TH = 2; TH <= std::max(2, std::min(h, 64)); TH += 2) {
+        for (int TW = 2; TW <= std::max(2, std::min(w, 128)); TW += 2) {
+            const int smem = fused_smem_bytes(lay.Lp, cb, TW, TH, K);
+            if (smem > dv->smem_optin)
+                break;
+            const long long ctas = (long long)((w + TW - 1) / TW) * ((h + TH - 1) / TH);
+            double work = 0.0;
+            for (int i = 0; i < K; ++i)
+                work += (double)std::min(TW + 2 * (K - i), w) * std::min(TH + 2 * (K - i), h);
+            const double t = (double)((ctas + dv->sms - 1) / dv->sms) * work;
+            if (t < best * 0.999) {
+                best = t;
+                plan = FusedPlan{K, TW, TH, 1};
+            }
+        }
+    }
+    // the fewest lanes per direction pair (measured fastest: the longer
+    // chain of one lane costs less than the joins of several)
+    for (int NS : {1, 2, 4})
+        if (fused_ns_ok(lay.Lp, NS)) {
+            plan.NS = NS;
+            break;
+        }
+    return plan;
+}
+
+// Test aid (vs_bp_select_fused): force the core tile and the lanes per
+// direction pair of every fused launch (0 = the plan's own).
+int g_fused_tw = 0, g_fused_th = 0, g_fused_ns = 0;
+
+// Plans recorded by vs_bp_autotune for the automatic mode, per (padded
+// labels, level size, iterations, byte costs); guarded by g_tune_mu.
+struct FusedTune {
+    int Lp, w, h, iters, cost_u8;
+    FusedPlan plan;   // K = 0: the level is faster unfused
+};
+std::vector<FusedTune> g_fused_tune;
+
+// Automatic mode without a recorded plan: one kernel per iteration.
+// Measured on B300 in graph replays (676 x 380, 64 labels, 4 x 10): levels
+// 1 / 2 / 3 take 41 / 29 / 25 us unfused against 80 / 41 / 25 us for the
+// fastest fused plans -- with programmatic dependent launch a coarse sweep
+// costs 2.5-4 us, less than a fused tile's repeated halo work and its one
+// CTA per SM.  Fused launches win only on small levels (16 labels at 80 x 60
+// to 160 x 90: 10.4 -> 8.3 us per level), so they run where vs_bp_autotune
+// measured them faster, or when iters_per_tile asks for them.
+FusedPlan fused_auto_default(const BpLayout &, const vs_bp_params *, int)
+{
+    return FusedPlan{0, 0, 0, 0};
+}
+
+// The plan for level l of a pair: K = 0 (one kernel per iteration), or K
+// iterations per launch on tiles.
+FusedPlan fused_plan(const BpLayout &lay, const vs_bp_params *p, int l)
+{
+    FusedPlan fp{0, 0, 0, 0};
+    if (l < lay.fused_min_level)
+        return fp;
+    int tw, th, ns;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tw = g_fused_tw;
+        th = g_fused_th;
+        ns = g_fused_ns;
+        if (p->iters_per_tile == 0) {
+            bool found = false;
+            for (const FusedTune &e : g_fused_tune)
+                if (e.Lp == lay.Lp && e.w == lay.w[l] && e.h == lay.h[l] && e.iters == p->iters &&
+                    e.cost_u8 == lay.cost_u8[l]) {
+                    fp = e.plan;
+                    found = true;
+                }
+            if (found)
+                return fp;
+        }
+    }
+    fp = p->iters_per_tile >= 2 ? fused_default(lay, l, std::min(p->iters_per_tile, p->iters))
+                                : fused_auto_default(lay, p, l);
+    if (fp.K == 0)
+        return fp;
+    // test overrides of the tile and the lanes, where they fit
+    const DeviceInfo *dv = device_info();
+    const int cb = lay.cost_u8[l] ? 1 : 2;
+    if (tw > 0 && th > 0 && dv && fused_smem_bytes(lay.Lp, cb, tw, th, fp.K) <= dv->smem_optin) {
+        fp.TW = tw;
+        fp.TH = th;
+    }
+    if (ns > 0 && fused_ns_ok(lay.Lp, ns))
+        fp.NS = ns;
+    return fp;
+}
+
+template <int LP, typename CostT, bool BYTES, bool FULL, int NS>
+bool launch_fused_t(const FusedArgs &a, unsigned grid, int threads, int smem, cudaStream_t st)
+{
+    constexpr int kMaxDev = 64;
+    static std::mutex mu;
+    static bool ready[kMaxDev] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev)
+        return false;
+    const DeviceInfo *dv = device_info();
+    if (!dv || smem > dv->smem_optin)
+        return false;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!ready[dev]) {
+            if (cudaFuncSetAttribute(k_bp_fused<LP, CostT, BYTES, FULL, NS>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, dv->smem_optin) != cudaSuccess)
+                return false;
+            ready[dev] = true;
+        }
+    }
+    launch_pdl_smem(k_bp_fused<LP, CostT, BYTES, FULL, NS>, dim3(grid), dim3(threads), (size_t)smem, st, a);
+    return true;
+}
+
+template <int LP, typename CostT, bool BYTES, bool FULL>
+bool launch_fused_ns(int NS, const FusedArgs &a, unsigned grid, int threads, int smem, cudaStream_t st)
+{
+    if constexpr (LP % 64 == 0)
+        if (NS == 4)
+            return launch_fused_t<LP, CostT, BYTES, FULL, 4>(a, grid, threads, smem, st);
+    if constexpr (LP % 32 == 0)
+        if (NS == 2 || LP > 64)
+            return launch_fused_t<LP, CostT, BYTES, FULL, 2>(a, grid, threads, smem, st);
+    if constexpr (LP <= 64)
+        return launch_fused_t<LP, CostT, BYTES, FULL, 1>(a, grid, threads, smem, st);
+    return false;
+}
+
+template <int LP>
+bool launch_fused_lp(int NS, bool full, bool cost8, bool bytes, const FusedArgs &a, unsigned grid, int threads,
+                     int smem, cudaStream_t st)
+{
+    if (cost8 && bytes)
+        return full ? launch_fused_ns<LP, uint8_t, true, true>(NS, a, grid, threads, smem, st)
+                    : launch_fused_ns<LP, uint8_t, true, false>(NS, a, grid, threads, smem, st);
+    if (cost8)
+        return full ? launch_fused_ns<LP, uint8_t, false, true>(NS, a, grid, threads, smem, st)
+                    : launch_fused_ns<LP, uint8_t, false, false>(NS, a, grid, threads, smem, st);
+    return full ? launch_fused_ns<LP, uint16_t, false, true>(NS, a, grid, threads, smem, st)
+                : launch_fused_ns<LP, uint16_t, false, false>(NS, a, grid, threads, smem, st);
+}
+
+bool launch_fused(int Lp, int NS, bool full, bool cost8, bool bytes, const FusedArgs &a, unsigned grid,
+                  int threads, int smem, cudaStream_t st)
+{
+    switch (Lp) {
+    case 16: return launch_fused_lp<16>(NS, full, cost8, bytes, a, grid, threads, smem, st);
+    case 32: return launch_fused_lp<32>(NS, full, cost8, bytes, a, grid, threads, smem, st);
+    case 48: return launch_fused_lp<48>(NS, full, cost8, bytes, a, grid, threads, smem, st);
+    case 64: return launch_fused_lp<64>(NS, full, cost8, bytes, a, grid, threads, smem, st);
+    case 96: return launch_fused_lp<96>(NS, full, cost8, bytes, a, grid, threads, smem, st);
+    default: return launch_fused_lp<128>(NS, full, cost8, bytes, a, grid, threads, smem, st);
+    }
+}
+
 // Arguments of the sweep at level l, iteration t of one pair.
 SweepArgs sweep_args(const BpLayout &lay, uint8_t *ws, const vs_bp_params *p, int l, int t, uint8_t *labels,
                      int labels_pitch)
@@ -1511,12 +2115,72 @@ void launch_labels(const BpLayout &lay, uint8_t *ws, uint8_t *labels, int labels
     note_launch();
 }
 
+// Every iteration of level l in fused launches of fp.K iterations: the
+// launches alternate between the level's message buffer and the fused
+// scratch buffer, the last one writing the level's own, so the finished
+// level sits where the unfused path leaves it.  The launch ending level 0
+// writes the labels.  False (nothing launched) if the plan cannot run here.
+bool run_level_fused(const BpLayout &lay, uint8_t *ws, const vs_bp_params *p, int l, const FusedPlan &fp,
+                     uint8_t *labels, int labels_pitch, cudaStream_t st)
+{
+    const int K = fp.K, iters = p->iters;
+    const int nl = (iters + K - 1) / K;
+    const int smem = fused_smem_bytes(lay.Lp, lay.cost_u8[l] ? 1 : 2, fp.TW, fp.TH, K);
+    const DeviceInfo *dv = device_info();
+    if (!dv || smem > dv->smem_optin || (nl > 1 && lay.fused_bytes < lay.msg_bytes[l]))
+        return false;
+    uint8_t *bufs[2] = {ws + lay.msg_off[l], ws + lay.fused_off};
+    int b = (nl & 1) ? 0 : 1;   // the last launch writes bufs[0]
+    FusedArgs a;
+    a.cost = ws + lay.cost_off[l];
+    a.w = lay.w[l];
+    a.h = lay.h[l];
+    a.wg = lay.wg[l];
+    a.L = lay.L;
+    a.pw = l + 1 < lay.levels ? lay.w[l + 1] : 0;
+    a.ph = l + 1 < lay.levels ? lay.h[l + 1] : 0;
+    a.pwg = l + 1 < lay.levels ? lay.wg[l + 1] : 0;
+    a.TW = fp.TW;
+    a.TH = fp.TH;
+    a.tiles_x = (lay.w[l] + fp.TW - 1) / fp.TW;
+    const unsigned grid = (unsigned)a.tiles_x * (unsigned)((lay.h[l] + fp.TH - 1) / fp.TH);
+    const int ceff = std::min(p->smooth_slope, p->smooth_trunc);   // same V for any larger slope
+    a.c2 = (uint32_t)ceff * 0x10001u;
+    a.ts2 = (uint32_t)p->smooth_trunc * 0x10001u;
+    a.labels_pitch = labels_pitch;
+    const bool full = lay.L == lay.Lp;
+    for (int q = 0; q < nl; ++q) {
+        a.t0 = q * K;
+        a.K = std::min(K, iters - a.t0);
+        a.from_parent = q == 0 && l + 1 < lay.levels;
+        a.zero_in = q == 0 && l + 1 == lay.levels;
+        a.src = a.from_parent ? ws + lay.msg_off[l + 1] : bufs[b ^ 1];
+        a.dst = bufs[b];
+        a.labels = (l == 0 && q == nl - 1) ? labels : nullptr;
+        const int slot = prof_begin(l == 0 ? kProfSweepL0 : kProfSweepCoarse, st);
+        const bool ok = launch_fused(lay.Lp, fp.NS, full, lay.cost_u8[l], lay.bytes[l], a, grid,
+                                     fused_threads(fp.TW, fp.TH, fp.K, fp.NS), smem, st);
+        prof_end(slot, st);
+        if (!ok)
+            return q == 0 ? false : true;   // a later launch cannot fail where the first ran
+        note_launch();
+        b ^= 1;
+    }
+    return true;
+}
+
 // Eq. 1 for one pair on `st`: costs and pyramid, every level-iteration, labels.
 void run_pair(const BpLayout &lay, uint8_t *ws, const uint8_t *left, const uint8_t *right, int pitch,
               const vs_bp_params *p, uint8_t *labels, int labels_pitch, cudaStream_t st)
 {
     launch_costs(lay, ws, left, right, pitch, p, st);
+    bool labelled = false;
     for (int l = lay.levels - 1; l >= 0; --l) {
+        const FusedPlan fp = fused_plan(lay, p, l);
+        if (fp.K > 0 && run_level_fused(lay, ws, p, l, fp, labels, labels_pitch, st)) {
+            labelled = labelled || l == 0;
+            continue;
+        }
         for (int t = 0; t < p->iters; ++t) {
             const SweepArgs a = sweep_args(lay, ws, p, l, t, labels, labels_pitch);
             const int slot = prof_begin(l == 0 ? kProfSweepL0 : kProfSweepCoarse, st);
@@ -1525,7 +2189,8 @@ void run_pair(const BpLayout &lay, uint8_t *ws, const uint8_t *left, const uint8
             note_launch();
         }
     }
-    launch_labels(lay, ws, labels, labels_pitch, p, st);
+    if (!labelled)
+        launch_labels(lay, ws, labels, labels_pitch, p, st);
 }
 
 }  // namespace
@@ -1765,6 +2430,170 @@ extern "C" int vs_bp_stereo_batch(const vs_bp_job *jobs, int n, void *workspace,
 // ---------------------------------------------------------------------------
 // autotuner
 
+namespace vs {
+namespace {
+
+std::vector<int> g_fused_last;       // plans of the last vs_bp_autotune: K, TW, TH, NS per level
+std::vector<float> g_fused_last_ms;  // and per level: ms unfused, ms of the fastest fused plan (-1: none)
+
+// Milliseconds per run of level l's iterations -- one kernel per iteration
+// (fp.K == 0) or fused launches -- replayed from a CUDA graph on the private
+// stream `cs`, the way pipelines run them (launches then overlap through
+// programmatic dependent launch; eager launches would mostly time the
+// launch latency): one eager run first, then 2 warm-up replays and the mean
+// of 10.  -1 on an error or when the plan cannot run here.
+float time_level(const BpLayout &lay, uint8_t *ws, const vs_bp_params *p, int l, const FusedPlan &fp,
+                 cudaStream_t cs, cudaEvent_t e0, cudaEvent_t e1)
+{
+    auto run = [&]() -> bool {
+        if (fp.K > 0)
+            return run_level_fused(lay, ws, p, l, fp, nullptr, 0, cs);
+        for (int t = 0; t < p->iters; ++t) {
+            const SweepArgs a = sweep_args(lay, ws, p, l, t, nullptr, 0);
+            launch_sweep(lay.Lp, a, lay.cost_u8[l], lay.bytes[l], cs);
+            note_launch();
+        }
+        return true;
+    };
+    if (!run() || cudaStreamSynchronize(cs) != cudaSuccess)
+        return -1.0f;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+        return -1.0f;
+    const bool ok = run();
+    if (cudaStreamEndCapture(cs, &graph) != cudaSuccess || !ok || !graph)
+        return -1.0f;
+    float ms = -1.0f;
+    if (cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+        const int reps = 10;
+        bool good = cudaGraphLaunch(exec, cs) == cudaSuccess && cudaGraphLaunch(exec, cs) == cudaSuccess &&
+                    cudaEventRecord(e0, cs) == cudaSuccess;
+        for (int r = 0; r < reps && good; ++r)
+            good = cudaGraphLaunch(exec, cs) == cudaSuccess;
+        float t = 0.0f;
+        if (good && cudaEventRecord(e1, cs) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+            cudaEventElapsedTime(&t, e0, e1) == cudaSuccess)
+            ms = t / reps;
+        cudaGraphExecDestroy(exec);
+    }
+    cudaGraphDestroy(graph);
+    return ms;
+}
+
+// Fused plans for the automatic mode: for every level that may be fused,
+// one kernel per iteration against K = 2..10 iterations per launch on the
+// model's tile, tiles of half and twice its sides, and every lane count;
+// the fastest is recorded for levels of that size.  The coarser levels'
+// messages must be in place (a full run first): each level then starts from
+// the same parent state every time.  Level 0 writes labels and stays
+// unfused in the automatic mode.
+int tune_fused(const BpLayout &lay, uint8_t *ws, const vs_bp_params *p, cudaStream_t st, cudaEvent_t e0,
+               cudaEvent_t e1, std::vector<int> &plans, std::vector<float> &level_ms)
+{
+    plans.assign((size_t)lay.levels * 4, 0);
+    level_ms.assign((size_t)lay.levels * 2, -1.0f);
+    const DeviceInfo *dv = device_info();
+    if (!dv)
+        return VS_ECUDA;
+    // a private stream for the captures, after the caller's stream's work
+    if (cudaStreamSynchronize(st) != cudaSuccess)
+        return VS_ECUDA;
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)
+        return VS_ECUDA;
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() { cudaStreamDestroy(s); }
+    } guard{cs};
+    for (int l = lay.levels - 1; l >= std::max(1, lay.fused_min_level); --l) {
+        const int cb = lay.cost_u8[l] ? 1 : 2;
+        std::vector<FusedPlan> cands;
+        cands.push_back(FusedPlan{0, 0, 0, 0});
+        for (int K : {2, 3, 4, 5, 6, 8, 10}) {
+            if (K > p->iters)
+                break;
+            const FusedPlan d = fused_default(lay, l, K);
+            if (d.K == 0)
+                continue;
+            const int sides[7][2] = {{2, 2}, {1, 2}, {2, 1}, {4, 2}, {2, 4}, {1, 1}, {4, 4}};   // halves
+            for (const auto &sc : sides) {
+                const int TW = std::max(2, d.TW * sc[0] / 4 * 2), TH = std::max(2, d.TH * sc[1] / 4 * 2);
+                if (fused_smem_bytes(lay.Lp, cb, TW, TH, d.K) > dv->smem_optin)
+                    continue;
+                for (int NS : {1, 2, 4}) {
+                    if (!fused_ns_ok(lay.Lp, NS))
+                        continue;
+                    const FusedPlan c{d.K, TW, TH, NS};
+                    bool dup = false;
+                    for (const FusedPlan &o : cands)
+                        dup = dup || (o.K == c.K && o.TW == c.TW && o.TH == c.TH && o.NS == c.NS);
+                    if (!dup)
+                        cands.push_back(c);
+                }
+            }
+        }
+        float best = 3.4e38f, best_fused = -1.0f;
+        FusedPlan best_plan{0, 0, 0, 0};
+        for (const FusedPlan &c : cands) {
+            const float ms = time_level(lay, ws, p, l, c, cs, e0, e1);
+            if (ms < 0.0f) {
+                if (c.K == 0)
+                    return VS_ECUDA;
+                (void)cudaGetLastError();
+                continue;
+            }
+            if (c.K == 0)
+                level_ms[(size_t)l * 2] = ms;
+            else if (best_fused < 0.0f || ms < best_fused)
+                best_fused = ms;
+            if (ms < best) {
+                best = ms;
+                best_plan = c;
+            }
+        }
+        level_ms[(size_t)l * 2 + 1] = best_fused;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            bool found = false;
+            for (FusedTune &e : g_fused_tune)
+                if (e.Lp == lay.Lp && e.w == lay.w[l] && e.h == lay.h[l] && e.iters == p->iters &&
+                    e.cost_u8 == lay.cost_u8[l]) {
+                    e.plan = best_plan;
+                    found = true;
+                }
+            if (!found)
+                g_fused_tune.push_back(FusedTune{lay.Lp, lay.w[l], lay.h[l], p->iters, lay.cost_u8[l], best_plan});
+        }
+        plans[(size_t)l * 4 + 0] = best_plan.K;
+        plans[(size_t)l * 4 + 1] = best_plan.TW;
+        plans[(size_t)l * 4 + 2] = best_plan.TH;
+        plans[(size_t)l * 4 + 3] = best_plan.NS;
+    }
+    return VS_OK;
+}
+
+}  // namespace
+}  // namespace vs
+
+extern "C" int vs_bp_autotune_plans(int *out, int max)
+{
+    std::lock_guard<std::mutex> lk(vs::g_tune_mu);
+    const int n = (int)vs::g_fused_last.size() < max ? (int)vs::g_fused_last.size() : max;
+    for (int i = 0; i < n; ++i)
+        out[i] = vs::g_fused_last[i];
+    return n;
+}
+
+extern "C" int vs_bp_autotune_level_times(float *ms, int max)
+{
+    std::lock_guard<std::mutex> lk(vs::g_tune_mu);
+    const int n = (int)vs::g_fused_last_ms.size() < max ? (int)vs::g_fused_last_ms.size() : max;
+    for (int i = 0; i < n; ++i)
+        ms[i] = vs::g_fused_last_ms[i];
+    return n;
+}
+
 extern "C" int vs_bp_autotune(const uint8_t *left, const uint8_t *right, int w, int h, int pitch,
                               const vs_bp_params *p, uint8_t *labels, int labels_pitch, void *workspace,
                               size_t ws_bytes, void *stream, int *chosen)
@@ -1834,6 +2663,15 @@ extern "C" int vs_bp_autotune(const uint8_t *left, const uint8_t *right, int w, 
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_last = times;
     }
+    if (rc == VS_OK && p->iters_per_tile == 0) {
+        // the sweep variants are chosen now: time the levels with them
+        std::vector<int> plans;
+        std::vector<float> level_ms;
+        rc = tune_fused(lay, ws, p, st, e0, e1, plans, level_ms);
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_fused_last = plans;
+        g_fused_last_ms = level_ms;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != VS_OK)
@@ -1892,6 +2730,19 @@ extern "C" void vs_bp_autotune_reset(void)
 {
     std::lock_guard<std::mutex> lk(vs::g_tune_mu);
     vs::g_tune.clear();
+    vs::g_fused_tune.clear();
+}
+
+extern "C" int vs_bp_select_fused(int tile_w, int tile_h, int lanes)
+{
+    if (tile_w < 0 || tile_h < 0 || tile_w > 1024 || tile_h > 1024 || (tile_w == 0) != (tile_h == 0) ||
+        (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4))
+        return VS_EINVAL;
+    std::lock_guard<std::mutex> lk(vs::g_tune_mu);
+    vs::g_fused_tw = tile_w;
+    vs::g_fused_th = tile_h;
+    vs::g_fused_ns = lanes;
+    return VS_OK;
 }
 
 extern "C" int vs_bp_export_messages(const void *workspace, size_t ws_bytes, int w, int h,

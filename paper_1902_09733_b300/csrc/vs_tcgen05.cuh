@@ -39,14 +39,31 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity, uint32_
     return done != 0;
 }
 
-// Bounded wait: at most `limit` attempts of up to 100 us each (the work
-// waited on here, MMAs or bulk copies, takes microseconds; the bound is
-// about a second).  Returns false if the phase never completed.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit = 10000)
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ uint64_t globaltimer_ns()
 {
-    for (uint32_t i = 0; i < limit; ++i)
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait: attempts of up to 100 us each until the phase completes or
+// `limit_ns` of wall time (read from the global timer, so the bound holds
+// however soon each attempt returns) have passed.  The work waited on here,
+// MMAs or bulk copies, takes microseconds; the default bound is one second,
+// long enough that time slicing with other contexts does not end a wait
+// early.  A cap of 2^26 attempts (each lasts well over 15 ns, so the cap
+// lies beyond the time bound) ends the loop even if the timer stalled.
+// Returns false if the phase never completed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns = 1000000000ull)
+{
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t i = 0; i < (1u << 26); ++i) {
         if (mbar_try(bar, parity, 100000u))
             return true;
+        if (globaltimer_ns() - t0 > limit_ns)
+            return false;
+    }
     return false;
 }
 

@@ -39,15 +39,24 @@ def test_status_strings(lib):
 
 
 def test_workspace_sizes_and_parameter_ranges(lib):
-    ok = vs.BPParams(labels=64, levels=4, iters=10, data_trunc=20, smooth_slope=10, smooth_trunc=40)
+    ok = vs.BPParams(labels=64, levels=4, iters=10, data_trunc=20, smooth_slope=10, smooth_trunc=40,
+                     iters_per_tile=1)
     n = vs.bp_workspace_size(676, 380, ok)
     # level 0: costs 2*380*338*64 + messages 8*380*338*64 bytes; coarser levels add about a third
     lvl0 = 10 * 380 * 338 * 64
     assert lvl0 < n < 1.45 * lvl0
+    # fused sweeps add a second message buffer: the largest coarse level in the
+    # automatic mode (level 1: 8*190*176*64 bytes with its rows padded to
+    # 16-slot groups), level 0 (8*380*352*64) when every level may be fused
+    auto = vs.bp_workspace_size(676, 380, vs.BPParams(**{**ok.__dict__, "iters_per_tile": 0}))
+    assert auto - n == 8 * 190 * 176 * 64
+    every = vs.bp_workspace_size(676, 380, vs.BPParams(**{**ok.__dict__, "iters_per_tile": 3}))
+    assert every - n == 8 * 380 * 352 * 64
     bad = [
         dict(labels=1), dict(labels=129), dict(levels=0), dict(levels=9), dict(iters=0),
         dict(data_trunc=128), dict(smooth_trunc=128), dict(smooth_slope=-1),
         dict(levels=7, data_trunc=20),            # 20 * 4^6 overflows the 16-bit sums
+        dict(iters_per_tile=-1), dict(iters_per_tile=65),
     ]
     for b in bad:
         p = vs.BPParams(**{**ok.__dict__, **b})
@@ -91,6 +100,10 @@ def test_bad_arguments_are_rejected_on_the_host(lib):
     assert lib.vs_bp_select_sweep(5) == vs.VS_EINVAL
     assert lib.vs_bp_select_sweep(-2) == vs.VS_EINVAL
     assert lib.vs_bp_test_withhold_copies(2) == vs.VS_EINVAL
+    # fused tiles: both sides or neither, lanes 0, 1, 2 or 4
+    for args in ((-1, 4, 0), (4, 0, 0), (0, 4, 0), (4, 4, 3), (2000, 4, 1)):
+        assert lib.vs_bp_select_fused(*args) == vs.VS_EINVAL, args
+    assert lib.vs_bp_select_fused(0, 0, 0) == vs.VS_OK
 
 
 def test_pipeline_host_checks(lib):
