@@ -40,13 +40,13 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile ``vsref.c`` and ``vsref_smooth.c`` into ``oracle/_build/libvsref.so`` with gcc."""
+    """Compile ``vsref.c`` and ``vsref_smooth.c`` into ``oracle/_build/libvsref.so`` with gcc (OpenMP rows)."""
     os.makedirs(_BUILD_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f) for f in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
            "-shared", "-fPIC", "-o", tmp, *_SRCS, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
@@ -78,6 +78,8 @@ def _load():
         lib.vsref_guided_upsample.restype = I
         lib.vsref_reproject.argtypes = [P, I, I, P, D, P]
         lib.vsref_reproject.restype = None
+        lib.vsref_set_threads.argtypes = [I]
+        lib.vsref_set_threads.restype = I
         lib.vsref_sp_message.argtypes = [P, I, D, D, D, P, P]
         lib.vsref_sp_message.restype = None
         lib.vsref_sp_forward.argtypes = [P, I, I, I, I, D, D, D, P, P]
@@ -86,6 +88,11 @@ def _load():
         lib.vsref_sp_backward.restype = I
         _lib = lib
         return lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the row loops (n <= 0 keeps the setting); returns the count in use."""
+    return int(_load().vsref_set_threads(int(n)))
 
 
 def _ptr(a: np.ndarray) -> int:

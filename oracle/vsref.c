@@ -16,6 +16,10 @@
  *   Eq. 3                  reprojection to camera-frame (x, y, z)
  * Integer stages use int32/int64; floating-point stages use double.
  * Where the paper is silent the chosen reading is stated beside the code.
+ * Built with OpenMP, the rows of a stage are shared among threads where no
+ * row reads what another row writes (every loop below says so); the
+ * arithmetic and its order per element are the same with one thread or many,
+ * so results do not depend on the thread count.
  *
  * Status codes: 0 ok, -1 invalid argument, -2 out of memory.
  */
@@ -23,6 +27,41 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads for the row loops (1 without OpenMP); n <= 0 keeps the current
+ * setting.  Returns the number the next parallel loop will use. */
+int vsref_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0)
+        omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+static int thread_slot(void)
+{
+#ifdef _OPENMP
+    return omp_get_thread_num();
+#else
+    return 0;
+#endif
+}
+
+static int max_slots(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 #define VSREF_OK 0
 #define VSREF_EINVAL (-1)
@@ -61,6 +100,8 @@ int vsref_rectify_remap(const uint8_t *src, int W, int H, int src_pitch,
     if (!src || !dst || !cam || W <= 0 || H <= 0 || src_pitch < 3 * W || dst_pitch < 3 * W)
         return VSREF_EINVAL;
     const double fx = cam[0], fy = cam[1], cx = cam[2], cy = cam[3], k1 = cam[4], k2 = cam[5];
+    /* rows are independent: each writes only its own destination row */
+#pragma omp parallel for schedule(static)
     for (int v = 0; v < H; ++v) {
         for (int u = 0; u < W; ++u) {
             double xn = (u - cx) / fx;
@@ -125,6 +166,7 @@ int vsref_downsample_luma(const uint8_t *rgb, int W, int H, int pitch, int s,
     if (!rgb || W <= 0 || H <= 0 || s <= 0 || pitch < 3 * W)
         return VSREF_EINVAL;
     int w = (W + s - 1) / s, h = (H + s - 1) / s;
+#pragma omp parallel for schedule(static)
     for (int yl = 0; yl < h; ++yl) {
         for (int xl = 0; xl < w; ++xl) {
             int64_t sum[3] = {0, 0, 0};
@@ -164,6 +206,7 @@ int vsref_downsample_luma(const uint8_t *rgb, int W, int H, int pitch, int s,
  */
 void vsref_cost_level0(const uint8_t *left, const uint8_t *right, int w, int h, int L, int Td, int32_t *D0)
 {
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < h; ++y)
         for (int x = 0; x < w; ++x)
             for (int d = 0; d < L; ++d) {
@@ -185,6 +228,7 @@ void vsref_cost_level0(const uint8_t *left, const uint8_t *right, int w, int h, 
 void vsref_cost_coarsen(const int32_t *fine, int wf, int hf, int L, int32_t *coarse)
 {
     int wc = (wf + 1) / 2, hc = (hf + 1) / 2;
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < hc; ++y)
         for (int x = 0; x < wc; ++x)
             for (int d = 0; d < L; ++d) {
@@ -320,12 +364,14 @@ int vsref_bp(const uint8_t *left, const uint8_t *right, int w, int h, int L, int
 
     {
         int32_t *msg = NULL, *parent = NULL;
-        int32_t *hv = (int32_t *)malloc(sizeof(int32_t) * L);
-        int32_t *mv = (int32_t *)malloc(sizeof(int32_t) * L);
-        if (!hv || !mv) {
+        /* one h and one message buffer per thread */
+        const int nslots = max_slots();
+        int32_t *hv_all = (int32_t *)malloc(sizeof(int32_t) * L * (size_t)nslots);
+        int32_t *mv_all = (int32_t *)malloc(sizeof(int32_t) * L * (size_t)nslots);
+        if (!hv_all || !mv_all) {
             rc = VSREF_ENOMEM;
-            free(hv);
-            free(mv);
+            free(hv_all);
+            free(mv_all);
             goto done_cost;
         }
         for (int l = levels - 1; l >= 0; --l) {
@@ -335,8 +381,8 @@ int vsref_bp(const uint8_t *left, const uint8_t *right, int w, int h, int L, int
             if (!msg) {
                 rc = VSREF_ENOMEM;
                 free(parent);
-                free(hv);
-                free(mv);
+                free(hv_all);
+                free(mv_all);
                 goto done_cost;
             }
             if (parent) { /* coarse-to-fine initialisation */
@@ -353,7 +399,13 @@ int vsref_bp(const uint8_t *left, const uint8_t *right, int w, int h, int L, int
             }
             const int32_t *D = cost[l];
             for (int t = 0; t < iters; ++t) {
+                /* rows are independent within an iteration: a pixel reads only
+                 * its own incoming messages and writes only its neighbours',
+                 * which are inactive (the other colour) in this iteration */
+#pragma omp parallel for schedule(static)
                 for (int y = 0; y < ch; ++y) {
+                    int32_t *hv = hv_all + (size_t)thread_slot() * L;
+                    int32_t *mv = mv_all + (size_t)thread_slot() * L;
                     for (int x = 0; x < cw; ++x) {
                         if (((x + y + t) & 1) != 0)
                             continue;
@@ -386,6 +438,7 @@ int vsref_bp(const uint8_t *left, const uint8_t *right, int w, int h, int L, int
         /* labels from the level-0 beliefs */
         {
             size_t plane = (size_t)w * h * L;
+#pragma omp parallel for schedule(static)
             for (int y = 0; y < h; ++y)
                 for (int x = 0; x < w; ++x) {
                     size_t p = (size_t)y * w + x;
@@ -410,8 +463,8 @@ int vsref_bp(const uint8_t *left, const uint8_t *right, int w, int h, int L, int
                 memcpy(msgs_out, parent, sizeof(int32_t) * 4 * plane);
         }
         free(parent);
-        free(hv);
-        free(mv);
+        free(hv_all);
+        free(mv_all);
     }
 done_cost:
     for (int l = 0; l < levels; ++l)
@@ -446,14 +499,19 @@ int vsref_guided_upsample(const uint8_t *labels, int w, int h, const uint8_t *gu
         r < 0 || !(sigma_s > 0.0) || !(sigma_r > 0.0))
         return VSREF_EINVAL;
     int nt = (2 * r + 1) * (2 * r + 1);
-    double *ex = (double *)malloc(sizeof(double) * nt);
-    double *dv = (double *)malloc(sizeof(double) * nt);
-    if (!ex || !dv) {
-        free(ex);
-        free(dv);
+    /* one pair of tap buffers per thread; rows are independent */
+    const int nslots = max_slots();
+    double *ex_all = (double *)malloc(sizeof(double) * nt * (size_t)nslots);
+    double *dv_all = (double *)malloc(sizeof(double) * nt * (size_t)nslots);
+    if (!ex_all || !dv_all) {
+        free(ex_all);
+        free(dv_all);
         return VSREF_ENOMEM;
     }
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < H; ++y) {
+        double *ex = ex_all + (size_t)thread_slot() * nt;
+        double *dv = dv_all + (size_t)thread_slot() * nt;
         for (int x = 0; x < W; ++x) {
             double px = (x + 0.5) / s - 0.5, py = (y + 0.5) / s - 0.5;
             int cxl = (int)floor(px + 0.5), cyl = (int)floor(py + 0.5);
@@ -487,8 +545,8 @@ int vsref_guided_upsample(const uint8_t *labels, int w, int h, const uint8_t *gu
             disp[(size_t)y * W + x] = (double)s * num / K;
         }
     }
-    free(ex);
-    free(dv);
+    free(ex_all);
+    free(dv_all);
     return VSREF_OK;
 }
 
@@ -506,6 +564,7 @@ int vsref_guided_upsample(const uint8_t *labels, int w, int h, const uint8_t *gu
 void vsref_reproject(const double *disp, int W, int H, const double *cam, double B, double *xyz)
 {
     const double fx = cam[0], fy = cam[1], cx = cam[2], cy = cam[3];
+#pragma omp parallel for schedule(static)
     for (int v = 0; v < H; ++v)
         for (int u = 0; u < W; ++u) {
             size_t p = (size_t)v * W + u;

@@ -486,3 +486,30 @@ def test_reproject_inverts_the_forward_projection():
     ok = disp > 0
     np.testing.assert_allclose(xyz[ok], np.stack([x, y, z], -1)[ok], rtol=1e-12, atol=1e-12)
     assert np.isnan(xyz[~ok]).all()
+
+
+# ---------------------------------------------------------------------------
+# threads
+
+
+def test_thread_count_does_not_change_results():
+    """The row loops run over OpenMP threads; one thread and many give the same
+    remap, grey, BP labels and messages, and JBU disparities, bit for bit."""
+    g = np.random.default_rng(50)
+    frame = g.integers(0, 256, size=(47, 61, 3)).astype(np.uint8)
+    cam = (60.0, 58.0, 30.0, 23.0, -0.2, 0.05)
+    left, right, _ = synth.noise_pair(4, w=61, h=47, max_disp=8.0)
+    n0 = oracle.set_threads(0)
+    try:
+        out = []
+        for n in (1, max(2, n0)):
+            oracle.set_threads(n)
+            rem = oracle.rectify_remap(frame, cam)
+            low, grey = oracle.downsample_luma(rem, 2)
+            lab, msg = oracle.bp(left, right, 16, 3, 4, 20, 10, 40, mode=oracle.MSG_DT, return_messages=True)
+            disp = oracle.guided_upsample(lab[:24, :31].copy(), low, rem, 2, 2, 1.0, 12.0)
+            out.append((rem, grey, lab, msg, disp))
+        for a, b in zip(*out):
+            np.testing.assert_array_equal(a, b)
+    finally:
+        oracle.set_threads(n0)
