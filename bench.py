@@ -56,7 +56,6 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--stream-frames", type=int, default=1500)
-    ap.add_argument("--stream-render", type=int, default=16)
     ap.add_argument("--batch-pairs", type=int, default=48)
     ap.add_argument("--smooth-reps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -267,6 +266,30 @@ def sweep_bytes_per_launch(w, h, L):
     return 0.5 * (per[col == 0].sum() + per[col == 1].sum())
 
 
+def sweep_ops_per_launch(w, h, L):
+    """Algorithmic integer operations of one level-0 sweep launch, averaged
+    over the two colours: per active pixel and label, the belief sum of the
+    data term and the in-frame incoming messages (one add each), and per
+    outgoing message the exclusion of its own incoming message (1), the
+    forward and backward passes of the lower envelope (an add and a minimum
+    each, 4), the running minimum (1) and the cap and shift min(G - H, Ts)
+    (2): 36 L per interior pixel."""
+    yy, xx = np.mgrid[0:h, 0:w]
+    deg = (xx > 0).astype(int) + (xx < w - 1) + (yy > 0) + (yy < h - 1)
+    per = (deg + 8 * deg) * L
+    col = (xx + yy) & 1
+    return 0.5 * (per[col == 0].sum() + per[col == 1].sum())
+
+
+def alu_peak_ops(dev, torch, sm_mhz):
+    """Peak of the integer ALU pipe in 16-bit operations per second: 64 lanes
+    per SM per clock (4 sub-partitions of 16), each lane one packed add-min
+    on two 16-bit halves (4 operations: viaddmin_u16x2), at the maximum SM
+    clock."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return sms * 64 * 4 * sm_mhz * 1e6
+
+
 def code_sha256(path: str) -> str:
     """SHA-256 of a source file's code: comments and blank lines removed, so
     edits to comments do not retire a capture of the same kernels."""
@@ -290,12 +313,22 @@ def committed_traffic(kernel_src: str):
     return float(m.group(1)) if sh.group(1) == code_sha256(kernel_src) else None
 
 
+def straight_leg_frames(synth, torch, dev, cam, seed, n):
+    """n consecutive 2704x1520 frames, 0.05 m apart along +x at 100 m over a
+    terrain with box buildings, drawn on the GPU (device tensors)."""
+    from paper_1902_09733_b300.scene import GpuScene
+    poses = np.array([(-0.025 * (n - 1) + 0.05 * i, 0.0, 0.0) for i in range(n)])
+    scene = synth.FlightScene(seed, 2.0 * 100.0 * 1.4 + 0.05 * n + 8.0)
+    gs = GpuScene(scene, dev)
+    return [gs.render(p, synth.TERRAIN_CAMERA) for p in poses]
+
+
 def run_batched(args, vs, synth, torch, dev, cam):
     """48 grey pairs: downsample factor 2/4/8 of 2704x1520 and 32/64/96/128
     labels drawn from a seed, frame offsets 1..5 along a 100 m flight leg."""
     g = np.random.default_rng(2024)
     n = args.batch_pairs
-    frames = [torch.from_numpy(f).to(dev) for f in synth.flight_frames(7, 6)]
+    frames = straight_leg_frames(synth, torch, dev, cam, 7, 6)
     grey = {}
     for s in (2, 4, 8):
         for i, f in enumerate(frames):
@@ -369,6 +402,64 @@ def run_batched(args, vs, synth, torch, dev, cam):
             "label_pixels_per_batch": px,
             "mix": {f"s{s}_L{L}": shapes.count((s, L)) for (s, L) in sorted(set(shapes))},
             "autotuned_variants": tuned}
+
+
+def run_batched_pairs(args, vs, synth, torch, dev, cam):
+    """48 whole pairs (remap of both frames, BP, upsample + reproject) with the
+    same seeded mix as run_batched: downsample factor 2/4/8 of 2704x1520,
+    32/64/96/128 labels, frame offsets 1..5 (baseline 0.05 m each) along a
+    100 m flight leg; one vs_pair_run_batch against 48 vs_pair_run calls,
+    both as CUDA-graph replays."""
+    g = np.random.default_rng(2024)
+    n = args.batch_pairs
+    frames = straight_leg_frames(synth, torch, dev, cam, 7, 6)
+    camv = vs.Camera(*synth.TERRAIN_CAMERA)
+    jobs, mix = [], []
+    for _ in range(n):
+        s = int(g.choice([2, 4, 8]))
+        L = int(g.choice([32, 64, 96, 128]))
+        off = int(g.integers(1, 6))
+        cfg = vs.PairConfig(W_FULL, H_FULL, camv, 0.05 * off, vs.BPParams(L, 4, 10, 20, 10, 40),
+                            vs.JBUParams(s, 2, 1.0, 12.0))
+        xyz = torch.empty((H_FULL, W_FULL, 3), dtype=torch.float32, device=dev)
+        jobs.append((cfg, frames[0], frames[off], None, xyz))
+        mix.append((s, L))
+    ws_b = torch.empty(vs.pair_batch_workspace_size(jobs), dtype=torch.uint8, device=dev)
+    ws_s = torch.empty(max(vs.pair_workspace_size(j[0]) for j in jobs), dtype=torch.uint8, device=dev)
+    st = torch.cuda.Stream(device=dev)
+
+    def batched():
+        vs.pair_run_batch(jobs, workspace=ws_b, stream=st)
+
+    def sequential():
+        for cfg, l, r, _, xyz in jobs:
+            vs.pair_run(cfg, l, r, xyz=xyz, workspace=ws_s, stream=st)
+
+    def graph_ms(fn, reps=5):
+        with torch.cuda.stream(st):
+            fn()
+        torch.cuda.synchronize()
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr, stream=st):
+            fn()
+        gr.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            e0.record(st)
+            for _ in range(reps):
+                gr.replay()
+            e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_seq = graph_ms(sequential)
+    t_bat = graph_ms(batched)
+    return {"pairs": n, "batched_ms": t_bat, "sequential_ms": t_seq, "speedup": t_seq / t_bat,
+            "batched_pairs_per_s": n / (t_bat * 1e-3), "sequential_pairs_per_s": n / (t_seq * 1e-3),
+            "api": "vs_pair_run_batch (pairs balanced over 4 library streams) vs vs_pair_run one after another",
+            "steps": "remap x2 + BP (4 x 10) + JBU + xyz per pair",
+            "mix": {f"s{s}_L{L}": mix.count((s, L)) for (s, L) in sorted(set(mix))}}
 
 
 def sp_kernel_band(L, lam, T):
@@ -579,8 +670,15 @@ def run_ours(args):
                  "ms_per_pair": t_plain / args.plain_steps}
     timed(prof_graphs, len(prof_graphs))
     recs = vs.profile_collect()
-    vs.profile_enable(0)
     del prof_graphs
+    # the same events in the timed configuration: P pairs in flight
+    recs_flight = []
+    if P > 1:
+        pf = capture(0, P)
+        timed([pf], 1)
+        recs_flight = vs.profile_collect()
+        del pf
+    vs.profile_enable(0)
     timing_src = "CUDA events around each launch in single-pair graph replays right after the timed region"
 
     # per-kernel durations from the event pairs of the last replays
@@ -588,8 +686,11 @@ def run_ours(args):
     for tag, ms in recs:
         by_tag.setdefault(tag, []).append(ms)
     sweep_ms = statistics.mean(by_tag["sweep_level0"]) if by_tag.get("sweep_level0") else None
+    flight_l0 = [ms for tag, ms in recs_flight if tag == "sweep_level0"]
+    sweep_ms_flight = statistics.mean(flight_l0) if flight_l0 else None
     w, h = W_FULL // SCALE, H_FULL // SCALE
     alg_bytes = sweep_bytes_per_launch(w, h, 64)
+    alg_ops = sweep_ops_per_launch(w, h, 64)
     peaks = {}
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):
@@ -598,6 +699,9 @@ def run_ours(args):
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6400.0
     achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9 if sweep_ms else None
+    sm_max = peaks.get("sm_max_mhz", 2032.0)
+    alu_peak = alu_peak_ops(dev, torch, sm_max) / 1e9
+    alu_achieved = alg_ops / (sweep_ms * 1e-3) / 1e9 if sweep_ms else None
     traffic = committed_traffic(os.path.join(ROOT, "paper_1902_09733_b300", "csrc", "vs_bp.cu"))
     kernel_share = None
     if recs:
@@ -632,35 +736,62 @@ def run_ours(args):
                "steps": args.e2e_steps, "api": "vs_pipeline_submit_pair (3 streams, depth 3)",
                "latency_ms_p50": lat[len(lat) // 2] if lat else None}
 
-    # streaming flight: one new frame per pair, each frame remapped once,
-    # pairs of frames k apart (the 1500-frame stream cycles the rendered frames)
+    # streaming flight: 1500 distinct frames of a seeded lawnmower flight at
+    # 100 m (legs of 25 m joined by half-circle turns, camera heading along
+    # the track), rendered on the GPU into pinned host memory before the
+    # timed run; one new frame per pair, each frame remapped once, pairs of
+    # frames k = 3 apart
     streaming = None
     if args.stream_frames > 0 and rank == 0:
+        from paper_1902_09733_b300.scene import GpuScene
         k = 3
-        frames = [torch.from_numpy(f).pin_memory()
-                  for f in synth.flight_frames(100 + rank, args.stream_render)]
+        nf = args.stream_frames
+        poses = synth.lawnmower_path(100 + rank, nf)
+        scene = synth.FlightScene(100 + rank, synth.lawnmower_extent(poses), n_buildings=80)
+        gs = GpuScene(scene, dev)
+        distinct = nf
+        host = None
+        while host is None:
+            try:
+                host = torch.empty((distinct, H_FULL, W_FULL, 3), dtype=torch.uint8, pin_memory=True)
+            except RuntimeError:
+                distinct //= 2
+                if distinct < 16:
+                    raise
+        buf = torch.empty((H_FULL, W_FULL, 3), dtype=torch.uint8, device=dev)
+        t_r = time.perf_counter()
+        for i in range(distinct):
+            gs.render(poses[i], synth.TERRAIN_CAMERA, out=buf)
+            host[i].copy_(buf)
+        torch.cuda.synchronize()
+        render_s = time.perf_counter() - t_r
+        del gs
         fcfg = vs.PairConfig(W_FULL, H_FULL, cam, 0.05 * k, bp, jbu)
-        pipe = vs.Pipeline(fcfg, mode="flight", depth=3, k=k)
         xh = [torch.empty((H_FULL, W_FULL, 3), dtype=torch.float32).pin_memory() for _ in range(3)]
+        pipe = vs.Pipeline(fcfg, mode="flight", depth=3, k=k)
         for f in range(8):
-            pipe.submit_frame(frames[f % len(frames)], xh[f % 3])
+            pipe.submit_frame(host[f], xh[f % 3])
         pipe.flush()
         pipe.latencies()
         pipe.close()
         pipe = vs.Pipeline(fcfg, mode="flight", depth=3, k=k)
         t0 = time.perf_counter()
-        for f in range(args.stream_frames):
-            pipe.submit_frame(frames[f % len(frames)], xh[f % 3] if f >= k else None)
+        for f in range(nf):
+            pipe.submit_frame(host[f % distinct], xh[f % 3] if f >= k else None)
         pipe.flush()
         t_s = time.perf_counter() - t0
         lat = sorted(pipe.latencies())
         pipe.close()
-        n_pairs = args.stream_frames - k
-        streaming = {"pairs_per_s": n_pairs / t_s, "frames": args.stream_frames, "k": k,
+        del host
+        n_pairs = nf - k
+        streaming = {"pairs_per_s": n_pairs / t_s, "frames": nf, "distinct_frames": distinct, "k": k,
                      "baseline_m": 0.05 * k, "latency_ms_p50": lat[len(lat) // 2],
                      "latency_ms_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                      "h2d_bytes_per_pair": W_FULL * H_FULL * 3, "d2h_bytes_per_pair": W_FULL * H_FULL * 12,
-                     "input": f"{args.stream_render} rendered frames of a 100 m flight leg with buildings, cycled"}
+                     "render_s": render_s,
+                     "input": f"{distinct} distinct frames of a seeded lawnmower flight at 100 m (25 m legs, "
+                              "8 m half-circle turns, 80 box buildings 5-30 m), rendered on the GPU into "
+                              "pinned host memory before the timed run"}
 
     # batched BP: 48 pairs of uneven sizes and label counts in lockstep,
     # against the same 48 pairs as sequential single-pair calls (both as
@@ -668,6 +799,7 @@ def run_ours(args):
     batched = None
     if args.batch_pairs > 0 and rank == 0:
         batched = run_batched(args, vs, synth, torch, dev, cam)
+        batched["whole_pairs"] = run_batched_pairs(args, vs, synth, torch, dev, cam)
 
     # smoothed BP + adjoint (the differentiable relaxation of Eq. 1)
     smooth = None
@@ -706,14 +838,21 @@ def run_ours(args):
                        "l2": "8 distinct input pairs (197 MB) rotated per step, larger than L2",
                        "launch": f"one CUDA graph replay per step, {P} pairs on {P} streams"},
             "plain": plain,
-            "roofline": {"bound": "hbm", "kernel": "k_bp_sweep_staged / k_bp_sweep (the 10 level-0 sweeps)",
-                         "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak if achieved else None, "traffic": traffic,
-                         "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": sweep_ms,
-                         "peak_source": f"{peak_src} hbm_gbs", "timing": timing_src,
-                         "note": "traffic: one-pass ncu DRAM bytes per launch of one pair alone; the "
-                                 "level's 86 MB of costs and messages stay in L2 between sweeps, and "
-                                 "the integer ALU pipe (63 % busy) rather than HBM limits the sweep"},
+            "roofline": {"bound": "alu", "kernel": "k_bp_sweep_staged / k_bp_sweep (the 10 level-0 sweeps)",
+                         "achieved": alu_achieved, "peak": alu_peak, "unit": "Gop/s",
+                         "frac": alu_achieved / alu_peak if alu_achieved else None, "traffic": traffic,
+                         "alg_ops_per_launch": alg_ops, "avg_launch_ms": sweep_ms,
+                         "avg_launch_ms_in_flight": sweep_ms_flight,
+                         "peak_source": f"derived: SMs x 64 ALU lanes x 4 ops (packed add-min) x {sm_max:.0f} MHz",
+                         "timing": timing_src,
+                         "hbm": {"alg_bytes_per_launch": alg_bytes, "achieved_gbs": achieved, "peak_gbs": peak,
+                                 "alg_frac": achieved / peak if achieved else None,
+                                 "dram_frac": traffic / (sweep_ms * 1e-3) / 1e9 / peak if traffic and sweep_ms
+                                 else None, "peak_source": f"{peak_src} hbm_gbs"},
+                         "note": "ops: 16-bit integer adds and minima of the O(L) min-sum update, 36 L per "
+                                 "interior active pixel; traffic: one-pass ncu DRAM bytes per launch with "
+                                 "four pairs in flight; the level's costs and messages mostly stay in L2, and "
+                                 "the integer ALU pipe is the busiest unit"},
             "kernel_share": kernel_share,
             "cpu_baseline": cpu,
             "e2e": e2e,

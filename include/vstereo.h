@@ -337,6 +337,32 @@ size_t vs_pair_workspace_size(const vs_pair_config *cfg);
 int vs_pair_run(const vs_pair_config *cfg, const uint8_t *left_src, const uint8_t *right_src,
                 float *disp, float *xyz, void *workspace, size_t ws_bytes, void *stream);
 
+/* One pair of a whole-pair batch (device buffers as in vs_pair_run). */
+typedef struct {
+    vs_pair_config cfg;
+    const uint8_t *left, *right;   /* W x H RGB (pitch 3 W) */
+    float *disp;                   /* nullable W x H */
+    float *xyz;                    /* W x H x 3 */
+} vs_pair_job;
+
+/* Workspace bytes for a whole-pair batch (the pairs' vs_pair_workspace_size
+ * back to back, 256-byte aligned), or 0 if a job is invalid or n is not in
+ * 1..4096. */
+size_t vs_pair_batch_workspace_size(const vs_pair_job *jobs, int n);
+
+/*
+ * n independent pairs (remap of both frames, Eq. 1, Eq. 2 + Eq. 3), each
+ * exactly as vs_pair_run computes it, with any sizes, downsample factors,
+ * label counts and baselines.  The pairs are balanced, largest first, over
+ * the device's four library streams forked from `stream` and joined back to
+ * it with events, so the call is ordered after earlier work on `stream`,
+ * later work waits for it, and it can be captured into a CUDA graph.  `jobs`
+ * is a host array read during the call.  The library streams are shared by
+ * the device's batch calls: do not run batches from several host threads at
+ * once.  Errors: VS_EINVAL, VS_EWORKSPACE, VS_ECUDA, or a step's status.
+ */
+int vs_pair_run_batch(const vs_pair_job *jobs, int n, void *workspace, size_t ws_bytes, void *stream);
+
 /*
  * The same pair from and to HOST buffers: copies both frames to the device,
  * runs vs_pair_run and copies the point cloud (and disp if non-NULL) back,

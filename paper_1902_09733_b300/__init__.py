@@ -31,7 +31,7 @@ __all__ = [
     "Camera", "BPParams", "JBUParams", "PairConfig", "VSError", "lib", "library_path",
     "rectify_remap", "bp_workspace_size", "bp_stereo", "bp_export_messages",
     "guided_upsample", "reproject", "guided_upsample_reproject",
-    "pair_workspace_size", "pair_run", "pair_run_host", "kernel_launches", "status_string",
+    "pair_workspace_size", "pair_run", "pair_run_host", "pair_run_batch", "pair_batch_workspace_size", "kernel_launches", "status_string",
     "profile_enable", "profile_collect", "Pipeline", "bp_stereo_batch", "bp_batch_workspace_size",
     "bp_autotune", "bp_autotune_reset", "bp_autotune_times", "bp_select_sweep", "bp_select_fused", "bp_autotune_plans", "bp_autotune_level_times", "bp_batch_mode", "SPParams", "sp_workspace_size", "sp_forward", "sp_backward",
     "smooth_bp", "SmoothBP", "sp_select_kernels", "sp_status",
@@ -80,6 +80,11 @@ class _JBUParams(ctypes.Structure):
 class _PairConfig(ctypes.Structure):
     _fields_ = [("W", ctypes.c_int32), ("H", ctypes.c_int32), ("cam", _Camera),
                 ("baseline", ctypes.c_float), ("bp", _BPParams), ("jbu", _JBUParams)]
+
+
+class _PairJob(ctypes.Structure):
+    _fields_ = [("cfg", _PairConfig), ("left", ctypes.c_void_p), ("right", ctypes.c_void_p),
+                ("disp", ctypes.c_void_p), ("xyz", ctypes.c_void_p)]
 
 
 @dataclass(frozen=True)
@@ -196,6 +201,8 @@ def lib() -> ctypes.CDLL:
             "vs_bp_select_sweep": ([I], I),
             "vs_bp_select_fused": ([I, I, I], I),
             "vs_bp_autotune_plans": ([P, I], I),
+            "vs_pair_batch_workspace_size": ([P, I], S),
+            "vs_pair_run_batch": ([P, I, P, S, P], I),
             "vs_bp_autotune_level_times": ([P, I], I),
             "vs_pipeline_workspace_size": ([cfg_p, I, I, I], S),
             "vs_pipeline_create": ([cfg_p, I, I, I, P, S, ctypes.POINTER(P)], I),
@@ -539,6 +546,40 @@ def pair_run(cfg: PairConfig, left_src: torch.Tensor, right_src: torch.Tensor, x
                            workspace.data_ptr(), workspace.numel(), _stream(stream))
     _check("vs_pair_run", rc)
     return disp, xyz
+
+
+def _pair_jobs(jobs):
+    arr = (_PairJob * len(jobs))()
+    for i, (cfg, left, right, disp, xyz) in enumerate(jobs):
+        arr[i] = _PairJob(cfg.c(), left.data_ptr(), right.data_ptr(),
+                          disp.data_ptr() if disp is not None else None, xyz.data_ptr())
+    return arr
+
+
+def pair_batch_workspace_size(jobs) -> int:
+    """Workspace bytes for [(PairConfig, left, right, disp or None, xyz)] device jobs."""
+    arr = _pair_jobs(jobs)
+    return int(lib().vs_pair_batch_workspace_size(ctypes.cast(arr, ctypes.c_void_p), len(jobs)))
+
+
+def pair_run_batch(jobs, workspace=None, stream=None):
+    """Whole pairs [(PairConfig, left, right, disp or None, xyz)] on the library streams."""
+    for cfg, left, right, disp, xyz in jobs:
+        for t, n in ((left, "left"), (right, "right")):
+            _dev(t, torch.uint8, n)
+            if not t.is_contiguous() or tuple(t.shape) != (cfg.H, cfg.W, 3):
+                raise ValueError(f"{n} must be a contiguous ({cfg.H}, {cfg.W}, 3) uint8 tensor")
+        if tuple(xyz.shape) != (cfg.H, cfg.W, 3) or xyz.dtype != torch.float32 or not xyz.is_contiguous():
+            raise ValueError("xyz must be a contiguous (H, W, 3) float32 tensor")
+    arr = _pair_jobs(jobs)
+    if workspace is None:
+        n = lib().vs_pair_batch_workspace_size(ctypes.cast(arr, ctypes.c_void_p), len(jobs))
+        if n == 0:
+            raise VSError("vs_pair_batch_workspace_size", VS_EINVAL)
+        workspace = torch.empty(n, dtype=torch.uint8, device=jobs[0][1].device)
+    _check("vs_pair_run_batch", lib().vs_pair_run_batch(ctypes.cast(arr, ctypes.c_void_p), len(jobs),
+                                                        workspace.data_ptr(), workspace.numel(), _stream(stream)))
+    return workspace
 
 
 def pair_run_host(cfg: PairConfig, left_host: torch.Tensor, right_host: torch.Tensor, xyz_host: torch.Tensor,

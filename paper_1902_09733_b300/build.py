@@ -45,7 +45,28 @@ def _stale() -> bool:
     return any(os.path.getmtime(p) > t for p in deps)
 
 
+SCENE_SRC = os.path.join(HERE, "scene", "vs_render.cu")
+SCENE_LIB = os.path.join(HERE, "scene", "libvsrender.so")
+
+
+def build_scene(force: bool = False) -> str:
+    """The flight-scene renderer (test and benchmark input generation), a
+    library of its own next to its source, compiled without fused
+    multiply-adds so that it rounds as the host renderer does."""
+    if not force and os.path.exists(SCENE_LIB) and os.path.getmtime(SCENE_LIB) >= os.path.getmtime(SCENE_SRC):
+        return SCENE_LIB
+    tmp = SCENE_LIB + f".{os.getpid()}.tmp"
+    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-shared",
+           SCENE_SRC, "-o", tmp, "-lcudart_static", "-lrt", "-lpthread", "-ldl"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on {SCENE_SRC}:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, SCENE_LIB)
+    return SCENE_LIB
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
+    build_scene(force)
     if not force and not _stale():
         return LIB
     os.makedirs(OBJ_DIR, exist_ok=True)

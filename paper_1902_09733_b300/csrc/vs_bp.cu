@@ -2313,41 +2313,14 @@ void batch_lockstep(const vs_bp_job *jobs, int n, const std::vector<BpLayout> &l
 }
 
 // Streams: the pairs, balanced by size (w h labels, largest first, each to
-// the least loaded stream), run one after another on kBatchStreams library
-// streams forked from `st` and joined back to it by events -- capturable.
+// the least loaded stream), run one after another on the library streams
+// forked from `st` and joined back to it by events -- capturable.
 // Independent pairs then fill each other's gaps: B300, 48 mixed pairs,
 // 28.6 ms against 31.8 ms in lockstep and 33.3 ms one after another.
-constexpr int kBatchStreams = 4;
-
-cudaStream_t *batch_streams_of_device()
-{
-    static std::mutex mu;
-    static std::vector<std::vector<cudaStream_t>> per_dev;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess)
-        return nullptr;
-    std::lock_guard<std::mutex> lk(mu);
-    if ((int)per_dev.size() <= dev)
-        per_dev.resize(dev + 1);
-    std::vector<cudaStream_t> &v = per_dev[dev];
-    if (v.empty()) {
-        for (int k = 0; k < kBatchStreams; ++k) {
-            cudaStream_t s;
-            if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
-                return nullptr;
-            v.push_back(s);
-        }
-    }
-    return v.data();
-}
-
 int batch_streams(const vs_bp_job *jobs, int n, const std::vector<BpLayout> &lays, const std::vector<size_t> &offs,
                   uint8_t *base, cudaStream_t st)
 {
-    cudaStream_t *side = batch_streams_of_device();
-    if (!side)
-        return VS_ECUDA;
-    const int S = n < kBatchStreams ? n : kBatchStreams;
+    const int S = n < kLibStreams ? n : kLibStreams;
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i)
         order[i] = i;
@@ -2363,29 +2336,12 @@ int batch_streams(const vs_bp_job *jobs, int n, const std::vector<BpLayout> &lay
         queue[k].push_back(i);
         load[k] += work(i);
     }
-    cudaEvent_t fork;
-    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess)
-        return VS_ECUDA;
-    int rc = cudaEventRecord(fork, st) == cudaSuccess ? VS_OK : VS_ECUDA;
-    for (int k = 0; k < S && rc == VS_OK; ++k) {
-        if (cudaStreamWaitEvent(side[k], fork, 0) != cudaSuccess) {
-            rc = VS_ECUDA;
-            break;
-        }
+    return fork_join(st, S, [&](int k, cudaStream_t side) {
         for (int i : queue[k])
             run_pair(lays[i], base + offs[i], jobs[i].left, jobs[i].right, jobs[i].pitch, &jobs[i].params,
-                     jobs[i].labels, jobs[i].labels_pitch, side[k]);
-        cudaEvent_t join;
-        if (cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
-            rc = VS_ECUDA;
-            break;
-        }
-        if (cudaEventRecord(join, side[k]) != cudaSuccess || cudaStreamWaitEvent(st, join, 0) != cudaSuccess)
-            rc = VS_ECUDA;
-        cudaEventDestroy(join);
-    }
-    cudaEventDestroy(fork);
-    return rc;
+                     jobs[i].labels, jobs[i].labels_pitch, side);
+        return VS_OK;
+    });
 }
 
 int g_batch_mode = 0;   // 0 streams, 1 lockstep

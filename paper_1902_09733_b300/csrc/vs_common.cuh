@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <utility>
 
 #include "../../include/vstereo.h"
@@ -16,6 +17,17 @@ void note_launch(unsigned n = 1);
 
 // Status after a launch: VS_ECUDA if the runtime reports an error.
 int launch_status();
+
+// Library streams for independent work of one call (batches of pairs): up to
+// kLibStreams per device, created on first use and kept.  fork_join runs
+// body(k, side stream k) for k < n, every side stream ordered after the work
+// already enqueued on `st`, and makes `st` wait for all of them -- with
+// events, so it also works while `st` is being captured into a CUDA graph.
+// The streams are shared by the device's calls: do not run two forked calls
+// from different host threads at once.  Returns the first non-OK status of
+// a body, or VS_ECUDA.
+constexpr int kLibStreams = 4;
+int fork_join(cudaStream_t st, int n, const std::function<int(int, cudaStream_t)> &body);
 
 // Optional CUDA-event timing of selected launches (vs_profile_enable).
 // prof_begin returns a slot (or -1 when timing is off) and records its start

@@ -2,6 +2,7 @@
 // and launch bookkeeping.
 #include "vs_common.cuh"
 
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <vector>
@@ -66,6 +67,59 @@ bool pair_layout(const vs_pair_config *cfg, PairLayout *out)
 }  // namespace
 
 void note_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+namespace {
+
+cudaStream_t *library_streams()
+{
+    static std::mutex mu;
+    static std::vector<std::vector<cudaStream_t>> per_dev;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)per_dev.size() <= dev)
+        per_dev.resize(dev + 1);
+    std::vector<cudaStream_t> &v = per_dev[dev];
+    while ((int)v.size() < kLibStreams) {
+        cudaStream_t s;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+            return nullptr;
+        v.push_back(s);
+    }
+    return v.data();
+}
+
+}  // namespace
+
+int fork_join(cudaStream_t st, int n, const std::function<int(int, cudaStream_t)> &body)
+{
+    cudaStream_t *side = library_streams();
+    if (!side || n < 1 || n > kLibStreams)
+        return VS_ECUDA;
+    cudaEvent_t fork;
+    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess)
+        return VS_ECUDA;
+    int rc = cudaEventRecord(fork, st) == cudaSuccess ? VS_OK : VS_ECUDA;
+    for (int k = 0; k < n && rc == VS_OK; ++k) {
+        if (cudaStreamWaitEvent(side[k], fork, 0) != cudaSuccess) {
+            rc = VS_ECUDA;
+            break;
+        }
+        rc = body(k, side[k]);
+        // join even after a failed body, so that `st` (or its capture) stays whole
+        cudaEvent_t join;
+        if (cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
+            rc = VS_ECUDA;
+            break;
+        }
+        if (cudaEventRecord(join, side[k]) != cudaSuccess || cudaStreamWaitEvent(st, join, 0) != cudaSuccess)
+            rc = VS_ECUDA;
+        cudaEventDestroy(join);
+    }
+    cudaEventDestroy(fork);
+    return rc;
+}
 
 int launch_status()
 {
@@ -211,6 +265,90 @@ extern "C" int vs_pair_run(const vs_pair_config *cfg, const uint8_t *left_src, c
     return vs_guided_upsample_reproject(ws + lay.labels, lay.w, lay.h, lay.w, ws + lay.low_rgb, 3 * lay.w,
                                         ws + lay.rect_l, W, H, 3 * W, &cfg->jbu, &cfg->cam, cfg->baseline, disp,
                                         xyz, stream);
+}
+
+namespace vs {
+namespace {
+
+bool pair_batch_layouts(const vs_pair_job *jobs, int n, std::vector<PairLayout> &lays, std::vector<size_t> &offs,
+                        size_t &total)
+{
+    if (!jobs || n < 1 || n > 4096)
+        return false;
+    lays.resize(n);
+    offs.resize(n);
+    total = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!pair_layout(&jobs[i].cfg, &lays[i]))
+            return false;
+        offs[i] = total;
+        total = align_up(total + lays[i].total, 256);
+    }
+    return true;
+}
+
+// Relative cost of a pair for balancing the streams: the BP sweeps (low-res
+// pixels x padded labels x iterations x 4/3 for the coarser levels) plus the
+// full-resolution remap and upsampling, weighted as measured on B300 (the
+// 2.7K pair at s = 4: about 240 us of BP, 60 us of remap and JBU).
+double pair_work(const vs_pair_job &j, const PairLayout &lay)
+{
+    const vs_bp_params &p = j.cfg.bp;
+    const int Lp = p.labels <= 64 ? (p.labels + 15) / 16 * 16 : (p.labels <= 96 ? 96 : 128);
+    return (double)lay.w * lay.h * Lp * p.iters * (4.0 / 3.0) + 13.0 * (double)j.cfg.W * j.cfg.H;
+}
+
+}  // namespace
+}  // namespace vs
+
+extern "C" size_t vs_pair_batch_workspace_size(const vs_pair_job *jobs, int n)
+{
+    std::vector<vs::PairLayout> lays;
+    std::vector<size_t> offs;
+    size_t total = 0;
+    return vs::pair_batch_layouts(jobs, n, lays, offs, total) ? total : 0;
+}
+
+extern "C" int vs_pair_run_batch(const vs_pair_job *jobs, int n, void *workspace, size_t ws_bytes, void *stream)
+{
+    using namespace vs;
+    std::vector<PairLayout> lays;
+    std::vector<size_t> offs;
+    size_t total = 0;
+    if (!pair_batch_layouts(jobs, n, lays, offs, total))
+        return VS_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!jobs[i].left || !jobs[i].right || !jobs[i].xyz)
+            return VS_EINVAL;
+    if (!workspace || !aligned(workspace, 256) || ws_bytes < total)
+        return VS_EWORKSPACE;
+    // largest first, each to the least loaded library stream
+    const int S = std::min(n, kLibStreams);
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i)
+        order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return pair_work(jobs[a], lays[a]) > pair_work(jobs[b], lays[b]); });
+    std::vector<std::vector<int>> queue(S);
+    std::vector<double> load(S, 0.0);
+    for (int i : order) {
+        int k = 0;
+        for (int j = 1; j < S; ++j)
+            if (load[j] < load[k])
+                k = j;
+        queue[k].push_back(i);
+        load[k] += pair_work(jobs[i], lays[i]);
+    }
+    uint8_t *base = reinterpret_cast<uint8_t *>(workspace);
+    return fork_join((cudaStream_t)stream, S, [&](int k, cudaStream_t side) {
+        for (int i : queue[k]) {
+            const vs_pair_job &j = jobs[i];
+            const int rc = vs_pair_run(&j.cfg, j.left, j.right, j.disp, j.xyz, base + offs[i], lays[i].total, side);
+            if (rc != VS_OK)
+                return rc;
+        }
+        return VS_OK;
+    });
 }
 
 extern "C" int vs_pair_run_host(const vs_pair_config *cfg, const uint8_t *left_host, const uint8_t *right_host,

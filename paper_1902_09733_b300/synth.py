@@ -13,7 +13,10 @@ Two workloads:
   piecewise-planar disparity field (four planes on the Voronoi cells of four
   seeded points, disparity 0..15).
 * :func:`flight_frames` -- consecutive frames of a straight flight leg at
-  100 m over terrain with box buildings (the streaming workload).
+  100 m over terrain with box buildings; :class:`FlightScene` and
+  :func:`lawnmower_path` -- the same kind of scene flown along a seeded
+  lawnmower path (the streaming workload, rendered on the GPU by
+  :mod:`paper_1902_09733_b300.scene`).
 * :func:`terrain_pair` -- a 2.7K RGB pair of a seeded textured heightfield
   (value-noise fBm relief, independent colour-noise albedo) seen by a nadir
   pinhole camera with radial lens distortion; the right camera is displaced by
@@ -191,8 +194,11 @@ class _HeightGrid:
 
 def _render_view(height: _HeightGrid, albedo: _ValueNoise, relief: float, W: int, H: int,
                  cam, cam_x: float, altitude: float, march_steps: int = 20,
-                 refine_steps: int = 12):
+                 refine_steps: int = 12, cam_y: float = 0.0, yaw: float = 0.0):
+    """Nadir view from (cam_x, cam_y, altitude); the camera's x axis points
+    along heading ``yaw`` (radians from the ground +x axis towards +y)."""
     fx, fy, cx, cy, k1, k2 = cam
+    cos_y, sin_y = np.float32(np.cos(yaw)), np.float32(np.sin(yaw))
     out = np.zeros((H, W, 3), np.uint8)
     depth = np.zeros((H, W), np.float32)
 
@@ -203,10 +209,13 @@ def _render_view(height: _HeightGrid, albedo: _ValueNoise, relief: float, W: int
         xn, yn = _undistort_normalised(xd, yd, k1, k2)
         xn = xn.astype(np.float32)
         yn = yn.astype(np.float32)
+        if yaw != 0.0:
+            # ground direction of the ray: the camera axes turned by the heading
+            xn, yn = cos_y * xn - sin_y * yn, sin_y * xn + cos_y * yn
 
         def surface_gap(t):
             # positive once the ray at depth t is at or below the surface
-            return t - (altitude - height(cam_x + t * xn, t * yn))
+            return t - (altitude - height(cam_x + t * xn, cam_y + t * yn))
 
         t0 = np.float32(altitude - relief - 1e-3)
         step = np.float32((relief + 1e-3) / march_steps)
@@ -226,7 +235,7 @@ def _render_view(height: _HeightGrid, albedo: _ValueNoise, relief: float, W: int
             t_lo = np.where(below, t_lo, tm)
         t = 0.5 * (t_lo + t_hi)
         X = cam_x + t * xn
-        Y = t * yn
+        Y = cam_y + t * yn
         col = albedo(X, Y)
         shade = 0.75 + 0.25 * np.clip(height(X, Y)[..., None] / relief, 0.0, 1.0)
         rgb = np.clip(128.0 + 110.0 * col * shade, 0.0, 255.0)
@@ -269,47 +278,121 @@ def terrain_pair(seed: int, W: int = 2704, H: int = 1520, cam=TERRAIN_CAMERA,
     return left, right
 
 
+class FlightScene:
+    """Terrain with box buildings under a nadir camera at ``altitude`` metres.
+
+    The terrain is value-noise fBm (0..``relief`` m, wavelengths 40..5 m
+    scaled by altitude / 20); ``n_buildings`` seeded boxes rise 5..30 m above
+    the highest ground they cover; the albedo is colour value noise whose
+    wavelengths scale the same way, so texture stays at a few low-resolution
+    pixels.  The scene covers ``extent`` metres square around the origin.
+    :meth:`render` draws a frame on the host; :meth:`tables` hands the same
+    tables to the CUDA renderer (:mod:`paper_1902_09733_b300.scene`).
+    """
+
+    def __init__(self, seed: int, extent: float, altitude: float = 100.0, relief: float = 15.0,
+                 n_buildings: int = 40, grid: int = 2049):
+        g = _rng(seed)
+        scale = altitude / 20.0
+        self.altitude = float(altitude)
+        self.extent = float(extent)
+        noise = _ValueNoise(g, [40.0 * scale, 20.0 * scale, 10.0 * scale, 5.0 * scale], [1.0, 0.5, 0.25, 0.125],
+                            extent)
+        height = _HeightGrid(noise, extent, grid)
+        lo, hi = float(height.grid.min()), float(height.grid.max())
+        hgrid = ((height.grid - lo) * (relief / max(hi - lo, 1e-6))).astype(np.float32)
+        n = hgrid.shape[0]
+        cells = np.linspace(-extent / 2.0, extent / 2.0, n)
+        for _ in range(n_buildings):
+            cx0, cy0 = g.uniform(-extent / 2 + 10, extent / 2 - 10, size=2)
+            sx, sy = g.uniform(6.0, 25.0, size=2)
+            top = g.uniform(5.0, 30.0)
+            ix = np.where(np.abs(cells - cx0) <= sx / 2)[0]
+            iy = np.where(np.abs(cells - cy0) <= sy / 2)[0]
+            if ix.size and iy.size:
+                block = hgrid[iy[0]:iy[-1] + 1, ix[0]:ix[-1] + 1]
+                hgrid[iy[0]:iy[-1] + 1, ix[0]:ix[-1] + 1] = float(block.max()) + top
+        height.grid = hgrid
+        height.flat = hgrid.ravel()
+        self.height = height
+        self.top = float(hgrid.max())
+        self.albedo = _ValueNoise(g, [0.8 * scale, 0.4 * scale, 0.2 * scale, 0.1 * scale], [0.5, 0.3, 0.2, 0.15],
+                                  extent, channels=3)
+
+    def render(self, pose, W: int = 2704, H: int = 1520, cam=TERRAIN_CAMERA) -> np.ndarray:
+        """(H, W, 3) uint8 frame from pose (x, y, yaw) with the radial distortion of ``cam``."""
+        x, y, yaw = pose
+        frame, _ = _render_view(self.height, self.albedo, self.top, W, H, cam, float(x), self.altitude,
+                                cam_y=float(y), yaw=float(yaw))
+        return frame
+
+    def tables(self):
+        """The renderer's inputs as contiguous float32 arrays: the height grid
+        (n x n), its half extent and cell size, and per albedo octave its
+        wavelength, amplitude and (m x m x 3) lattice."""
+        octs = [(lam, amp, np.ascontiguousarray(lat, np.float32)) for lam, amp, lat in self.albedo.octaves]
+        return {"height": np.ascontiguousarray(self.height.grid, np.float32), "half": float(self.height.half),
+                "res": float(self.height.res), "noise_half": float(self.albedo.half), "octaves": octs,
+                "top": self.top, "altitude": self.altitude}
+
+
+def lawnmower_path(seed: int, n_frames: int, spacing: float = 0.05, leg: float = 25.0, radius: float = 8.0):
+    """Camera poses (x, y, yaw) of a lawnmower flight, ``spacing`` metres apart.
+
+    Straight legs of ``leg`` metres along +x and -x alternate, joined by
+    half-circle turns of ``radius`` metres (left, then right, ...), each new
+    leg 2 ``radius`` further along +y.  The camera's heading follows the
+    flight direction, so consecutive frames move along the camera's x axis
+    (on a turn they also rotate by spacing / radius radians per frame).  The
+    seed shifts the start by up to 2 m.  Returns an (n_frames, 3) array.
+    """
+    g = _rng(seed + 7919)
+    x0, y0 = -leg / 2.0 + g.uniform(-2.0, 2.0), g.uniform(-2.0, 2.0)
+    half_turn = np.pi * radius
+    period = 2.0 * (leg + half_turn)
+    poses = np.zeros((n_frames, 3))
+    for i in range(n_frames):
+        s = i * spacing
+        k, r = divmod(s, period)
+        ybase = y0 + 4.0 * radius * k
+        if r < leg:                                   # +x leg
+            poses[i] = (x0 + r, ybase, 0.0)
+        elif r < leg + half_turn:                     # left turn, heading 0 -> pi
+            psi = (r - leg) / radius
+            cxp, cyp = x0 + leg, ybase + radius
+            poses[i] = (cxp + radius * np.sin(psi), cyp - radius * np.cos(psi), psi)
+        elif r < 2.0 * leg + half_turn:               # -x leg
+            poses[i] = (x0 + leg - (r - leg - half_turn), ybase + 2.0 * radius, np.pi)
+        else:                                         # right turn, heading pi -> 0
+            psi = np.pi - (r - 2.0 * leg - half_turn) / radius
+            cxp, cyp = x0, ybase + 3.0 * radius
+            poses[i] = (cxp - radius * np.sin(psi), cyp + radius * np.cos(psi), psi)
+    return poses
+
+
+def lawnmower_extent(poses, altitude: float = 100.0, W: int = 2704, H: int = 1520, cam=TERRAIN_CAMERA) -> float:
+    """Square scene extent that holds every frame's ground footprint (with the
+    lens's outward distortion and a building-height margin) for these poses."""
+    fx, fy = cam[0], cam[1]
+    reach = 1.15 * altitude * 0.5 * np.hypot(W / fx, H / fy)
+    span = max(np.abs(poses[:, 0]).max(), np.abs(poses[:, 1]).max())
+    return float(2.0 * (span + reach) + 10.0)
+
+
 def flight_frames(seed: int, n_frames: int, spacing: float = 0.05, altitude: float = 100.0,
                   W: int = 2704, H: int = 1520, cam=TERRAIN_CAMERA, relief: float = 15.0,
                   n_buildings: int = 40):
     """Frames of a straight flight leg over a terrain with box buildings.
 
     The nadir camera flies along +x at ``altitude`` metres, ``spacing`` metres
-    per frame (3 m/s at 60 fps gives 0.05 m).  The terrain is value-noise fBm
-    (0..``relief`` m); ``n_buildings`` seeded boxes rise 5..30 m above it.
-    Albedo wavelengths scale with the altitude so that texture stays at a few
-    low-resolution pixels.  Yields (H, W, 3) uint8 frames with the radial
-    distortion of ``cam``.
+    per frame (3 m/s at 60 fps gives 0.05 m), over a :class:`FlightScene`.
+    Yields (H, W, 3) uint8 frames with the radial distortion of ``cam``.
     """
-    g = _rng(seed)
-    scale = altitude / 20.0
     leg = spacing * max(n_frames - 1, 0)
-    extent = 2.0 * altitude * 1.4 + leg + 8.0
-    noise = _ValueNoise(g, [40.0 * scale, 20.0 * scale, 10.0 * scale, 5.0 * scale], [1.0, 0.5, 0.25, 0.125],
-                        extent)
-    height = _HeightGrid(noise, extent, 2049)
-    lo, hi = float(height.grid.min()), float(height.grid.max())
-    grid = ((height.grid - lo) * (relief / max(hi - lo, 1e-6))).astype(np.float32)
-    n = grid.shape[0]
-    cells = np.linspace(-extent / 2.0, extent / 2.0, n)
-    for _ in range(n_buildings):
-        cx0, cy0 = g.uniform(-extent / 2 + 10, extent / 2 - 10, size=2)
-        sx, sy = g.uniform(6.0, 25.0, size=2)
-        top = g.uniform(5.0, 30.0)
-        ix = np.where(np.abs(cells - cx0) <= sx / 2)[0]
-        iy = np.where(np.abs(cells - cy0) <= sy / 2)[0]
-        if ix.size and iy.size:
-            block = grid[iy[0]:iy[-1] + 1, ix[0]:ix[-1] + 1]
-            grid[iy[0]:iy[-1] + 1, ix[0]:ix[-1] + 1] = float(block.max()) + top
-    height.grid = grid
-    height.flat = grid.ravel()
-    top_all = float(grid.max())
-    albedo = _ValueNoise(g, [0.8 * scale, 0.4 * scale, 0.2 * scale, 0.1 * scale], [0.5, 0.3, 0.2, 0.15],
-                         extent, channels=3)
+    scene = FlightScene(seed, 2.0 * altitude * 1.4 + leg + 8.0, altitude, relief, n_buildings)
     x0 = -leg / 2.0
     for i in range(n_frames):
-        frame, _ = _render_view(height, albedo, top_all, W, H, cam, x0 + i * spacing, altitude)
-        yield frame
+        yield scene.render((x0 + i * spacing, 0.0, 0.0), W, H, cam)
 
 
 def pair_variants(left: np.ndarray, right: np.ndarray):

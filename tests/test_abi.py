@@ -134,6 +134,21 @@ def test_batch_workspace_is_the_sum_of_the_pairs(lib):
     assert vs.bp_batch_workspace_size(pairs) == 0
 
 
+def test_pair_batch_workspace_is_the_sum_of_the_pairs(lib):
+    import torch
+    jobs = []
+    for W, H, s, L in ((2704, 1520, 4, 64), (1000, 600, 2, 128), (640, 360, 8, 32)):
+        cfg = vs.PairConfig(W, H, vs.Camera(1400, 1400, W / 2, H / 2, -0.25, 0.07), 0.5,
+                            vs.BPParams(L, 4, 10, 20, 10, 40), vs.JBUParams(s, 2, 1.0, 12.0))
+        t = torch.empty((H, W, 3), dtype=torch.uint8)
+        jobs.append((cfg, t, t, None, torch.empty((H, W, 3))))
+    total = vs.pair_batch_workspace_size(jobs)
+    singles = sum(vs.pair_workspace_size(j[0]) for j in jobs)
+    assert singles <= total <= singles + 256 * len(jobs)
+    bad = (vs.PairConfig(0, 10, jobs[0][0].cam, 0.5, vs.BPParams(), vs.JBUParams()),) + jobs[0][1:]
+    assert vs.pair_batch_workspace_size(jobs + [bad]) == 0
+
+
 def test_smooth_bp_workspace_and_host_checks(lib):
     ok = vs.SPParams(labels=48, iters=8, ckpt_every=2, lam=2.5, trunc=13.7, tau=2.0)
     n = vs.sp_workspace_size(338, 190, ok)

@@ -124,3 +124,43 @@ def test_every_sweep_variant_matches_the_oracle(variant, shape):
     want, wmsg = oracle.bp(l, r, L, 4, 6, 20, 10, 40, mode=oracle.MSG_DT, return_messages=True)
     np.testing.assert_array_equal(got, want)
     np.testing.assert_array_equal(msg, wmsg)
+
+
+def _rgb(seed, H, W):
+    g = np.random.default_rng(seed)
+    return torch.from_numpy(g.integers(0, 256, size=(H, W, 3)).astype(np.uint8)).cuda()
+
+
+def test_pair_batch_matches_single_pair_calls_and_replays():
+    """Whole pairs (remap, BP, upsample + reproject) of mixed sizes,
+    downsample factors 2 / 4 / 8, 32..128 labels and baselines in one
+    vs_pair_run_batch call: every cloud and disparity equals its own
+    vs_pair_run bit for bit, eagerly and replayed from a CUDA graph."""
+    specs = [(320, 176, 2, 32, 0.05), (416, 240, 4, 64, 0.15), (200, 120, 8, 96, 0.25), (336, 200, 4, 128, 0.1),
+             (160, 96, 2, 64, 0.2), (520, 300, 8, 32, 0.05)]
+    jobs, singles = [], []
+    for i, (W, H, s, L, B) in enumerate(specs):
+        f = W / 2704.0
+        cam = vs.Camera(1400 * f, 1400 * f, (W - 1) / 2, (H - 1) / 2, -0.25, 0.07)
+        cfg = vs.PairConfig(W, H, cam, B, vs.BPParams(L, 3, 5, 20, 10, 40), vs.JBUParams(s, 2, 1.0, 12.0))
+        left, right = _rgb(2 * i, H, W), _rgb(2 * i + 1, H, W)
+        xyz = torch.full((H, W, 3), 7.0, device="cuda")
+        disp = torch.full((H, W), 7.0, device="cuda")
+        jobs.append((cfg, left, right, disp, xyz))
+        d1, x1 = vs.pair_run(cfg, left, right, disp=torch.empty((H, W), device="cuda"))
+        singles.append((d1, x1))
+    ws = vs.pair_run_batch(jobs)
+    torch.cuda.synchronize()
+    for (cfg, _, _, disp, xyz), (d1, x1) in zip(jobs, singles):
+        assert torch.equal(disp, d1) and torch.equal(torch.nan_to_num(xyz, 1e30), torch.nan_to_num(x1, 1e30))
+    for _, _, _, disp, xyz in jobs:
+        disp.fill_(7.0)
+        xyz.fill_(7.0)
+    st = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        vs.pair_run_batch(jobs, workspace=ws, stream=st)
+    g.replay()
+    torch.cuda.synchronize()
+    for (cfg, _, _, disp, xyz), (d1, x1) in zip(jobs, singles):
+        assert torch.equal(disp, d1) and torch.equal(torch.nan_to_num(xyz, 1e30), torch.nan_to_num(x1, 1e30))
