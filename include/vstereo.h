@@ -55,10 +55,15 @@ typedef struct {
  * min(smooth_slope * |dp - dq|, smooth_trunc); `labels` disparities
  * 0..labels-1 of the left image (IL(x) is compared with IR(x - d));
  * `levels` pyramid levels with `iters` red-black iterations each.
- * Ranges: w h <= 2^26 pixels, 2 <= labels <= 128, 1 <= levels <= 8, 1 <= iters <= 1000,
- * 0 <= data_trunc <= 127, 0 <= smooth_slope, 0 <= smooth_trunc <= 127, and
- * data_trunc * 4^(levels-1) + 4 * smooth_trunc <= 32767 (messages are kept
- * in 8 bits and sums of a data term and four messages in 16 bits).
+ * Ranges: w h <= 2^26 pixels, 2 <= labels <= 256, 1 <= levels <= 8,
+ * 1 <= iters <= 1000, 0 <= smooth_slope, 0 <= smooth_trunc <= 65535,
+ * 0 <= data_trunc with data_trunc * 4^(levels-1) <= 2^28.  Pairs with at
+ * most 128 labels, data_trunc and smooth_trunc <= 127 and data_trunc *
+ * 4^(levels-1) + 4 * smooth_trunc <= 32767 run the fast path (messages kept
+ * in 8 bits, sums of a data term and four messages in 16-bit lanes); all
+ * others run the general path (16-bit messages, 32-bit sums, one warp per
+ * pixel, about half the speed per label), which computes the same
+ * definition.
  * `iters_per_tile` (0..64) chooses how the iterations are launched, never
  * what they compute: 1 runs one kernel per iteration everywhere; k >= 2
  * runs up to k iterations per kernel on every level, each CTA iterating a
@@ -67,7 +72,8 @@ typedef struct {
  * memory); 0 (automatic) runs fused tiles on the coarse levels where
  * vs_bp_autotune measured them faster for levels of that size, one kernel
  * per iteration elsewhere.  The workspace of k != 1 holds one more message
- * buffer (the largest level that may be fused). */
+ * buffer (the largest level that may be fused).  The general path runs one
+ * kernel per iteration whatever iters_per_tile says. */
 typedef struct {
     int32_t labels, levels, iters, data_trunc, smooth_slope, smooth_trunc;
     int32_t iters_per_tile;

@@ -32,6 +32,7 @@
 // packed 16-bit add-min (DPX) operations; the forward results stay in
 // registers.  All lane values stay below 2^15 (ABI limits), so the packed
 // adds never carry across lanes and the signed form is exact too.
+#include "vs_bp_wide.cuh"
 #include "vs_common.cuh"
 #include "vs_tcgen05.cuh"
 
@@ -48,6 +49,8 @@ constexpr uint32_t kBig2 = 0x7FFF7FFFu;   // "label does not exist" in both halv
 constexpr int kSweepThreads = 128;        // 64 pixels x 2 direction pairs per CTA
 
 struct BpLayout {
+    int wide;                  // the general path (vs_bp_wide.cu) runs this pair; only w[0], h[0],
+                               // L, levels, status_off and total are set then
     int L, Lp, levels;
     int w[kMaxLevels], h[kMaxLevels], wh[kMaxLevels];
     int wg[kMaxLevels];        // 16-slot groups per row
@@ -62,7 +65,9 @@ struct BpLayout {
     size_t total;
 };
 
-bool params_ok(int w, int h, const vs_bp_params *p)
+// Parameters of the byte-message kernels in this file; anything else that
+// bp_wide_params_ok accepts runs the general path.
+bool narrow_ok(int w, int h, const vs_bp_params *p)
 {
     if (!p || w <= 0 || h <= 0)
         return false;
@@ -83,9 +88,27 @@ bool params_ok(int w, int h, const vs_bp_params *p)
     return true;
 }
 
+bool params_ok(int w, int h, const vs_bp_params *p)
+{
+    return narrow_ok(w, h, p) || bp_wide_params_ok(w, h, p);
+}
+
 BpLayout make_layout(int w, int h, const vs_bp_params *p)
 {
     BpLayout lay;
+    lay.wide = !narrow_ok(w, h, p);
+    if (lay.wide) {
+        lay.L = p->labels;
+        lay.Lp = 0;
+        lay.levels = p->levels;
+        lay.w[0] = w;
+        lay.h[0] = h;
+        lay.fused_min_level = p->levels;
+        lay.fused_bytes = 0;
+        lay.status_off = bp_wide_status_offset(w, h, p);
+        lay.total = bp_wide_workspace_size(w, h, p);
+        return lay;
+    }
     lay.L = p->labels;
     // padded label count: one of the compiled sizes 16, 32, 48, 64, 96, 128
     lay.Lp = p->labels <= 64 ? (p->labels + 15) / 16 * 16 : (p->labels <= 96 ? 96 : 128);
@@ -2173,6 +2196,10 @@ bool run_level_fused(const BpLayout &lay, uint8_t *ws, const vs_bp_params *p, in
 void run_pair(const BpLayout &lay, uint8_t *ws, const uint8_t *left, const uint8_t *right, int pitch,
               const vs_bp_params *p, uint8_t *labels, int labels_pitch, cudaStream_t st)
 {
+    if (lay.wide) {
+        bp_wide_run(left, right, lay.w[0], lay.h[0], pitch, p, labels, labels_pitch, ws, st);
+        return;
+    }
     launch_costs(lay, ws, left, right, pitch, p, st);
     bool labelled = false;
     for (int l = lay.levels - 1; l >= 0; --l) {
@@ -2258,8 +2285,15 @@ namespace {
 void batch_lockstep(const vs_bp_job *jobs, int n, const std::vector<BpLayout> &lays,
                     const std::vector<size_t> &offs, uint8_t *base, cudaStream_t st)
 {
+    // pairs of the general path run one after another, ahead of the lockstep ones
     for (int i = 0; i < n; ++i)
-        launch_costs(lays[i], base + offs[i], jobs[i].left, jobs[i].right, jobs[i].pitch, &jobs[i].params, st);
+        if (lays[i].wide)
+            run_pair(lays[i], base + offs[i], jobs[i].left, jobs[i].right, jobs[i].pitch, &jobs[i].params,
+                     jobs[i].labels, jobs[i].labels_pitch, st);
+    for (int i = 0; i < n; ++i)
+        if (!lays[i].wide)
+            launch_costs(lays[i], base + offs[i], jobs[i].left, jobs[i].right, jobs[i].pitch, &jobs[i].params,
+                         st);
 
     const int levels = jobs[0].params.levels, iters = jobs[0].params.iters;
     struct Group {
@@ -2272,6 +2306,8 @@ void batch_lockstep(const vs_bp_job *jobs, int n, const std::vector<BpLayout> &l
             groups.clear();
             for (int i = 0; i < n; ++i) {
                 const BpLayout &lay = lays[i];
+                if (lay.wide)
+                    continue;
                 const SweepArgs a = sweep_args(lay, base + offs[i], &jobs[i].params, l, t, jobs[i].labels,
                                                jobs[i].labels_pitch);
                 const int labels = a.labels != nullptr;
@@ -2308,7 +2344,8 @@ void batch_lockstep(const vs_bp_job *jobs, int n, const std::vector<BpLayout> &l
         }
     }
     for (int i = 0; i < n; ++i)
-        launch_labels(lays[i], base + offs[i], jobs[i].labels, jobs[i].labels_pitch, &jobs[i].params, st);
+        if (!lays[i].wide)
+            launch_labels(lays[i], base + offs[i], jobs[i].labels, jobs[i].labels_pitch, &jobs[i].params, st);
 
 }
 
@@ -2324,7 +2361,10 @@ int batch_streams(const vs_bp_job *jobs, int n, const std::vector<BpLayout> &lay
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i)
         order[i] = i;
-    auto work = [&](int i) { return (double)jobs[i].w * (double)jobs[i].h * (double)lays[i].Lp; };
+    auto work = [&](int i) {
+        const int Lp = lays[i].wide ? 2 * jobs[i].params.labels : lays[i].Lp;   // the general path: about 2x a label
+        return (double)jobs[i].w * (double)jobs[i].h * (double)Lp;
+    };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
     std::vector<std::vector<int>> queue(S);
     std::vector<double> load(S, 0.0);
@@ -2562,6 +2602,16 @@ extern "C" int vs_bp_autotune(const uint8_t *left, const uint8_t *right, int w, 
     cudaStream_t st = (cudaStream_t)stream;
     const BpLayout lay = make_layout(w, h, p);
     uint8_t *ws = reinterpret_cast<uint8_t *>(workspace);
+    if (lay.wide) {   // the general path has one kernel per step: nothing to choose
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_last.clear();
+        g_fused_last.assign((size_t)lay.levels * 4, 0);
+        g_fused_last_ms.assign((size_t)lay.levels * 2, -1.0f);
+        if (chosen)
+            for (int l = 0; l < lay.levels; ++l)
+                chosen[l] = -1;
+        return VS_OK;
+    }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess)
         return VS_ECUDA;
@@ -2714,6 +2764,10 @@ extern "C" int vs_bp_export_messages(const void *workspace, size_t ws_bytes, int
     const long long n = 4LL * h * w * lay.L;
     if (n >= (1LL << 31))
         return VS_EINVAL;
+    if (lay.wide) {
+        bp_wide_export(reinterpret_cast<const uint8_t *>(workspace), w, h, p, out, (cudaStream_t)stream);
+        return launch_status();
+    }
     ExportArgs a{reinterpret_cast<const uint8_t *>(workspace) + lay.msg_off[0], out, w, h, lay.wh[0], lay.wg[0], lay.L,
                  lay.Lp};
     launch_pdl(k_bp_export, dim3((unsigned)((n + 255) / 256)), dim3(256), (cudaStream_t)stream, a);

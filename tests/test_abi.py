@@ -53,14 +53,25 @@ def test_workspace_sizes_and_parameter_ranges(lib):
     every = vs.bp_workspace_size(676, 380, vs.BPParams(**{**ok.__dict__, "iters_per_tile": 3}))
     assert every - n == 8 * 380 * 352 * 64
     bad = [
-        dict(labels=1), dict(labels=129), dict(levels=0), dict(levels=9), dict(iters=0),
-        dict(data_trunc=128), dict(smooth_trunc=128), dict(smooth_slope=-1),
-        dict(levels=7, data_trunc=20),            # 20 * 4^6 overflows the 16-bit sums
+        dict(labels=1), dict(labels=257), dict(levels=0), dict(levels=9), dict(iters=0),
+        dict(smooth_trunc=65536), dict(smooth_slope=-1), dict(data_trunc=-1), dict(smooth_trunc=-1),
+        dict(levels=8, data_trunc=20000),         # 20000 * 4^7 is beyond 2^28
         dict(iters_per_tile=-1), dict(iters_per_tile=65),
     ]
     for b in bad:
         p = vs.BPParams(**{**ok.__dict__, **b})
         assert vs.bp_workspace_size(676, 380, p) == 0, b
+    # the general path (16-bit messages, int32 data terms in 32-label lane blocks) beyond the byte
+    # path's limits: 256 labels, truncations above 127, coarse sums beyond 16 bits
+    for b, Lp in ((dict(labels=129), 256), (dict(labels=256), 256), (dict(data_trunc=128), 64),
+                  (dict(smooth_trunc=200), 64), (dict(levels=7, data_trunc=20), 64), (dict(labels=40), 64)):
+        p = vs.BPParams(**{**ok.__dict__, **b})
+        n = vs.bp_workspace_size(676, 380, p)
+        if b == dict(labels=40):
+            assert n < 1.45 * lvl0            # the byte path
+            continue
+        lvl0_wide = 2 * 380 * 338 * Lp * (4 + 4 * 2)
+        assert lvl0_wide < n < 1.45 * lvl0_wide + 4096, (b, n)
     assert vs.bp_workspace_size(0, 10, ok) == 0
     cfg = vs.PairConfig(2704, 1520, vs.Camera(1400, 1400, 1351.5, 759.5, -0.25, 0.07), 0.5, ok, vs.JBUParams())
     assert vs.pair_workspace_size(cfg) > n + 2 * 2704 * 1520 * 3
