@@ -481,6 +481,13 @@ int vs_sp_backward(const float *cost, int w, int h, const vs_sp_params *p, const
  * Errors: VS_EINVAL. */
 int vs_sp_select_kernels(int family);
 
+/* Test aid for the tensor-core kernels' bounded waits: with on = 1, their
+ * launches from then on issue no MMA and no completion signal, so each
+ * kernel's wait for its MMAs runs out (about a second, with nothing in
+ * flight), the calls' outputs are invalid and vs_sp_status reports
+ * VS_ETIMEOUT; on = 0 restores normal operation.  Errors: VS_EINVAL. */
+int vs_sp_test_withhold_mma(int on);
+
 /* Synchronises `stream` and reports whether a tensor-core kernel of the
  * vs_sp_forward / vs_sp_backward calls since the last vs_sp_forward on this
  * workspace gave up a bounded wait for its MMAs (VS_ETIMEOUT; its outputs are

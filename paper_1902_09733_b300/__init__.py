@@ -200,6 +200,7 @@ def lib() -> ctypes.CDLL:
             "vs_bp_autotune_times": ([P, I], I),
             "vs_bp_select_sweep": ([I], I),
             "vs_bp_select_fused": ([I, I, I], I),
+            "vs_sp_test_withhold_mma": ([I], I),
             "vs_bp_autotune_plans": ([P, I], I),
             "vs_pair_batch_workspace_size": ([P, I], S),
             "vs_pair_run_batch": ([P, I, P, S, P], I),
@@ -722,6 +723,11 @@ def sp_backward(cost: torch.Tensor, params: SPParams, grad_beliefs: torch.Tensor
 def sp_select_kernels(family: str) -> None:
     """"simt" (FP32 multiply-adds, the default) or "tensor" (tcgen05) kernels for sp_forward / sp_backward."""
     _check("vs_sp_select_kernels", lib().vs_sp_select_kernels({"tensor": 0, "simt": 1}[family]))
+
+
+def sp_test_withhold_mma(on: bool) -> None:
+    """Test aid: the tensor-core smoothed-BP kernels issue no MMA, so their bounded waits run out."""
+    _check("vs_sp_test_withhold_mma", lib().vs_sp_test_withhold_mma(1 if on else 0))
 
 
 def sp_status(workspace: torch.Tensor, w: int, h: int, params: SPParams, stream=None) -> None:

@@ -29,6 +29,7 @@
 // Threads: 4 per pixel (one per slot or per outgoing direction), 32 pixels
 // per 128-thread CTA, every label vector in registers, the K tables in the
 // kernel parameters (constant bank) so each multiply-add is one FFMA.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 
@@ -53,6 +54,8 @@ struct SpArgs {
     const float *gbel;     // adjoint: dL/dbeliefs (initial value of dL/dD)
     double *partial;       // adjoint: per-CTA (lambda, T, tau) sums, 4 doubles per CTA
     int *err;              // set to 1 by a tensor-core kernel whose MMA wait timed out
+    int withhold_mma;      // test aid: the tensor-core kernels issue no MMA and no commit, so every
+                           // bounded wait runs out with nothing in flight
     int w, h, npix;
     int from_belief, first;
     float nc;              // -log2(e) / tau
@@ -596,7 +599,8 @@ __device__ __forceinline__ void tc_teardown(const SpArgs &a, uint8_t *sm, uint32
 {
     using P = TcPlan<L, ADJ>;
     if (failed && (threadIdx.x & (kTcRows - 1)) == 0) {
-        tc::mbar_wait(reinterpret_cast<uint64_t *>(sm + P::kBar) + g, pending_parity);
+        if (!a.withhold_mma)   // nothing was issued under the test aid
+            tc::mbar_wait(reinterpret_cast<uint64_t *>(sm + P::kBar) + g, pending_parity);
         atomicExch(a.err, 1);
     }
     tc::fence_before_sync();
@@ -644,7 +648,7 @@ __global__ void __launch_bounds__(TcPlan<L, false>::kThreads, 1) k_sp_fwd_tc(con
         tc::fence_proxy_async_smem();
         tc::fence_before_sync();
         group_sync(g);
-        if (tid == 0) {
+        if (tid == 0 && !a.withhold_mma) {
             tc::fence_after_sync();
             issue_mma_3x<L, P::NB>(sm, P::kAhi(g), P::kAlo(g), P::kBhi, P::kBlo, 0, tmem, tmem + P::kCorr, idesc);
             tc::mma_commit(bar);
@@ -751,7 +755,7 @@ __global__ void __launch_bounds__(TcPlan<L, true>::kThreads, 1) k_sp_adj_tc(cons
         tc::fence_proxy_async_smem();
         tc::fence_before_sync();
         group_sync(g);
-        if (tid == 0) {
+        if (tid == 0 && !a.withhold_mma) {
             tc::fence_after_sync();
             issue_mma_3x<L, P::NB>(sm, P::kAhi(g), P::kAlo(g), P::kBhi, P::kBlo, 0, tmem, tmem + P::kCorr, idesc);
             tc::mma_commit(bar);
@@ -819,7 +823,7 @@ __global__ void __launch_bounds__(TcPlan<L, true>::kThreads, 1) k_sp_adj_tc(cons
         tc::fence_proxy_async_smem();
         tc::fence_before_sync();
         group_sync(g);
-        if (tid == 0) {
+        if (tid == 0 && !a.withhold_mma) {
             tc::fence_after_sync();
             issue_mma_3x<L, P::NB>(sm, P::kAhi(g), P::kAlo(g), P::kBhi, P::kBlo, L, tmem, tmem + P::kCorr, idesc);
             tc::mma_commit(bar);
@@ -1012,6 +1016,7 @@ void fill_tables(SpArgs &a, const vs_sp_params *p)
 // contraction is small next to the gathers, which leave the tensor-core
 // kernels latency-bound with one CTA per SM.
 int g_sp_kernels = 1;
+std::atomic<int> g_withhold_mma{0};   // vs_sp_test_withhold_mma
 
 // Persistent grid of a tensor-core kernel: resident CTAs per SM x SMs, at
 // most one CTA per tile.  The kernel asks for the largest shared-memory
@@ -1215,6 +1220,7 @@ extern "C" int vs_sp_forward(const float *cost, int w, int h, const vs_sp_params
     fill_tables(a, p);
     a.cost = cost;
     a.err = S.err();
+    a.withhold_mma = g_withhold_mma.load(std::memory_order_relaxed);
     a.w = w, a.h = h, a.npix = w * h;
     a.beliefs = beliefs;
     const int K = p->iters, c = p->ckpt_every;
@@ -1253,6 +1259,7 @@ extern "C" int vs_sp_backward(const float *cost, int w, int h, const vs_sp_param
     fill_tables(a, p);
     a.cost = cost;
     a.err = S.err();
+    a.withhold_mma = g_withhold_mma.load(std::memory_order_relaxed);
     a.w = w, a.h = h, a.npix = w * h;
     a.gcost = grad_cost;
     a.gbel = grad_beliefs;
@@ -1297,6 +1304,14 @@ extern "C" int vs_sp_backward(const float *cost, int w, int h, const vs_sp_param
     if (err != cudaSuccess)
         return VS_ECUDA;
     return launch_status();
+}
+
+extern "C" int vs_sp_test_withhold_mma(int on)
+{
+    if (on != 0 && on != 1)
+        return VS_EINVAL;
+    vs::g_withhold_mma.store(on, std::memory_order_relaxed);
+    return VS_OK;
 }
 
 extern "C" int vs_sp_status(const void *workspace, size_t ws_bytes, int w, int h, const vs_sp_params *p,

@@ -44,3 +44,42 @@ def test_staged_sweep_wait_runs_out_and_is_reported():
         vs.bp_select_sweep(-1)
     want = oracle.bp(left, right, 16, 1, 3, 20, 10, 40)
     np.testing.assert_array_equal(lab.cpu().numpy(), want)
+
+
+def test_tensor_core_mma_wait_runs_out_and_is_reported():
+    """The tensor-core smoothed-BP kernels with their MMAs withheld (a test aid:
+    no MMA and no completion signal are issued, so nothing is in flight): each
+    bounded wait gives up, the forward and the adjoint report VS_ETIMEOUT
+    through vs_sp_status, and the next calls run normally and agree with the
+    SIMT kernels."""
+    g = torch.Generator(device="cuda").manual_seed(5)
+    p = vs.SPParams(labels=48, iters=2, ckpt_every=1, lam=2.5, trunc=13.75, tau=2.0)
+    cost = torch.rand((30, 40, 48), generator=g, device="cuda") * 20.0
+    gb = torch.randn((30, 40, 48), generator=g, device="cuda")
+    vs.sp_select_kernels("tensor")
+    try:
+        vs.sp_test_withhold_mma(True)
+        try:
+            _, ws = vs.sp_forward(cost, p)
+            with pytest.raises(vs.VSError) as e:
+                vs.sp_status(ws, 40, 30, p)
+            assert e.value.code == vs.VS_ETIMEOUT
+            vs.sp_backward(cost, p, gb, ws)
+            with pytest.raises(vs.VSError) as e:
+                vs.sp_status(ws, 40, 30, p)
+            assert e.value.code == vs.VS_ETIMEOUT
+        finally:
+            vs.sp_test_withhold_mma(False)
+        b_tc, ws = vs.sp_forward(cost, p)
+        gc_tc, gp_tc = vs.sp_backward(cost, p, gb, ws)
+        vs.sp_status(ws, 40, 30, p)
+    finally:
+        vs.sp_select_kernels("simt")
+    b_s, ws_s = vs.sp_forward(cost, p)
+    gc_s, gp_s = vs.sp_backward(cost, p, gb, ws_s)
+    torch.cuda.synchronize()
+    # each family is within 2e-5 (beliefs) and 1e-3 (gradients) of the FP64 oracle
+    scale = b_s.abs().max().item()
+    assert (b_tc - b_s).abs().max().item() <= 4e-5 * scale
+    assert (gc_tc - gc_s).abs().max().item() <= 2e-3 * gc_s.abs().max().item()
+    assert torch.allclose(gp_tc, gp_s, rtol=2e-3, atol=2e-3 * gp_s.abs().max().item())
