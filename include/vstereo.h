@@ -494,6 +494,21 @@ int vs_sp_test_withhold_mma(int on);
  * then invalid).  Errors: VS_EINVAL, VS_EWORKSPACE, VS_ECUDA. */
 int vs_sp_status(const void *workspace, size_t ws_bytes, int w, int h, const vs_sp_params *p, void *stream);
 
+/* The checked build (no counterpart in the paper): libvstereo_checked.so is
+ * built from the same sources with bounds checks on every global access of
+ * the min-sum kernels, tested against the address ranges of the call's
+ * buffers; the first access outside them is recorded and skipped, never
+ * made.  vs_check_report returns 1 and writes {site, address} to
+ * site_addr[0..1] (nullable) if an access was refused since the last
+ * report, 0 if none, and -1 in the product library, which carries no
+ * checks.  vs_check_test_shrink (test aid, checked build only) registers
+ * the BP workspace `bytes` shorter than it is from the next call on, so that
+ * an access to its end is refused without leaving the real buffer; 0
+ * restores; VS_EINVAL in the product library.  The checked build registers
+ * ranges with a synchronous copy per call: not for stream capture. */
+int vs_check_report(unsigned long long *site_addr);
+int vs_check_test_shrink(long long bytes);
+
 /* Name of a status code. */
 const char *vs_status_string(int status);
 

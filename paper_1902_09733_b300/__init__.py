@@ -20,6 +20,7 @@ Steps of the method (arXiv 1902.09733):
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import threading
@@ -160,6 +161,66 @@ _lock = threading.Lock()
 _lib = None
 
 
+def _load(path: str) -> ctypes.CDLL:
+    """A CDLL of the library at `path` with every entry point's argument and
+    result types set."""
+    L = ctypes.CDLL(path)
+    P, I, F, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_size_t
+    cam_p, bp_p = ctypes.POINTER(_Camera), ctypes.POINTER(_BPParams)
+    sp_p = ctypes.POINTER(_SPParams)
+    jbu_p, cfg_p = ctypes.POINTER(_JBUParams), ctypes.POINTER(_PairConfig)
+    sig = {
+        "vs_rectify_remap": ([P, I, I, I, cam_p, P, P, I, I, P, I, P, I, P], I),
+        "vs_bp_workspace_size": ([I, I, bp_p], S),
+        "vs_bp_stereo": ([P, P, I, I, I, bp_p, P, I, P, S, P], I),
+        "vs_bp_export_messages": ([P, S, I, I, bp_p, P, P], I),
+        "vs_bp_status": ([P, S, I, I, bp_p, P], I),
+        "vs_bp_test_withhold_copies": ([I], I),
+        "vs_guided_upsample": ([P, I, I, I, P, I, P, I, I, I, jbu_p, P, P], I),
+        "vs_reproject": ([P, I, I, cam_p, F, P, P], I),
+        "vs_guided_upsample_reproject": ([P, I, I, I, P, I, P, I, I, I, jbu_p, cam_p, F, P, P, P], I),
+        "vs_pair_workspace_size": ([cfg_p], S),
+        "vs_pair_run": ([cfg_p, P, P, P, P, P, S, P], I),
+        "vs_pair_run_host": ([cfg_p, P, P, P, P, P, P, P, P, S, P], I),
+        "vs_status_string": ([I], ctypes.c_char_p),
+        "vs_kernel_launches": ([], ctypes.c_uint64),
+        "vs_profile_enable": ([I], I),
+        "vs_profile_collect": ([P, P, I], I),
+        "vs_bp_batch_workspace_size": ([P, I], S),
+        "vs_bp_stereo_batch": ([P, I, P, S, P], I),
+        "vs_bp_batch_mode": ([I], I),
+        "vs_bp_autotune": ([P, P, I, I, I, bp_p, P, I, P, S, P, P], I),
+        "vs_bp_autotune_reset": ([], None),
+        "vs_bp_autotune_times": ([P, I], I),
+        "vs_bp_select_sweep": ([I], I),
+        "vs_bp_select_fused": ([I, I, I], I),
+        "vs_sp_test_withhold_mma": ([I], I),
+        "vs_bp_autotune_plans": ([P, I], I),
+        "vs_pair_batch_workspace_size": ([P, I], S),
+        "vs_pair_run_batch": ([P, I, P, S, P], I),
+        "vs_bp_autotune_level_times": ([P, I], I),
+        "vs_pipeline_workspace_size": ([cfg_p, I, I, I], S),
+        "vs_pipeline_create": ([cfg_p, I, I, I, P, S, ctypes.POINTER(P)], I),
+        "vs_pipeline_submit_pair": ([P, P, P, P], I),
+        "vs_pipeline_submit_frame": ([P, P, P], I),
+        "vs_pipeline_flush": ([P], I),
+        "vs_pipeline_latencies": ([P, P, I], I),
+        "vs_pipeline_destroy": ([P], None),
+        "vs_sp_workspace_size": ([I, I, sp_p], S),
+        "vs_sp_forward": ([P, I, I, sp_p, P, P, S, P], I),
+        "vs_sp_backward": ([P, I, I, sp_p, P, P, P, P, S, P], I),
+        "vs_sp_select_kernels": ([I], I),
+        "vs_sp_status": ([P, S, I, I, sp_p, P], I),
+        "vs_check_report": ([P], I),
+        "vs_check_test_shrink": ([ctypes.c_longlong], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    return L
+
+
 def lib() -> ctypes.CDLL:
     """The loaded library; raises if it has not been built."""
     global _lib
@@ -170,60 +231,39 @@ def lib() -> ctypes.CDLL:
             raise RuntimeError(
                 f"{library_path} is missing: build it with "
                 "`python -m paper_1902_09733_b300.build` (nvcc, sm_103a); there is no CPU fallback")
-        L = ctypes.CDLL(library_path)
-        P, I, F, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_size_t
-        cam_p, bp_p = ctypes.POINTER(_Camera), ctypes.POINTER(_BPParams)
-        sp_p = ctypes.POINTER(_SPParams)
-        jbu_p, cfg_p = ctypes.POINTER(_JBUParams), ctypes.POINTER(_PairConfig)
-        sig = {
-            "vs_rectify_remap": ([P, I, I, I, cam_p, P, P, I, I, P, I, P, I, P], I),
-            "vs_bp_workspace_size": ([I, I, bp_p], S),
-            "vs_bp_stereo": ([P, P, I, I, I, bp_p, P, I, P, S, P], I),
-            "vs_bp_export_messages": ([P, S, I, I, bp_p, P, P], I),
-            "vs_bp_status": ([P, S, I, I, bp_p, P], I),
-            "vs_bp_test_withhold_copies": ([I], I),
-            "vs_guided_upsample": ([P, I, I, I, P, I, P, I, I, I, jbu_p, P, P], I),
-            "vs_reproject": ([P, I, I, cam_p, F, P, P], I),
-            "vs_guided_upsample_reproject": ([P, I, I, I, P, I, P, I, I, I, jbu_p, cam_p, F, P, P, P], I),
-            "vs_pair_workspace_size": ([cfg_p], S),
-            "vs_pair_run": ([cfg_p, P, P, P, P, P, S, P], I),
-            "vs_pair_run_host": ([cfg_p, P, P, P, P, P, P, P, P, S, P], I),
-            "vs_status_string": ([I], ctypes.c_char_p),
-            "vs_kernel_launches": ([], ctypes.c_uint64),
-            "vs_profile_enable": ([I], I),
-            "vs_profile_collect": ([P, P, I], I),
-            "vs_bp_batch_workspace_size": ([P, I], S),
-            "vs_bp_stereo_batch": ([P, I, P, S, P], I),
-            "vs_bp_batch_mode": ([I], I),
-            "vs_bp_autotune": ([P, P, I, I, I, bp_p, P, I, P, S, P, P], I),
-            "vs_bp_autotune_reset": ([], None),
-            "vs_bp_autotune_times": ([P, I], I),
-            "vs_bp_select_sweep": ([I], I),
-            "vs_bp_select_fused": ([I, I, I], I),
-            "vs_sp_test_withhold_mma": ([I], I),
-            "vs_bp_autotune_plans": ([P, I], I),
-            "vs_pair_batch_workspace_size": ([P, I], S),
-            "vs_pair_run_batch": ([P, I, P, S, P], I),
-            "vs_bp_autotune_level_times": ([P, I], I),
-            "vs_pipeline_workspace_size": ([cfg_p, I, I, I], S),
-            "vs_pipeline_create": ([cfg_p, I, I, I, P, S, ctypes.POINTER(P)], I),
-            "vs_pipeline_submit_pair": ([P, P, P, P], I),
-            "vs_pipeline_submit_frame": ([P, P, P], I),
-            "vs_pipeline_flush": ([P], I),
-            "vs_pipeline_latencies": ([P, P, I], I),
-            "vs_pipeline_destroy": ([P], None),
-            "vs_sp_workspace_size": ([I, I, sp_p], S),
-            "vs_sp_forward": ([P, I, I, sp_p, P, P, S, P], I),
-            "vs_sp_backward": ([P, I, I, sp_p, P, P, P, P, S, P], I),
-            "vs_sp_select_kernels": ([I], I),
-            "vs_sp_status": ([P, S, I, I, sp_p, P], I),
-        }
-        for name, (args, res) in sig.items():
-            fn = getattr(L, name)
-            fn.argtypes = args
-            fn.restype = res
-        _lib = L
-        return L
+        _lib = _load(library_path)
+        return _lib
+
+
+checked_library_path = os.path.join(_HERE, "libvstereo_checked.so")
+_checked = None
+
+
+def checked_lib() -> ctypes.CDLL:
+    """The checked build (bounds checks in the min-sum kernels, for tests)."""
+    global _checked
+    with _lock:
+        if _checked is None:
+            if not os.path.exists(checked_library_path):
+                raise RuntimeError(f"{checked_library_path} is missing: build it with "
+                                   "`python -m paper_1902_09733_b300.build`")
+            _checked = _load(checked_library_path)
+        return _checked
+
+
+@contextlib.contextmanager
+def using(library: ctypes.CDLL):
+    """Test aid: every wrapper of this module calls `library` (for example
+    checked_lib()) inside the block; one thread at a time."""
+    global _lib
+    lib()
+    with _lock:
+        old, _lib = _lib, library
+    try:
+        yield library
+    finally:
+        with _lock:
+            _lib = old
 
 
 def status_string(code: int) -> str:

@@ -33,6 +33,7 @@
 // registers.  All lane values stay below 2^15 (ABI limits), so the packed
 // adds never carry across lanes and the signed form is exact too.
 #include "vs_bp_wide.cuh"
+#include "vs_check.cuh"
 #include "vs_common.cuh"
 #include "vs_tcgen05.cuh"
 
@@ -150,13 +151,27 @@ __host__ __device__ __forceinline__ size_t slot_base(int row, int xh, int wg, in
 {
     return ((((size_t)row * wg + (xh >> 4)) * np) * 16 + (xh & 15)) * 16;
 }
+// Every global 16-byte piece goes through these (bounds-checked in the
+// checked build; shared-memory copies use them too, and chk() accepts none
+// of those addresses, so the sweeps that read shared memory pass SMEM to
+// sweep_pixel and load directly).
 __device__ __forceinline__ uint4 ld_piece(const uint8_t *base, int p)
 {
-    return *reinterpret_cast<const uint4 *>(base + (size_t)p * kPieceStride);
+    const uint8_t *q = base + (size_t)p * kPieceStride;
+    if (!chk(q, 16, kSitePieceLoad))
+        return make_uint4(0, 0, 0, 0);
+    return *reinterpret_cast<const uint4 *>(q);
 }
 __device__ __forceinline__ void st_piece(uint8_t *base, int p, const uint4 &v)
 {
-    *reinterpret_cast<uint4 *>(base + (size_t)p * kPieceStride) = v;
+    uint8_t *q = base + (size_t)p * kPieceStride;
+    if (chk(q, 16, kSitePieceStore))
+        *reinterpret_cast<uint4 *>(q) = v;
+}
+// The same without the check, for shared memory.
+__device__ __forceinline__ uint4 ld_piece_smem(const uint8_t *base, int p)
+{
+    return *reinterpret_cast<const uint4 *>(base + (size_t)p * kPieceStride);
 }
 
 // The level being swept reads and rewrites its message arrays every
@@ -172,6 +187,8 @@ __device__ __forceinline__ uint4 ld_piece_keep(const uint8_t *base, int p, uint6
 {
     uint4 v;
     const uint8_t *ptr = base + (size_t)p * kPieceStride;
+    if (!chk(ptr, 16, kSitePieceLoad))
+        return make_uint4(0, 0, 0, 0);
     asm volatile("ld.global.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
                  : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
                  : "l"(ptr), "l"(pol));
@@ -180,6 +197,8 @@ __device__ __forceinline__ uint4 ld_piece_keep(const uint8_t *base, int p, uint6
 __device__ __forceinline__ void st_piece_keep(uint8_t *base, int p, const uint4 &v, uint64_t pol)
 {
     uint8_t *ptr = base + (size_t)p * kPieceStride;
+    if (!chk(ptr, 16, kSitePieceStore))
+        return;
     asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(ptr), "r"(v.x), "r"(v.y),
                  "r"(v.z), "r"(v.w), "l"(pol)
                  : "memory");
@@ -208,7 +227,7 @@ struct Cost01Args {
 __device__ __forceinline__ uint4 cost0_chunk_slow(const Cost01Args &a, const uint8_t *rowL, const uint8_t *rowR,
                                                   int x, int j, uint32_t (&acc)[8])
 {
-    const int il = __ldg(rowL + x);
+    const int il = chk(rowL + x, 1, kSiteImage) ? __ldg(rowL + x) : 0;
     uint32_t wv[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
@@ -216,7 +235,7 @@ __device__ __forceinline__ uint4 cost0_chunk_slow(const Cost01Args &a, const uin
         int v = 0;
         if (d < a.L) {
             v = a.Td;
-            if (x - d >= 0)
+            if (x - d >= 0 && chk(rowR + x - d, 1, kSiteImage))
                 v = min(abs(il - (int)__ldg(rowR + x - d)), a.Td);
         }
         wv[i >> 2] |= (uint32_t)v << (8 * (i & 3));
@@ -239,7 +258,7 @@ __global__ void __launch_bounds__(128) k_cost01(Cost01Args a)
     const int chunks = a.Lp / 16;
     const int nxb = (a.w1 + 31) / 32;
     const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx == 0)
+    if (idx == 0 && chk(a.status, 4, kSiteStatus))
         *a.status = VS_OK;
     unsigned t = idx >> 5;
     const int j = (int)(t % (unsigned)chunks);
@@ -270,13 +289,15 @@ __global__ void __launch_bounds__(128) k_cost01(Cost01Args a)
             uint32_t w[5], W[5];
 #pragma unroll
             for (int k = 0; k < 5; ++k)
-                w[k] = __ldg(q + k);
+                w[k] = chk(q + k, 4, kSiteImage) ? __ldg(q + k) : 0u;
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 W[k] = __funnelshift_r(w[k], w[k + 1], sh);
             W[4] = w[4] >> sh;
-            const uint32_t il2 = (uint32_t)__ldg(reinterpret_cast<const uint8_t *>(rowL + 2 * X)) |
-                                 ((uint32_t)__ldg(rowL + 2 * X + 1) << 8);
+            const uint32_t il2 = chk(rowL + 2 * X, 2, kSiteImage)
+                                     ? (uint32_t)__ldg(reinterpret_cast<const uint8_t *>(rowL + 2 * X)) |
+                                           ((uint32_t)__ldg(rowL + 2 * X + 1) << 8)
+                                     : 0u;
 #pragma unroll
             for (int ii = 0; ii < 2; ++ii) {
                 const uint32_t il4 = ((il2 >> (8 * ii)) & 0xFFu) * 0x01010101u;
@@ -381,7 +402,8 @@ __global__ void k_cost_down(CostDownArgs a)
             const int frow = cf * a.hf + yf;
             if (a.fine_is_u8) {
                 const uint8_t *b = reinterpret_cast<const uint8_t *>(a.fine) + slot_base(frow, x, a.wgf, np16);
-                const uint2 v = *reinterpret_cast<const uint2 *>(b + (j >> 1) * kPieceStride + (j & 1) * 8);
+                const uint8_t *q = b + (j >> 1) * kPieceStride + (j & 1) * 8;
+                const uint2 v = chk(q, 8, kSiteCostWord) ? *reinterpret_cast<const uint2 *>(q) : make_uint2(0, 0);
                 // widen 8 bytes to 8 u16 lanes
                 acc[0] += prmt(v.x, 0, 0x4140);
                 acc[1] += prmt(v.x, 0, 0x4342);
@@ -399,9 +421,9 @@ __global__ void k_cost_down(CostDownArgs a)
     }
     uint8_t *cb = reinterpret_cast<uint8_t *>(a.coarse);
     if (a.coarse_is_u8) {   // every lane is <= 255 here: narrow back to bytes
-        uint8_t *b = cb + slot_base((int)row, xh, a.wgc, np16);
-        *reinterpret_cast<uint2 *>(b + (j >> 1) * kPieceStride + (j & 1) * 8) =
-            make_uint2(prmt(acc[0], acc[1], 0x6420u), prmt(acc[2], acc[3], 0x6420u));
+        uint8_t *b = cb + slot_base((int)row, xh, a.wgc, np16) + (j >> 1) * kPieceStride + (j & 1) * 8;
+        if (chk(b, 8, kSiteCostWord))
+            *reinterpret_cast<uint2 *>(b) = make_uint2(prmt(acc[0], acc[1], 0x6420u), prmt(acc[2], acc[3], 0x6420u));
     } else {
         st_piece(cb + slot_base((int)row, xh, a.wgc, 2 * np16), j, make_uint4(acc[0], acc[1], acc[2], acc[3]));
     }
@@ -444,6 +466,7 @@ template <>
 struct CostChunk<uint8_t> {
     uint4 v;
     __device__ __forceinline__ void load(const uint8_t *base, int j) { v = ld_piece(base, j); }
+    __device__ __forceinline__ void load_smem(const uint8_t *base, int j) { v = ld_piece_smem(base, j); }
     // shared-memory copy with `ps` pieces between consecutive pieces of a slot
     __device__ __forceinline__ void load_s(const uint4 *base, int j, int ps) { v = base[j * ps]; }
     __device__ __forceinline__ uint32_t word(int wi) const { return (&v.x)[wi]; }
@@ -464,6 +487,11 @@ struct CostChunk<uint16_t> {
     {
         v0 = ld_piece(base, 2 * j);
         v1 = ld_piece(base, 2 * j + 1);
+    }
+    __device__ __forceinline__ void load_smem(const uint8_t *base, int j)
+    {
+        v0 = ld_piece_smem(base, 2 * j);
+        v1 = ld_piece_smem(base, 2 * j + 1);
     }
     __device__ __forceinline__ void load_s(const uint4 *base, int j, int ps)
     {
@@ -588,8 +616,11 @@ __device__ __forceinline__ void sweep_pixel(const SweepArgs &a, int pair, int x,
         } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                m[k] = !use[k] ? make_uint4(0, 0, 0, 0) : (SMEM ? ld_piece(in[k], j) : ld_piece_keep(in[k], j, pol));
-            cc.load(cost, j);
+                m[k] = !use[k] ? make_uint4(0, 0, 0, 0) : (SMEM ? ld_piece_smem(in[k], j) : ld_piece_keep(in[k], j, pol));
+            if (SMEM)
+                cc.load_smem(cost, j);
+            else
+                cc.load(cost, j);
         }
         if (a.materialize) {
             const size_t k0 = 2 * pair;
@@ -642,7 +673,7 @@ __device__ __forceinline__ void sweep_pixel(const SweepArgs &a, int pair, int x,
         }
     }
 
-    if (LABELS && pair == 0)
+    if (LABELS && pair == 0 && chk(a.labels + (size_t)y * a.labels_pitch + x, 1, kSiteLabel))
         a.labels[(size_t)y * a.labels_pitch + x] = (uint8_t)(best_key & 0xFFu);
 
     // destinations: A = left / up neighbour, B = right / down neighbour
@@ -937,6 +968,12 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_staged(SweepArgs a)
         tc::mbar_expect_tx(bar + buf, 5 * bytes);
         if (a.withhold_copies)   // nothing completes the phase: the bounded wait runs out
             return;
+        bool in_range = chk(cost_in + off, bytes, kSiteBulkCopy);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            in_range = in_range && chk(msg_in + k * arr + off, bytes, kSiteBulkCopy);
+        if (!in_range)   // (checked build) the wait runs out and the call reports VS_ETIMEOUT
+            return;
 #pragma unroll
         for (int k = 0; k < 4; ++k)
             tc::bulk_g2s(dst + k * kBlock, msg_in + k * arr + off, bytes, bar + buf);
@@ -965,7 +1002,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_staged(SweepArgs a)
             // once.)  Only a copy that never lands at all, which no input can
             // cause, would still be pending when that second bound runs out.
             if (threadIdx.x == 0) {
-                atomicExch(a.status, VS_ETIMEOUT);
+                if (chk(a.status, 4, kSiteStatus))
+                    atomicExch(a.status, VS_ETIMEOUT);
                 if (!a.withhold_copies) {
                     tc::mbar_wait(bar + buf, (uint32_t)(it >> 1) & 1u, 4000000000ull);
                     if (next < ntiles)
@@ -1217,13 +1255,17 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_bp_fused(FusedArgs a)
                                     ? a.src + slot_base((((px + py) & 1) * 4 + k) * a.ph + py, px >> 1, a.pwg, NP)
                                     : a.src + slot_base((c * 4 + k) * a.h + y, xh, a.wg, NP);
 #pragma unroll
-            for (int j = 0; j < NP; ++j)
-                cp_async16(msg_s + ((c * 4 + k) * NP + j) * ps + r, use ? g0 + (size_t)j * kPieceStride : g0, use);
+            for (int j = 0; j < NP; ++j) {
+                const bool ok = use && chk(g0 + (size_t)j * kPieceStride, 16, kSiteAsyncCopy);
+                cp_async16(msg_s + ((c * 4 + k) * NP + j) * ps + r, ok ? g0 + (size_t)j * kPieceStride : a.cost, ok);
+            }
         } else {
             const uint8_t *g0 = in ? a.cost + slot_base(c * a.h + y, xh, a.wg, NPC) : a.cost;
 #pragma unroll
-            for (int jc = 0; jc < NPC; ++jc)
-                cp_async16(cost_s + (c * NPC + jc) * ps + r, in ? g0 + (size_t)jc * kPieceStride : g0, in);
+            for (int jc = 0; jc < NPC; ++jc) {
+                const bool ok = in && chk(g0 + (size_t)jc * kPieceStride, 16, kSiteAsyncCopy);
+                cp_async16(cost_s + (c * NPC + jc) * ps + r, ok ? g0 + (size_t)jc * kPieceStride : a.cost, ok);
+            }
         }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
@@ -1322,7 +1364,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_bp_fused(FusedArgs a)
                 }
             }
         }
-        a.labels[(size_t)y * a.labels_pitch + x] = (uint8_t)bestd;
+        if (chk(a.labels + (size_t)y * a.labels_pitch + x, 1, kSiteLabel))
+            a.labels[(size_t)y * a.labels_pitch + x] = (uint8_t)bestd;
     }
 }
 
@@ -1422,7 +1465,8 @@ __global__ void k_bp_labels(LabelArgs a)
             }
         }
     }
-    a.labels[(size_t)y * a.labels_pitch + x] = (uint8_t)bestd;
+    if (chk(a.labels + (size_t)y * a.labels_pitch + x, 1, kSiteLabel))
+        a.labels[(size_t)y * a.labels_pitch + x] = (uint8_t)bestd;
 }
 
 // k_bp_labels where the belief sum of every label fits a byte (level-0
@@ -1471,7 +1515,8 @@ __global__ void __launch_bounds__(128) k_bp_labels_bytes(LabelArgs a)
         }
     }
     const uint32_t best = min(best2 & 0xFFFFu, best2 >> 16);
-    a.labels[(size_t)y * a.labels_pitch + x] = (uint8_t)(best & 0xFFu);
+    if (chk(a.labels + (size_t)y * a.labels_pitch + x, 1, kSiteLabel))
+        a.labels[(size_t)y * a.labels_pitch + x] = (uint8_t)(best & 0xFFu);
 }
 
 struct ExportArgs {
@@ -1494,10 +1539,12 @@ __global__ void k_bp_export(ExportArgs a)
     const bool has = k == 0 ? x > 0 : k == 1 ? x < a.w - 1 : k == 2 ? y > 0 : y < a.h - 1;
     const int c = (x + y) & 1;
     int v = 0;
-    if (has)
-        v = a.msg[slot_base((c * 4 + k) * a.h + y, x >> 1, a.wg, a.Lp / 16) + (size_t)(d >> 4) * kPieceStride +
-                  (d & 15)];
-    a.out[idx] = v;
+    const uint8_t *src = a.msg + slot_base((c * 4 + k) * a.h + y, x >> 1, a.wg, a.Lp / 16) +
+                         (size_t)(d >> 4) * kPieceStride + (d & 15);
+    if (has && chk(src, 1, kSiteExport))
+        v = *src;
+    if (chk(a.out + idx, 4, kSiteExport))
+        a.out[idx] = v;
 }
 
 // ---------------------------------------------------------------------------
@@ -2031,6 +2078,12 @@ SweepArgs sweep_args(const BpLayout &lay, uint8_t *ws, const vs_bp_params *p, in
     return a;
 }
 
+// Checked build: bytes taken off the end of the workspace's registered range
+// (vs_check_test_shrink); set while a batch runs, whose call registered the
+// ranges of all its pairs at once.
+size_t g_check_shrink = 0;
+bool g_check_in_batch = false;
+
 int check_workspace(const BpLayout &lay, const void *ws, size_t ws_bytes)
 {
     if (!ws || !aligned(ws, 256) || ws_bytes < lay.total)
@@ -2197,7 +2250,8 @@ void run_pair(const BpLayout &lay, uint8_t *ws, const uint8_t *left, const uint8
               const vs_bp_params *p, uint8_t *labels, int labels_pitch, cudaStream_t st)
 {
     if (lay.wide) {
-        bp_wide_run(left, right, lay.w[0], lay.h[0], pitch, p, labels, labels_pitch, ws, st);
+        bp_wide_run(left, right, lay.w[0], lay.h[0], pitch, p, labels, labels_pitch, ws, st,
+                    g_check_in_batch ? kCheckKeepRanges : g_check_shrink);
         return;
     }
     launch_costs(lay, ws, left, right, pitch, p, st);
@@ -2234,6 +2288,10 @@ extern "C" int vs_bp_stereo(const uint8_t *left, const uint8_t *right, int w, in
     int rc = check_workspace(lay, workspace, ws_bytes);
     if (rc != VS_OK)
         return rc;
+    NvtxRange range("vs_bp_stereo");
+    check_ranges((cudaStream_t)stream, {{left, (size_t)(h - 1) * pitch + w}, {right, (size_t)(h - 1) * pitch + w},
+                                        {labels, (size_t)(h - 1) * labels_pitch + w}, {workspace, ws_bytes}},
+                 g_check_shrink);
     run_pair(lay, reinterpret_cast<uint8_t *>(workspace), left, right, pitch, p, labels, labels_pitch,
              (cudaStream_t)stream);
     return launch_status();
@@ -2414,13 +2472,30 @@ extern "C" int vs_bp_stereo_batch(const vs_bp_job *jobs, int n, void *workspace,
         return VS_EWORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
     uint8_t *base = reinterpret_cast<uint8_t *>(workspace);
-    if (g_batch_mode == 0) {
-        if (int rc = batch_streams(jobs, n, lays, offs, base, st))
-            return rc;
-    } else {
-        batch_lockstep(jobs, n, lays, offs, base, st);
+    NvtxRange range("vs_bp_stereo_batch");
+#ifdef VS_CHECKED
+    {
+        // every job's images and labels and the whole workspace (their hull beyond 64 ranges)
+        std::vector<std::pair<const void *, size_t>> bufs;
+        for (int i = 0; i < n; ++i) {
+            const vs_bp_job &j = jobs[i];
+            bufs.push_back({j.left, (size_t)(j.h - 1) * j.pitch + j.w});
+            bufs.push_back({j.right, (size_t)(j.h - 1) * j.pitch + j.w});
+            bufs.push_back({j.labels, (size_t)(j.h - 1) * j.labels_pitch + j.w});
+        }
+        bufs.push_back({workspace, ws_bytes});
+        check_ranges_list(st, bufs);
+        bp_wide_check_ranges(st, bufs);
     }
-    return launch_status();
+#endif
+    g_check_in_batch = true;
+    int rc = VS_OK;
+    if (g_batch_mode == 0)
+        rc = batch_streams(jobs, n, lays, offs, base, st);
+    else
+        batch_lockstep(jobs, n, lays, offs, base, st);
+    g_check_in_batch = false;
+    return rc != VS_OK ? rc : launch_status();
 }
 
 // ---------------------------------------------------------------------------
@@ -2739,6 +2814,37 @@ extern "C" void vs_bp_autotune_reset(void)
     vs::g_fused_tune.clear();
 }
 
+extern "C" int vs_check_report(unsigned long long *site_addr)
+{
+#ifdef VS_CHECKED
+    unsigned long long a0 = 0, a1 = 0;
+    const unsigned long long s0 = vs::check_take(&a0);
+    const unsigned long long s1 = vs::bp_wide_check_take(&a1);
+    const unsigned long long site = s0 ? s0 : s1, addr = s0 ? a0 : a1;
+    if (site_addr) {
+        site_addr[0] = site ? site - 1 : 0;
+        site_addr[1] = addr;
+    }
+    return site ? 1 : 0;
+#else
+    (void)site_addr;
+    return -1;
+#endif
+}
+
+extern "C" int vs_check_test_shrink(long long bytes)
+{
+#ifdef VS_CHECKED
+    if (bytes < 0)
+        return VS_EINVAL;
+    vs::g_check_shrink = (size_t)bytes;
+    return VS_OK;
+#else
+    (void)bytes;
+    return VS_EINVAL;
+#endif
+}
+
 extern "C" int vs_bp_select_fused(int tile_w, int tile_h, int lanes)
 {
     if (tile_w < 0 || tile_h < 0 || tile_w > 1024 || tile_h > 1024 || (tile_w == 0) != (tile_h == 0) ||
@@ -2768,6 +2874,7 @@ extern "C" int vs_bp_export_messages(const void *workspace, size_t ws_bytes, int
         bp_wide_export(reinterpret_cast<const uint8_t *>(workspace), w, h, p, out, (cudaStream_t)stream);
         return launch_status();
     }
+    check_ranges((cudaStream_t)stream, {{workspace, ws_bytes}, {out, (size_t)n * sizeof(int32_t)}});
     ExportArgs a{reinterpret_cast<const uint8_t *>(workspace) + lay.msg_off[0], out, w, h, lay.wh[0], lay.wg[0], lay.L,
                  lay.Lp};
     launch_pdl(k_bp_export, dim3((unsigned)((n + 255) / 256)), dim3(256), (cudaStream_t)stream, a);

@@ -23,6 +23,7 @@
 // F(end of block j - 1) + c (d - j LPL + 1)), and the mirror image for the
 // backward pass; the minimum over the labels is a warp reduction.
 #include "vs_bp_wide.cuh"
+#include "vs_check.cuh"
 
 #include <algorithm>
 
@@ -81,7 +82,7 @@ __global__ void k_wcost0(WCost0Args a)
 {
     pdl_begin();
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx == 0)
+    if (idx == 0 && chk(a.status, 4, kSiteStatus))
         *a.status = VS_OK;
     if (idx >= (size_t)2 * a.h * a.wh * a.Lp)
         return;
@@ -96,12 +97,12 @@ __global__ void k_wcost0(WCost0Args a)
     int32_t v = kWBig;
     if (d < a.L) {
         v = a.Td;
-        if (x - d >= 0) {
-            const int diff = abs((int)a.left[(size_t)y * a.pitch + x] - (int)a.right[(size_t)y * a.pitch + x - d]);
-            v = min(diff, a.Td);
-        }
+        const uint8_t *pl = a.left + (size_t)y * a.pitch + x, *pr = a.right + (size_t)y * a.pitch + x - d;
+        if (x - d >= 0 && chk(pl, 1, kSiteImage) && chk(pr, 1, kSiteImage))
+            v = min(abs((int)*pl - (int)*pr), a.Td);
     }
-    a.cost[idx] = v;
+    if (chk(a.cost + idx, 4, kSiteWideStore))
+        a.cost[idx] = v;
 }
 
 struct WCostDownArgs {
@@ -132,11 +133,13 @@ __global__ void k_wcost_down(WCostDownArgs a)
         for (int j = 0; j < 2; ++j)
             for (int i = 0; i < 2; ++i) {
                 const int xf = 2 * x + i, yf = 2 * y + j;
-                if (xf < a.wf && yf < a.hf)
-                    v += a.fine[((size_t)(((i + j) & 1) * a.hf + yf) * a.whf + x) * a.Lp + d];
+                const int32_t *q = a.fine + ((size_t)(((i + j) & 1) * a.hf + yf) * a.whf + x) * a.Lp + d;
+                if (xf < a.wf && yf < a.hf && chk(q, 4, kSiteWideLoad))
+                    v += *q;
             }
     }
-    a.coarse[idx] = v;
+    if (chk(a.coarse + idx, 4, kSiteWideStore))
+        a.coarse[idx] = v;
 }
 
 // --------------------------------------------------------------------------
@@ -157,6 +160,12 @@ struct WSweepArgs {
 template <int N>
 __device__ __forceinline__ void ld_u16(const uint16_t *p, int32_t (&v)[N])
 {
+    if (!chk(p, 2 * N, kSiteWideLoad)) {
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            v[i] = 0;
+        return;
+    }
     if constexpr (N == 8) {
         const uint4 q = *reinterpret_cast<const uint4 *>(p);
         const uint32_t w[4] = {q.x, q.y, q.z, q.w};
@@ -183,6 +192,8 @@ __device__ __forceinline__ void ld_u16(const uint16_t *p, int32_t (&v)[N])
 template <int N>
 __device__ __forceinline__ void st_u16(uint16_t *p, const int32_t (&v)[N])
 {
+    if (!chk(p, 2 * N, kSiteWideStore))
+        return;
     if constexpr (N == 8) {
         uint4 q;
         q.x = (uint32_t)v[0] | ((uint32_t)v[1] << 16);
@@ -203,6 +214,12 @@ __device__ __forceinline__ void st_u16(uint16_t *p, const int32_t (&v)[N])
 template <int N>
 __device__ __forceinline__ void ld_i32(const int32_t *p, int32_t (&v)[N])
 {
+    if (!chk(p, 4 * N, kSiteWideLoad)) {
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            v[i] = 0;
+        return;
+    }
     if constexpr (N >= 4) {
 #pragma unroll
         for (int i = 0; i < N; i += 4) {
@@ -380,7 +397,7 @@ __global__ void __launch_bounds__(kWThreads) k_wlabels(WLabelArgs a)
             bestd = od;
         }
     }
-    if (lane == 0)
+    if (lane == 0 && chk(a.labels + (size_t)y * a.labels_pitch + x, 1, kSiteLabel))
         a.labels[(size_t)y * a.labels_pitch + x] = (uint8_t)bestd;
 }
 
@@ -402,7 +419,10 @@ __global__ void k_wexport(WExportArgs a)
     const int y = (int)((px / (unsigned)a.w) % (unsigned)a.h);
     const int k = (int)(px / ((size_t)a.w * a.h));
     const bool has = k == 0 ? x > 0 : k == 1 ? x < a.w - 1 : k == 2 ? y > 0 : y < a.h - 1;
-    a.out[idx] = has ? (int32_t)a.msg[wslot((x + y) & 1, k, y, x >> 1, a.h, a.wh) * a.Lp + d] : 0;
+    const uint16_t *src = a.msg + wslot((x + y) & 1, k, y, x >> 1, a.h, a.wh) * a.Lp + d;
+    const int32_t v = has && chk(src, 2, kSiteExport) ? (int32_t)*src : 0;
+    if (chk(a.out + idx, 4, kSiteExport))
+        a.out[idx] = v;
 }
 
 template <typename Args>
@@ -443,9 +463,13 @@ size_t bp_wide_status_offset(int w, int h, const vs_bp_params *p)
 }
 
 void bp_wide_run(const uint8_t *left, const uint8_t *right, int w, int h, int pitch, const vs_bp_params *p,
-                 uint8_t *labels, int labels_pitch, uint8_t *ws, cudaStream_t st)
+                 uint8_t *labels, int labels_pitch, uint8_t *ws, cudaStream_t st, size_t check_shrink)
 {
     const WideLayout lay = wide_layout(w, h, p);
+    if (check_shrink != kCheckKeepRanges)
+        check_ranges(st, {{left, (size_t)(h - 1) * pitch + w}, {right, (size_t)(h - 1) * pitch + w},
+                          {labels, (size_t)(h - 1) * labels_pitch + w}, {ws, lay.total}},
+                     check_shrink);
     {
         WCost0Args a{left, right, pitch, w, h, lay.wh[0], lay.L, lay.Lp, p->data_trunc,
                      reinterpret_cast<int32_t *>(ws + lay.cost_off[0]), reinterpret_cast<int *>(ws + lay.status_off)};
@@ -507,10 +531,19 @@ void bp_wide_run(const uint8_t *left, const uint8_t *right, int w, int h, int pi
 void bp_wide_export(const uint8_t *ws, int w, int h, const vs_bp_params *p, int32_t *out, cudaStream_t st)
 {
     const WideLayout lay = wide_layout(w, h, p);
+    check_ranges(st, {{ws, lay.total}, {out, (size_t)16 * h * w * p->labels}});
     WExportArgs a{reinterpret_cast<const uint16_t *>(ws + lay.msg_off[0]), out, w, h, lay.wh[0], lay.L, lay.Lp};
     const size_t n = (size_t)4 * h * w * lay.L;
     launch_pdl(k_wexport, dim3((unsigned)((n + 255) / 256)), dim3(256), st, a);
     note_launch();
 }
+
+#ifdef VS_CHECKED
+unsigned long long bp_wide_check_take(unsigned long long *addr) { return check_take(addr); }
+void bp_wide_check_ranges(cudaStream_t st, const std::vector<std::pair<const void *, size_t>> &bufs)
+{
+    check_ranges_list(st, bufs);
+}
+#endif
 
 }  // namespace vs

@@ -8,9 +8,21 @@
 #include <functional>
 #include <utility>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/vstereo.h"
 
 namespace vs {
+
+// A named NVTX range around one entry point's work on the host (the stages
+// of a pair appear by name in a profiler's timeline; without a tool
+// attached a push and a pop cost a few nanoseconds).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Counts every kernel the library enqueues (vs_kernel_launches()).
 void note_launch(unsigned n = 1);

@@ -421,6 +421,7 @@ extern "C" int vs_guided_upsample(const uint8_t *labels, int w, int h, int label
                                   const uint8_t *guide_full, int W, int H, int guide_full_pitch,
                                   const vs_jbu_params *jp, float *disp, void *stream)
 {
+    vs::NvtxRange nvtx_range("vs_guided_upsample");
     if (!disp)
         return VS_EINVAL;
     return vs::jbu_common(labels, w, h, labels_pitch, guide_low, guide_low_pitch, guide_full, W, H,
@@ -433,6 +434,7 @@ extern "C" int vs_guided_upsample_reproject(const uint8_t *labels, int w, int h,
                                             const vs_jbu_params *jp, const vs_camera *cam, float baseline,
                                             float *disp, float *xyz, void *stream)
 {
+    vs::NvtxRange nvtx_range("vs_guided_upsample_reproject");
     if (!xyz)
         return VS_EINVAL;
     return vs::jbu_common(labels, w, h, labels_pitch, guide_low, guide_low_pitch, guide_full, W, H,
@@ -442,6 +444,7 @@ extern "C" int vs_guided_upsample_reproject(const uint8_t *labels, int w, int h,
 extern "C" int vs_reproject(const float *disp, int W, int H, const vs_camera *cam, float baseline,
                             float *xyz, void *stream)
 {
+    vs::NvtxRange nvtx_range("vs_reproject");
     using namespace vs;
     if (!disp || !xyz || W <= 0 || H <= 0 || !cam_ok(cam) || !(baseline > 0.0f) || !isfinite(baseline))
         return VS_EINVAL;

@@ -241,6 +241,7 @@ extern "C" size_t vs_pair_workspace_size(const vs_pair_config *cfg)
 extern "C" int vs_pair_run(const vs_pair_config *cfg, const uint8_t *left_src, const uint8_t *right_src,
                            float *disp, float *xyz, void *workspace, size_t ws_bytes, void *stream)
 {
+    vs::NvtxRange nvtx_range("vs_pair_run");
     using namespace vs;
     PairLayout lay;
     if (!pair_layout(cfg, &lay) || !left_src || !right_src || !xyz)
@@ -311,6 +312,7 @@ extern "C" size_t vs_pair_batch_workspace_size(const vs_pair_job *jobs, int n)
 
 extern "C" int vs_pair_run_batch(const vs_pair_job *jobs, int n, void *workspace, size_t ws_bytes, void *stream)
 {
+    vs::NvtxRange nvtx_range("vs_pair_run_batch");
     using namespace vs;
     std::vector<PairLayout> lays;
     std::vector<size_t> offs;
@@ -355,6 +357,7 @@ extern "C" int vs_pair_run_host(const vs_pair_config *cfg, const uint8_t *left_h
                                 float *disp_host, float *xyz_host, uint8_t *dev_in, float *dev_disp,
                                 float *dev_xyz, void *workspace, size_t ws_bytes, void *stream)
 {
+    vs::NvtxRange nvtx_range("vs_pair_run_host");
     using namespace vs;
     PairLayout lay;
     if (!pair_layout(cfg, &lay) || !left_host || !right_host || !xyz_host || !dev_in || !dev_xyz)

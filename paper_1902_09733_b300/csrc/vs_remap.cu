@@ -349,6 +349,7 @@ extern "C" int vs_rectify_remap(const uint8_t *src, int W, int H, int src_pitch,
                                 uint8_t *low_rgb, int low_rgb_pitch,
                                 uint8_t *low_gray, int low_gray_pitch, void *stream)
 {
+    vs::NvtxRange nvtx_range("vs_rectify_remap");
     using namespace vs;
     if (!src || !cam || W <= 0 || H <= 0 || src_pitch < 3 * W)
         return VS_EINVAL;

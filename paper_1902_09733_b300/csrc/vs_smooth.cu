@@ -1205,6 +1205,7 @@ extern "C" int vs_sp_select_kernels(int family)
 extern "C" int vs_sp_forward(const float *cost, int w, int h, const vs_sp_params *p, float *beliefs,
                              void *workspace, size_t ws_bytes, void *stream)
 {
+    vs::NvtxRange nvtx_range("vs_sp_forward");
     if (!sp_valid(w, h, p) || cost == nullptr || beliefs == nullptr)
         return VS_EINVAL;
     if (!aligned(cost, 16) || !aligned(beliefs, 16))
@@ -1245,6 +1246,7 @@ extern "C" int vs_sp_forward(const float *cost, int w, int h, const vs_sp_params
 extern "C" int vs_sp_backward(const float *cost, int w, int h, const vs_sp_params *p, const float *grad_beliefs,
                               float *grad_cost, float *grad_params, void *workspace, size_t ws_bytes, void *stream)
 {
+    vs::NvtxRange nvtx_range("vs_sp_backward");
     if (!sp_valid(w, h, p) || cost == nullptr || grad_beliefs == nullptr || grad_cost == nullptr ||
         grad_params == nullptr)
         return VS_EINVAL;

@@ -115,6 +115,9 @@ def test_bad_arguments_are_rejected_on_the_host(lib):
     for args in ((-1, 4, 0), (4, 0, 0), (0, 4, 0), (4, 4, 3), (2000, 4, 1)):
         assert lib.vs_bp_select_fused(*args) == vs.VS_EINVAL, args
     assert lib.vs_bp_select_fused(0, 0, 0) == vs.VS_OK
+    # the product library carries no bounds checks
+    assert lib.vs_check_report(None) == -1
+    assert lib.vs_check_test_shrink(256) == vs.VS_EINVAL
 
 
 def test_pipeline_host_checks(lib):
