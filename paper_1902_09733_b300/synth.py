@@ -319,12 +319,16 @@ class FlightScene:
         self.albedo = _ValueNoise(g, [0.8 * scale, 0.4 * scale, 0.2 * scale, 0.1 * scale], [0.5, 0.3, 0.2, 0.15],
                                   extent, channels=3)
 
-    def render(self, pose, W: int = 2704, H: int = 1520, cam=TERRAIN_CAMERA) -> np.ndarray:
-        """(H, W, 3) uint8 frame from pose (x, y, yaw) with the radial distortion of ``cam``."""
+    def render(self, pose, W: int = 2704, H: int = 1520, cam=TERRAIN_CAMERA, return_depth: bool = False):
+        """(H, W, 3) uint8 frame from pose (x, y, yaw) with the radial distortion of ``cam``; with
+        ``return_depth`` also the (H, W) float32 z-depth of each pixel along its undistorted ray.
+
+        Camera frame of a pose: z = depth below the camera, (x, y) = the ground offset from the
+        camera turned by -yaw, so that u = fx x / z + cx and v = fy y / z + cy (undistorted)."""
         x, y, yaw = pose
-        frame, _ = _render_view(self.height, self.albedo, self.top, W, H, cam, float(x), self.altitude,
-                                cam_y=float(y), yaw=float(yaw))
-        return frame
+        frame, depth = _render_view(self.height, self.albedo, self.top, W, H, cam, float(x), self.altitude,
+                                    cam_y=float(y), yaw=float(yaw))
+        return (frame, depth) if return_depth else frame
 
     def tables(self):
         """The renderer's inputs as contiguous float32 arrays: the height grid
@@ -368,6 +372,20 @@ def lawnmower_path(seed: int, n_frames: int, spacing: float = 0.05, leg: float =
             cxp, cyp = x0, ybase + 3.0 * radius
             poses[i] = (cxp - radius * np.sin(psi), cyp + radius * np.cos(psi), psi)
     return poses
+
+
+def relative_pose(pose1, pose2):
+    """[R, T] taking camera-frame points of pose 1 to camera-frame points of
+    pose 2 (both nadir at the same altitude, frames as in FlightScene.render):
+    a turn by yaw1 - yaw2 about the optical axis and the ground offset of the
+    two cameras turned into camera 2's axes."""
+    x1, y1, a1 = pose1
+    x2, y2, a2 = pose2
+    d = a1 - a2
+    R = np.array([[np.cos(d), -np.sin(d), 0.0], [np.sin(d), np.cos(d), 0.0], [0.0, 0.0, 1.0]])
+    c, s = np.cos(-a2), np.sin(-a2)
+    T = np.array([c * (x1 - x2) - s * (y1 - y2), s * (x1 - x2) + c * (y1 - y2), 0.0])
+    return R, T
 
 
 def lawnmower_extent(poses, altitude: float = 100.0, W: int = 2704, H: int = 1520, cam=TERRAIN_CAMERA) -> float:

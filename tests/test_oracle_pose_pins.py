@@ -1,0 +1,259 @@
+"""Pins of the pose-path oracle (Section 2.3, Eq. 4-7) against what the
+mathematics fixes: closed forms of Eq. 4 and Eq. 5 on linear ramps, Eq. 4's
+shifted-patch definition against (x, y) M (x, y)^T, exact invariances, known
+shifts for the ZSSD matcher (zero-mean: a brightness offset changes nothing),
+exact recovery of a known pose by EPnP, and the pose between two rendered
+frames against the renderer's own cameras.  No GPU is needed."""
+import numpy as np
+import pytest
+
+from oracle import pose
+from paper_1902_09733_b300 import synth
+
+
+def _grey_rgb(g):
+    """An RGB frame whose luma is g exactly (R = G = B)."""
+    g = np.asarray(g, np.uint8)
+    return np.repeat(g[..., None], 3, axis=2)
+
+
+# ---------------------------------------------------------------------------
+# Eq. 4, Eq. 5
+
+
+@pytest.mark.parametrize("a,b", [(1, 0), (0, 2), (1, 1), (2, -1), (-3, 1)])
+def test_harris_linear_ramp_closed_form(a, b):
+    """I = a x + b y: the central differences are 2a and 2b everywhere inside,
+    the window weights sum to 256, so M = 256 [4a^2, 4ab; 4ab, 4b^2]: det M = 0
+    and 25 R = -(tr M)^2 = -(1024 (a^2 + b^2))^2."""
+    H, W = 24, 30
+    yy, xx = np.mgrid[0:H, 0:W]
+    g = 100 + a * (xx - W // 2) + b * (yy - H // 2)
+    r25 = pose.harris_response25(_grey_rgb(g))
+    want = -(1024 * (a * a + b * b)) ** 2
+    assert (r25[3:-3, 3:-3] == want).all()
+
+
+def test_harris_matrix_is_eq4_of_shifted_patches():
+    """Eq. 4: for a linear patch I = a x + b y the windowed change of
+    intensity under a shift (x, y) is sum w (a x + b y)^2 = (x, y) M' (x, y)^T
+    with M' built from the true derivatives (a, b); the central differences
+    are twice those, so (x, y) M (x, y)^T = 4 E(x, y), for every shift."""
+    a, b = 2, -1
+    H, W = 21, 21
+    yy, xx = np.mgrid[0:H, 0:W]
+    g = 120 + a * (xx - 10) + b * (yy - 10)
+    rgb = _grey_rgb(g)
+    # M at the centre from the response's own pieces: recover it from 25R for two ramps is not
+    # enough, so rebuild it as the oracle defines it and compare with the shift energy
+    gi = pose.grey(rgb)
+    A = np.zeros_like(gi)
+    B = np.zeros_like(gi)
+    A[:, 1:-1] = gi[:, 2:] - gi[:, :-2]
+    B[1:-1, :] = gi[2:, :] - gi[:-2, :]
+    w = np.outer(pose.BINOMIAL, pose.BINOMIAL)
+    win = (slice(8, 13), slice(8, 13))
+    M = np.array([[np.sum(w * A[win] ** 2), np.sum(w * A[win] * B[win])],
+                  [np.sum(w * A[win] * B[win]), np.sum(w * B[win] ** 2)]])
+    for sx, sy in [(1, 0), (0, 1), (1, 1), (2, -1), (-1, 3)]:
+        E = np.sum(w * (gi[8 + sy:13 + sy, 8 + sx:13 + sx] - gi[win]) ** 2)
+        assert np.array([sx, sy]) @ M @ np.array([sx, sy]) == 4 * E
+    # and the oracle's response at the centre is 25 det M - tr(M)^2 of that M
+    r25 = pose.harris_response25(rgb)
+    assert r25[10, 10] == 25 * int(round(np.linalg.det(M))) - int(np.trace(M)) ** 2
+
+
+def test_harris_quadratic_bowl_closed_form():
+    """I = 100 + x^2 + 2 y^2 around the centre: A = 4x, B = 8y, and the
+    binomial window's moments (sum of weights 256, sum of w x^2 = 256, sum of
+    w x y = 0) give M = 256 [16, 0; 0, 64] at the centre, so 25 R = 25 det M
+    - tr(M)^2 = 25 * 67108864 - 20480^2 = 1258291200 (k = 0.04 enters here)."""
+    yy, xx = np.mgrid[-5:6, -5:6]
+    g = 100 + xx * xx + 2 * yy * yy
+    r25 = pose.harris_response25(_grey_rgb(g))
+    assert r25[5, 5] == 1258291200
+
+
+def test_harris_quarter_turn_invariance():
+    """Central differences and the symmetric window commute with a quarter
+    turn of the image: the response map turns with it, exactly."""
+    g = np.random.default_rng(3).integers(0, 256, size=(17, 23, 3)).astype(np.uint8)
+    r = pose.harris_response25(g)
+    np.testing.assert_array_equal(pose.harris_response25(np.ascontiguousarray(np.rot90(g))), np.rot90(r))
+    np.testing.assert_array_equal(pose.harris_response25(np.ascontiguousarray(g[::-1])), r[::-1])
+
+
+def test_harris_flat_edge_corner_signs():
+    """Flat: R = 0.  Straight edge: det M = 0, R < 0.  Corner of a bright
+    square: R > 0, the largest values beside the square's corner point."""
+    g = np.zeros((40, 40), np.uint8)
+    g[15:30, 12:28] = 200
+    r = pose.harris_response25(_grey_rgb(g))
+    assert r[3, 3] == 0                         # flat
+    assert r[22, 12] < 0 and r[15, 20] < 0      # on the edges, away from the corners
+    iy, ix = np.unravel_index(np.argmax(r[5:25, 5:22]), (20, 17))
+    assert abs(iy + 5 - 14.5) <= 1.5 and abs(ix + 5 - 11.5) <= 1.5
+
+
+def test_corner_selection_rules():
+    """One corner per cell; local maxima with ties to the smaller raster
+    index; the margin and the threshold are respected; cells of an odd-sized
+    frame split by integer division."""
+    H, W = 23, 31
+    r = np.zeros((H, W), np.int64)
+    r[4, 5] = 50                 # cell (0, 0) with grid 2: x < 15, y < 11
+    r[6, 9] = 70                 # same cell, larger
+    r[15, 20] = 30               # cell (1, 1)
+    r[15, 21] = 30               # its equal neighbour: the smaller index (15, 20) is the maximum
+    r[2, 25] = 99                # inside the margin 3: not a candidate
+    r[18, 3] = 5                 # below the threshold 10
+    r[8, 1] = 99                 # inside the margin on x
+    c = pose.harris_corners(r, grid=2, margin=3, threshold25=10)
+    assert c.tolist() == [[9, 6], [-1, -1], [-1, -1], [20, 15]]
+    # equal neighbours across a cell boundary (x = 15): only the smaller index is a maximum
+    r3 = np.zeros((H, W), np.int64)
+    r3[5, 14] = r3[5, 15] = 40
+    assert pose.harris_corners(r3, grid=2, margin=1, threshold25=0).tolist() == [[14, 5], [-1, -1], [-1, -1],
+                                                                                   [-1, -1]]
+    # cell bounds: x in [gx W / grid, (gx + 1) W / grid)
+    r2 = np.zeros((H, W), np.int64)
+    r2[11, 15] = 7               # y = 11 is the first row of cell row 1 (23 * 1 // 2 = 11), x = 15 likewise
+    assert pose.harris_corners(r2, grid=2, margin=1, threshold25=0).tolist() == [[-1, -1], [-1, -1], [-1, -1],
+                                                                                   [15, 11]]
+
+
+# ---------------------------------------------------------------------------
+# ZSSD
+
+
+def test_zssd_integer_form_equals_the_zero_mean_definition():
+    g = np.random.default_rng(4)
+    for _ in range(50):
+        P1 = g.integers(0, 256, size=(11, 11))
+        P2 = g.integers(0, 256, size=(11, 11))
+        n = P1.size
+        D = P1 - P2
+        integer = n * int((D * D).sum()) - int(D.sum()) ** 2
+        direct = np.sum(((P1 - P1.mean()) - (P2 - P2.mean())) ** 2)
+        # sum((D - mean D)^2) = sum(D^2) - (sum D)^2 / n
+        assert abs(integer - n * direct) <= 1e-9 * max(1.0, n * direct)
+
+
+def test_zssd_recovers_integer_shifts_under_a_brightness_offset():
+    """Frame 2 = frame 1 shifted by (dx, dy) plus 17 grey levels: the
+    zero-mean cost is 0 at the true shift (a plain SSD would not be)."""
+    g = np.random.default_rng(5)
+    base = synth._gauss_blur(g.uniform(0, 255, size=(60, 80)), 1.5, 5)
+    f1 = np.clip(np.rint(base), 0, 200).astype(np.uint8)
+    for dx, dy in [(3, -2), (-5, 4), (0, 0), (7, 7)]:
+        f2 = np.zeros_like(f1)
+        f2[max(dy, 0):60 + min(dy, 0), max(dx, 0):80 + min(dx, 0)] = \
+            f1[max(-dy, 0):60 - max(dy, 0), max(-dx, 0):80 - max(dx, 0)] + 17
+        corners = np.array([[40, 30], [25, 20], [55, 38], [-1, -1]])
+        pos, cost = pose.zssd_match(_grey_rgb(f1), _grey_rgb(f2), corners, radius=5, search=8)
+        for k in range(3):
+            assert cost[k] == 0
+            assert np.all(np.abs(pos[k] - (corners[k] + [dx, dy])) < 0.5)
+        assert np.isnan(pos[3]).all() and cost[3] == -1
+
+
+def test_zssd_sub_pixel_position_of_a_smooth_blob():
+    """A Gaussian blob moved by a fractional shift: the parabola through the
+    costs around the best integer displacement lands within 0.15 px."""
+    H, W = 48, 48
+    yy, xx = np.mgrid[0:H, 0:W].astype(float)
+    for fx, fy in [(0.3, -0.2), (-0.4, 0.1), (1.25, 0.75)]:
+        b1 = 40 + 160 * np.exp(-((xx - 24) ** 2 + (yy - 24) ** 2) / (2 * 3.0 ** 2))
+        b2 = 40 + 160 * np.exp(-((xx - 24 - fx) ** 2 + (yy - 24 - fy) ** 2) / (2 * 3.0 ** 2))
+        f1, f2 = np.rint(b1).astype(np.uint8), np.rint(b2).astype(np.uint8)
+        pos, _ = pose.zssd_match(_grey_rgb(f1), _grey_rgb(f2), np.array([[24, 24]]), radius=5, search=3)
+        assert abs(pos[0, 0] - (24 + fx)) < 0.15 and abs(pos[0, 1] - (24 + fy)) < 0.15
+
+
+# ---------------------------------------------------------------------------
+# EPnP (Eq. 6, Eq. 7)
+
+
+def _rot(axis, ang):
+    a = np.asarray(axis, float) / np.linalg.norm(axis)
+    K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    return np.eye(3) + np.sin(ang) * K + (1 - np.cos(ang)) * K @ K
+
+
+CAM = (1400.0, 1400.0, 1351.5, 759.5)
+
+
+def _project(P, R, T, cam=CAM):
+    pc = (R @ P.T).T + T
+    return np.column_stack([cam[0] * pc[:, 0] / pc[:, 2] + cam[2], cam[1] * pc[:, 1] / pc[:, 2] + cam[3]])
+
+
+@pytest.mark.parametrize("n", [6, 12, 30, 300])
+def test_epnp_recovers_an_exact_pose(n):
+    g = np.random.default_rng(n)
+    P = g.uniform(-8, 8, size=(n, 3)) + [0, 0, 40]
+    R = _rot(g.normal(size=3), g.uniform(0.05, 0.6))
+    T = g.normal(size=3)
+    Re, Te, err = pose.epnp(P, _project(P, R, T), CAM)
+    assert np.abs(Re - R).max() < 1e-8 and np.abs(Te - T).max() < 1e-7 and err < 1e-6
+    # the order of the points does not matter
+    perm = g.permutation(n)
+    Rp, Tp, _ = pose.epnp(P[perm], _project(P, R, T)[perm], CAM)
+    assert np.abs(Rp - Re).max() < 1e-9 and np.abs(Tp - Te).max() < 1e-8
+
+
+def test_epnp_virtual_stereo_translation():
+    """A camera moved by the stereo baseline along its x axis: R = I and T =
+    (-B, 0, 0) for points given in the first camera's frame."""
+    g = np.random.default_rng(9)
+    P = np.column_stack([g.uniform(-40, 40, 100), g.uniform(-25, 25, 100), g.uniform(85, 100, 100)])
+    R, T = np.eye(3), np.array([-0.5, 0.0, 0.0])
+    Re, Te, _ = pose.epnp(P, _project(P, R, T), CAM)
+    assert np.abs(Re - R).max() < 1e-9 and np.abs(Te - T).max() < 1e-7
+
+
+def test_epnp_with_pixel_noise():
+    g = np.random.default_rng(11)
+    P = np.column_stack([g.uniform(-60, 60, 400), g.uniform(-35, 35, 400), g.uniform(70, 100, 400)])
+    R = _rot([0, 0, 1], 0.03) @ _rot([1, 0.5, 0], 0.01)
+    T = np.array([0.3, -0.1, 0.05])
+    uv = _project(P, R, T) + g.normal(scale=0.5, size=(400, 2))
+    Re, Te, err = pose.epnp(P, uv, CAM)
+    ang = np.degrees(np.arccos(np.clip((np.trace(Re.T @ R) - 1) / 2, -1, 1)))
+    assert ang < 0.05 and np.linalg.norm(Te - T) < 0.1 and err < 1.0
+
+
+# ---------------------------------------------------------------------------
+# the whole pose step on rendered frames
+
+
+def test_pose_between_rendered_frames_matches_the_cameras():
+    """Two undistorted frames of a flight scene ten frames apart on a turn of
+    the lawnmower path (the heading turns 3.6 degrees): Harris corners of
+    frame 1 with their rendered depth, ZSSD matches in frame 2, EPnP with the
+    inlier step: the relative pose of the two cameras (a turn by yaw1 - yaw2
+    about the optical axis and their ground offset) comes back, the turn
+    within 0.05 degrees and the 0.5 m offset within 0.1 m (at this reduced
+    width 0.5 m is 1.7 px, and the parabolic sub-pixel step's pull towards
+    whole pixels is a few tenths of a pixel)."""
+    W, H = 640, 360
+    s = W / 2704.0
+    cam = (1400.0 * s, 1400.0 * s, (W - 1) / 2.0, (H - 1) / 2.0, 0.0, 0.0)
+    poses = synth.lawnmower_path(1, 800)
+    scene = synth.FlightScene(1, synth.lawnmower_extent(poses), n_buildings=80)
+    p1, p2 = poses[600], poses[610]
+    f1, d1 = scene.render(p1, W, H, cam, return_depth=True)
+    f2 = scene.render(p2, W, H, cam)
+    r25 = pose.harris_response25(f1)
+    corners = pose.harris_corners(r25, grid=16, margin=12, threshold25=0)
+    pos, cost = pose.zssd_match(f1, f2, corners, radius=5, search=24)
+    ok = (corners[:, 0] >= 0) & ~np.isnan(pos[:, 0])
+    c = corners[ok]
+    z = d1[c[:, 1], c[:, 0]].astype(float)
+    P = np.column_stack([(c[:, 0] - cam[2]) * z / cam[0], (c[:, 1] - cam[3]) * z / cam[1], z])
+    R, T, err, keep = pose.epnp_inliers(P, pos[ok], cam[:4])
+    Rt, Tt = synth.relative_pose(p1, p2)
+    ang = np.degrees(np.arccos(np.clip((np.trace(R.T @ Rt) - 1) / 2, -1, 1)))
+    assert ok.sum() > 150 and keep.sum() > 0.9 * ok.sum()
+    assert ang < 0.05, ang
+    assert np.linalg.norm(T - Tt) < 0.1, (T, Tt)
