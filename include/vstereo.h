@@ -509,6 +509,81 @@ int vs_sp_status(const void *workspace, size_t ws_bytes, int w, int h, const vs_
 int vs_check_report(unsigned long long *site_addr);
 int vs_check_test_shrink(long long bytes);
 
+/*
+ * Pose between two frames (Section 2.3, Eq. 4-7): Harris corners of frame 1,
+ * their matches in frame 2 by zero-mean SSD, and EPnP on the corners' 3D
+ * points (from frame 1's point cloud) and the matched pixels.  The paper
+ * uses it to re-estimate the relative pose of frames whose stereo
+ * assumption fails and to chain point clouds along the flight.
+ *   grid          cells per side (1..64); each cell keeps its strongest
+ *                 corner (the paper divides the image into 30 x 30 cells).
+ *   margin        corners lie at least this far inside the frame
+ *                 (radius + 1 .. less than half the frame).
+ *   threshold25   25 R must exceed this (R = det M - 0.04 tr(M)^2).
+ *   radius        ZSSD patch radius r (1..8): (2r+1)^2 pixels.
+ *   search        ZSSD displacements in [-search, search]^2 (0..32).
+ */
+typedef struct {
+    int32_t grid, margin;
+    int64_t threshold25;
+    int32_t radius, search;
+} vs_pose_params;
+
+/* Workspace bytes of vs_harris_corners / vs_pose_estimate (0 if invalid):
+ * the W H int64 response map and the per-cell corners, matches and points. */
+size_t vs_pose_workspace_size(int W, int H, const vs_pose_params *p);
+
+/* Eq. 4 + Eq. 5 at every pixel of a W x H RGB frame (pitch bytes per row):
+ * A, B = central differences of the integer luma (77 R + 150 G + 29 B +
+ * 128) >> 8 with the frame edge repeated; M = the 5 x 5 binomial window
+ * ([1 4 6 4 1]^T [1 4 6 4 1], a discrete Gaussian; taps outside the frame
+ * skipped) of [A^2, AB; AB, B^2]; r25 (W H int64 out) = 25 R = 25 det M -
+ * tr(M)^2, exact.  Errors: VS_EINVAL, VS_ECUDA. */
+int vs_harris_response(const uint8_t *rgb, int W, int H, int pitch, int64_t *r25, void *stream);
+
+/* Section 3.2: corners (grid^2 x 2 int32 out, (x, y) per cell in row-major
+ * cell order, -1 where none): in cell (gx, gy) -- x in [gx W / grid, (gx+1) W
+ * / grid), y likewise -- the largest 25 R (the smaller raster index on ties)
+ * among pixels inside the margin, above the threshold, that beat each of
+ * their 8 neighbours in (R, then the smaller raster index).
+ * Errors: VS_EINVAL, VS_EWORKSPACE, VS_ECUDA. */
+int vs_harris_corners(const uint8_t *rgb, int W, int H, int pitch, const vs_pose_params *p, int32_t *corners,
+                      void *workspace, size_t ws_bytes, void *stream);
+
+/* Matches of n corners (n x 2 int32, -1 = none; n <= 4096) of frame 1 in
+ * frame 2 (both W x H RGB, same pitch): the displacement d in [-search,
+ * search]^2 with the (2r+1)^2 patch inside frame 2 minimising n Z = n sum D^2
+ * - (sum D)^2 (D = patch 1 - patch 2 in luma, exact int64; the first in
+ * raster order of (dy, dx) on ties), then on each axis the parabola through
+ * the costs at d - 1 and d + 1 where both exist: pos (n x 2 double out,
+ * NaN where none), cost (n int64 out, -1 where none).
+ * Errors: VS_EINVAL, VS_ECUDA. */
+int vs_zssd_match(const uint8_t *rgb1, const uint8_t *rgb2, int W, int H, int pitch, const int32_t *corners, int n,
+                  const vs_pose_params *p, double *pos, int64_t *cost, void *stream);
+
+/* Eq. 6 + Eq. 7 (EPnP, FP64): [R, T] with camera point = R P + T from world
+ * points (n x 3 double) and their pixels (n x 2 double) in a camera of
+ * intrinsics cam (fx, fy, cx, cy; no distortion); rows with a NaN are
+ * skipped; 6 <= usable points, n <= 4096.  The points as weighted sums of
+ * four control points (centroid and principal axes), the four smallest
+ * eigenvectors of the 12 x 12 normal matrix of Eq. 6, N = 1, 2, 3 of them
+ * refined by Gauss-Newton on the control-point distances, orthogonal
+ * Procrustes, the smallest mean reprojection error; then twice again on the
+ * points whose error is below max(2 px, 3 x the median) (the paper names no
+ * outlier step).  out (14 doubles, device): R row-major, T, the mean
+ * reprojection error of the inliers (px), the inlier count (NaN pose if
+ * fewer than 6 usable points).  Errors: VS_EINVAL, VS_ECUDA. */
+int vs_epnp(const double *points, const double *uv, int n, const vs_camera *cam, double *out, void *stream);
+
+/* The whole pose step: vs_harris_corners on frame 1, their 3D points read
+ * from xyz1 (frame 1's W x H x 3 float cloud, NaN where none, e.g. from
+ * vs_pair_run), vs_zssd_match in frame 2, vs_epnp: out as vs_epnp, the pose
+ * of camera 2 relative to camera 1 (camera-1 coordinates to camera-2
+ * coordinates).  Errors: VS_EINVAL, VS_EWORKSPACE, VS_ECUDA. */
+int vs_pose_estimate(const uint8_t *rgb1, const uint8_t *rgb2, const float *xyz1, int W, int H, int pitch,
+                     const vs_camera *cam, const vs_pose_params *p, double *out, void *workspace, size_t ws_bytes,
+                     void *stream);
+
 /* Name of a status code. */
 const char *vs_status_string(int status);
 

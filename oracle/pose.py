@@ -28,7 +28,8 @@ outside the frame are skipped); k = 0.04; a local maximum beats each of its
 order (dy, then dx), followed by a parabola through the costs of the two
 neighbouring displacements on each axis (sub-pixel position); EPnP keeps the
 solution of N = 1, 2 or 3 null-space vectors (each refined by Gauss-Newton)
-with the smallest reprojection error; at least 6 points (with 4 or 5 the
+with the smallest reprojection error, the equations of Eq. 6 taken in
+normalised image coordinates (divided by fx and fy); at least 6 points (with 4 or 5 the
 null space of the linear system has more than the 3 directions searched).
 """
 from __future__ import annotations
@@ -180,6 +181,11 @@ def _control_points(P: np.ndarray) -> np.ndarray:
     c0 = P.mean(axis=0)
     Q = P - c0
     lam, V = np.linalg.eigh(Q.T @ Q / len(P))
+    # each axis with its largest-magnitude component positive (a fixed choice of the
+    # eigenvectors' signs, so that the control points do not depend on the eigen-solver)
+    for k in range(3):
+        if V[np.argmax(np.abs(V[:, k])), k] < 0:
+            V[:, k] = -V[:, k]
     cw = [c0]
     for k in (2, 1, 0):
         cw.append(c0 + np.sqrt(max(lam[k], 0.0)) * V[:, k])
@@ -240,14 +246,17 @@ def epnp(P: np.ndarray, uv: np.ndarray, cam):
     fx, fy, cx, cy = cam
     cw = _control_points(P)
     alphas = _alphas(P, cw)
-    # Eq. 6: w_i [u_i, 1] = A sum_j alpha_ij c_j^c gives two equations per point
+    # Eq. 6: w_i [u_i, 1] = A sum_j alpha_ij c_j^c gives two equations per point; divided by
+    # fx and fy they read in normalised image coordinates (the same equations, a 12 x 12
+    # normal matrix of order 1 instead of fx^2, whose smallest eigenvectors come out accurate)
     n = len(P)
+    un, vn = (uv[:, 0] - cx) / fx, (uv[:, 1] - cy) / fy
     M = np.zeros((2 * n, 12))
     for j in range(4):
-        M[0::2, 3 * j + 0] = alphas[:, j] * fx
-        M[0::2, 3 * j + 2] = alphas[:, j] * (cx - uv[:, 0])
-        M[1::2, 3 * j + 1] = alphas[:, j] * fy
-        M[1::2, 3 * j + 2] = alphas[:, j] * (cy - uv[:, 1])
+        M[0::2, 3 * j + 0] = alphas[:, j]
+        M[0::2, 3 * j + 2] = -alphas[:, j] * un
+        M[1::2, 3 * j + 1] = alphas[:, j]
+        M[1::2, 3 * j + 2] = -alphas[:, j] * vn
     _, Vm = np.linalg.eigh(M.T @ M)
     V4 = Vm[:, :4]                            # the four smallest eigenvalues
     dw = np.array([np.sum((cw[i] - cw[j]) ** 2) for (i, j) in _PAIRS])

@@ -32,7 +32,8 @@ __all__ = [
     "Camera", "BPParams", "JBUParams", "PairConfig", "VSError", "lib", "library_path",
     "rectify_remap", "bp_workspace_size", "bp_stereo", "bp_export_messages",
     "guided_upsample", "reproject", "guided_upsample_reproject",
-    "pair_workspace_size", "pair_run", "pair_run_host", "pair_run_batch", "pair_batch_workspace_size", "kernel_launches", "status_string",
+    "pair_workspace_size", "pair_run", "pair_run_host", "PoseParams", "pose_workspace_size", "harris_response",
+    "harris_corners", "zssd_match", "epnp", "pose_estimate", "pair_run_batch", "pair_batch_workspace_size", "kernel_launches", "status_string",
     "profile_enable", "profile_collect", "Pipeline", "bp_stereo_batch", "bp_batch_workspace_size",
     "bp_autotune", "bp_autotune_reset", "bp_autotune_times", "bp_select_sweep", "bp_select_fused", "bp_autotune_plans", "bp_autotune_level_times", "bp_batch_mode", "SPParams", "sp_workspace_size", "sp_forward", "sp_backward",
     "smooth_bp", "SmoothBP", "sp_select_kernels", "sp_status",
@@ -83,6 +84,11 @@ class _PairConfig(ctypes.Structure):
                 ("baseline", ctypes.c_float), ("bp", _BPParams), ("jbu", _JBUParams)]
 
 
+class _PoseParams(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_int32), ("margin", ctypes.c_int32), ("threshold25", ctypes.c_int64),
+                ("radius", ctypes.c_int32), ("search", ctypes.c_int32)]
+
+
 class _PairJob(ctypes.Structure):
     _fields_ = [("cfg", _PairConfig), ("left", ctypes.c_void_p), ("right", ctypes.c_void_p),
                 ("disp", ctypes.c_void_p), ("xyz", ctypes.c_void_p)]
@@ -128,6 +134,21 @@ class SPParams:
 
     def c(self) -> _SPParams:
         return _SPParams(self.labels, self.iters, self.ckpt_every, self.lam, self.trunc, self.tau)
+
+
+@dataclass(frozen=True)
+class PoseParams:
+    """Pose path (Section 2.3): grid x grid cells of one corner each, corners
+    at least `margin` inside the frame with 25 R above `threshold25`, ZSSD
+    patches of radius `radius` searched over [-search, search]^2."""
+    grid: int = 30
+    margin: int = 16
+    threshold25: int = 0
+    radius: int = 5
+    search: int = 24
+
+    def c(self) -> _PoseParams:
+        return _PoseParams(self.grid, self.margin, self.threshold25, self.radius, self.search)
 
 
 @dataclass(frozen=True)
@@ -212,6 +233,12 @@ def _load(path: str) -> ctypes.CDLL:
         "vs_sp_select_kernels": ([I], I),
         "vs_sp_status": ([P, S, I, I, sp_p, P], I),
         "vs_check_report": ([P], I),
+        "vs_pose_workspace_size": ([I, I, ctypes.POINTER(_PoseParams)], S),
+        "vs_harris_response": ([P, I, I, I, P, P], I),
+        "vs_harris_corners": ([P, I, I, I, ctypes.POINTER(_PoseParams), P, P, S, P], I),
+        "vs_zssd_match": ([P, P, I, I, I, P, I, ctypes.POINTER(_PoseParams), P, P, P], I),
+        "vs_epnp": ([P, P, I, cam_p, P, P], I),
+        "vs_pose_estimate": ([P, P, P, I, I, I, cam_p, ctypes.POINTER(_PoseParams), P, P, S, P], I),
         "vs_check_test_shrink": ([ctypes.c_longlong], I),
     }
     for name, (args, res) in sig.items():
@@ -621,6 +648,85 @@ def pair_run_batch(jobs, workspace=None, stream=None):
     _check("vs_pair_run_batch", lib().vs_pair_run_batch(ctypes.cast(arr, ctypes.c_void_p), len(jobs),
                                                         workspace.data_ptr(), workspace.numel(), _stream(stream)))
     return workspace
+
+
+# ---------------------------------------------------------------------------
+# pose path (Section 2.3)
+
+
+def _rgb(t: torch.Tensor, name: str):
+    _dev(t, torch.uint8, name)
+    if t.dim() != 3 or t.shape[2] != 3 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous (H, W, 3) uint8 tensor")
+    return t.shape[0], t.shape[1]
+
+
+def pose_workspace_size(W: int, H: int, params: PoseParams) -> int:
+    p = params.c()
+    return int(lib().vs_pose_workspace_size(W, H, ctypes.byref(p)))
+
+
+def harris_response(rgb: torch.Tensor, stream=None) -> torch.Tensor:
+    """25 R of Eq. 5 at every pixel (int64 (H, W))."""
+    H, W = _rgb(rgb, "rgb")
+    out = torch.empty((H, W), dtype=torch.int64, device=rgb.device)
+    _check("vs_harris_response", lib().vs_harris_response(rgb.data_ptr(), W, H, 3 * W, out.data_ptr(),
+                                                          _stream(stream)))
+    return out
+
+
+def harris_corners(rgb: torch.Tensor, params: PoseParams, workspace=None, stream=None) -> torch.Tensor:
+    """(grid^2, 2) int32 corners, -1 where a cell has none."""
+    H, W = _rgb(rgb, "rgb")
+    p = params.c()
+    if workspace is None:
+        workspace = torch.empty(pose_workspace_size(W, H, params), dtype=torch.uint8, device=rgb.device)
+    out = torch.empty((params.grid * params.grid, 2), dtype=torch.int32, device=rgb.device)
+    _check("vs_harris_corners", lib().vs_harris_corners(rgb.data_ptr(), W, H, 3 * W, ctypes.byref(p), out.data_ptr(),
+                                                        workspace.data_ptr(), workspace.numel(), _stream(stream)))
+    return out
+
+
+def zssd_match(rgb1: torch.Tensor, rgb2: torch.Tensor, corners: torch.Tensor, params: PoseParams, stream=None):
+    """(pos (n, 2) float64, cost (n,) int64) of the corners of frame 1 in frame 2."""
+    H, W = _rgb(rgb1, "rgb1")
+    _rgb(rgb2, "rgb2")
+    corners = corners.to(torch.int32).contiguous()
+    n = corners.shape[0]
+    p = params.c()
+    pos = torch.empty((n, 2), dtype=torch.float64, device=rgb1.device)
+    cost = torch.empty((n,), dtype=torch.int64, device=rgb1.device)
+    _check("vs_zssd_match", lib().vs_zssd_match(rgb1.data_ptr(), rgb2.data_ptr(), W, H, 3 * W, corners.data_ptr(), n,
+                                                ctypes.byref(p), pos.data_ptr(), cost.data_ptr(), _stream(stream)))
+    return pos, cost
+
+
+def epnp(points: torch.Tensor, uv: torch.Tensor, cam: Camera, stream=None) -> torch.Tensor:
+    """(14,) float64: R (row-major), T, mean reprojection error, inlier count."""
+    points = points.to(torch.float64).contiguous()
+    uv = uv.to(torch.float64).contiguous()
+    out = torch.empty(14, dtype=torch.float64, device=points.device)
+    c = cam.c()
+    _check("vs_epnp", lib().vs_epnp(points.data_ptr(), uv.data_ptr(), points.shape[0], ctypes.byref(c),
+                                    out.data_ptr(), _stream(stream)))
+    return out
+
+
+def pose_estimate(rgb1: torch.Tensor, rgb2: torch.Tensor, xyz1: torch.Tensor, cam: Camera, params: PoseParams,
+                  workspace=None, stream=None) -> torch.Tensor:
+    """Pose of camera 2 relative to camera 1 from frame 1's cloud: (14,) as :func:`epnp`."""
+    H, W = _rgb(rgb1, "rgb1")
+    _rgb(rgb2, "rgb2")
+    if tuple(xyz1.shape) != (H, W, 3) or xyz1.dtype != torch.float32 or not xyz1.is_contiguous():
+        raise ValueError("xyz1 must be a contiguous (H, W, 3) float32 tensor")
+    if workspace is None:
+        workspace = torch.empty(pose_workspace_size(W, H, params), dtype=torch.uint8, device=rgb1.device)
+    out = torch.empty(14, dtype=torch.float64, device=rgb1.device)
+    c, p = cam.c(), params.c()
+    _check("vs_pose_estimate", lib().vs_pose_estimate(rgb1.data_ptr(), rgb2.data_ptr(), xyz1.data_ptr(), W, H, 3 * W,
+                                                      ctypes.byref(c), ctypes.byref(p), out.data_ptr(),
+                                                      workspace.data_ptr(), workspace.numel(), _stream(stream)))
+    return out
 
 
 def pair_run_host(cfg: PairConfig, left_host: torch.Tensor, right_host: torch.Tensor, xyz_host: torch.Tensor,

@@ -1,0 +1,1098 @@
+// Pose path of Section 2.3 (Eq. 4-7): Harris corners, ZSSD matching, EPnP.
+//
+// k_harris_r25   Eq. 4 + Eq. 5 at every pixel: the integer luma of the RGB
+//                frame, central differences A, B (frame edge repeated), the
+//                products windowed by the 5 x 5 binomial [1 4 6 4 1]^T [1 4 6
+//                4 1] (taps outside the frame skipped), 25 R = 25 det M -
+//                tr(M)^2 (k = 0.04) -- exact int64, tiles staged in shared
+//                memory, the window applied as two 1-D passes.
+// k_harris_cells one CTA per cell of the grid (Section 3.2): the candidates
+//                (inside the margin, 25 R above the threshold, beating each
+//                of their 8 neighbours in (R, then the smaller raster index))
+//                reduced to the cell's largest (R, smaller index).
+// k_zssd         one CTA per corner: the patch and frame 2's search region
+//                in shared memory, one displacement per thread at a time,
+//                n Z = n sum D^2 - (sum D)^2 exact in int64, the first
+//                smallest in raster order of (dy, dx), then the parabola
+//                through the two neighbouring costs on each axis (FP64).
+// k_epnp         one CTA, FP64: the points as weighted sums of four control
+//                points (centroid and principal axes), the 12 x 12 normal
+//                matrix of Eq. 6 (in normalised image coordinates: each
+//                equation divided by fx or fy) and its four smallest eigenvectors (cyclic
+//                Jacobi), the control points' camera coordinates from N = 1,
+//                2, 3 of them (distance constraints, then Gauss-Newton on all
+//                four), [R, T] by orthogonal Procrustes (Eq. 7), the best
+//                reprojection error; then twice more on the points whose
+//                error is below max(2 px, 3 x the median).
+#include "vs_common.cuh"
+
+#include <math.h>
+
+namespace vs {
+namespace {
+
+constexpr int kHarrisTx = 32, kHarrisTy = 8;   // output tile
+constexpr int kHalo = 3;                       // window 2 + derivative 1
+constexpr int kMaxGrid = 64;
+constexpr int kMaxRadius = 8, kMaxSearch = 32;
+constexpr int kMaxPts = 4096;
+constexpr int kEpnpThreads = 256;
+
+__device__ __forceinline__ int luma(const uint8_t *p)
+{
+    return (77 * (int)p[0] + 150 * (int)p[1] + 29 * (int)p[2] + 128) >> 8;
+}
+
+// ---------------------------------------------------------------------------
+// Harris
+
+struct HarrisArgs {
+    const uint8_t *rgb;
+    int W, H, pitch;
+    int64_t *r25;
+};
+
+__global__ void __launch_bounds__(kHarrisTx * kHarrisTy) k_harris_r25(HarrisArgs a)
+{
+    pdl_begin();
+    constexpr int GW = kHarrisTx + 2 * kHalo, GH = kHarrisTy + 2 * kHalo;   // grey tile
+    constexpr int PW = kHarrisTx + 4, PH = kHarrisTy + 4;                   // products (window halo 2)
+    __shared__ int g[GH][GW];
+    __shared__ int pxx[PH][PW], pyy[PH][PW], pxy[PH][PW];
+    __shared__ int hxx[PH][kHarrisTx], hyy[PH][kHarrisTx], hxy[PH][kHarrisTx];
+    const int x0 = blockIdx.x * kHarrisTx, y0 = blockIdx.y * kHarrisTy;
+    const int tid = threadIdx.y * kHarrisTx + threadIdx.x, nt = kHarrisTx * kHarrisTy;
+    // grey with the frame edge repeated (what the central differences read)
+    for (int i = tid; i < GW * GH; i += nt) {
+        const int ty = i / GW, tx = i - ty * GW;
+        const int x = min(max(x0 - kHalo + tx, 0), a.W - 1), y = min(max(y0 - kHalo + ty, 0), a.H - 1);
+        g[ty][tx] = luma(a.rgb + (size_t)y * a.pitch + 3 * (size_t)x);
+    }
+    __syncthreads();
+    // products of the derivatives; 0 outside the frame (skipped window taps)
+    for (int i = tid; i < PW * PH; i += nt) {
+        const int ty = i / PW, tx = i - ty * PW;
+        const int x = x0 - 2 + tx, y = y0 - 2 + ty;
+        int A = 0, B = 0;
+        if (x >= 0 && x < a.W && y >= 0 && y < a.H) {
+            A = g[ty + 1][tx + 2] - g[ty + 1][tx];
+            B = g[ty + 2][tx + 1] - g[ty][tx + 1];
+        }
+        pxx[ty][tx] = A * A;
+        pyy[ty][tx] = B * B;
+        pxy[ty][tx] = A * B;
+    }
+    __syncthreads();
+    // window, horizontal pass
+    const int b[5] = {1, 4, 6, 4, 1};
+    for (int i = tid; i < PH * kHarrisTx; i += nt) {
+        const int ty = i / kHarrisTx, tx = i - ty * kHarrisTx;
+        int sxx = 0, syy = 0, sxy = 0;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            sxx += b[j] * pxx[ty][tx + j];
+            syy += b[j] * pyy[ty][tx + j];
+            sxy += b[j] * pxy[ty][tx + j];
+        }
+        hxx[ty][tx] = sxx;
+        hyy[ty][tx] = syy;
+        hxy[ty][tx] = sxy;
+    }
+    __syncthreads();
+    // vertical pass and the response
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x = x0 + tx, y = y0 + ty;
+    if (x >= a.W || y >= a.H)
+        return;
+    long long sxx = 0, syy = 0, sxy = 0;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        sxx += b[i] * hxx[ty + i][tx];
+        syy += b[i] * hyy[ty + i][tx];
+        sxy += b[i] * hxy[ty + i][tx];
+    }
+    const long long tr = sxx + syy;
+    a.r25[(size_t)y * a.W + x] = 25 * (sxx * syy - sxy * sxy) - tr * tr;
+}
+
+struct CellArgs {
+    const int64_t *r25;
+    int W, H, grid, margin;
+    long long thr;
+    int32_t *corners;   // grid^2 x 2
+};
+
+// (R, index) pairs: larger R wins, then the smaller index
+__device__ __forceinline__ bool beats(long long ra, long long ia, long long rb, long long ib)
+{
+    return ra > rb || (ra == rb && ia < ib);
+}
+
+__global__ void __launch_bounds__(256) k_harris_cells(CellArgs a)
+{
+    pdl_begin();
+    const int gx = blockIdx.x % a.grid, gy = blockIdx.x / a.grid;
+    const int x0 = (int)((long long)gx * a.W / a.grid), x1 = (int)((long long)(gx + 1) * a.W / a.grid);
+    const int y0 = (int)((long long)gy * a.H / a.grid), y1 = (int)((long long)(gy + 1) * a.H / a.grid);
+    const int cw = x1 - x0, n = cw * (y1 - y0);
+    long long best_r = LLONG_MIN, best_i = -1;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int y = y0 + k / cw, x = x0 + k % cw;
+        if (x < a.margin || x >= a.W - a.margin || y < a.margin || y >= a.H - a.margin)
+            continue;
+        const long long r = a.r25[(size_t)y * a.W + x];
+        if (r <= a.thr)
+            continue;
+        const long long idx = (long long)y * a.W + x;
+        bool is_max = true;
+        for (int dy = -1; dy <= 1 && is_max; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                if ((dx == 0 && dy == 0) || x + dx < 0 || x + dx >= a.W || y + dy < 0 || y + dy >= a.H)
+                    continue;
+                const long long q = (long long)(y + dy) * a.W + x + dx;
+                if (beats(a.r25[q], q, r, idx)) {
+                    is_max = false;
+                    break;
+                }
+            }
+        if (is_max && (best_i < 0 || beats(r, idx, best_r, best_i))) {
+            best_r = r;
+            best_i = idx;
+        }
+    }
+    __shared__ long long sr[256], si[256];
+    sr[threadIdx.x] = best_r;
+    si[threadIdx.x] = best_i;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            const long long ri = sr[threadIdx.x + o], ii = si[threadIdx.x + o];
+            if (ii >= 0 && (si[threadIdx.x] < 0 || beats(ri, ii, sr[threadIdx.x], si[threadIdx.x]))) {
+                sr[threadIdx.x] = ri;
+                si[threadIdx.x] = ii;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const long long i = si[0];
+        a.corners[2 * blockIdx.x] = i < 0 ? -1 : (int32_t)(i % a.W);
+        a.corners[2 * blockIdx.x + 1] = i < 0 ? -1 : (int32_t)(i / a.W);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// ZSSD
+
+struct ZssdArgs {
+    const uint8_t *rgb1, *rgb2;
+    int W, H, pitch, r, S;
+    const int32_t *corners;
+    double *pos;      // n x 2
+    int64_t *cost;    // n
+};
+
+__global__ void __launch_bounds__(256) k_zssd(ZssdArgs a)
+{
+    pdl_begin();
+    constexpr int kMaxP = 2 * kMaxRadius + 1, kMaxReg = 2 * (kMaxSearch + kMaxRadius) + 1;
+    __shared__ int p1[kMaxP * kMaxP];
+    __shared__ int reg[kMaxReg * kMaxReg];     // frame 2 around the corner, -1 outside the frame
+    __shared__ long long sz[256];
+    __shared__ int sk[256];
+    const int ci = blockIdx.x;
+    const int x = a.corners[2 * ci], y = a.corners[2 * ci + 1];
+    const int r = a.r, S = a.S, P = 2 * r + 1, RG = 2 * (S + r) + 1, ND = (2 * S + 1) * (2 * S + 1);
+    const bool ok = x >= r && x < a.W - r && y >= r && y < a.H - r;
+    if (!ok) {   // no corner, or its patch leaves frame 1
+        if (threadIdx.x == 0) {
+            a.pos[2 * ci] = a.pos[2 * ci + 1] = __longlong_as_double(0x7FF8000000000000LL);
+            a.cost[ci] = -1;
+        }
+        return;
+    }
+    for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
+        const int py = i / P, px = i - py * P;
+        p1[i] = luma(a.rgb1 + (size_t)(y - r + py) * a.pitch + 3 * (size_t)(x - r + px));
+    }
+    for (int i = threadIdx.x; i < RG * RG; i += blockDim.x) {
+        const int ry = i / RG, rx = i - ry * RG;
+        const int xx = x - S - r + rx, yy = y - S - r + ry;
+        reg[i] = (xx >= 0 && xx < a.W && yy >= 0 && yy < a.H) ? luma(a.rgb2 + (size_t)yy * a.pitch + 3 * (size_t)xx)
+                                                             : -1;
+    }
+    __syncthreads();
+    const long long npx = (long long)P * P;
+    auto zcost = [&](int dx, int dy) -> long long {   // -1 where the patch leaves frame 2
+        const int xx = x + dx, yy = y + dy;
+        if (xx < r || xx >= a.W - r || yy < r || yy >= a.H - r)
+            return -1;
+        long long s2 = 0, s1 = 0;
+        for (int py = 0; py < P; ++py) {
+            const int *row = reg + (dy + S + py) * RG + (dx + S);
+            const int *q = p1 + py * P;
+            for (int px = 0; px < P; ++px) {
+                const int d = q[px] - row[px];
+                s2 += d * d;
+                s1 += d;
+            }
+        }
+        return npx * s2 - s1 * s1;
+    };
+    long long best = -1;
+    int bk = ND;
+    for (int k = threadIdx.x; k < ND; k += blockDim.x) {
+        const int dy = k / (2 * S + 1) - S, dx = k % (2 * S + 1) - S;
+        const long long z = zcost(dx, dy);
+        if (z >= 0 && (best < 0 || z < best)) {   // k rises within a thread: the first smallest
+            best = z;
+            bk = k;
+        }
+    }
+    sz[threadIdx.x] = best;
+    sk[threadIdx.x] = bk;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            const long long zo = sz[threadIdx.x + o];
+            const int ko = sk[threadIdx.x + o];
+            const long long zm = sz[threadIdx.x];
+            if (zo >= 0 && (zm < 0 || zo < zm || (zo == zm && ko < sk[threadIdx.x]))) {
+                sz[threadIdx.x] = zo;
+                sk[threadIdx.x] = ko;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0)
+        return;
+    if (sz[0] < 0) {
+        a.pos[2 * ci] = a.pos[2 * ci + 1] = __longlong_as_double(0x7FF8000000000000LL);
+        a.cost[ci] = -1;
+        return;
+    }
+    const int k = sk[0];
+    const int by = k / (2 * S + 1) - S, bx = k % (2 * S + 1) - S;
+    const long long c0 = sz[0];
+    double off[2] = {0.0, 0.0};
+    for (int axis = 0; axis < 2; ++axis) {
+        const int ex = axis == 0 ? 1 : 0, ey = axis == 0 ? 0 : 1;
+        const int mx = bx - ex, my = by - ey, qx = bx + ex, qy = by + ey;
+        if (mx < -S || my < -S || qx > S || qy > S)
+            continue;
+        const long long cm = zcost(mx, my), cp = zcost(qx, qy);
+        if (cm < 0 || cp < 0)
+            continue;
+        const long long den = cm - 2 * c0 + cp;
+        if (den > 0)
+            off[axis] = (double)(cm - cp) / (2.0 * (double)den);
+    }
+    a.pos[2 * ci] = (double)(x + bx) + off[0];
+    a.pos[2 * ci + 1] = (double)(y + by) + off[1];
+    a.cost[ci] = c0;
+}
+
+// ---------------------------------------------------------------------------
+// EPnP, FP64, one CTA
+
+// Cyclic Jacobi: A (n x n, row-major, symmetric) is diagonalised in place,
+// V receives the eigenvectors as columns; then both are sorted by eigenvalue,
+// ascending.  One thread.
+__device__ void jacobi_eigen(double *A, double *V, double *ev, int n)
+{
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            V[i * n + j] = i == j ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0, diag = 0.0;
+        for (int p = 0; p < n; ++p) {
+            diag += A[p * n + p] * A[p * n + p];
+            for (int q = p + 1; q < n; ++q)
+                off += A[p * n + q] * A[p * n + q];
+        }
+        if (off <= 1e-30 * diag || off == 0.0)
+            break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[p * n + q];
+                if (apq == 0.0)
+                    continue;
+                const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {   // columns p, q
+                    const double akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - s * akq;
+                    A[k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {   // rows p, q
+                    const double apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - s * aqk;
+                    A[q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double vkp = V[k * n + p], vkq = V[k * n + q];
+                    V[k * n + p] = c * vkp - s * vkq;
+                    V[k * n + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    for (int i = 0; i < n; ++i)
+        ev[i] = A[i * n + i];
+    for (int i = 0; i < n; ++i) {   // selection sort, ascending
+        int m = i;
+        for (int j = i + 1; j < n; ++j)
+            if (ev[j] < ev[m])
+                m = j;
+        if (m != i) {
+            const double t = ev[i];
+            ev[i] = ev[m];
+            ev[m] = t;
+            for (int k = 0; k < n; ++k) {
+                const double v = V[k * n + i];
+                V[k * n + i] = V[k * n + m];
+                V[k * n + m] = v;
+            }
+        }
+    }
+}
+
+// Solves the symmetric positive semi-definite system (A^T A) x = A^T b of a
+// least-squares problem given as the normal matrix N (m x m) and right side
+// g, by Gaussian elimination with partial pivoting; one thread.
+__device__ void solve_small(double *N, double *g, double *x, int m)
+{
+    for (int c = 0; c < m; ++c) {
+        int p = c;
+        for (int r = c + 1; r < m; ++r)
+            if (fabs(N[r * m + c]) > fabs(N[p * m + c]))
+                p = r;
+        if (p != c) {
+            for (int k = 0; k < m; ++k) {
+                const double t = N[c * m + k];
+                N[c * m + k] = N[p * m + k];
+                N[p * m + k] = t;
+            }
+            const double t = g[c];
+            g[c] = g[p];
+            g[p] = t;
+        }
+        const double d = N[c * m + c];
+        if (fabs(d) < 1e-300)
+            continue;
+        for (int r = c + 1; r < m; ++r) {
+            const double f = N[r * m + c] / d;
+            for (int k = c; k < m; ++k)
+                N[r * m + k] -= f * N[c * m + k];
+            g[r] -= f * g[c];
+        }
+    }
+    for (int c = m - 1; c >= 0; --c) {
+        double s = g[c];
+        for (int k = c + 1; k < m; ++k)
+            s -= N[c * m + k] * x[k];
+        x[c] = fabs(N[c * m + c]) < 1e-300 ? 0.0 : s / N[c * m + c];
+    }
+}
+
+struct EpnpArgs {
+    const double *P;    // n x 3 world points
+    const double *uv;   // n x 2 pixels
+    int n;
+    double fx, fy, cx, cy;
+    double *out;        // R (9, row-major), T (3), mean error of the inliers, inlier count
+};
+
+__constant__ int kPairI[6] = {0, 0, 0, 1, 1, 2};
+__constant__ int kPairJ[6] = {1, 2, 3, 2, 3, 3};
+
+// Block-wide sum of `k` per-thread values (k <= 80): red holds k x blockDim doubles.
+__device__ void block_sum(double *vals, int k, double *red)
+{
+    const int t = threadIdx.x, nt = blockDim.x;
+    for (int i = 0; i < k; ++i)
+        red[i * nt + t] = vals[i];
+    __syncthreads();
+    for (int o = nt / 2; o > 0; o >>= 1) {
+        if (t < o)
+            for (int i = 0; i < k; ++i)
+                red[i * nt + t] += red[i * nt + t + o];
+        __syncthreads();
+    }
+    for (int i = 0; i < k; ++i)
+        vals[i] = red[i * nt];
+    __syncthreads();
+}
+
+struct EpnpShared {
+    double cw[4][3];       // world control points
+    double Cinv[3][3];     // inverse of [c1 - c0, c2 - c0, c3 - c0]
+    double V4[12][4];      // the four null-space directions
+    double dw[6];          // squared control-point distances
+    double R[9], T[3], err;
+    double bestR[9], bestT[3], besterr;
+    double scratch[144 + 144 + 12];
+    int ninl;
+};
+
+// Pose of the current betas: control points and points in the camera frame,
+// orthogonal Procrustes, mean reprojection error -- all threads.
+__device__ void pose_from_betas(const EpnpArgs &a, const unsigned char *inl, const double *betas, EpnpShared &sh,
+                                double *red)
+{
+    double cc[12];
+    for (int r = 0; r < 12; ++r)
+        cc[r] = betas[0] * sh.V4[r][0] + betas[1] * sh.V4[r][1] + betas[2] * sh.V4[r][2] + betas[3] * sh.V4[r][3];
+    // the sign: most points in front of the camera
+    double v[16];
+    v[0] = 0.0;
+    for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+        if (!inl[i])
+            continue;
+        double al[4];
+        const double d[3] = {a.P[3 * i] - sh.cw[0][0], a.P[3 * i + 1] - sh.cw[0][1], a.P[3 * i + 2] - sh.cw[0][2]};
+        for (int k = 0; k < 3; ++k)
+            al[k + 1] = sh.Cinv[k][0] * d[0] + sh.Cinv[k][1] * d[1] + sh.Cinv[k][2] * d[2];
+        al[0] = 1.0 - al[1] - al[2] - al[3];
+        const double z = al[0] * cc[2] + al[1] * cc[5] + al[2] * cc[8] + al[3] * cc[11];
+        v[0] += z < 0.0 ? 1.0 : -1.0;
+    }
+    block_sum(v, 1, red);
+    const double sgn = v[0] > 0.0 ? -1.0 : 1.0;   // more negative than positive depths: flip
+    for (int r = 0; r < 12; ++r)
+        cc[r] *= sgn;
+    // centroids and the cross-covariance of camera and world points
+    for (int k = 0; k < 16; ++k)
+        v[k] = 0.0;
+    for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+        if (!inl[i])
+            continue;
+        double al[4];
+        const double d[3] = {a.P[3 * i] - sh.cw[0][0], a.P[3 * i + 1] - sh.cw[0][1], a.P[3 * i + 2] - sh.cw[0][2]};
+        for (int k = 0; k < 3; ++k)
+            al[k + 1] = sh.Cinv[k][0] * d[0] + sh.Cinv[k][1] * d[1] + sh.Cinv[k][2] * d[2];
+        al[0] = 1.0 - al[1] - al[2] - al[3];
+        double pc[3];
+        for (int c = 0; c < 3; ++c)
+            pc[c] = al[0] * cc[c] + al[1] * cc[3 + c] + al[2] * cc[6 + c] + al[3] * cc[9 + c];
+        const double *pw = a.P + 3 * i;
+        for (int c = 0; c < 3; ++c) {
+            v[c] += pc[c];
+            v[3 + c] += pw[c];
+        }
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c)
+                v[6 + 3 * r + c] += pc[r] * pw[c];
+        v[15] += 1.0;
+    }
+    block_sum(v, 16, red);
+    if (threadIdx.x == 0) {
+        const double m = v[15];
+        double mc[3], mw[3], H[9];
+        for (int c = 0; c < 3; ++c) {
+            mc[c] = v[c] / m;
+            mw[c] = v[3 + c] / m;
+        }
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c)
+                H[3 * r + c] = v[6 + 3 * r + c] - m * mc[r] * mw[c];
+        // H = U S V^T: V from the eigenvectors of H^T H, U = H V / s, R = U D V^T
+        double HtH[9], Vv[9], ev[3];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c)
+                HtH[3 * r + c] = H[r] * H[c] + H[3 + r] * H[3 + c] + H[6 + r] * H[6 + c];
+        jacobi_eigen(HtH, Vv, ev, 3);
+        // descending singular values: columns 2, 1, 0 of Vv
+        double Vd[9], U[9];
+        for (int k = 0; k < 3; ++k)
+            for (int r = 0; r < 3; ++r)
+                Vd[3 * r + k] = Vv[3 * r + (2 - k)];
+        for (int k = 0; k < 2; ++k) {
+            double u[3], nrm = 0.0;
+            for (int r = 0; r < 3; ++r) {
+                u[r] = H[3 * r] * Vd[k] + H[3 * r + 1] * Vd[3 + k] + H[3 * r + 2] * Vd[6 + k];
+            }
+            for (int j = 0; j < k; ++j) {   // Gram-Schmidt against the earlier columns
+                const double d = u[0] * U[j] + u[1] * U[3 + j] + u[2] * U[6 + j];
+                for (int r = 0; r < 3; ++r)
+                    u[r] -= d * U[3 * r + j];
+            }
+            for (int r = 0; r < 3; ++r)
+                nrm += u[r] * u[r];
+            nrm = sqrt(nrm);
+            for (int r = 0; r < 3; ++r)
+                U[3 * r + k] = nrm > 0.0 ? u[r] / nrm : (r == k ? 1.0 : 0.0);
+        }
+        // third column: the cross product (a right-handed U), then the determinant of U V^T
+        U[2] = U[3] * U[7] - U[6] * U[4];
+        U[5] = U[6] * U[1] - U[0] * U[7];
+        U[8] = U[0] * U[4] - U[3] * U[1];
+        const double detV = Vd[0] * (Vd[4] * Vd[8] - Vd[5] * Vd[7]) - Vd[1] * (Vd[3] * Vd[8] - Vd[5] * Vd[6]) +
+                            Vd[2] * (Vd[3] * Vd[7] - Vd[4] * Vd[6]);
+        // U right-handed: det(U V^T) = det V; the reflection fix flips the last singular pair
+        const double dl = detV >= 0.0 ? 1.0 : -1.0;
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c)
+                sh.R[3 * r + c] = U[3 * r] * Vd[3 * c] + U[3 * r + 1] * Vd[3 * c + 1] + dl * U[3 * r + 2] * Vd[3 * c + 2];
+        for (int r = 0; r < 3; ++r)
+            sh.T[r] = mc[r] - (sh.R[3 * r] * mw[0] + sh.R[3 * r + 1] * mw[1] + sh.R[3 * r + 2] * mw[2]);
+    }
+    __syncthreads();
+    // mean reprojection error
+    v[0] = 0.0;
+    v[1] = 0.0;
+    for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+        if (!inl[i])
+            continue;
+        const double *pw = a.P + 3 * i;
+        double pc[3];
+        for (int r = 0; r < 3; ++r)
+            pc[r] = sh.R[3 * r] * pw[0] + sh.R[3 * r + 1] * pw[1] + sh.R[3 * r + 2] * pw[2] + sh.T[r];
+        const double du = a.fx * pc[0] / pc[2] + a.cx - a.uv[2 * i], dv = a.fy * pc[1] / pc[2] + a.cy - a.uv[2 * i + 1];
+        v[0] += sqrt(du * du + dv * dv);
+        v[1] += 1.0;
+    }
+    block_sum(v, 2, red);
+    if (threadIdx.x == 0)
+        sh.err = v[0] / v[1];
+    __syncthreads();
+}
+
+// Gauss-Newton on the four betas: the six squared control-point distances.
+__device__ void gauss_newton(double *b, const EpnpShared &sh)
+{
+    for (int it = 0; it < 5; ++it) {
+        double N[16] = {0}, g[4] = {0};
+        for (int p = 0; p < 6; ++p) {
+            const int i = kPairI[p], j = kPairJ[p];
+            double vd[4][3], d[3];
+            for (int k = 0; k < 4; ++k)
+                for (int c = 0; c < 3; ++c)
+                    vd[k][c] = sh.V4[3 * i + c][k] - sh.V4[3 * j + c][k];
+            for (int c = 0; c < 3; ++c)
+                d[c] = b[0] * vd[0][c] + b[1] * vd[1][c] + b[2] * vd[2][c] + b[3] * vd[3][c];
+            const double res = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] - sh.dw[p];
+            double J[4];
+            for (int k = 0; k < 4; ++k)
+                J[k] = 2.0 * (d[0] * vd[k][0] + d[1] * vd[k][1] + d[2] * vd[k][2]);
+            for (int r = 0; r < 4; ++r) {
+                for (int c = 0; c < 4; ++c)
+                    N[4 * r + c] += J[r] * J[c];
+                g[r] -= J[r] * res;
+            }
+        }
+        double step[4];
+        solve_small(N, g, step, 4);
+        for (int k = 0; k < 4; ++k)
+            b[k] += step[k];
+    }
+}
+
+// One EPnP solve on the points marked in `inl` (all threads).
+__device__ void epnp_solve(const EpnpArgs &a, const unsigned char *inl, EpnpShared &sh, double *red)
+{
+    double v[80];
+    // centroid and covariance
+    for (int k = 0; k < 4; ++k)
+        v[k] = 0.0;
+    for (int i = threadIdx.x; i < a.n; i += blockDim.x)
+        if (inl[i]) {
+            v[0] += a.P[3 * i];
+            v[1] += a.P[3 * i + 1];
+            v[2] += a.P[3 * i + 2];
+            v[3] += 1.0;
+        }
+    block_sum(v, 4, red);
+    const double m = v[3];
+    const double c0[3] = {v[0] / m, v[1] / m, v[2] / m};
+    for (int k = 0; k < 6; ++k)
+        v[k] = 0.0;
+    for (int i = threadIdx.x; i < a.n; i += blockDim.x)
+        if (inl[i]) {
+            const double d[3] = {a.P[3 * i] - c0[0], a.P[3 * i + 1] - c0[1], a.P[3 * i + 2] - c0[2]};
+            v[0] += d[0] * d[0];
+            v[1] += d[0] * d[1];
+            v[2] += d[0] * d[2];
+            v[3] += d[1] * d[1];
+            v[4] += d[1] * d[2];
+            v[5] += d[2] * d[2];
+        }
+    block_sum(v, 6, red);
+    if (threadIdx.x == 0) {
+        double C[9] = {v[0] / m, v[1] / m, v[2] / m, v[1] / m, v[3] / m, v[4] / m, v[2] / m, v[4] / m, v[5] / m};
+        double Vv[9], ev[3];
+        jacobi_eigen(C, Vv, ev, 3);
+        // each axis with its largest-magnitude component positive (the control
+        // points must not depend on the eigen-solver's choice of signs)
+        for (int k = 0; k < 3; ++k) {
+            int m = 0;
+            for (int r = 1; r < 3; ++r)
+                if (fabs(Vv[3 * r + k]) > fabs(Vv[3 * m + k]))
+                    m = r;
+            if (Vv[3 * m + k] < 0.0)
+                for (int r = 0; r < 3; ++r)
+                    Vv[3 * r + k] = -Vv[3 * r + k];
+        }
+        for (int c = 0; c < 3; ++c)
+            sh.cw[0][c] = c0[c];
+        for (int k = 0; k < 3; ++k) {   // largest variance first
+            const double s = sqrt(fmax(ev[2 - k], 0.0));
+            for (int c = 0; c < 3; ++c)
+                sh.cw[k + 1][c] = c0[c] + s * Vv[3 * c + (2 - k)];
+        }
+        // inverse of the 3 x 3 matrix of control-point offsets (columns)
+        double Cm[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int k = 0; k < 3; ++k)
+                Cm[r][k] = sh.cw[k + 1][r] - sh.cw[0][r];
+        const double det = Cm[0][0] * (Cm[1][1] * Cm[2][2] - Cm[1][2] * Cm[2][1]) -
+                           Cm[0][1] * (Cm[1][0] * Cm[2][2] - Cm[1][2] * Cm[2][0]) +
+                           Cm[0][2] * (Cm[1][0] * Cm[2][1] - Cm[1][1] * Cm[2][0]);
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                const int r1 = (c + 1) % 3, r2 = (c + 2) % 3, c1 = (r + 1) % 3, c2 = (r + 2) % 3;
+                sh.Cinv[r][c] = (Cm[r1][c1] * Cm[r2][c2] - Cm[r1][c2] * Cm[r2][c1]) / det;
+            }
+        for (int p = 0; p < 6; ++p) {
+            const int i = kPairI[p], j = kPairJ[p];
+            double d2 = 0.0;
+            for (int c = 0; c < 3; ++c)
+                d2 += (sh.cw[i][c] - sh.cw[j][c]) * (sh.cw[i][c] - sh.cw[j][c]);
+            sh.dw[p] = d2;
+        }
+    }
+    __syncthreads();
+    // the 12 x 12 normal matrix of Eq. 6 (upper triangle, 78 entries)
+    for (int k = 0; k < 78; ++k)
+        v[k] = 0.0;
+    for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+        if (!inl[i])
+            continue;
+        double al[4];
+        const double d[3] = {a.P[3 * i] - sh.cw[0][0], a.P[3 * i + 1] - sh.cw[0][1], a.P[3 * i + 2] - sh.cw[0][2]};
+        for (int k = 0; k < 3; ++k)
+            al[k + 1] = sh.Cinv[k][0] * d[0] + sh.Cinv[k][1] * d[1] + sh.Cinv[k][2] * d[2];
+        al[0] = 1.0 - al[1] - al[2] - al[3];
+        // the two equations of Eq. 6 divided by fx and fy (normalised image coordinates)
+        const double un = (a.uv[2 * i] - a.cx) / a.fx, vn = (a.uv[2 * i + 1] - a.cy) / a.fy;
+        double r1[12], r2[12];
+        for (int j = 0; j < 4; ++j) {
+            r1[3 * j] = al[j];
+            r1[3 * j + 1] = 0.0;
+            r1[3 * j + 2] = -al[j] * un;
+            r2[3 * j] = 0.0;
+            r2[3 * j + 1] = al[j];
+            r2[3 * j + 2] = -al[j] * vn;
+        }
+        int t = 0;
+        for (int r = 0; r < 12; ++r)
+            for (int c = r; c < 12; ++c)
+                v[t++] += r1[r] * r1[c] + r2[r] * r2[c];
+    }
+    block_sum(v, 78, red);
+    if (threadIdx.x == 0) {
+        double *MtM = sh.scratch, *Vm = sh.scratch + 144, *ev = sh.scratch + 288;
+        int t = 0;
+        for (int r = 0; r < 12; ++r)
+            for (int c = r; c < 12; ++c) {
+                MtM[12 * r + c] = v[t];
+                MtM[12 * c + r] = v[t];
+                ++t;
+            }
+        jacobi_eigen(MtM, Vm, ev, 12);
+        for (int r = 0; r < 12; ++r)
+            for (int k = 0; k < 4; ++k)
+                sh.V4[r][k] = Vm[12 * r + k];
+        sh.besterr = 1e300;
+    }
+    __syncthreads();
+    for (int cand = 0; cand < 3; ++cand) {
+        __shared__ double betas[4];
+        if (threadIdx.x == 0) {
+            double vd[4][6][3];
+            for (int k = 0; k < 4; ++k)
+                for (int p = 0; p < 6; ++p)
+                    for (int c = 0; c < 3; ++c)
+                        vd[k][p][c] = sh.V4[3 * kPairI[p] + c][k] - sh.V4[3 * kPairJ[p] + c][k];
+            auto dot = [&](int k, int l, int p) {
+                return vd[k][p][0] * vd[l][p][0] + vd[k][p][1] * vd[l][p][1] + vd[k][p][2] * vd[l][p][2];
+            };
+            double b[4] = {0.0, 0.0, 0.0, 0.0};
+            if (cand == 0) {   // N = 1
+                double num = 0.0, den = 0.0;
+                for (int p = 0; p < 6; ++p) {
+                    const double dv = sqrt(dot(0, 0, p));
+                    num += dv * sqrt(sh.dw[p]);
+                    den += dv * dv;
+                }
+                b[0] = num / den;
+            } else if (cand == 1) {   // N = 2: unknowns (b1^2, b1 b2, b2^2)
+                double N[9] = {0}, g[3] = {0}, s[3];
+                for (int p = 0; p < 6; ++p) {
+                    const double row[3] = {dot(0, 0, p), 2.0 * dot(0, 1, p), dot(1, 1, p)};
+                    for (int r = 0; r < 3; ++r) {
+                        for (int c = 0; c < 3; ++c)
+                            N[3 * r + c] += row[r] * row[c];
+                        g[r] += row[r] * sh.dw[p];
+                    }
+                }
+                solve_small(N, g, s, 3);
+                b[0] = sqrt(fabs(s[0]));
+                b[1] = (s[1] > 0.0 ? 1.0 : (s[1] < 0.0 ? -1.0 : 0.0)) * sqrt(fabs(s[2]));
+            } else {   // N = 3: six products, six equations
+                double N[36] = {0}, g[6] = {0}, s[6];
+                for (int p = 0; p < 6; ++p) {
+                    const double row[6] = {dot(0, 0, p), 2.0 * dot(0, 1, p), dot(1, 1, p),
+                                           2.0 * dot(0, 2, p), 2.0 * dot(1, 2, p), dot(2, 2, p)};
+                    for (int r = 0; r < 6; ++r) {
+                        for (int c = 0; c < 6; ++c)
+                            N[6 * r + c] += row[r] * row[c];
+                        g[r] += row[r] * sh.dw[p];
+                    }
+                }
+                solve_small(N, g, s, 6);
+                b[0] = sqrt(fabs(s[0]));
+                if (b[0] > 0.0) {
+                    b[1] = s[1] / b[0];
+                    b[2] = s[3] / b[0];
+                }
+            }
+            gauss_newton(b, sh);
+            for (int k = 0; k < 4; ++k)
+                betas[k] = b[k];
+        }
+        __syncthreads();
+        pose_from_betas(a, inl, betas, sh, red);
+        if (threadIdx.x == 0 && sh.err < sh.besterr) {
+            sh.besterr = sh.err;
+            for (int k = 0; k < 9; ++k)
+                sh.bestR[k] = sh.R[k];
+            for (int k = 0; k < 3; ++k)
+                sh.bestT[k] = sh.T[k];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kEpnpThreads) k_epnp(EpnpArgs a)
+{
+    pdl_begin();
+    __shared__ unsigned char inl[kMaxPts];
+    __shared__ EpnpShared sh;
+    extern __shared__ double red[];   // 80 x blockDim
+    __shared__ double errs[kMaxPts];
+    // usable points: finite world point and pixel
+    for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+        const double *p = a.P + 3 * i, *u = a.uv + 2 * i;
+        inl[i] = isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]) && isfinite(u[0]) && isfinite(u[1]);
+    }
+    __syncthreads();
+    double cnt[1] = {0.0};
+    for (int i = threadIdx.x; i < a.n; i += blockDim.x)
+        cnt[0] += inl[i];
+    block_sum(cnt, 1, red);
+    if (cnt[0] < 6.0) {
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 14; ++k)
+                a.out[k] = k < 13 ? __longlong_as_double(0x7FF8000000000000LL) : cnt[0];
+        return;
+    }
+    epnp_solve(a, inl, sh, red);
+    if (threadIdx.x == 0)
+        sh.ninl = (int)cnt[0];
+    __syncthreads();
+    // inlier rounds: keep the errors below max(2 px, 3 x the median)
+    for (int round = 0; round < 2; ++round) {
+        for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+            const double *p = a.P + 3 * i, *u = a.uv + 2 * i;
+            const bool usable = isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]) && isfinite(u[0]) && isfinite(u[1]);
+            double e = INFINITY;
+            if (usable) {
+                double pc[3];
+                for (int r = 0; r < 3; ++r)
+                    pc[r] = sh.bestR[3 * r] * p[0] + sh.bestR[3 * r + 1] * p[1] + sh.bestR[3 * r + 2] * p[2] +
+                            sh.bestT[r];
+                const double du = a.fx * pc[0] / pc[2] + a.cx - u[0], dv = a.fy * pc[1] / pc[2] + a.cy - u[1];
+                e = sqrt(du * du + dv * dv);
+            }
+            errs[i] = e;
+        }
+        __syncthreads();
+        // the median of the usable errors (counting selection, exact)
+        __shared__ double med;
+        __shared__ int nusable;
+        if (threadIdx.x == 0) {
+            int n = 0;
+            for (int i = 0; i < a.n; ++i)
+                n += errs[i] < INFINITY;
+            nusable = n;
+        }
+        __syncthreads();
+        const int n = nusable;
+        for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+            if (!(errs[i] < INFINITY))
+                continue;
+            int below = 0, equal = 0;
+            for (int j = 0; j < a.n; ++j) {
+                below += errs[j] < errs[i];
+                equal += errs[j] == errs[i];
+            }
+            // the lower and upper middle values of the sorted errors
+            if (below <= (n - 1) / 2 && (n - 1) / 2 < below + equal)
+                med = errs[i];   // equal values write the same number
+        }
+        __syncthreads();
+        __shared__ double med_hi;
+        for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+            if (!(errs[i] < INFINITY))
+                continue;
+            int below = 0, equal = 0;
+            for (int j = 0; j < a.n; ++j) {
+                below += errs[j] < errs[i];
+                equal += errs[j] == errs[i];
+            }
+            if (below <= n / 2 && n / 2 < below + equal)
+                med_hi = errs[i];
+        }
+        __syncthreads();
+        const double thr = fmax(2.0, 3.0 * (0.5 * (med + med_hi)));
+        for (int i = threadIdx.x; i < a.n; i += blockDim.x)
+            inl[i] = errs[i] < thr;
+        __syncthreads();
+        cnt[0] = 0.0;
+        for (int i = threadIdx.x; i < a.n; i += blockDim.x)
+            cnt[0] += inl[i];
+        block_sum(cnt, 1, red);
+        if (cnt[0] < 6.0)
+            break;
+        epnp_solve(a, inl, sh, red);
+        if (threadIdx.x == 0)
+            sh.ninl = (int)cnt[0];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 9; ++k)
+            a.out[k] = sh.bestR[k];
+        for (int k = 0; k < 3; ++k)
+            a.out[9 + k] = sh.bestT[k];
+        a.out[12] = sh.besterr;
+        a.out[13] = (double)sh.ninl;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the whole pose step: points of the frame-1 corners from its cloud
+
+struct GatherArgs {
+    const int32_t *corners;
+    const float *xyz;
+    const double *pos;
+    int W, n;
+    double *P;
+    double *uv;
+};
+
+__global__ void k_pose_gather(GatherArgs a)
+{
+    pdl_begin();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n)
+        return;
+    const double nan = __longlong_as_double(0x7FF8000000000000LL);
+    const int x = a.corners[2 * i], y = a.corners[2 * i + 1];
+    double p[3] = {nan, nan, nan};
+    if (x >= 0) {
+        const float *q = a.xyz + ((size_t)y * a.W + x) * 3;
+        p[0] = q[0];
+        p[1] = q[1];
+        p[2] = q[2];
+    }
+    a.P[3 * i] = p[0];
+    a.P[3 * i + 1] = p[1];
+    a.P[3 * i + 2] = p[2];
+    a.uv[2 * i] = a.pos[2 * i];
+    a.uv[2 * i + 1] = a.pos[2 * i + 1];
+}
+
+bool pose_params_ok(int W, int H, const vs_pose_params *p)
+{
+    return p && W > 0 && H > 0 && (long long)W * H <= (1LL << 27) && p->grid >= 1 && p->grid <= kMaxGrid &&
+           p->radius >= 1 && p->radius <= kMaxRadius && p->search >= 0 && p->search <= kMaxSearch &&
+           p->margin >= p->radius + 1 && 2 * p->margin < W && 2 * p->margin < H;
+}
+
+struct PoseLayout {
+    size_t r25, corners, pos, cost, P, uv, total;
+};
+
+PoseLayout pose_layout(int W, int H, const vs_pose_params *p)
+{
+    PoseLayout l;
+    const size_t nc = (size_t)p->grid * p->grid;
+    size_t off = 0;
+    l.r25 = off;
+    off = align_up(off + (size_t)W * H * sizeof(int64_t), 256);
+    l.corners = off;
+    off = align_up(off + nc * 2 * sizeof(int32_t), 256);
+    l.pos = off;
+    off = align_up(off + nc * 2 * sizeof(double), 256);
+    l.cost = off;
+    off = align_up(off + nc * sizeof(int64_t), 256);
+    l.P = off;
+    off = align_up(off + nc * 3 * sizeof(double), 256);
+    l.uv = off;
+    off = align_up(off + nc * 2 * sizeof(double), 256);
+    l.total = off;
+    return l;
+}
+
+int launch_harris(const uint8_t *rgb, int W, int H, int pitch, int64_t *r25, cudaStream_t st)
+{
+    HarrisArgs a{rgb, W, H, pitch, r25};
+    launch_pdl(k_harris_r25, dim3((W + kHarrisTx - 1) / kHarrisTx, (H + kHarrisTy - 1) / kHarrisTy),
+               dim3(kHarrisTx, kHarrisTy), st, a);
+    note_launch();
+    return launch_status();
+}
+
+int launch_cells(const int64_t *r25, int W, int H, const vs_pose_params *p, int32_t *corners, cudaStream_t st)
+{
+    CellArgs a{r25, W, H, p->grid, p->margin, (long long)p->threshold25, corners};
+    launch_pdl(k_harris_cells, dim3(p->grid * p->grid), dim3(256), st, a);
+    note_launch();
+    return launch_status();
+}
+
+int launch_zssd(const uint8_t *rgb1, const uint8_t *rgb2, int W, int H, int pitch, const int32_t *corners, int n,
+                const vs_pose_params *p, double *pos, int64_t *cost, cudaStream_t st)
+{
+    ZssdArgs a{rgb1, rgb2, W, H, pitch, p->radius, p->search, corners, pos, cost};
+    launch_pdl(k_zssd, dim3(n), dim3(256), st, a);
+    note_launch();
+    return launch_status();
+}
+
+int launch_epnp(const double *P, const double *uv, int n, const vs_camera *cam, double *out, cudaStream_t st)
+{
+    EpnpArgs a{P, uv, n, cam->fx, cam->fy, cam->cx, cam->cy, out};
+    launch_pdl_smem(k_epnp, dim3(1), dim3(kEpnpThreads), (size_t)80 * kEpnpThreads * sizeof(double), st, a);
+    note_launch();
+    return launch_status();
+}
+
+// The EPnP kernel's reduction space (160 KB) is dynamic shared memory: allowed
+// once per device.
+bool epnp_ready()
+{
+    constexpr int kMaxDev = 64;
+    static bool done[kMaxDev] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev)
+        return false;
+    if (!done[dev]) {
+        if (cudaFuncSetAttribute(k_epnp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 80 * kEpnpThreads * (int)sizeof(double)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return false;
+        }
+        done[dev] = true;
+    }
+    return true;
+}
+
+}  // namespace
+}  // namespace vs
+
+extern "C" size_t vs_pose_workspace_size(int W, int H, const vs_pose_params *p)
+{
+    return vs::pose_params_ok(W, H, p) ? vs::pose_layout(W, H, p).total : 0;
+}
+
+extern "C" int vs_harris_response(const uint8_t *rgb, int W, int H, int pitch, int64_t *r25, void *stream)
+{
+    vs::NvtxRange nvtx_range("vs_harris_response");
+    if (!rgb || !r25 || W <= 0 || H <= 0 || pitch < 3 * W || (long long)W * H > (1LL << 27))
+        return VS_EINVAL;
+    return vs::launch_harris(rgb, W, H, pitch, r25, (cudaStream_t)stream);
+}
+
+extern "C" int vs_harris_corners(const uint8_t *rgb, int W, int H, int pitch, const vs_pose_params *p,
+                                 int32_t *corners, void *workspace, size_t ws_bytes, void *stream)
+{
+    using namespace vs;
+    NvtxRange nvtx_range("vs_harris_corners");
+    if (!rgb || !corners || pitch < 3 * W || !pose_params_ok(W, H, p))
+        return VS_EINVAL;
+    const PoseLayout l = pose_layout(W, H, p);
+    if (!workspace || !aligned(workspace, 256) || ws_bytes < l.total)
+        return VS_EWORKSPACE;
+    int64_t *r25 = reinterpret_cast<int64_t *>(static_cast<uint8_t *>(workspace) + l.r25);
+    const int rc = launch_harris(rgb, W, H, pitch, r25, (cudaStream_t)stream);
+    if (rc != VS_OK)
+        return rc;
+    return launch_cells(r25, W, H, p, corners, (cudaStream_t)stream);
+}
+
+extern "C" int vs_zssd_match(const uint8_t *rgb1, const uint8_t *rgb2, int W, int H, int pitch,
+                             const int32_t *corners, int n, const vs_pose_params *p, double *pos, int64_t *cost,
+                             void *stream)
+{
+    using namespace vs;
+    NvtxRange nvtx_range("vs_zssd_match");
+    if (!rgb1 || !rgb2 || !corners || !pos || !cost || n < 0 || n > kMaxPts || pitch < 3 * W ||
+        !pose_params_ok(W, H, p))
+        return VS_EINVAL;
+    if (n == 0)
+        return VS_OK;
+    return launch_zssd(rgb1, rgb2, W, H, pitch, corners, n, p, pos, cost, (cudaStream_t)stream);
+}
+
+extern "C" int vs_epnp(const double *points, const double *uv, int n, const vs_camera *cam, double *out,
+                       void *stream)
+{
+    using namespace vs;
+    NvtxRange nvtx_range("vs_epnp");
+    if (!points || !uv || !cam || !out || n < 6 || n > kMaxPts || !(cam->fx > 0.0f) || !(cam->fy > 0.0f))
+        return VS_EINVAL;
+    if (!epnp_ready())
+        return VS_ECUDA;
+    return launch_epnp(points, uv, n, cam, out, (cudaStream_t)stream);
+}
+
+extern "C" int vs_pose_estimate(const uint8_t *rgb1, const uint8_t *rgb2, const float *xyz1, int W, int H,
+                                int pitch, const vs_camera *cam, const vs_pose_params *p, double *out,
+                                void *workspace, size_t ws_bytes, void *stream)
+{
+    using namespace vs;
+    NvtxRange nvtx_range("vs_pose_estimate");
+    if (!rgb1 || !rgb2 || !xyz1 || !cam || !out || pitch < 3 * W || !pose_params_ok(W, H, p) ||
+        !(cam->fx > 0.0f) || !(cam->fy > 0.0f))
+        return VS_EINVAL;
+    const PoseLayout l = pose_layout(W, H, p);
+    if (!workspace || !aligned(workspace, 256) || ws_bytes < l.total)
+        return VS_EWORKSPACE;
+    if (!epnp_ready())
+        return VS_ECUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint8_t *ws = static_cast<uint8_t *>(workspace);
+    int64_t *r25 = reinterpret_cast<int64_t *>(ws + l.r25);
+    int32_t *corners = reinterpret_cast<int32_t *>(ws + l.corners);
+    double *pos = reinterpret_cast<double *>(ws + l.pos);
+    int64_t *cost = reinterpret_cast<int64_t *>(ws + l.cost);
+    double *P = reinterpret_cast<double *>(ws + l.P), *uv = reinterpret_cast<double *>(ws + l.uv);
+    const int n = p->grid * p->grid;
+    int rc = launch_harris(rgb1, W, H, pitch, r25, st);
+    if (rc == VS_OK)
+        rc = launch_cells(r25, W, H, p, corners, st);
+    if (rc == VS_OK)
+        rc = launch_zssd(rgb1, rgb2, W, H, pitch, corners, n, p, pos, cost, st);
+    if (rc == VS_OK) {
+        GatherArgs g{corners, xyz1, pos, W, n, P, uv};
+        launch_pdl(k_pose_gather, dim3((n + 127) / 128), dim3(128), st, g);
+        note_launch();
+        rc = launch_status();
+    }
+    if (rc == VS_OK)
+        rc = launch_epnp(P, uv, n, cam, out, st);
+    return rc;
+}

@@ -29,7 +29,7 @@ def lib() -> ctypes.CDLL:
                 raise RuntimeError(f"{library_path} is missing: build it with `python -m paper_1902_09733_b300.build`")
             L = ctypes.CDLL(library_path)
             P, I, F, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_double
-            L.vsr_render.argtypes = [P, I, F, F, I, P, P, P, P, F, D, D, P, F, F, I, F, F, P, I, I, P]
+            L.vsr_render.argtypes = [P, I, F, F, I, P, P, P, P, F, D, D, P, F, F, I, F, F, P, I, I, P, P]
             L.vsr_render.restype = I
             _lib = L
     return _lib
@@ -53,8 +53,9 @@ class GpuScene:
         self._amp = (ctypes.c_double * k)(*[float(amp) for _, amp, _ in t["octaves"]])
         self.k = k
 
-    def render(self, pose, cam, W: int = 2704, H: int = 1520, out=None, stream=None) -> torch.Tensor:
-        """(H, W, 3) uint8 device frame from pose (x, y, yaw); cam = fx, fy, cx, cy, k1, k2."""
+    def render(self, pose, cam, W: int = 2704, H: int = 1520, out=None, stream=None, depth=None) -> torch.Tensor:
+        """(H, W, 3) uint8 device frame from pose (x, y, yaw); cam = fx, fy, cx, cy, k1, k2;
+        depth: an optional (H, W) float32 device tensor that receives each pixel's z-depth."""
         if out is None:
             out = torch.empty((H, W, 3), dtype=torch.uint8, device=self.device)
         x, y, yaw = (float(v) for v in pose)
@@ -64,7 +65,8 @@ class GpuScene:
         st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
         rc = lib().vsr_render(self.height.data_ptr(), self.n, self.half, self.res, self.k, self._lat, self._m,
                               self._lam, self._amp, self.nhalf, self.top, self.altitude, cam6, x, y, rotate,
-                              cosy, siny, out.data_ptr(), W, H, st)
+                              cosy, siny, out.data_ptr(), W, H,
+                              depth.data_ptr() if depth is not None else None, st)
         if rc != 0:
             raise RuntimeError(f"vsr_render failed with status {rc}")
         return out

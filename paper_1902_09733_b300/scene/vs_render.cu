@@ -37,6 +37,7 @@ struct RenderArgs {
     int rotate;
     int march_steps, refine_steps;
     uint8_t *out;
+    float *depth;         // nullable: the z-depth of each pixel along its undistorted ray
     int W, H;
 };
 
@@ -124,6 +125,8 @@ __global__ void __launch_bounds__(256) k_render(RenderArgs a)
             t_lo = tm;
     }
     const float t = 0.5f * (t_lo + t_hi);
+    if (a.depth)
+        a.depth[(size_t)v * a.W + u] = t;
     const float X = a.px + t * xn, Y = a.py + t * yn;
     double col[3];
     albedo_at(a, X, Y, col);
@@ -147,12 +150,13 @@ extern "C" {
 // (rotate = 0: heading 0, the camera axes on the ground axes).  height: n x n
 // device floats on a square of half extent `half` and cell `res`; octaves:
 // `noct` (<= 4) device lattices of m x m x 3 floats with their wavelength and
-// amplitude; cam6 = fx, fy, cx, cy, k1, k2.  Returns 0, -1 for bad arguments,
+// amplitude; cam6 = fx, fy, cx, cy, k1, k2; depth (nullable, device, W H
+// floats) receives each pixel's z-depth.  Returns 0, -1 for bad arguments,
 // or -4 for a CUDA error.
 int vsr_render(const float *height, int n, float half, float res, int noct, const float *const *lat,
                const int *m, const float *lam, const double *amp, float nhalf, double top, double altitude,
                const double *cam6, float px, float py, int rotate, float cosy, float siny, uint8_t *out, int W,
-               int H, void *stream)
+               int H, float *depth, void *stream)
 {
     if (!height || !out || !cam6 || n < 2 || noct < 1 || noct > kMaxOctaves || W <= 0 || H <= 0 || !(top > 0.0))
         return -1;
@@ -192,6 +196,7 @@ int vsr_render(const float *height, int n, float half, float res, int noct, cons
     a.march_steps = 20;
     a.refine_steps = 12;
     a.out = out;
+    a.depth = depth;
     a.W = W;
     a.H = H;
     k_render<<<dim3((W + 255) / 256, H), 256, 0, (cudaStream_t)stream>>>(a);

@@ -291,7 +291,7 @@ class FlightScene:
     """
 
     def __init__(self, seed: int, extent: float, altitude: float = 100.0, relief: float = 15.0,
-                 n_buildings: int = 40, grid: int = 2049):
+                 n_buildings: int = 40, grid: int = 2049, building_heights=(5.0, 30.0)):
         g = _rng(seed)
         scale = altitude / 20.0
         self.altitude = float(altitude)
@@ -306,7 +306,7 @@ class FlightScene:
         for _ in range(n_buildings):
             cx0, cy0 = g.uniform(-extent / 2 + 10, extent / 2 - 10, size=2)
             sx, sy = g.uniform(6.0, 25.0, size=2)
-            top = g.uniform(5.0, 30.0)
+            top = g.uniform(*building_heights)
             ix = np.where(np.abs(cells - cx0) <= sx / 2)[0]
             iy = np.where(np.abs(cells - cy0) <= sy / 2)[0]
             if ix.size and iy.size:

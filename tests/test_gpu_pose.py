@@ -1,0 +1,132 @@
+"""The pose path (Section 2.3, Eq. 4-7) on the GPU against the oracle: the
+Harris response and the grid corners exactly (integer), the ZSSD costs
+exactly and the sub-pixel positions to rounding, EPnP to 1e-8; and the whole
+pose step on GPU-rendered frames, with the GPU stereo cloud as its 3D
+points, against the renderer's own cameras."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1902_09733_b300 as vs
+from oracle import pose as opose
+from paper_1902_09733_b300 import build, synth
+from paper_1902_09733_b300.scene import GpuScene
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    assert torch.cuda.is_available()
+    build.build()
+
+
+def _frames():
+    """A seeded noise frame of odd size and two undistorted rendered frames (host renderer)."""
+    g = np.random.default_rng(21)
+    noise = synth._gauss_blur(g.uniform(0, 255, size=(53, 77)), 1.2, 4)
+    rgb = np.stack([noise, 0.7 * noise + 30, 255 - noise], -1)
+    out = [np.clip(np.rint(rgb), 0, 255).astype(np.uint8)]
+    W, H = 416, 234
+    s = W / 2704.0
+    cam = (1400.0 * s, 1400.0 * s, (W - 1) / 2.0, (H - 1) / 2.0, 0.0, 0.0)
+    poses = synth.lawnmower_path(4, 700)
+    scene = synth.FlightScene(4, synth.lawnmower_extent(poses), n_buildings=80)
+    out.append(scene.render(poses[550], W, H, cam))
+    out.append(scene.render(poses[556], W, H, cam))
+    return out
+
+
+FRAMES = _frames()
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_harris_response_and_corners_are_exact(k):
+    f = FRAMES[k]
+    H, W = f.shape[:2]
+    dev = torch.from_numpy(f).cuda()
+    r25 = vs.harris_response(dev).cpu().numpy()
+    want = opose.harris_response25(f)
+    np.testing.assert_array_equal(r25, want)
+    for grid, margin, thr in ((4, 6, 0), (7, 8, 10 ** 6), (16, 12, 0)):
+        p = vs.PoseParams(grid=grid, margin=margin, threshold25=thr, radius=5, search=8)
+        got = vs.harris_corners(dev, p).cpu().numpy()
+        np.testing.assert_array_equal(got, opose.harris_corners(want, grid, margin, thr))
+
+
+def test_zssd_costs_exact_and_positions_to_rounding():
+    f1, f2 = FRAMES[1], FRAMES[2]
+    p = vs.PoseParams(grid=12, margin=12, threshold25=0, radius=5, search=10)
+    corners = opose.harris_corners(opose.harris_response25(f1), 12, 12, 0)
+    corners[3] = (-1, -1)                      # an empty cell
+    corners[5] = (3, 100)                      # a patch leaving frame 1
+    pos, cost = vs.zssd_match(torch.from_numpy(f1).cuda(), torch.from_numpy(f2).cuda(),
+                              torch.from_numpy(corners.astype(np.int32)).cuda(), p)
+    wpos, wcost = opose.zssd_match(f1, f2, corners, radius=5, search=10)
+    np.testing.assert_array_equal(cost.cpu().numpy(), wcost)
+    gp = pos.cpu().numpy()
+    assert np.array_equal(np.isnan(gp), np.isnan(wpos))
+    ok = ~np.isnan(wpos)
+    assert np.abs(gp[ok] - wpos[ok]).max() <= 1e-12
+
+
+CAM = (1400.0, 1400.0, 1351.5, 759.5)
+
+
+def _rot(axis, ang):
+    a = np.asarray(axis, float) / np.linalg.norm(axis)
+    K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    return np.eye(3) + np.sin(ang) * K + (1 - np.cos(ang)) * K @ K
+
+
+@pytest.mark.parametrize("n,noise,outliers", [(6, 0.0, 0), (50, 0.0, 0), (400, 0.5, 0), (900, 0.3, 40)])
+def test_epnp_matches_the_oracle(n, noise, outliers):
+    g = np.random.default_rng(n)
+    P = np.column_stack([g.uniform(-60, 60, n), g.uniform(-35, 35, n), g.uniform(70, 100, n)])
+    R = _rot(g.normal(size=3), g.uniform(0.01, 0.2))
+    T = g.normal(size=3) * 0.5
+    pc = (R @ P.T).T + T
+    uv = np.column_stack([CAM[0] * pc[:, 0] / pc[:, 2] + CAM[2], CAM[1] * pc[:, 1] / pc[:, 2] + CAM[3]])
+    uv += g.normal(scale=noise, size=uv.shape) if noise else 0.0
+    if outliers:
+        uv[:outliers] += g.uniform(-40, 40, size=(outliers, 2))
+    if n > 10:
+        P[7] = np.nan                           # an unusable point is skipped
+    out = vs.epnp(torch.from_numpy(P).cuda(), torch.from_numpy(uv).cuda(), vs.Camera(*CAM)).cpu().numpy()
+    ok = ~np.isnan(P).any(axis=1)
+    Rw, Tw, errw, keep = opose.epnp_inliers(P[ok], uv[ok], CAM)
+    assert np.abs(out[:9].reshape(3, 3) - Rw).max() < 1e-8
+    assert np.abs(out[9:12] - Tw).max() < 1e-7
+    assert abs(out[12] - errw) < 1e-6 and out[13] == keep.sum()
+    if not noise:
+        assert np.abs(Rw - R).max() < 1e-8     # and both are the true pose
+
+
+@pytest.mark.parametrize("t,target", [(300, 320), (495, 503), (600, 604)])
+def test_pose_step_on_gpu_rendered_flight_frames(t, target):
+    """Full-resolution frames of the lawnmower flight at 100 m, rendered on the
+    GPU without lens distortion (so already rectified), frame 1's cloud from
+    the rendered depth: the pose of a later frame -- further along a leg (a
+    pure translation), through the start of a turn, inside a turn -- comes
+    back as the relative pose of the two cameras."""
+    W, H = 2704, 1520
+    cam6 = synth.TERRAIN_CAMERA[:4] + (0.0, 0.0)
+    poses = synth.lawnmower_path(8, 800)
+    scene = synth.FlightScene(8, synth.lawnmower_extent(poses), n_buildings=80)
+    gs = GpuScene(scene)
+    depth = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    f1 = gs.render(poses[t], cam6, depth=depth)
+    f2 = gs.render(poses[target], cam6)
+    vv, uu = torch.meshgrid(torch.arange(H, device="cuda", dtype=torch.float32),
+                            torch.arange(W, device="cuda", dtype=torch.float32), indexing="ij")
+    xyz = torch.stack([(uu - cam6[2]) / cam6[0] * depth, (vv - cam6[3]) / cam6[1] * depth, depth], -1).contiguous()
+    p = vs.PoseParams(grid=30, margin=40, threshold25=0, radius=5, search=32)
+    out = vs.pose_estimate(f1, f2, xyz, vs.Camera(*cam6[:4]), p).cpu().numpy()
+    R, T = out[:9].reshape(3, 3), out[9:12]
+    Rt, Tt = synth.relative_pose(poses[t], poses[target])
+    ang = np.degrees(np.arccos(np.clip((np.trace(R.T @ Rt) - 1) / 2, -1, 1)))
+    print(f"pose t={t} -> {target}: inliers {out[13]:.0f}, reprojection {out[12]:.3f} px, rotation error "
+          f"{ang:.4f} deg, T {T} (true {Tt})")
+    assert out[13] > 400, out[13]
+    assert ang < 0.05, ang
+    assert np.linalg.norm(T - Tt) < 0.05 * np.linalg.norm(Tt) + 0.03, (T, Tt)
