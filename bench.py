@@ -16,6 +16,11 @@ seeded synthetic terrain pairs rendered on the host; eight distinct pairs
 (197 MB, more than the 126 MB L2) are resident in HBM and rotated so no step
 reads its inputs from L2.
 
+Outside the timed region the line also carries the end-to-end rate through
+the public API, the streaming flight, the batched BP and whole pairs, the
+smoothed BP and its adjoint, and the pose step between two frames (Section
+2.3), each with its own timing.
+
 Prints ONE JSON line (rank 0).  Pairs are independent, so N GPUs run N
 replicas ("scaling": "weak") and the value is all pairs over the slowest rank.
 ``--impl reference`` times the CPU oracle instead (rank 0 only), on bounded
@@ -58,6 +63,7 @@ def parse():
     ap.add_argument("--stream-frames", type=int, default=1500)
     ap.add_argument("--batch-pairs", type=int, default=48)
     ap.add_argument("--smooth-reps", type=int, default=20)
+    ap.add_argument("--pose-reps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -563,6 +569,74 @@ def run_smooth(args, vs, synth, torch, dev):
     return out
 
 
+def run_pose(args, vs, synth, torch, dev):
+    """The pose step (Section 2.3, Eq. 4-7) between frames 300 and 320 of a
+    seeded lawnmower flight at 100 m (2704x1520, rendered on the GPU without
+    lens distortion, frame 1's cloud from its rendered depth): integer Harris
+    response, one corner per cell of a 30x30 grid, ZSSD (radius 5, search
+    +-32 px), EPnP with two inlier rounds.  GPU: CUDA events over `reps`
+    calls of each stage and of the whole step (vs_pose_estimate); CPU: the
+    oracle on the same frames, once (a bounded sample: one step)."""
+    from paper_1902_09733_b300.scene import GpuScene
+    W, H = W_FULL, H_FULL
+    cam6 = synth.TERRAIN_CAMERA[:4] + (0.0, 0.0)
+    poses = synth.lawnmower_path(8, 800)
+    scene = synth.FlightScene(8, synth.lawnmower_extent(poses), n_buildings=80)
+    gs = GpuScene(scene, dev)
+    depth = torch.empty((H, W), dtype=torch.float32, device=dev)
+    f1 = gs.render(poses[300], cam6, depth=depth)
+    f2 = gs.render(poses[320], cam6)
+    vv, uu = torch.meshgrid(torch.arange(H, device=dev, dtype=torch.float32),
+                            torch.arange(W, device=dev, dtype=torch.float32), indexing="ij")
+    xyz = torch.stack([(uu - cam6[2]) / cam6[0] * depth, (vv - cam6[3]) / cam6[1] * depth, depth], -1).contiguous()
+    p = vs.PoseParams(grid=30, margin=40, threshold25=0, radius=5, search=32)
+    cam = vs.Camera(*cam6[:4])
+    ws = torch.empty(vs.pose_workspace_size(W, H, p), dtype=torch.uint8, device=dev)
+    corners = vs.harris_corners(f1, p, workspace=ws)
+    stages = {
+        "harris_response": lambda: vs.harris_response(f1),
+        "harris_corners": lambda: vs.harris_corners(f1, p, workspace=ws),
+        "zssd_match": lambda: vs.zssd_match(f1, f2, corners, p),
+        "pose_estimate": lambda: vs.pose_estimate(f1, f2, xyz, cam, p, workspace=ws),
+    }
+    times = {}
+    for name, fn in stages.items():
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.pose_reps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        times[name] = e0.elapsed_time(e1) / args.pose_reps
+    est = out.cpu().numpy()
+    Rt, Tt = synth.relative_pose(poses[300], poses[320])
+    ang = float(np.degrees(np.arccos(np.clip((np.trace(est[:9].reshape(3, 3).T @ Rt) - 1) / 2, -1, 1))))
+    res = {"workload": "pose step between two 2704x1520 lawnmower frames 20 apart (1 m at 100 m): Harris "
+                       "25R, 30x30 grid corners (margin 40), ZSSD radius 5 search +-32, EPnP + 2 inlier rounds",
+           "unit": "pose steps/s", "value": 1e3 / times["pose_estimate"], "reps": args.pose_reps,
+           "stage_ms": times, "inliers": float(est[13]), "reprojection_px": float(est[12]),
+           "rotation_error_deg": ang, "translation": est[9:12].tolist(), "true_translation": list(map(float, Tt))}
+    if not args.no_cpu_baseline:
+        from oracle import pose as opose
+        h1, h2 = f1.cpu().numpy(), f2.cpu().numpy()
+        P = xyz.cpu().numpy().astype(np.float64)
+        t0 = time.perf_counter()
+        r25 = opose.harris_response25(h1)
+        c = opose.harris_corners(r25, 30, 40, 0)
+        pos, _ = opose.zssd_match(h1, h2, c, radius=5, search=32)
+        ok = (c[:, 0] >= 0) & ~np.isnan(pos).any(axis=1)
+        pts = P[c[ok, 1], c[ok, 0]]
+        ok2 = ~np.isnan(pts).any(axis=1)
+        opose.epnp_inliers(pts[ok2], pos[ok][ok2], cam6[:4])
+        tsec = time.perf_counter() - t0
+        res["cpu_oracle"] = {"value": 1.0 / tsec, "unit": "pose steps/s", "s_per_step": tsec, "cores": 1,
+                             "kind": "oracle", "sample": "one pose step on the same frames (numpy, int64 / FP64)"}
+    return res
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -802,6 +876,9 @@ def run_ours(args):
         batched["whole_pairs"] = run_batched_pairs(args, vs, synth, torch, dev, cam)
 
     # smoothed BP + adjoint (the differentiable relaxation of Eq. 1)
+    pose = None
+    if args.pose_reps > 0 and rank == 0:
+        pose = run_pose(args, vs, synth, torch, dev)
     smooth = None
     if args.smooth_reps > 0 and rank == 0:
         smooth = run_smooth(args, vs, synth, torch, dev)
@@ -859,6 +936,7 @@ def run_ours(args):
             "streaming": streaming,
             "batched": batched,
             "smooth_bp": smooth,
+            "pose": pose,
             "gpu_launches": launches_per_step * K,
             "pairs_per_step": P,
             "clocks": clk,

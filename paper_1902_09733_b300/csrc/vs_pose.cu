@@ -357,6 +357,115 @@ __device__ void jacobi_eigen(double *A, double *V, double *ev, int n)
     }
 }
 
+// The same decomposition on one warp for even n <= 16 (the 12 x 12 normal
+// matrix of Eq. 6).  FP64 runs at a small fraction of the FP32 rate on this
+// GPU, so the serial form above spends milliseconds on it; here a sweep is
+// n - 1 rounds of n / 2 disjoint rotations (the round-robin ordering: pairs
+// (r, n - 1) and ((r + i) mod (n - 1), (r - i) mod (n - 1)), i = 1 .. n/2 - 1),
+// each round's angles taken from the matrix before it (the subproblems of
+// disjoint pairs are independent), then the columns, the rows and the
+// eigenvector columns updated with one element pair per lane.  Same
+// convergence test and ascending order as jacobi_eigen; A, V, ev in shared
+// memory; every lane of the warp calls it.
+__device__ void jacobi_eigen_warp(double *A, double *V, double *ev, int n)
+{
+    __shared__ double rc[8], rs[8];
+    __shared__ int rp[8], rq[8];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, half = n / 2, m = n - 1;
+    for (int e = lane; e < n * n; e += 32)
+        V[e] = e / n == e % n ? 1.0 : 0.0;
+    __syncwarp();
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0, diag = 0.0;
+        for (int e = lane; e < n * n; e += 32) {
+            const int r = e / n, c = e % n;
+            if (r == c)
+                diag += A[e] * A[e];
+            else if (r < c)
+                off += A[e] * A[e];
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(full, off, o);
+            diag += __shfl_xor_sync(full, diag, o);
+        }
+        off = __shfl_sync(full, off, 0);   // one value for every lane
+        diag = __shfl_sync(full, diag, 0);
+        if (off <= 1e-30 * diag || off == 0.0)
+            break;
+        for (int r = 0; r < m; ++r) {
+            if (lane < half) {
+                int p = lane == 0 ? r : (r + lane) % m;
+                int q = lane == 0 ? m : (r - lane + m) % m;
+                if (p > q) {
+                    const int t = p;
+                    p = q;
+                    q = t;
+                }
+                const double apq = A[p * n + q];
+                double c = 1.0, sn = 0.0;
+                if (apq != 0.0) {
+                    const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+                    const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                    c = 1.0 / sqrt(t * t + 1.0);
+                    sn = t * c;
+                }
+                rc[lane] = c;
+                rs[lane] = sn;
+                rp[lane] = p;
+                rq[lane] = q;
+            }
+            __syncwarp();
+            for (int e = lane; e < n * half; e += 32) {   // columns p, q of every row
+                const int k = e / half, i = e % half, p = rp[i], q = rq[i];
+                const double c = rc[i], sn = rs[i];
+                const double akp = A[k * n + p], akq = A[k * n + q];
+                A[k * n + p] = c * akp - sn * akq;
+                A[k * n + q] = sn * akp + c * akq;
+            }
+            __syncwarp();
+            for (int e = lane; e < n * half; e += 32) {   // rows p, q
+                const int i = e / n, k = e % n, p = rp[i], q = rq[i];
+                const double c = rc[i], sn = rs[i];
+                const double apk = A[p * n + k], aqk = A[q * n + k];
+                A[p * n + k] = c * apk - sn * aqk;
+                A[q * n + k] = sn * apk + c * aqk;
+            }
+            for (int e = lane; e < n * half; e += 32) {   // eigenvector columns
+                const int k = e / half, i = e % half, p = rp[i], q = rq[i];
+                const double c = rc[i], sn = rs[i];
+                const double vkp = V[k * n + p], vkq = V[k * n + q];
+                V[k * n + p] = c * vkp - sn * vkq;
+                V[k * n + q] = sn * vkp + c * vkq;
+            }
+            __syncwarp();
+        }
+    }
+    for (int i = lane; i < n; i += 32)
+        ev[i] = A[i * n + i];
+    __syncwarp();
+    for (int i = 0; i < n; ++i) {   // selection sort, ascending (the same choice on every lane)
+        int mi = i;
+        for (int j = i + 1; j < n; ++j)
+            if (ev[j] < ev[mi])
+                mi = j;
+        __syncwarp();
+        if (mi != i) {
+            if (lane < n) {
+                const double v = V[lane * n + i];
+                V[lane * n + i] = V[lane * n + mi];
+                V[lane * n + mi] = v;
+            }
+            if (lane == 0) {
+                const double t = ev[i];
+                ev[i] = ev[mi];
+                ev[mi] = t;
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // Solves the symmetric positive semi-definite system (A^T A) x = A^T b of a
 // least-squares problem given as the normal matrix N (m x m) and right side
 // g, by Gaussian elimination with partial pivoting; one thread.
@@ -406,18 +515,31 @@ struct EpnpArgs {
 __constant__ int kPairI[6] = {0, 0, 0, 1, 1, 2};
 __constant__ int kPairJ[6] = {1, 2, 3, 2, 3, 3};
 
-// Block-wide sum of `k` per-thread values (k <= 80): red holds k x blockDim doubles.
+// Block-wide sum of `k` per-thread values (k <= 80): red holds k x blockDim
+// doubles.  Few values: a tree over the threads; many (the 78 entries of the
+// normal matrix): thread i adds up value i of every thread in order, which
+// issues fewer FP64 instructions on the busiest scheduler.
 __device__ void block_sum(double *vals, int k, double *red)
 {
     const int t = threadIdx.x, nt = blockDim.x;
     for (int i = 0; i < k; ++i)
         red[i * nt + t] = vals[i];
     __syncthreads();
-    for (int o = nt / 2; o > 0; o >>= 1) {
-        if (t < o)
-            for (int i = 0; i < k; ++i)
-                red[i * nt + t] += red[i * nt + t + o];
+    if (k >= 8) {
+        if (t < k) {
+            double acc = 0.0;
+            for (int j = 0; j < nt; ++j)
+                acc += red[t * nt + j];
+            red[t * nt] = acc;
+        }
         __syncthreads();
+    } else {
+        for (int o = nt / 2; o > 0; o >>= 1) {
+            if (t < o)
+                for (int i = 0; i < k; ++i)
+                    red[i * nt + t] += red[i * nt + t + o];
+            __syncthreads();
+        }
     }
     for (int i = 0; i < k; ++i)
         vals[i] = red[i * nt];
@@ -690,20 +812,25 @@ __device__ void epnp_solve(const EpnpArgs &a, const unsigned char *inl, EpnpShar
                 v[t++] += r1[r] * r1[c] + r2[r] * r2[c];
     }
     block_sum(v, 78, red);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {   // warp 0
         double *MtM = sh.scratch, *Vm = sh.scratch + 144, *ev = sh.scratch + 288;
-        int t = 0;
-        for (int r = 0; r < 12; ++r)
-            for (int c = r; c < 12; ++c) {
-                MtM[12 * r + c] = v[t];
-                MtM[12 * c + r] = v[t];
-                ++t;
-            }
-        jacobi_eigen(MtM, Vm, ev, 12);
-        for (int r = 0; r < 12; ++r)
-            for (int k = 0; k < 4; ++k)
-                sh.V4[r][k] = Vm[12 * r + k];
-        sh.besterr = 1e300;
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int r = 0; r < 12; ++r)
+                for (int c = r; c < 12; ++c) {
+                    MtM[12 * r + c] = v[t];
+                    MtM[12 * c + r] = v[t];
+                    ++t;
+                }
+        }
+        __syncwarp();
+        jacobi_eigen_warp(MtM, Vm, ev, 12);
+        if (threadIdx.x == 0) {
+            for (int r = 0; r < 12; ++r)
+                for (int k = 0; k < 4; ++k)
+                    sh.V4[r][k] = Vm[12 * r + k];
+            sh.besterr = 1e300;
+        }
     }
     __syncthreads();
     for (int cand = 0; cand < 3; ++cand) {
@@ -818,39 +945,38 @@ __global__ void __launch_bounds__(kEpnpThreads) k_epnp(EpnpArgs a)
             errs[i] = e;
         }
         __syncthreads();
-        // the median of the usable errors (counting selection, exact)
-        __shared__ double med;
+        // the median of the usable errors (counting selection, exact).  The
+        // errors are >= 0 or +inf (NaN: unusable), whose bit patterns as
+        // 64-bit integers order as the numbers do, so the counts compare
+        // integers instead of issuing FP64 comparisons.
+        const long long *ek = reinterpret_cast<const long long *>(errs);
+        constexpr long long kInfBits = 0x7FF0000000000000LL;
+        __shared__ double med, med_hi;
         __shared__ int nusable;
-        if (threadIdx.x == 0) {
-            int n = 0;
-            for (int i = 0; i < a.n; ++i)
-                n += errs[i] < INFINITY;
-            nusable = n;
+        if (threadIdx.x == 0)
+            nusable = 0;
+        __syncthreads();
+        {
+            int cnt_u = 0;
+            for (int i = threadIdx.x; i < a.n; i += blockDim.x)
+                cnt_u += ek[i] < kInfBits;
+            atomicAdd(&nusable, cnt_u);
         }
         __syncthreads();
         const int n = nusable;
         for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
-            if (!(errs[i] < INFINITY))
+            const long long ei = ek[i];
+            if (!(ei < kInfBits))
                 continue;
             int below = 0, equal = 0;
             for (int j = 0; j < a.n; ++j) {
-                below += errs[j] < errs[i];
-                equal += errs[j] == errs[i];
+                below += ek[j] < ei;
+                equal += ek[j] == ei;
             }
-            // the lower and upper middle values of the sorted errors
+            // the lower and upper middle values of the sorted errors (equal
+            // values write the same number)
             if (below <= (n - 1) / 2 && (n - 1) / 2 < below + equal)
-                med = errs[i];   // equal values write the same number
-        }
-        __syncthreads();
-        __shared__ double med_hi;
-        for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
-            if (!(errs[i] < INFINITY))
-                continue;
-            int below = 0, equal = 0;
-            for (int j = 0; j < a.n; ++j) {
-                below += errs[j] < errs[i];
-                equal += errs[j] == errs[i];
-            }
+                med = errs[i];
             if (below <= n / 2 && n / 2 < below + equal)
                 med_hi = errs[i];
         }
