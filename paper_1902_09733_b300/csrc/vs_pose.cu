@@ -295,6 +295,29 @@ __global__ void __launch_bounds__(256) k_zssd(ZssdArgs a)
 // ---------------------------------------------------------------------------
 // EPnP, FP64, one CTA
 
+// The rotation (c, s) of a Jacobi step on the pair (p, q).  The angle only
+// has to be close to the one that zeroes A[p][q]: the step is an exact
+// orthogonal transform whatever t is, because c = 1 / sqrt(1 + t^2) and
+// s = t c are taken in FP64 from t, and a slightly inexact angle leaves a
+// residue of A[p][q] about 1e-7 of its size, which later sweeps remove (the
+// convergence test is unchanged).  So tan(angle) is formed in FP32 -- FP64
+// divisions and square roots are long chains of FP64 instructions, which on
+// this GPU run at a small fraction of the FP32 rate -- from
+// theta = (A[q][q] - A[p][p]) / (2 A[p][q]) as t = sign(theta) /
+// (|theta| + sqrt(theta^2 + 1)); a theta beyond the FP32 range gives t = 0
+// (then |A[p][q]| < 1e-38 |A[q][q] - A[p][p]|, negligible).
+__device__ __forceinline__ void jacobi_angle(double app, double aqq, double apq, double &c, double &s)
+{
+    const float theta = (float)(aqq - app) / (2.0f * (float)apq);
+    const float at = fabsf(theta);
+    float tf = 1.0f / (at + sqrtf(fmaf(at, at, 1.0f)));
+    if (!(at < 1e30f))
+        tf = 0.0f;
+    const double t = theta >= 0.0f ? (double)tf : -(double)tf;
+    c = rsqrt(fma(t, t, 1.0));
+    s = t * c;
+}
+
 // Cyclic Jacobi: A (n x n, row-major, symmetric) is diagonalised in place,
 // V receives the eigenvectors as columns; then both are sorted by eigenvalue,
 // ascending.  One thread.
@@ -317,9 +340,8 @@ __device__ void jacobi_eigen(double *A, double *V, double *ev, int n)
                 const double apq = A[p * n + q];
                 if (apq == 0.0)
                     continue;
-                const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
-                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                double c, s;
+                jacobi_angle(A[p * n + p], A[q * n + q], apq, c, s);
                 for (int k = 0; k < n; ++k) {   // columns p, q
                     const double akp = A[k * n + p], akq = A[k * n + q];
                     A[k * n + p] = c * akp - s * akq;
@@ -357,46 +379,57 @@ __device__ void jacobi_eigen(double *A, double *V, double *ev, int n)
     }
 }
 
-// The same decomposition on one warp for even n <= 16 (the 12 x 12 normal
-// matrix of Eq. 6).  FP64 runs at a small fraction of the FP32 rate on this
-// GPU, so the serial form above spends milliseconds on it; here a sweep is
-// n - 1 rounds of n / 2 disjoint rotations (the round-robin ordering: pairs
-// (r, n - 1) and ((r + i) mod (n - 1), (r - i) mod (n - 1)), i = 1 .. n/2 - 1),
-// each round's angles taken from the matrix before it (the subproblems of
-// disjoint pairs are independent), then the columns, the rows and the
-// eigenvector columns updated with one element pair per lane.  Same
-// convergence test and ascending order as jacobi_eigen; A, V, ev in shared
-// memory; every lane of the warp calls it.
-__device__ void jacobi_eigen_warp(double *A, double *V, double *ev, int n)
+// The same decomposition on three warps (threads 0-95, which all call it)
+// for even n <= 16: the 12 x 12 normal matrix of Eq. 6.  A sweep is n - 1
+// rounds of n / 2 disjoint rotations (the round-robin ordering: pairs
+// (r, n - 1) and ((r + i) mod (n - 1), (r - i) mod (n - 1)), i = 1 ..
+// n/2 - 1); each round's angles come from the matrix before it (the 2 x 2
+// subproblems of disjoint pairs are independent), then the columns and the
+// eigenvector columns, and then the rows, are updated with one element pair
+// per thread.  The three warps run on three schedulers, whose FP64 units
+// work in parallel; they meet at named barrier 1.  Same convergence test and
+// ascending order as jacobi_eigen; A, V, ev in shared memory.
+__device__ __forceinline__ void bar_jacobi()
 {
-    __shared__ double rc[8], rs[8];
+    asm volatile("bar.sync 1, 96;" ::: "memory");
+}
+
+__device__ void jacobi_eigen_warps(double *A, double *V, double *ev, int n)
+{
+    __shared__ double rc[8], rs[8], conv[2];
     __shared__ int rp[8], rq[8];
     const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31, half = n / 2, m = n - 1;
-    for (int e = lane; e < n * n; e += 32)
+    const int tid = threadIdx.x, half = n / 2, m = n - 1, np = n * half;
+    for (int e = tid; e < n * n; e += 96)
         V[e] = e / n == e % n ? 1.0 : 0.0;
-    __syncwarp();
+    bar_jacobi();
     for (int sweep = 0; sweep < 60; ++sweep) {
-        double off = 0.0, diag = 0.0;
-        for (int e = lane; e < n * n; e += 32) {
-            const int r = e / n, c = e % n;
-            if (r == c)
-                diag += A[e] * A[e];
-            else if (r < c)
-                off += A[e] * A[e];
+        if (tid < 32) {   // convergence sums on warp 0
+            double off = 0.0, diag = 0.0;
+            for (int e = tid; e < n * n; e += 32) {
+                const int r = e / n, c = e % n;
+                if (r == c)
+                    diag += A[e] * A[e];
+                else if (r < c)
+                    off += A[e] * A[e];
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                off += __shfl_xor_sync(full, off, o);
+                diag += __shfl_xor_sync(full, diag, o);
+            }
+            if (tid == 0) {
+                conv[0] = off;
+                conv[1] = diag;
+            }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            off += __shfl_xor_sync(full, off, o);
-            diag += __shfl_xor_sync(full, diag, o);
-        }
-        off = __shfl_sync(full, off, 0);   // one value for every lane
-        diag = __shfl_sync(full, diag, 0);
+        bar_jacobi();
+        const double off = conv[0], diag = conv[1];
         if (off <= 1e-30 * diag || off == 0.0)
             break;
         for (int r = 0; r < m; ++r) {
-            if (lane < half) {
-                int p = lane == 0 ? r : (r + lane) % m;
-                int q = lane == 0 ? m : (r - lane + m) % m;
+            if (tid < half) {
+                int p = tid == 0 ? r : (r + tid) % m;
+                int q = tid == 0 ? m : (r - tid + m) % m;
                 if (p > q) {
                     const int t = p;
                     p = q;
@@ -404,65 +437,57 @@ __device__ void jacobi_eigen_warp(double *A, double *V, double *ev, int n)
                 }
                 const double apq = A[p * n + q];
                 double c = 1.0, sn = 0.0;
-                if (apq != 0.0) {
-                    const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
-                    const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                    c = 1.0 / sqrt(t * t + 1.0);
-                    sn = t * c;
-                }
-                rc[lane] = c;
-                rs[lane] = sn;
-                rp[lane] = p;
-                rq[lane] = q;
+                if (apq != 0.0)
+                    jacobi_angle(A[p * n + p], A[q * n + q], apq, c, sn);
+                rc[tid] = c;
+                rs[tid] = sn;
+                rp[tid] = p;
+                rq[tid] = q;
             }
-            __syncwarp();
-            for (int e = lane; e < n * half; e += 32) {   // columns p, q of every row
-                const int k = e / half, i = e % half, p = rp[i], q = rq[i];
+            bar_jacobi();
+            // columns p, q of every row of A, and of V
+            for (int e = tid; e < 2 * np; e += 96) {
+                double *M = e < np ? A : V;
+                const int f = e < np ? e : e - np;
+                const int k = f / half, i = f % half, p = rp[i], q = rq[i];
                 const double c = rc[i], sn = rs[i];
-                const double akp = A[k * n + p], akq = A[k * n + q];
-                A[k * n + p] = c * akp - sn * akq;
-                A[k * n + q] = sn * akp + c * akq;
+                const double mkp = M[k * n + p], mkq = M[k * n + q];
+                M[k * n + p] = c * mkp - sn * mkq;
+                M[k * n + q] = sn * mkp + c * mkq;
             }
-            __syncwarp();
-            for (int e = lane; e < n * half; e += 32) {   // rows p, q
+            bar_jacobi();
+            for (int e = tid; e < np; e += 96) {   // rows p, q of A
                 const int i = e / n, k = e % n, p = rp[i], q = rq[i];
                 const double c = rc[i], sn = rs[i];
                 const double apk = A[p * n + k], aqk = A[q * n + k];
                 A[p * n + k] = c * apk - sn * aqk;
                 A[q * n + k] = sn * apk + c * aqk;
             }
-            for (int e = lane; e < n * half; e += 32) {   // eigenvector columns
-                const int k = e / half, i = e % half, p = rp[i], q = rq[i];
-                const double c = rc[i], sn = rs[i];
-                const double vkp = V[k * n + p], vkq = V[k * n + q];
-                V[k * n + p] = c * vkp - sn * vkq;
-                V[k * n + q] = sn * vkp + c * vkq;
-            }
-            __syncwarp();
+            bar_jacobi();
         }
     }
-    for (int i = lane; i < n; i += 32)
+    for (int i = tid; i < n; i += 96)
         ev[i] = A[i * n + i];
-    __syncwarp();
-    for (int i = 0; i < n; ++i) {   // selection sort, ascending (the same choice on every lane)
+    bar_jacobi();
+    for (int i = 0; i < n; ++i) {   // selection sort, ascending (the same choice on every thread)
         int mi = i;
         for (int j = i + 1; j < n; ++j)
             if (ev[j] < ev[mi])
                 mi = j;
-        __syncwarp();
+        bar_jacobi();
         if (mi != i) {
-            if (lane < n) {
-                const double v = V[lane * n + i];
-                V[lane * n + i] = V[lane * n + mi];
-                V[lane * n + mi] = v;
+            if (tid < n) {
+                const double v = V[tid * n + i];
+                V[tid * n + i] = V[tid * n + mi];
+                V[tid * n + mi] = v;
             }
-            if (lane == 0) {
+            if (tid == 0) {
                 const double t = ev[i];
                 ev[i] = ev[mi];
                 ev[mi] = t;
             }
         }
-        __syncwarp();
+        bar_jacobi();
     }
 }
 
@@ -812,7 +837,7 @@ __device__ void epnp_solve(const EpnpArgs &a, const unsigned char *inl, EpnpShar
                 v[t++] += r1[r] * r1[c] + r2[r] * r2[c];
     }
     block_sum(v, 78, red);
-    if (threadIdx.x < 32) {   // warp 0
+    if (threadIdx.x < 96) {   // warps 0-2
         double *MtM = sh.scratch, *Vm = sh.scratch + 144, *ev = sh.scratch + 288;
         if (threadIdx.x == 0) {
             int t = 0;
@@ -823,8 +848,8 @@ __device__ void epnp_solve(const EpnpArgs &a, const unsigned char *inl, EpnpShar
                     ++t;
                 }
         }
-        __syncwarp();
-        jacobi_eigen_warp(MtM, Vm, ev, 12);
+        bar_jacobi();
+        jacobi_eigen_warps(MtM, Vm, ev, 12);
         if (threadIdx.x == 0) {
             for (int r = 0; r < 12; ++r)
                 for (int k = 0; k < 4; ++k)
@@ -833,9 +858,12 @@ __device__ void epnp_solve(const EpnpArgs &a, const unsigned char *inl, EpnpShar
         }
     }
     __syncthreads();
-    for (int cand = 0; cand < 3; ++cand) {
-        __shared__ double betas[4];
-        if (threadIdx.x == 0) {
+    // the betas of the three candidates (N = 1, 2, 3), one per warp: their
+    // serial FP64 chains run side by side on three schedulers
+    __shared__ double betas_c[3][4];
+    if ((threadIdx.x & 31) == 0 && threadIdx.x < 96) {
+        const int cand = threadIdx.x >> 5;
+        {
             double vd[4][6][3];
             for (int k = 0; k < 4; ++k)
                 for (int p = 0; p < 6; ++p)
@@ -886,10 +914,12 @@ __device__ void epnp_solve(const EpnpArgs &a, const unsigned char *inl, EpnpShar
             }
             gauss_newton(b, sh);
             for (int k = 0; k < 4; ++k)
-                betas[k] = b[k];
+                betas_c[cand][k] = b[k];
         }
-        __syncthreads();
-        pose_from_betas(a, inl, betas, sh, red);
+    }
+    __syncthreads();
+    for (int cand = 0; cand < 3; ++cand) {
+        pose_from_betas(a, inl, betas_c[cand], sh, red);
         if (threadIdx.x == 0 && sh.err < sh.besterr) {
             sh.besterr = sh.err;
             for (int k = 0; k < 9; ++k)
