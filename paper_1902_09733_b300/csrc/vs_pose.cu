@@ -576,132 +576,160 @@ struct EpnpShared {
     double Cinv[3][3];     // inverse of [c1 - c0, c2 - c0, c3 - c0]
     double V4[12][4];      // the four null-space directions
     double dw[6];          // squared control-point distances
-    double R[9], T[3], err;
+    double R[3][9], T[3][3], err[3];   // the pose of each beta candidate
     double bestR[9], bestT[3], besterr;
     double scratch[144 + 144 + 12];
     int ninl;
 };
 
-// Pose of the current betas: control points and points in the camera frame,
-// orthogonal Procrustes, mean reprojection error -- all threads.
-__device__ void pose_from_betas(const EpnpArgs &a, const unsigned char *inl, const double *betas, EpnpShared &sh,
-                                double *red)
+// Orthogonal Procrustes for Eq. 7 from the sums of one candidate (v: the
+// sums of the camera points (3), of the world points (3), of their outer
+// products (9) and the point count): R, T with camera = R world + T.  One
+// thread.
+__device__ void procrustes(const double *v, double *R, double *T)
 {
-    double cc[12];
-    for (int r = 0; r < 12; ++r)
-        cc[r] = betas[0] * sh.V4[r][0] + betas[1] * sh.V4[r][1] + betas[2] * sh.V4[r][2] + betas[3] * sh.V4[r][3];
+    const double m = v[15];
+    double mc[3], mw[3], H[9];
+    for (int c = 0; c < 3; ++c) {
+        mc[c] = v[c] / m;
+        mw[c] = v[3 + c] / m;
+    }
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            H[3 * r + c] = v[6 + 3 * r + c] - m * mc[r] * mw[c];
+    // H = U S V^T: V from the eigenvectors of H^T H, U = H V / s, R = U D V^T
+    double HtH[9], Vv[9], ev[3];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            HtH[3 * r + c] = H[r] * H[c] + H[3 + r] * H[3 + c] + H[6 + r] * H[6 + c];
+    jacobi_eigen(HtH, Vv, ev, 3);
+    // descending singular values: columns 2, 1, 0 of Vv
+    double Vd[9], U[9];
+    for (int k = 0; k < 3; ++k)
+        for (int r = 0; r < 3; ++r)
+            Vd[3 * r + k] = Vv[3 * r + (2 - k)];
+    for (int k = 0; k < 2; ++k) {
+        double u[3], nrm = 0.0;
+        for (int r = 0; r < 3; ++r)
+            u[r] = H[3 * r] * Vd[k] + H[3 * r + 1] * Vd[3 + k] + H[3 * r + 2] * Vd[6 + k];
+        for (int j = 0; j < k; ++j) {   // Gram-Schmidt against the earlier columns
+            const double d = u[0] * U[j] + u[1] * U[3 + j] + u[2] * U[6 + j];
+            for (int r = 0; r < 3; ++r)
+                u[r] -= d * U[3 * r + j];
+        }
+        for (int r = 0; r < 3; ++r)
+            nrm += u[r] * u[r];
+        nrm = sqrt(nrm);
+        for (int r = 0; r < 3; ++r)
+            U[3 * r + k] = nrm > 0.0 ? u[r] / nrm : (r == k ? 1.0 : 0.0);
+    }
+    // third column: the cross product (a right-handed U), then the determinant of U V^T
+    U[2] = U[3] * U[7] - U[6] * U[4];
+    U[5] = U[6] * U[1] - U[0] * U[7];
+    U[8] = U[0] * U[4] - U[3] * U[1];
+    const double detV = Vd[0] * (Vd[4] * Vd[8] - Vd[5] * Vd[7]) - Vd[1] * (Vd[3] * Vd[8] - Vd[5] * Vd[6]) +
+                        Vd[2] * (Vd[3] * Vd[7] - Vd[4] * Vd[6]);
+    // U right-handed: det(U V^T) = det V; the reflection fix flips the last singular pair
+    const double dl = detV >= 0.0 ? 1.0 : -1.0;
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            R[3 * r + c] = U[3 * r] * Vd[3 * c] + U[3 * r + 1] * Vd[3 * c + 1] + dl * U[3 * r + 2] * Vd[3 * c + 2];
+    for (int r = 0; r < 3; ++r)
+        T[r] = mc[r] - (R[3 * r] * mw[0] + R[3 * r + 1] * mw[1] + R[3 * r + 2] * mw[2]);
+}
+
+// The alphas of point i: its barycentric coordinates in the control points.
+__device__ __forceinline__ void point_alphas(const EpnpArgs &a, const EpnpShared &sh, int i, double (&al)[4])
+{
+    const double d[3] = {a.P[3 * i] - sh.cw[0][0], a.P[3 * i + 1] - sh.cw[0][1], a.P[3 * i + 2] - sh.cw[0][2]};
+    for (int k = 0; k < 3; ++k)
+        al[k + 1] = sh.Cinv[k][0] * d[0] + sh.Cinv[k][1] * d[1] + sh.Cinv[k][2] * d[2];
+    al[0] = 1.0 - al[1] - al[2] - al[3];
+}
+
+// Poses of the three beta candidates: control points and points in the
+// camera frame, orthogonal Procrustes, mean reprojection error -- all
+// threads, each pass over the points serving the three candidates (the
+// alphas of a point once), the three Procrustes solutions on warps 0-2.
+__device__ void pose_from_betas3(const EpnpArgs &a, const unsigned char *inl, const double (*betas)[4],
+                                 EpnpShared &sh, double *red)
+{
+    double cc[3][12];
+    for (int c = 0; c < 3; ++c)
+        for (int r = 0; r < 12; ++r)
+            cc[c][r] = betas[c][0] * sh.V4[r][0] + betas[c][1] * sh.V4[r][1] + betas[c][2] * sh.V4[r][2] +
+                       betas[c][3] * sh.V4[r][3];
     // the sign: most points in front of the camera
-    double v[16];
-    v[0] = 0.0;
+    double v[48];
+    for (int c = 0; c < 3; ++c)
+        v[c] = 0.0;
     for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
         if (!inl[i])
             continue;
         double al[4];
-        const double d[3] = {a.P[3 * i] - sh.cw[0][0], a.P[3 * i + 1] - sh.cw[0][1], a.P[3 * i + 2] - sh.cw[0][2]};
-        for (int k = 0; k < 3; ++k)
-            al[k + 1] = sh.Cinv[k][0] * d[0] + sh.Cinv[k][1] * d[1] + sh.Cinv[k][2] * d[2];
-        al[0] = 1.0 - al[1] - al[2] - al[3];
-        const double z = al[0] * cc[2] + al[1] * cc[5] + al[2] * cc[8] + al[3] * cc[11];
-        v[0] += z < 0.0 ? 1.0 : -1.0;
+        point_alphas(a, sh, i, al);
+        for (int c = 0; c < 3; ++c) {
+            const double z = al[0] * cc[c][2] + al[1] * cc[c][5] + al[2] * cc[c][8] + al[3] * cc[c][11];
+            v[c] += z < 0.0 ? 1.0 : -1.0;
+        }
     }
-    block_sum(v, 1, red);
-    const double sgn = v[0] > 0.0 ? -1.0 : 1.0;   // more negative than positive depths: flip
-    for (int r = 0; r < 12; ++r)
-        cc[r] *= sgn;
+    block_sum(v, 3, red);
+    for (int c = 0; c < 3; ++c) {
+        const double sgn = v[c] > 0.0 ? -1.0 : 1.0;   // more negative than positive depths: flip
+        for (int r = 0; r < 12; ++r)
+            cc[c][r] *= sgn;
+    }
     // centroids and the cross-covariance of camera and world points
-    for (int k = 0; k < 16; ++k)
+    for (int k = 0; k < 48; ++k)
         v[k] = 0.0;
     for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
         if (!inl[i])
             continue;
         double al[4];
-        const double d[3] = {a.P[3 * i] - sh.cw[0][0], a.P[3 * i + 1] - sh.cw[0][1], a.P[3 * i + 2] - sh.cw[0][2]};
-        for (int k = 0; k < 3; ++k)
-            al[k + 1] = sh.Cinv[k][0] * d[0] + sh.Cinv[k][1] * d[1] + sh.Cinv[k][2] * d[2];
-        al[0] = 1.0 - al[1] - al[2] - al[3];
-        double pc[3];
-        for (int c = 0; c < 3; ++c)
-            pc[c] = al[0] * cc[c] + al[1] * cc[3 + c] + al[2] * cc[6 + c] + al[3] * cc[9 + c];
+        point_alphas(a, sh, i, al);
         const double *pw = a.P + 3 * i;
         for (int c = 0; c < 3; ++c) {
-            v[c] += pc[c];
-            v[3 + c] += pw[c];
+            double pc[3];
+            for (int k = 0; k < 3; ++k)
+                pc[k] = al[0] * cc[c][k] + al[1] * cc[c][3 + k] + al[2] * cc[c][6 + k] + al[3] * cc[c][9 + k];
+            double *w = v + 16 * c;
+            for (int k = 0; k < 3; ++k) {
+                w[k] += pc[k];
+                w[3 + k] += pw[k];
+            }
+            for (int r = 0; r < 3; ++r)
+                for (int k = 0; k < 3; ++k)
+                    w[6 + 3 * r + k] += pc[r] * pw[k];
+            w[15] += 1.0;
         }
-        for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c)
-                v[6 + 3 * r + c] += pc[r] * pw[c];
-        v[15] += 1.0;
     }
-    block_sum(v, 16, red);
-    if (threadIdx.x == 0) {
-        const double m = v[15];
-        double mc[3], mw[3], H[9];
-        for (int c = 0; c < 3; ++c) {
-            mc[c] = v[c] / m;
-            mw[c] = v[3 + c] / m;
-        }
-        for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c)
-                H[3 * r + c] = v[6 + 3 * r + c] - m * mc[r] * mw[c];
-        // H = U S V^T: V from the eigenvectors of H^T H, U = H V / s, R = U D V^T
-        double HtH[9], Vv[9], ev[3];
-        for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c)
-                HtH[3 * r + c] = H[r] * H[c] + H[3 + r] * H[3 + c] + H[6 + r] * H[6 + c];
-        jacobi_eigen(HtH, Vv, ev, 3);
-        // descending singular values: columns 2, 1, 0 of Vv
-        double Vd[9], U[9];
-        for (int k = 0; k < 3; ++k)
-            for (int r = 0; r < 3; ++r)
-                Vd[3 * r + k] = Vv[3 * r + (2 - k)];
-        for (int k = 0; k < 2; ++k) {
-            double u[3], nrm = 0.0;
-            for (int r = 0; r < 3; ++r) {
-                u[r] = H[3 * r] * Vd[k] + H[3 * r + 1] * Vd[3 + k] + H[3 * r + 2] * Vd[6 + k];
-            }
-            for (int j = 0; j < k; ++j) {   // Gram-Schmidt against the earlier columns
-                const double d = u[0] * U[j] + u[1] * U[3 + j] + u[2] * U[6 + j];
-                for (int r = 0; r < 3; ++r)
-                    u[r] -= d * U[3 * r + j];
-            }
-            for (int r = 0; r < 3; ++r)
-                nrm += u[r] * u[r];
-            nrm = sqrt(nrm);
-            for (int r = 0; r < 3; ++r)
-                U[3 * r + k] = nrm > 0.0 ? u[r] / nrm : (r == k ? 1.0 : 0.0);
-        }
-        // third column: the cross product (a right-handed U), then the determinant of U V^T
-        U[2] = U[3] * U[7] - U[6] * U[4];
-        U[5] = U[6] * U[1] - U[0] * U[7];
-        U[8] = U[0] * U[4] - U[3] * U[1];
-        const double detV = Vd[0] * (Vd[4] * Vd[8] - Vd[5] * Vd[7]) - Vd[1] * (Vd[3] * Vd[8] - Vd[5] * Vd[6]) +
-                            Vd[2] * (Vd[3] * Vd[7] - Vd[4] * Vd[6]);
-        // U right-handed: det(U V^T) = det V; the reflection fix flips the last singular pair
-        const double dl = detV >= 0.0 ? 1.0 : -1.0;
-        for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c)
-                sh.R[3 * r + c] = U[3 * r] * Vd[3 * c] + U[3 * r + 1] * Vd[3 * c + 1] + dl * U[3 * r + 2] * Vd[3 * c + 2];
-        for (int r = 0; r < 3; ++r)
-            sh.T[r] = mc[r] - (sh.R[3 * r] * mw[0] + sh.R[3 * r + 1] * mw[1] + sh.R[3 * r + 2] * mw[2]);
+    block_sum(v, 48, red);
+    if ((threadIdx.x & 31) == 0 && threadIdx.x < 96) {
+        const int c = threadIdx.x >> 5;
+        procrustes(v + 16 * c, sh.R[c], sh.T[c]);
     }
     __syncthreads();
-    // mean reprojection error
-    v[0] = 0.0;
-    v[1] = 0.0;
+    // mean reprojection errors
+    for (int k = 0; k < 6; ++k)
+        v[k] = 0.0;
     for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
         if (!inl[i])
             continue;
         const double *pw = a.P + 3 * i;
-        double pc[3];
-        for (int r = 0; r < 3; ++r)
-            pc[r] = sh.R[3 * r] * pw[0] + sh.R[3 * r + 1] * pw[1] + sh.R[3 * r + 2] * pw[2] + sh.T[r];
-        const double du = a.fx * pc[0] / pc[2] + a.cx - a.uv[2 * i], dv = a.fy * pc[1] / pc[2] + a.cy - a.uv[2 * i + 1];
-        v[0] += sqrt(du * du + dv * dv);
-        v[1] += 1.0;
+        for (int c = 0; c < 3; ++c) {
+            double pc[3];
+            for (int r = 0; r < 3; ++r)
+                pc[r] = sh.R[c][3 * r] * pw[0] + sh.R[c][3 * r + 1] * pw[1] + sh.R[c][3 * r + 2] * pw[2] + sh.T[c][r];
+            const double du = a.fx * pc[0] / pc[2] + a.cx - a.uv[2 * i];
+            const double dv = a.fy * pc[1] / pc[2] + a.cy - a.uv[2 * i + 1];
+            v[2 * c] += sqrt(du * du + dv * dv);
+            v[2 * c + 1] += 1.0;
+        }
     }
-    block_sum(v, 2, red);
+    block_sum(v, 6, red);
     if (threadIdx.x == 0)
-        sh.err = v[0] / v[1];
+        for (int c = 0; c < 3; ++c)
+            sh.err[c] = v[2 * c] / v[2 * c + 1];
     __syncthreads();
 }
 
@@ -809,43 +837,46 @@ __device__ void epnp_solve(const EpnpArgs &a, const unsigned char *inl, EpnpShar
         }
     }
     __syncthreads();
-    // the 12 x 12 normal matrix of Eq. 6 (upper triangle, 78 entries)
-    for (int k = 0; k < 78; ++k)
+    // the 12 x 12 normal matrix of Eq. 6.  Its 3 x 3 block (j, k) is
+    //   sum al_j al_k [[1, 0, -u], [0, 1, -v], [-u, -v, u^2 + v^2]]
+    // (u, v: normalised image coordinates), so four sums per pair j <= k of
+    // control points -- 40 in all -- give every entry.
+    for (int k = 0; k < 40; ++k)
         v[k] = 0.0;
+    const double inv_fx = 1.0 / a.fx, inv_fy = 1.0 / a.fy;
     for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
         if (!inl[i])
             continue;
         double al[4];
-        const double d[3] = {a.P[3 * i] - sh.cw[0][0], a.P[3 * i + 1] - sh.cw[0][1], a.P[3 * i + 2] - sh.cw[0][2]};
-        for (int k = 0; k < 3; ++k)
-            al[k + 1] = sh.Cinv[k][0] * d[0] + sh.Cinv[k][1] * d[1] + sh.Cinv[k][2] * d[2];
-        al[0] = 1.0 - al[1] - al[2] - al[3];
+        point_alphas(a, sh, i, al);
         // the two equations of Eq. 6 divided by fx and fy (normalised image coordinates)
-        const double un = (a.uv[2 * i] - a.cx) / a.fx, vn = (a.uv[2 * i + 1] - a.cy) / a.fy;
-        double r1[12], r2[12];
-        for (int j = 0; j < 4; ++j) {
-            r1[3 * j] = al[j];
-            r1[3 * j + 1] = 0.0;
-            r1[3 * j + 2] = -al[j] * un;
-            r2[3 * j] = 0.0;
-            r2[3 * j + 1] = al[j];
-            r2[3 * j + 2] = -al[j] * vn;
-        }
+        const double un = (a.uv[2 * i] - a.cx) * inv_fx, vn = (a.uv[2 * i + 1] - a.cy) * inv_fy;
+        const double w2 = un * un + vn * vn;
         int t = 0;
-        for (int r = 0; r < 12; ++r)
-            for (int c = r; c < 12; ++c)
-                v[t++] += r1[r] * r1[c] + r2[r] * r2[c];
+        for (int j = 0; j < 4; ++j)
+            for (int k = j; k < 4; ++k, ++t) {
+                const double pjk = al[j] * al[k];
+                v[t] += pjk;
+                v[10 + t] += pjk * un;
+                v[20 + t] += pjk * vn;
+                v[30 + t] += pjk * w2;
+            }
     }
-    block_sum(v, 78, red);
+    block_sum(v, 40, red);
     if (threadIdx.x < 96) {   // warps 0-2
         double *MtM = sh.scratch, *Vm = sh.scratch + 144, *ev = sh.scratch + 288;
         if (threadIdx.x == 0) {
             int t = 0;
-            for (int r = 0; r < 12; ++r)
-                for (int c = r; c < 12; ++c) {
-                    MtM[12 * r + c] = v[t];
-                    MtM[12 * c + r] = v[t];
-                    ++t;
+            for (int j = 0; j < 4; ++j)
+                for (int k = j; k < 4; ++k, ++t) {
+                    const double blk[3][3] = {{v[t], 0.0, -v[10 + t]},
+                                              {0.0, v[t], -v[20 + t]},
+                                              {-v[10 + t], -v[20 + t], v[30 + t]}};
+                    for (int r = 0; r < 3; ++r)
+                        for (int c = 0; c < 3; ++c) {
+                            MtM[12 * (3 * j + r) + 3 * k + c] = blk[r][c];
+                            MtM[12 * (3 * k + c) + 3 * j + r] = blk[r][c];
+                        }
                 }
         }
         bar_jacobi();
@@ -918,17 +949,17 @@ __device__ void epnp_solve(const EpnpArgs &a, const unsigned char *inl, EpnpShar
         }
     }
     __syncthreads();
-    for (int cand = 0; cand < 3; ++cand) {
-        pose_from_betas(a, inl, betas_c[cand], sh, red);
-        if (threadIdx.x == 0 && sh.err < sh.besterr) {
-            sh.besterr = sh.err;
-            for (int k = 0; k < 9; ++k)
-                sh.bestR[k] = sh.R[k];
-            for (int k = 0; k < 3; ++k)
-                sh.bestT[k] = sh.T[k];
-        }
-        __syncthreads();
-    }
+    pose_from_betas3(a, inl, betas_c, sh, red);
+    if (threadIdx.x == 0)
+        for (int cand = 0; cand < 3; ++cand)   // in order: the first of equal errors wins
+            if (sh.err[cand] < sh.besterr) {
+                sh.besterr = sh.err[cand];
+                for (int k = 0; k < 9; ++k)
+                    sh.bestR[k] = sh.R[cand][k];
+                for (int k = 0; k < 3; ++k)
+                    sh.bestT[k] = sh.T[cand][k];
+            }
+    __syncthreads();
 }
 
 __global__ void __launch_bounds__(kEpnpThreads) k_epnp(EpnpArgs a)
