@@ -733,28 +733,49 @@ __device__ void pose_from_betas3(const EpnpArgs &a, const unsigned char *inl, co
     __syncthreads();
 }
 
-// Gauss-Newton on the four betas: the six squared control-point distances.
-__device__ void gauss_newton(double *b, const EpnpShared &sh)
+// Gauss-Newton on the four betas: the six squared control-point distances,
+// on one warp (every lane calls it with the same b).  Lane p < 6 forms the
+// residual and Jacobian row of pair p; the 10 distinct entries of the
+// normal matrix and the 4 right sides are summed over lanes 0-7 (6 and 7
+// add zeros) by a butterfly and taken from lane 0, so every lane solves the
+// same 4 x 4 system and b stays the same on all of them.
+__device__ void gauss_newton_warp(double *b, const EpnpShared &sh)
 {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    double vd[4][3] = {};
+    double dwp = 0.0;
+    if (lane < 6) {
+        const int i = kPairI[lane], j = kPairJ[lane];
+        for (int k = 0; k < 4; ++k)
+            for (int c = 0; c < 3; ++c)
+                vd[k][c] = sh.V4[3 * i + c][k] - sh.V4[3 * j + c][k];
+        dwp = sh.dw[lane];
+    }
+    auto sum8 = [&](double v) {
+        v += __shfl_xor_sync(full, v, 1);
+        v += __shfl_xor_sync(full, v, 2);
+        v += __shfl_xor_sync(full, v, 4);
+        return __shfl_sync(full, v, 0);
+    };
     for (int it = 0; it < 5; ++it) {
-        double N[16] = {0}, g[4] = {0};
-        for (int p = 0; p < 6; ++p) {
-            const int i = kPairI[p], j = kPairJ[p];
-            double vd[4][3], d[3];
-            for (int k = 0; k < 4; ++k)
-                for (int c = 0; c < 3; ++c)
-                    vd[k][c] = sh.V4[3 * i + c][k] - sh.V4[3 * j + c][k];
+        double J[4] = {0.0, 0.0, 0.0, 0.0}, res = 0.0;
+        if (lane < 6) {
+            double d[3];
             for (int c = 0; c < 3; ++c)
                 d[c] = b[0] * vd[0][c] + b[1] * vd[1][c] + b[2] * vd[2][c] + b[3] * vd[3][c];
-            const double res = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] - sh.dw[p];
-            double J[4];
+            res = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] - dwp;
             for (int k = 0; k < 4; ++k)
                 J[k] = 2.0 * (d[0] * vd[k][0] + d[1] * vd[k][1] + d[2] * vd[k][2]);
-            for (int r = 0; r < 4; ++r) {
-                for (int c = 0; c < 4; ++c)
-                    N[4 * r + c] += J[r] * J[c];
-                g[r] -= J[r] * res;
+        }
+        double N[16], g[4];
+        for (int r = 0; r < 4; ++r) {
+            for (int c = r; c < 4; ++c) {
+                const double v = sum8(J[r] * J[c]);
+                N[4 * r + c] = v;
+                N[4 * c + r] = v;
             }
+            g[r] = sum8(-J[r] * res);
         }
         double step[4];
         solve_small(N, g, step, 4);
@@ -892,9 +913,10 @@ __device__ void epnp_solve(const EpnpArgs &a, const unsigned char *inl, EpnpShar
     // the betas of the three candidates (N = 1, 2, 3), one per warp: their
     // serial FP64 chains run side by side on three schedulers
     __shared__ double betas_c[3][4];
-    if ((threadIdx.x & 31) == 0 && threadIdx.x < 96) {
-        const int cand = threadIdx.x >> 5;
-        {
+    if (threadIdx.x < 96) {
+        const int cand = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        double b[4] = {0.0, 0.0, 0.0, 0.0};
+        if (lane == 0) {
             double vd[4][6][3];
             for (int k = 0; k < 4; ++k)
                 for (int p = 0; p < 6; ++p)
@@ -903,7 +925,6 @@ __device__ void epnp_solve(const EpnpArgs &a, const unsigned char *inl, EpnpShar
             auto dot = [&](int k, int l, int p) {
                 return vd[k][p][0] * vd[l][p][0] + vd[k][p][1] * vd[l][p][1] + vd[k][p][2] * vd[l][p][2];
             };
-            double b[4] = {0.0, 0.0, 0.0, 0.0};
             if (cand == 0) {   // N = 1
                 double num = 0.0, den = 0.0;
                 for (int p = 0; p < 6; ++p) {
@@ -943,10 +964,13 @@ __device__ void epnp_solve(const EpnpArgs &a, const unsigned char *inl, EpnpShar
                     b[2] = s[3] / b[0];
                 }
             }
-            gauss_newton(b, sh);
+        }
+        for (int k = 0; k < 4; ++k)
+            b[k] = __shfl_sync(0xffffffffu, b[k], 0);
+        gauss_newton_warp(b, sh);
+        if (lane == 0)
             for (int k = 0; k < 4; ++k)
                 betas_c[cand][k] = b[k];
-        }
     }
     __syncthreads();
     pose_from_betas3(a, inl, betas_c, sh, red);
@@ -1006,16 +1030,22 @@ __global__ void __launch_bounds__(kEpnpThreads) k_epnp(EpnpArgs a)
             errs[i] = e;
         }
         __syncthreads();
-        // the median of the usable errors (counting selection, exact).  The
-        // errors are >= 0 or +inf (NaN: unusable), whose bit patterns as
-        // 64-bit integers order as the numbers do, so the counts compare
-        // integers instead of issuing FP64 comparisons.
+        // the median of the usable errors, exact: the errors are >= 0 or +inf
+        // (NaN: unusable), whose bit patterns as 64-bit integers order as the
+        // numbers do, so they are sorted as integers (a bitonic network over
+        // the next power of two, padded with the largest key, in the
+        // reduction scratch) and the middle one or two read off
         const long long *ek = reinterpret_cast<const long long *>(errs);
         constexpr long long kInfBits = 0x7FF0000000000000LL;
-        __shared__ double med, med_hi;
         __shared__ int nusable;
         if (threadIdx.x == 0)
             nusable = 0;
+        long long *key = reinterpret_cast<long long *>(red);   // 80 x blockDim doubles >= kMaxPts
+        int N = 1;
+        while (N < a.n)
+            N <<= 1;
+        for (int i = threadIdx.x; i < N; i += blockDim.x)
+            key[i] = i < a.n ? ek[i] : LLONG_MAX;
         __syncthreads();
         {
             int cnt_u = 0;
@@ -1023,25 +1053,23 @@ __global__ void __launch_bounds__(kEpnpThreads) k_epnp(EpnpArgs a)
                 cnt_u += ek[i] < kInfBits;
             atomicAdd(&nusable, cnt_u);
         }
-        __syncthreads();
-        const int n = nusable;
-        for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
-            const long long ei = ek[i];
-            if (!(ei < kInfBits))
-                continue;
-            int below = 0, equal = 0;
-            for (int j = 0; j < a.n; ++j) {
-                below += ek[j] < ei;
-                equal += ek[j] == ei;
+        for (int k = 2; k <= N; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < N; i += blockDim.x) {
+                    const int l = i ^ j;
+                    if (l > i) {
+                        const long long x = key[i], y = key[l];
+                        if ((x > y) == ((i & k) == 0)) {
+                            key[i] = y;
+                            key[l] = x;
+                        }
+                    }
+                }
+                __syncthreads();
             }
-            // the lower and upper middle values of the sorted errors (equal
-            // values write the same number)
-            if (below <= (n - 1) / 2 && (n - 1) / 2 < below + equal)
-                med = errs[i];
-            if (below <= n / 2 && n / 2 < below + equal)
-                med_hi = errs[i];
-        }
-        __syncthreads();
+        const int n = nusable;
+        const double med = __longlong_as_double(key[(n - 1) / 2]), med_hi = __longlong_as_double(key[n / 2]);
+        __syncthreads();   // the scratch is the reductions' again
         const double thr = fmax(2.0, 3.0 * (0.5 * (med + med_hi)));
         for (int i = threadIdx.x; i < a.n; i += blockDim.x)
             inl[i] = errs[i] < thr;
