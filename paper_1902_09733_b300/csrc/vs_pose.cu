@@ -192,17 +192,32 @@ struct ZssdArgs {
     int64_t *cost;    // n
 };
 
+// One CTA per corner.  With D = I1 - I2 over the patch, exactly in integers,
+//   sum D = sum I1 - sum I2,   sum D^2 = sum I1^2 - 2 sum I1 I2 + sum I2^2,
+// and the three sums over the displaced patch of frame 2 come from dp4a on
+// packed luma bytes: the cross-correlation with the patch of frame 1, the
+// byte sum (dp4a with ones) and the sum of squares (dp4a of a word with
+// itself), four pixels per instruction.  Frame 2's search region is staged
+// as bytes in four copies shifted by 0..3 bytes, so the patch row at any
+// column starts on a word.  The sums of frame 1's patch are taken once.
+constexpr int kZssdWords = (2 * kMaxRadius + 1 + 3) / 4;            // words per patch row
+constexpr int kZssdRegion = 2 * (kMaxSearch + kMaxRadius) + 1;      // region rows and columns
+constexpr int kZssdRegionWords = (2 * kMaxSearch) / 4 + kZssdWords;  // words per shifted region row
+
 __global__ void __launch_bounds__(256) k_zssd(ZssdArgs a)
 {
     pdl_begin();
-    constexpr int kMaxP = 2 * kMaxRadius + 1, kMaxReg = 2 * (kMaxSearch + kMaxRadius) + 1;
-    __shared__ int p1[kMaxP * kMaxP];
-    __shared__ int reg[kMaxReg * kMaxReg];     // frame 2 around the corner, -1 outside the frame
+    __shared__ uint32_t p1w[2 * kMaxRadius + 1][kZssdWords];
+    __shared__ __align__(16) uint8_t reg8[kZssdRegion][4 * (kZssdRegionWords + 1)];   // frame 2 around the corner, 0 outside
+    __shared__ uint32_t r4[4][kZssdRegion][kZssdRegionWords];           // reg8 rows from byte 4w + s
+    __shared__ long long p1sums[2];                                     // sum I1, sum I1^2
     __shared__ long long sz[256];
     __shared__ int sk[256];
     const int ci = blockIdx.x;
     const int x = a.corners[2 * ci], y = a.corners[2 * ci + 1];
     const int r = a.r, S = a.S, P = 2 * r + 1, RG = 2 * (S + r) + 1, ND = (2 * S + 1) * (2 * S + 1);
+    const int WP = (P + 3) / 4, RW = (2 * S) / 4 + WP;
+    const uint32_t lastmask = (P & 3) ? (1u << (8 * (P & 3))) - 1u : 0xFFFFFFFFu;
     const bool ok = x >= r && x < a.W - r && y >= r && y < a.H - r;
     if (!ok) {   // no corner, or its patch leaves frame 1
         if (threadIdx.x == 0) {
@@ -211,33 +226,64 @@ __global__ void __launch_bounds__(256) k_zssd(ZssdArgs a)
         }
         return;
     }
-    for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
-        const int py = i / P, px = i - py * P;
-        p1[i] = luma(a.rgb1 + (size_t)(y - r + py) * a.pitch + 3 * (size_t)(x - r + px));
+    for (int i = threadIdx.x; i < P * kZssdWords; i += blockDim.x) {
+        const int py = i / kZssdWords, w = i - py * kZssdWords;
+        uint32_t v = 0u;
+        for (int b = 0; b < 4; ++b) {
+            const int px = 4 * w + b;
+            if (px < P)
+                v |= (uint32_t)luma(a.rgb1 + (size_t)(y - r + py) * a.pitch + 3 * (size_t)(x - r + px)) << (8 * b);
+        }
+        p1w[py][w] = v;
     }
-    for (int i = threadIdx.x; i < RG * RG; i += blockDim.x) {
-        const int ry = i / RG, rx = i - ry * RG;
+    constexpr int RB = 4 * (kZssdRegionWords + 1);
+    for (int i = threadIdx.x; i < RG * RB; i += blockDim.x) {
+        const int ry = i / RB, rx = i - ry * RB;
         const int xx = x - S - r + rx, yy = y - S - r + ry;
-        reg[i] = (xx >= 0 && xx < a.W && yy >= 0 && yy < a.H) ? luma(a.rgb2 + (size_t)yy * a.pitch + 3 * (size_t)xx)
-                                                             : -1;
+        reg8[ry][rx] = (rx < RG && xx >= 0 && xx < a.W && yy >= 0 && yy < a.H)
+                           ? (uint8_t)luma(a.rgb2 + (size_t)yy * a.pitch + 3 * (size_t)xx)
+                           : (uint8_t)0;
     }
     __syncthreads();
-    const long long npx = (long long)P * P;
+    for (int i = threadIdx.x; i < 4 * RG * RW; i += blockDim.x) {
+        const int s = i / (RG * RW), rem = i - s * RG * RW, ry = rem / RW, w = rem - ry * RW;
+        const uint32_t *row = reinterpret_cast<const uint32_t *>(reg8[ry]);
+        r4[s][ry][w] = __funnelshift_r(row[w], row[w + 1], 8 * s);
+    }
+    if (threadIdx.x == 0) {
+        int s1 = 0, q1 = 0;
+        for (int py = 0; py < P; ++py)
+            for (int w = 0; w < WP; ++w) {
+                s1 = (int)__dp4a(p1w[py][w], 0x01010101u, (unsigned)s1);
+                q1 = (int)__dp4a(p1w[py][w], p1w[py][w], (unsigned)q1);
+            }
+        p1sums[0] = s1;
+        p1sums[1] = q1;
+    }
+    __syncthreads();
+    const long long npx = (long long)P * P, S1 = p1sums[0], Q1 = p1sums[1];
     auto zcost = [&](int dx, int dy) -> long long {   // -1 where the patch leaves frame 2
         const int xx = x + dx, yy = y + dy;
         if (xx < r || xx >= a.W - r || yy < r || yy >= a.H - r)
             return -1;
-        long long s2 = 0, s1 = 0;
+        const int cx = dx + S, cy = dy + S, sh = cx & 3, w0 = cx >> 2;
+        unsigned cross = 0u, s2 = 0u, q2 = 0u;
         for (int py = 0; py < P; ++py) {
-            const int *row = reg + (dy + S + py) * RG + (dx + S);
-            const int *q = p1 + py * P;
-            for (int px = 0; px < P; ++px) {
-                const int d = q[px] - row[px];
-                s2 += d * d;
-                s1 += d;
+            const uint32_t *row = r4[sh][cy + py] + w0;
+            const uint32_t *p = p1w[py];
+#pragma unroll
+            for (int w = 0; w < kZssdWords; ++w) {
+                if (w >= WP)
+                    break;
+                const uint32_t rw = w == WP - 1 ? row[w] & lastmask : row[w];
+                cross = __dp4a(p[w], rw, cross);
+                s2 = __dp4a(rw, 0x01010101u, s2);
+                q2 = __dp4a(rw, rw, q2);
             }
         }
-        return npx * s2 - s1 * s1;
+        const long long sumD = S1 - (long long)s2;
+        const long long sumD2 = Q1 - 2 * (long long)cross + (long long)q2;
+        return npx * sumD2 - sumD * sumD;
     };
     long long best = -1;
     int bk = ND;
