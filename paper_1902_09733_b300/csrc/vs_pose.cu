@@ -440,14 +440,44 @@ __device__ __forceinline__ void bar_jacobi()
     asm volatile("bar.sync 1, 96;" ::: "memory");
 }
 
-__device__ void jacobi_eigen_warps(double *A, double *V, double *ev, int n)
+// warm: V holds an orthogonal matrix on entry (the eigenvectors of a
+// nearby matrix); A is first replaced by V^T A V (T: n x n scratch) and
+// the sweeps start from there, so a matrix close to the earlier one needs
+// fewer of them.  The result is the same decomposition, to rounding.
+__device__ void jacobi_eigen_warps(double *A, double *V, double *ev, int n, bool warm, double *T)
 {
     __shared__ double rc[8], rs[8], conv[2];
     __shared__ int rp[8], rq[8];
     const unsigned full = 0xffffffffu;
     const int tid = threadIdx.x, half = n / 2, m = n - 1, np = n * half;
-    for (int e = tid; e < n * n; e += 96)
-        V[e] = e / n == e % n ? 1.0 : 0.0;
+    if (warm) {
+        for (int e = tid; e < n * n; e += 96) {   // T = A V
+            const int i = e / n, j = e % n;
+            double acc = 0.0;
+            for (int k = 0; k < n; ++k)
+                acc += A[i * n + k] * V[k * n + j];
+            T[e] = acc;
+        }
+        bar_jacobi();
+        for (int e = tid; e < n * n; e += 96) {   // A = V^T T, upper triangle
+            const int i = e / n, j = e % n;
+            if (j < i)
+                continue;
+            double acc = 0.0;
+            for (int k = 0; k < n; ++k)
+                acc += V[k * n + i] * T[k * n + j];
+            A[i * n + j] = acc;
+        }
+        bar_jacobi();
+        for (int e = tid; e < n * n; e += 96) {   // mirrored: A stays exactly symmetric
+            const int i = e / n, j = e % n;
+            if (j < i)
+                A[e] = A[j * n + i];
+        }
+    } else {
+        for (int e = tid; e < n * n; e += 96)
+            V[e] = e / n == e % n ? 1.0 : 0.0;
+    }
     bar_jacobi();
     for (int sweep = 0; sweep < 60; ++sweep) {
         if (tid < 32) {   // convergence sums on warp 0
@@ -624,7 +654,7 @@ struct EpnpShared {
     double dw[6];          // squared control-point distances
     double R[3][9], T[3][3], err[3];   // the pose of each beta candidate
     double bestR[9], bestT[3], besterr;
-    double scratch[144 + 144 + 12];
+    double scratch[144 + 144 + 12 + 144];   // normal matrix, eigenvectors, eigenvalues, temporary
     int ninl;
 };
 
@@ -830,8 +860,9 @@ __device__ void gauss_newton_warp(double *b, const EpnpShared &sh)
     }
 }
 
-// One EPnP solve on the points marked in `inl` (all threads).
-__device__ void epnp_solve(const EpnpArgs &a, const unsigned char *inl, EpnpShared &sh, double *red)
+// One EPnP solve on the points marked in `inl` (all threads); warm: the
+// 12 x 12 eigen-solve starts from the eigenvectors of the previous solve.
+__device__ void epnp_solve(const EpnpArgs &a, const unsigned char *inl, EpnpShared &sh, double *red, bool warm)
 {
     double v[80];
     // centroid and covariance
@@ -947,7 +978,7 @@ __device__ void epnp_solve(const EpnpArgs &a, const unsigned char *inl, EpnpShar
                 }
         }
         bar_jacobi();
-        jacobi_eigen_warps(MtM, Vm, ev, 12);
+        jacobi_eigen_warps(MtM, Vm, ev, 12, warm, sh.scratch + 300);
         if (threadIdx.x == 0) {
             for (int r = 0; r < 12; ++r)
                 for (int k = 0; k < 4; ++k)
@@ -1055,7 +1086,7 @@ __global__ void __launch_bounds__(kEpnpThreads) k_epnp(EpnpArgs a)
                 a.out[k] = k < 13 ? __longlong_as_double(0x7FF8000000000000LL) : cnt[0];
         return;
     }
-    epnp_solve(a, inl, sh, red);
+    epnp_solve(a, inl, sh, red, false);
     if (threadIdx.x == 0)
         sh.ninl = (int)cnt[0];
     __syncthreads();
@@ -1126,7 +1157,7 @@ __global__ void __launch_bounds__(kEpnpThreads) k_epnp(EpnpArgs a)
         block_sum(cnt, 1, red);
         if (cnt[0] < 6.0)
             break;
-        epnp_solve(a, inl, sh, red);
+        epnp_solve(a, inl, sh, red, true);   // the inliers: a nearby normal matrix
         if (threadIdx.x == 0)
             sh.ninl = (int)cnt[0];
         __syncthreads();
