@@ -70,6 +70,28 @@ def test_zssd_costs_exact_and_positions_to_rounding():
     assert np.abs(gp[ok] - wpos[ok]).max() <= 1e-12
 
 
+
+@pytest.mark.parametrize("radius,search", [(1, 0), (2, 3), (3, 7), (8, 32), (6, 32)])
+def test_zssd_patch_and_search_sizes(radius, search):
+    """Patch widths 3 .. 17 (every remainder of the width by 4, so every mask
+    of the last packed word) and searches up to the largest, exact costs;
+    corners near the frame edges whose displaced patches leave frame 2."""
+    f1, f2 = FRAMES[1], FRAMES[2]
+    H, W = f1.shape[:2]
+    p = vs.PoseParams(grid=8, margin=radius + 1, threshold25=0, radius=radius, search=search)
+    corners = opose.harris_corners(opose.harris_response25(f1), 8, radius + 1, 0)
+    corners[0] = (radius, radius)               # at the corner of the frame (patch just inside)
+    corners[1] = (W - 1 - radius, H // 2)       # at the right edge
+    pos, cost = vs.zssd_match(torch.from_numpy(f1).cuda(), torch.from_numpy(f2).cuda(),
+                              torch.from_numpy(corners.astype(np.int32)).cuda(), p)
+    wpos, wcost = opose.zssd_match(f1, f2, corners, radius=radius, search=search)
+    np.testing.assert_array_equal(cost.cpu().numpy(), wcost)
+    gp = pos.cpu().numpy()
+    assert np.array_equal(np.isnan(gp), np.isnan(wpos))
+    ok = ~np.isnan(wpos)
+    assert np.abs(gp[ok] - wpos[ok]).max() <= 1e-12
+
+
 CAM = (1400.0, 1400.0, 1351.5, 759.5)
 
 
@@ -79,7 +101,8 @@ def _rot(axis, ang):
     return np.eye(3) + np.sin(ang) * K + (1 - np.cos(ang)) * K @ K
 
 
-@pytest.mark.parametrize("n,noise,outliers", [(6, 0.0, 0), (50, 0.0, 0), (400, 0.5, 0), (900, 0.3, 40)])
+@pytest.mark.parametrize("n,noise,outliers", [(6, 0.0, 0), (7, 0.2, 0), (50, 0.0, 0), (400, 0.5, 0), (900, 0.3, 40),
+                                              (1025, 0.3, 60), (4096, 0.4, 200)])
 def test_epnp_matches_the_oracle(n, noise, outliers):
     g = np.random.default_rng(n)
     P = np.column_stack([g.uniform(-60, 60, n), g.uniform(-35, 35, n), g.uniform(70, 100, n)])
