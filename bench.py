@@ -563,6 +563,19 @@ def run_smooth(args, vs, synth, torch, dev):
                         "adjoint_achieved": fl_a / (adj_us * 1e-6) / 1e12}
             r["alu"]["forward_frac"] = r["alu"]["forward_achieved"] / fp32_peak
             r["alu"]["adjoint_frac"] = r["alu"]["adjoint_achieved"] / fp32_peak
+            # algorithmic bytes per iteration: forward, per pixel, D and the four
+            # incoming rows read and the four outgoing messages written (9 L
+            # floats); adjoint, the four gradients of the messages it sent and D
+            # plus the four rows it recomputes from read, the four slot
+            # gradients written and dL/dD read and written (15 L floats)
+            pix = W * H
+            fb, ab = 9 * L * 4 * pix, 15 * L * 4 * pix
+            hbm_peak = float(json.load(open(pk_path)).get("hbm_gbs", 6400.0)) if os.path.exists(pk_path) else 6400.0
+            r["hbm"] = {"unit": "GB/s", "peak": hbm_peak, "forward_alg_bytes": fb, "adjoint_alg_bytes": ab,
+                        "forward_achieved": fb / (fwd_us * 1e-6) / 1e9,
+                        "adjoint_achieved": ab / (adj_us * 1e-6) / 1e9}
+            r["hbm"]["forward_frac"] = r["hbm"]["forward_achieved"] / hbm_peak
+            r["hbm"]["adjoint_frac"] = r["hbm"]["adjoint_achieved"] / hbm_peak
         out[fam] = r
     vs.sp_select_kernels("simt")
     out["default_kernels"] = "simt"
