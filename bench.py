@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--batch-pairs", type=int, default=48)
     ap.add_argument("--smooth-reps", type=int, default=20)
     ap.add_argument("--pose-reps", type=int, default=20)
+    ap.add_argument("--small-reps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -582,6 +583,58 @@ def run_smooth(args, vs, synth, torch, dev):
     return out
 
 
+def run_small(args, vs, synth, torch, dev):
+    """The small configuration: BP on a 160x120 grey noise pair, 16 labels,
+    3 levels x 5 iterations (its state sits in L2; the call is latency- and
+    launch-bound).  Per-call latency with CUDA events, 20 warm-up and `reps`
+    timed calls, median and p99, launched eagerly and as one CUDA-graph
+    replay; the oracle on the same pair (DT messages), median of 3, on one
+    thread and on all cores."""
+    left, right, _ = synth.noise_pair(0)
+    p = vs.BPParams(16, 3, 5, 20, 10, 40)
+    L_t, R_t = torch.from_numpy(left).to(dev), torch.from_numpy(right).to(dev)
+    h, w = left.shape
+    ws = torch.empty(vs.bp_workspace_size(w, h, p), dtype=torch.uint8, device=dev)
+    lab = torch.empty((h, w), dtype=torch.uint8, device=dev)
+    st = torch.cuda.Stream(device=dev)
+    call = lambda: vs.bp_stereo(L_t, R_t, p, labels=lab, workspace=ws)
+    with torch.cuda.stream(st):
+        call()
+    torch.cuda.synchronize()
+    gr = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gr, stream=st):
+        call()
+    out = {"workload": "BP 160x120 grey noise pair, 16 labels, 3 levels x 5 iterations", "unit": "us per call",
+           "reps": args.small_reps}
+    for mode, fn in (("eager", call), ("graph", gr.replay)):
+        ts = []
+        with torch.cuda.stream(st):
+            for i in range(20 + args.small_reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                fn()
+                e1.record(st)
+                e1.synchronize()
+                if i >= 20:
+                    ts.append(1e3 * e0.elapsed_time(e1))
+        ts.sort()
+        out[mode] = {"median_us": ts[len(ts) // 2], "p99_us": ts[min(len(ts) - 1, int(0.99 * len(ts)))]}
+    if not args.no_cpu_baseline:
+        import oracle
+        cpu = {}
+        for n in (1, os.cpu_count() or 1):
+            used = oracle_threads(n)
+            tt = []
+            for _ in range(3):
+                t0 = time.perf_counter()
+                oracle.bp(left, right, 16, 3, 5, 20, 10, 40, mode=oracle.MSG_DT)
+                tt.append(time.perf_counter() - t0)
+            cpu[str(used)] = 1e6 * statistics.median(tt)
+        oracle_threads(os.cpu_count() or 1)
+        out["cpu_oracle_us"] = cpu
+    return out
+
+
 def run_pose(args, vs, synth, torch, dev):
     """The pose step (Section 2.3, Eq. 4-7) between frames 300 and 320 of a
     seeded lawnmower flight at 100 m (2704x1520, rendered on the GPU without
@@ -889,6 +942,9 @@ def run_ours(args):
         batched["whole_pairs"] = run_batched_pairs(args, vs, synth, torch, dev, cam)
 
     # smoothed BP + adjoint (the differentiable relaxation of Eq. 1)
+    small = None
+    if args.small_reps > 0 and rank == 0:
+        small = run_small(args, vs, synth, torch, dev)
     pose = None
     if args.pose_reps > 0 and rank == 0:
         pose = run_pose(args, vs, synth, torch, dev)
@@ -950,6 +1006,7 @@ def run_ours(args):
             "batched": batched,
             "smooth_bp": smooth,
             "pose": pose,
+            "small_config": small,
             "gpu_launches": launches_per_step * K,
             "pairs_per_step": P,
             "clocks": clk,
