@@ -847,6 +847,30 @@ def run_ours(args):
     if recs:
         tot = sum(ms for _, ms in recs)
         kernel_share = {k: round(sum(v) / tot, 4) for k, v in by_tag.items()}
+    # the other HBM-facing stages of the pair, by their own algorithmic bytes:
+    # remap -- both frames read, the left written at full resolution with its
+    # low-res RGB and both low-res greys (two launches per pair); upsample --
+    # labels, low-res and full-res guides read, the FP32 cloud written, and
+    # one ex2 per pixel and tap against the measured special-function rate
+    # (30 per clock per SM on this GPU)
+    stage_rooflines = None
+    if by_tag.get("remap") and by_tag.get("upsample"):
+        full, low = W_FULL * H_FULL * 3, w * h * 3
+        remap_bytes = 2 * full + full + low + 2 * w * h
+        remap_ms = 2 * statistics.mean(by_tag["remap"])
+        up_bytes = w * h + low + full + W_FULL * H_FULL * 12
+        up_ms = statistics.mean(by_tag["upsample"])
+        ex2 = W_FULL * H_FULL * 25
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        mufu_peak = nsm * 30 * sm_max * 1e6
+        stage_rooflines = {
+            "remap": {"alg_bytes_per_pair": remap_bytes, "ms_per_pair": remap_ms,
+                      "achieved_gbs": remap_bytes / (remap_ms * 1e-3) / 1e9,
+                      "frac": remap_bytes / (remap_ms * 1e-3) / 1e9 / peak, "bound": "instruction issue"},
+            "upsample": {"alg_bytes": up_bytes, "ms": up_ms, "achieved_gbs": up_bytes / (up_ms * 1e-3) / 1e9,
+                         "frac": up_bytes / (up_ms * 1e-3) / 1e9 / peak, "ex2_per_launch": ex2,
+                         "mufu_frac": ex2 / (up_ms * 1e-3) / mufu_peak, "bound": "instruction issue"},
+            "peak_gbs": peak, "timing": timing_src}
 
     # end to end through the public streaming API from pinned host memory:
     # every step copies both frames in and the point cloud out; consecutive
@@ -1000,6 +1024,7 @@ def run_ours(args):
                                  "the default pairs in flight; the level's costs and messages mostly stay in L2, and "
                                  "the integer ALU pipe is the busiest unit"},
             "kernel_share": kernel_share,
+            "stage_rooflines": stage_rooflines,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "streaming": streaming,
