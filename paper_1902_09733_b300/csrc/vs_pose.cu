@@ -364,64 +364,74 @@ __device__ __forceinline__ void jacobi_angle(double app, double aqq, double apq,
     s = t * c;
 }
 
-// Cyclic Jacobi: A (n x n, row-major, symmetric) is diagonalised in place,
-// V receives the eigenvectors as columns; then both are sorted by eigenvalue,
-// ascending.  One thread.
-__device__ void jacobi_eigen(double *A, double *V, double *ev, int n)
+// Cyclic Jacobi for a 3 x 3 symmetric matrix on one warp: A (row-major) is
+// diagonalised in place and V receives the eigenvectors as columns, both
+// then sorted by eigenvalue, ascending; the sweeps stop once the squares of
+// the off-diagonal entries sum to at most 1e-30 of the diagonal's.  Every
+// lane calls it (A, V, ev in shared memory) and takes the same angles; lanes
+// 0-2 update one element of each column, row and eigenvector pass.
+__device__ void jacobi3_warp(double *A, double *V, double *ev)
 {
-    for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j)
-            V[i * n + j] = i == j ? 1.0 : 0.0;
+    const int lane = threadIdx.x & 31;
+    if (lane < 9)
+        V[lane] = lane % 4 == 0 ? 1.0 : 0.0;
+    __syncwarp();
     for (int sweep = 0; sweep < 60; ++sweep) {
         double off = 0.0, diag = 0.0;
-        for (int p = 0; p < n; ++p) {
-            diag += A[p * n + p] * A[p * n + p];
-            for (int q = p + 1; q < n; ++q)
-                off += A[p * n + q] * A[p * n + q];
+        for (int p = 0; p < 3; ++p) {
+            diag += A[p * 3 + p] * A[p * 3 + p];
+            for (int q = p + 1; q < 3; ++q)
+                off += A[p * 3 + q] * A[p * 3 + q];
         }
         if (off <= 1e-30 * diag || off == 0.0)
             break;
-        for (int p = 0; p < n; ++p)
-            for (int q = p + 1; q < n; ++q) {
-                const double apq = A[p * n + q];
+        for (int p = 0; p < 3; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                const double apq = A[p * 3 + q];
                 if (apq == 0.0)
                     continue;
-                double c, s;
-                jacobi_angle(A[p * n + p], A[q * n + q], apq, c, s);
-                for (int k = 0; k < n; ++k) {   // columns p, q
-                    const double akp = A[k * n + p], akq = A[k * n + q];
-                    A[k * n + p] = c * akp - s * akq;
-                    A[k * n + q] = s * akp + c * akq;
+                double c, sn;
+                jacobi_angle(A[p * 3 + p], A[q * 3 + q], apq, c, sn);
+                __syncwarp();
+                if (lane < 3) {   // columns p, q
+                    const double akp = A[lane * 3 + p], akq = A[lane * 3 + q];
+                    A[lane * 3 + p] = c * akp - sn * akq;
+                    A[lane * 3 + q] = sn * akp + c * akq;
                 }
-                for (int k = 0; k < n; ++k) {   // rows p, q
-                    const double apk = A[p * n + k], aqk = A[q * n + k];
-                    A[p * n + k] = c * apk - s * aqk;
-                    A[q * n + k] = s * apk + c * aqk;
+                __syncwarp();
+                if (lane < 3) {   // rows p, q and the eigenvector columns
+                    const double apk = A[p * 3 + lane], aqk = A[q * 3 + lane];
+                    A[p * 3 + lane] = c * apk - sn * aqk;
+                    A[q * 3 + lane] = sn * apk + c * aqk;
+                    const double vkp = V[lane * 3 + p], vkq = V[lane * 3 + q];
+                    V[lane * 3 + p] = c * vkp - sn * vkq;
+                    V[lane * 3 + q] = sn * vkp + c * vkq;
                 }
-                for (int k = 0; k < n; ++k) {
-                    const double vkp = V[k * n + p], vkq = V[k * n + q];
-                    V[k * n + p] = c * vkp - s * vkq;
-                    V[k * n + q] = s * vkp + c * vkq;
-                }
+                __syncwarp();
             }
     }
-    for (int i = 0; i < n; ++i)
-        ev[i] = A[i * n + i];
-    for (int i = 0; i < n; ++i) {   // selection sort, ascending
-        int m = i;
-        for (int j = i + 1; j < n; ++j)
-            if (ev[j] < ev[m])
-                m = j;
-        if (m != i) {
-            const double t = ev[i];
-            ev[i] = ev[m];
-            ev[m] = t;
-            for (int k = 0; k < n; ++k) {
-                const double v = V[k * n + i];
-                V[k * n + i] = V[k * n + m];
-                V[k * n + m] = v;
+    if (lane < 3)
+        ev[lane] = A[lane * 3 + lane];
+    __syncwarp();
+    for (int i = 0; i < 3; ++i) {   // selection sort, ascending (the same choice on every lane)
+        int mi = i;
+        for (int j = i + 1; j < 3; ++j)
+            if (ev[j] < ev[mi])
+                mi = j;
+        __syncwarp();
+        if (mi != i) {
+            if (lane < 3) {
+                const double v = V[lane * 3 + i];
+                V[lane * 3 + i] = V[lane * 3 + mi];
+                V[lane * 3 + mi] = v;
+            }
+            if (lane == 0) {
+                const double t = ev[i];
+                ev[i] = ev[mi];
+                ev[mi] = t;
             }
         }
+        __syncwarp();
     }
 }
 
@@ -434,7 +444,7 @@ __device__ void jacobi_eigen(double *A, double *V, double *ev, int n)
 // eigenvector columns, and then the rows, are updated with one element pair
 // per thread.  The three warps run on three schedulers, whose FP64 units
 // work in parallel; they meet at named barrier 1.  Same convergence test and
-// ascending order as jacobi_eigen; A, V, ev in shared memory.
+// ascending order as jacobi3_warp; A, V, ev in shared memory.
 __device__ __forceinline__ void bar_jacobi()
 {
     asm volatile("bar.sync 1, 96;" ::: "memory");
@@ -654,6 +664,7 @@ struct EpnpShared {
     double dw[6];          // squared control-point distances
     double R[3][9], T[3][3], err[3];   // the pose of each beta candidate
     double bestR[9], bestT[3], besterr;
+    double j3[3][21];      // 3 x 3 eigen-solves of warps 0-2: A, V, eigenvalues
     double scratch[144 + 144 + 12 + 144];   // normal matrix, eigenvectors, eigenvalues, temporary
     int ninl;
 };
@@ -661,9 +672,11 @@ struct EpnpShared {
 // Orthogonal Procrustes for Eq. 7 from the sums of one candidate (v: the
 // sums of the camera points (3), of the world points (3), of their outer
 // products (9) and the point count): R, T with camera = R world + T.  One
-// thread.
-__device__ void procrustes(const double *v, double *R, double *T)
+// warp (every lane holds the same v and computes the same numbers; js: its
+// 21 doubles of shared scratch); lane 0 writes R and T.
+__device__ void procrustes(const double *v, double *R, double *T, double *js)
 {
+    const int lane = threadIdx.x & 31;
     const double m = v[15];
     double mc[3], mw[3], H[9];
     for (int c = 0; c < 3; ++c) {
@@ -674,11 +687,13 @@ __device__ void procrustes(const double *v, double *R, double *T)
         for (int c = 0; c < 3; ++c)
             H[3 * r + c] = v[6 + 3 * r + c] - m * mc[r] * mw[c];
     // H = U S V^T: V from the eigenvectors of H^T H, U = H V / s, R = U D V^T
-    double HtH[9], Vv[9], ev[3];
-    for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c)
-            HtH[3 * r + c] = H[r] * H[c] + H[3 + r] * H[3 + c] + H[6 + r] * H[6 + c];
-    jacobi_eigen(HtH, Vv, ev, 3);
+    if (lane == 0)
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c)
+                js[3 * r + c] = H[r] * H[c] + H[3 + r] * H[3 + c] + H[6 + r] * H[6 + c];
+    __syncwarp();
+    jacobi3_warp(js, js + 9, js + 18);
+    const double *Vv = js + 9;
     // descending singular values: columns 2, 1, 0 of Vv
     double Vd[9], U[9];
     for (int k = 0; k < 3; ++k)
@@ -707,11 +722,16 @@ __device__ void procrustes(const double *v, double *R, double *T)
                         Vd[2] * (Vd[3] * Vd[7] - Vd[4] * Vd[6]);
     // U right-handed: det(U V^T) = det V; the reflection fix flips the last singular pair
     const double dl = detV >= 0.0 ? 1.0 : -1.0;
+    double Rl[9];
     for (int r = 0; r < 3; ++r)
         for (int c = 0; c < 3; ++c)
-            R[3 * r + c] = U[3 * r] * Vd[3 * c] + U[3 * r + 1] * Vd[3 * c + 1] + dl * U[3 * r + 2] * Vd[3 * c + 2];
-    for (int r = 0; r < 3; ++r)
-        T[r] = mc[r] - (R[3 * r] * mw[0] + R[3 * r + 1] * mw[1] + R[3 * r + 2] * mw[2]);
+            Rl[3 * r + c] = U[3 * r] * Vd[3 * c] + U[3 * r + 1] * Vd[3 * c + 1] + dl * U[3 * r + 2] * Vd[3 * c + 2];
+    if (lane == 0) {
+        for (int k = 0; k < 9; ++k)
+            R[k] = Rl[k];
+        for (int r = 0; r < 3; ++r)
+            T[r] = mc[r] - (Rl[3 * r] * mw[0] + Rl[3 * r + 1] * mw[1] + Rl[3 * r + 2] * mw[2]);
+    }
 }
 
 // The alphas of point i: its barycentric coordinates in the control points.
@@ -780,9 +800,9 @@ __device__ void pose_from_betas3(const EpnpArgs &a, const unsigned char *inl, co
         }
     }
     block_sum(v, 48, red);
-    if ((threadIdx.x & 31) == 0 && threadIdx.x < 96) {
+    if (threadIdx.x < 96) {
         const int c = threadIdx.x >> 5;
-        procrustes(v + 16 * c, sh.R[c], sh.T[c]);
+        procrustes(v + 16 * c, sh.R[c], sh.T[c], sh.j3[c]);
     }
     __syncthreads();
     // mean reprojection errors
@@ -891,10 +911,22 @@ __device__ void epnp_solve(const EpnpArgs &a, const unsigned char *inl, EpnpShar
             v[5] += d[2] * d[2];
         }
     block_sum(v, 6, red);
+    if (threadIdx.x < 32) {   // the principal axes on warp 0
+        double *Cs = sh.j3[0];
+        if (threadIdx.x == 0) {
+            const double C[9] = {v[0] / m, v[1] / m, v[2] / m, v[1] / m, v[3] / m, v[4] / m, v[2] / m, v[4] / m, v[5] / m};
+            for (int k = 0; k < 9; ++k)
+                Cs[k] = C[k];
+        }
+        __syncwarp();
+        jacobi3_warp(Cs, Cs + 9, Cs + 18);
+    }
     if (threadIdx.x == 0) {
-        double C[9] = {v[0] / m, v[1] / m, v[2] / m, v[1] / m, v[3] / m, v[4] / m, v[2] / m, v[4] / m, v[5] / m};
         double Vv[9], ev[3];
-        jacobi_eigen(C, Vv, ev, 3);
+        for (int k = 0; k < 9; ++k)
+            Vv[k] = sh.j3[0][9 + k];
+        for (int k = 0; k < 3; ++k)
+            ev[k] = sh.j3[0][18 + k];
         // each axis with its largest-magnitude component positive (the control
         // points must not depend on the eigen-solver's choice of signs)
         for (int k = 0; k < 3; ++k) {
