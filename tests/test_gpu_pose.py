@@ -153,3 +153,46 @@ def test_pose_step_on_gpu_rendered_flight_frames(t, target):
     assert out[13] > 400, out[13]
     assert ang < 0.05, ang
     assert np.linalg.norm(T - Tt) < 0.05 * np.linalg.norm(Tt) + 0.03, (T, Tt)
+
+
+def test_pose_step_on_flat_frames_reports_no_pose():
+    """Flat frames have no corner (25 R = 0 everywhere), so no point reaches
+    EPnP: the pose comes back as NaN with an inlier count of 0."""
+    W, H = 320, 200
+    flat = torch.full((H, W, 3), 117, dtype=torch.uint8, device="cuda")
+    xyz = torch.ones((H, W, 3), dtype=torch.float32, device="cuda")
+    p = vs.PoseParams(grid=6, margin=12, threshold25=0, radius=4, search=6)
+    assert (vs.harris_corners(flat, p).cpu().numpy() == -1).all()
+    out = vs.pose_estimate(flat, flat, xyz, vs.Camera(300.0, 300.0, 159.5, 99.5), p).cpu().numpy()
+    assert np.isnan(out[:13]).all() and out[13] == 0
+
+
+def test_pose_step_replays_in_a_cuda_graph():
+    """The whole pose step captured in a CUDA graph gives, replay after
+    replay, the same bits as the eager call (no host synchronisation or
+    allocation inside)."""
+    f1, f2 = FRAMES[1], FRAMES[2]
+    H, W = f1.shape[:2]
+    t1, t2 = torch.from_numpy(f1).cuda(), torch.from_numpy(f2).cuda()
+    vv, uu = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    z = 100.0 + 5.0 * np.sin(uu / 20.0) * np.cos(vv / 17.0)
+    cam = (215.0, 215.0, (W - 1) / 2.0, (H - 1) / 2.0)
+    xyz = np.stack([(uu - cam[2]) / cam[0] * z, (vv - cam[3]) / cam[1] * z, z], -1).astype(np.float32)
+    xyz = torch.from_numpy(xyz).cuda()
+    p = vs.PoseParams(grid=8, margin=10, threshold25=0, radius=4, search=8)
+    ws = torch.empty(vs.pose_workspace_size(W, H, p), dtype=torch.uint8, device="cuda")
+    eager = vs.pose_estimate(t1, t2, xyz, vs.Camera(*cam), p, workspace=ws).cpu().numpy()
+    st = torch.cuda.Stream()
+    out = torch.empty(14, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(st):
+        vs.pose_estimate(t1, t2, xyz, vs.Camera(*cam), p, workspace=ws)   # warm-up on the side stream
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        res = vs.pose_estimate(t1, t2, xyz, vs.Camera(*cam), p, workspace=ws, stream=st)
+        out.copy_(res)
+    for _ in range(2):
+        out.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy(), eager)
