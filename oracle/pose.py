@@ -17,6 +17,8 @@ Steps, in the order of Section 2.3:
 * :func:`epnp` -- Eq. 6 and Eq. 7 (the cited O(n) algorithm): the points as
   weighted sums of four control points, the control points in the camera
   frame from the null space of the linear system, and [R, T] from them.
+* :func:`pose_average` -- the poses of a later pair's left and right images,
+  averaged (the right one moved to the left camera through the virtual rig).
 
 Readings where the paper is silent (also listed in the design notes):
 derivatives are central differences of the integer luma (77 R + 150 G + 29 B
@@ -307,3 +309,35 @@ def epnp_inliers(P: np.ndarray, uv: np.ndarray, cam, threshold: float = 2.0, rou
             break
         R, T, err = epnp(P[keep], uv[keep], cam)
     return R, T, err, keep
+
+
+def pose_average(RL, TL, RR, TR, baseline: float):
+    """Section 2.3: the relative pose of a later stereo pair estimated from
+    its left image and from its right image, averaged.
+
+    Both estimates map frame-1 left-camera points to the later pair's
+    cameras: (RL, TL) to its left camera, (RR, TR) to its right camera.  The
+    virtual rig (a reading: the paper states only that it averages the left
+    and right poses) has the right camera ``baseline`` metres along the left
+    camera's +x with the same orientation, p_right = p_left - (baseline, 0,
+    0), so the right estimate gives the left camera's pose as (RR, TR + b).
+    The rotations are averaged by their chordal mean (the rotation nearest
+    to RL + RR, the polar factor of the sum; for two rotations the geodesic
+    midpoint), the translations arithmetically.  An estimate with a NaN
+    entry is left out; with both, NaN.  Returns (R, T)."""
+    b = np.array([baseline, 0.0, 0.0])
+    cand = []
+    for R, T in ((RL, TL), (RR, TR + b if TR is not None else None)):
+        if R is None or T is None:
+            continue
+        R, T = np.asarray(R, float), np.asarray(T, float)
+        if np.isfinite(R).all() and np.isfinite(T).all():
+            cand.append((R, T))
+    if not cand:
+        return np.full((3, 3), np.nan), np.full(3, np.nan)
+    if len(cand) == 1:
+        return cand[0]
+    M = cand[0][0] + cand[1][0]
+    U, _, Vt = np.linalg.svd(M)
+    D = np.diag([1.0, 1.0, np.sign(np.linalg.det(U @ Vt))])
+    return U @ D @ Vt, 0.5 * (cand[0][1] + cand[1][1])

@@ -257,3 +257,39 @@ def test_pose_between_rendered_frames_matches_the_cameras():
     assert ok.sum() > 150 and keep.sum() > 0.9 * ok.sum()
     assert ang < 0.05, ang
     assert np.linalg.norm(T - Tt) < 0.1, (T, Tt)
+
+
+def test_pose_average_of_two_rotations_is_the_geodesic_midpoint():
+    """For R2 = R1 Rot(axis, theta) the average is R1 Rot(axis, theta / 2)
+    (the polar factor of R1 + R2), whatever R1; the translations average."""
+    g = np.random.default_rng(5)
+    for _ in range(20):
+        R1 = _rot(g.normal(size=3), g.uniform(0, np.pi))
+        axis, th = g.normal(size=3), g.uniform(-2.0, 2.0)
+        R2 = R1 @ _rot(axis, th)
+        T1, T2 = g.normal(size=3), g.normal(size=3)
+        R, T = pose.pose_average(R1, T1, R2, T2 - np.array([0.4, 0.0, 0.0]), 0.4)
+        np.testing.assert_allclose(R, R1 @ _rot(axis, th / 2), atol=1e-12)
+        np.testing.assert_allclose(T, 0.5 * (T1 + T2), atol=1e-12)
+
+
+def test_pose_average_through_the_virtual_rig():
+    """The right camera sits `baseline` along the left camera's +x: a point
+    p of frame 1 lands at R p + T in the later left camera and at
+    R p + T - b in the later right camera, so exact estimates of both give
+    back (R, T); a NaN estimate is left out, two give NaN."""
+    R = _rot([0.3, -0.2, 1.0], 0.05)
+    T = np.array([-1.0, 0.02, 0.01])
+    b = 0.15
+    P = np.random.default_rng(6).normal(size=(10, 3)) * 20 + [0, 0, 100]
+    right = (R @ P.T).T + T - [b, 0, 0]
+    RR, TR = R, right[0] - R @ P[0]           # the right camera's pose from its own points
+    Ra, Ta = pose.pose_average(R, T, RR, TR, b)
+    np.testing.assert_allclose(Ra, R, atol=1e-14)
+    np.testing.assert_allclose(Ta, T, atol=1e-12)
+    nan3 = np.full((3, 3), np.nan)
+    Rb, Tb = pose.pose_average(nan3, np.full(3, np.nan), RR, TR, b)
+    np.testing.assert_allclose(Rb, R, atol=1e-14)
+    np.testing.assert_allclose(Tb, T, atol=1e-12)
+    Rc, Tc = pose.pose_average(nan3, np.full(3, np.nan), nan3, np.full(3, np.nan), b)
+    assert np.isnan(Rc).all() and np.isnan(Tc).all()
