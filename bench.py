@@ -640,9 +640,11 @@ def run_pose(args, vs, synth, torch, dev):
     seeded lawnmower flight at 100 m (2704x1520, rendered on the GPU without
     lens distortion, frame 1's cloud from its rendered depth): integer Harris
     response, one corner per cell of a 30x30 grid, ZSSD (radius 5, search
-    +-32 px), EPnP with two inlier rounds.  GPU: CUDA events over `reps`
-    calls of each stage and of the whole step (vs_pose_estimate); CPU: the
-    oracle on the same frames, once (a bounded sample: one step)."""
+    +-32 px), EPnP with two inlier rounds; and the same with the later
+    pair's right image too (frame 323), the two poses averaged.  GPU: CUDA
+    events over `reps` calls of each stage and of the whole step
+    (vs_pose_estimate, vs_pose_estimate_stereo); CPU: the oracle on the same
+    frames, once (a bounded sample: one step)."""
     from paper_1902_09733_b300.scene import GpuScene
     W, H = W_FULL, H_FULL
     cam6 = synth.TERRAIN_CAMERA[:4] + (0.0, 0.0)
@@ -652,18 +654,21 @@ def run_pose(args, vs, synth, torch, dev):
     depth = torch.empty((H, W), dtype=torch.float32, device=dev)
     f1 = gs.render(poses[300], cam6, depth=depth)
     f2 = gs.render(poses[320], cam6)
+    r2 = gs.render(poses[323], cam6)   # the later pair's right image (k = 3, 0.15 m on)
     vv, uu = torch.meshgrid(torch.arange(H, device=dev, dtype=torch.float32),
                             torch.arange(W, device=dev, dtype=torch.float32), indexing="ij")
     xyz = torch.stack([(uu - cam6[2]) / cam6[0] * depth, (vv - cam6[3]) / cam6[1] * depth, depth], -1).contiguous()
     p = vs.PoseParams(grid=30, margin=40, threshold25=0, radius=5, search=32)
     cam = vs.Camera(*cam6[:4])
     ws = torch.empty(vs.pose_workspace_size(W, H, p), dtype=torch.uint8, device=dev)
+    ws2 = torch.empty(vs.pose_stereo_workspace_size(W, H, p), dtype=torch.uint8, device=dev)
     corners = vs.harris_corners(f1, p, workspace=ws)
     stages = {
         "harris_response": lambda: vs.harris_response(f1),
         "harris_corners": lambda: vs.harris_corners(f1, p, workspace=ws),
         "zssd_match": lambda: vs.zssd_match(f1, f2, corners, p),
         "pose_estimate": lambda: vs.pose_estimate(f1, f2, xyz, cam, p, workspace=ws),
+        "pose_estimate_stereo": lambda: vs.pose_estimate_stereo(f1, f2, r2, xyz, cam, 0.15, p, workspace=ws2),
     }
     times = {}
     for name, fn in stages.items():
@@ -677,14 +682,20 @@ def run_pose(args, vs, synth, torch, dev):
         e1.record()
         torch.cuda.synchronize()
         times[name] = e0.elapsed_time(e1) / args.pose_reps
-    est = out.cpu().numpy()
+    est = vs.pose_estimate(f1, f2, xyz, cam, p, workspace=ws).cpu().numpy()
+    est2 = stages["pose_estimate_stereo"]().cpu().numpy()
     Rt, Tt = synth.relative_pose(poses[300], poses[320])
     ang = float(np.degrees(np.arccos(np.clip((np.trace(est[:9].reshape(3, 3).T @ Rt) - 1) / 2, -1, 1))))
     res = {"workload": "pose step between two 2704x1520 lawnmower frames 20 apart (1 m at 100 m): Harris "
                        "25R, 30x30 grid corners (margin 40), ZSSD radius 5 search +-32, EPnP + 2 inlier rounds",
            "unit": "pose steps/s", "value": 1e3 / times["pose_estimate"], "reps": args.pose_reps,
            "stage_ms": times, "inliers": float(est[13]), "reprojection_px": float(est[12]),
-           "rotation_error_deg": ang, "translation": est[9:12].tolist(), "true_translation": list(map(float, Tt))}
+           "rotation_error_deg": ang, "translation": est[9:12].tolist(), "true_translation": list(map(float, Tt)),
+           "stereo": {"what": "left and right images of the later pair (frames 320, 323), poses averaged through "
+                              "the virtual rig (vs_pose_estimate_stereo)",
+                      "ms": times["pose_estimate_stereo"], "translation": est2[9:12].tolist(),
+                      "rotation_error_deg": float(np.degrees(np.arccos(np.clip(
+                          (np.trace(est2[:9].reshape(3, 3).T @ Rt) - 1) / 2, -1, 1))))}}
     if not args.no_cpu_baseline:
         from oracle import pose as opose
         h1, h2 = f1.cpu().numpy(), f2.cpu().numpy()

@@ -584,6 +584,35 @@ int vs_pose_estimate(const uint8_t *rgb1, const uint8_t *rgb2, const float *xyz1
                      const vs_camera *cam, const vs_pose_params *p, double *out, void *workspace, size_t ws_bytes,
                      void *stream);
 
+/* Section 2.3 ("we calculate poses for both left and right images and
+ * average them"): `left` and `right` (14 doubles each, device, as
+ * vs_pose_estimate writes them) are the poses of a later stereo pair's left
+ * and right cameras relative to frame 1's left camera.  The virtual rig puts
+ * the right camera `baseline` metres along the left camera's +x with the
+ * same orientation (p_right = p_left - (baseline, 0, 0)), so the right
+ * estimate gives the left camera's pose as (R_right, T_right + b).  out (14
+ * doubles, device): R = the chordal mean of the two rotations (the rotation
+ * nearest to their sum, through the 3 x 3 eigen-decomposition of M^T M,
+ * M = R_left + R_right), T = the mean translation, the mean of the two
+ * reprojection errors, the sum of the inlier counts.  An estimate with a
+ * non-finite R or T is left out (out = the other; all NaN and a count of 0
+ * without either).  Errors: VS_EINVAL, VS_ECUDA. */
+int vs_pose_average(const double *left, const double *right, double baseline, double *out, void *stream);
+
+/* Workspace bytes of vs_pose_estimate_stereo (0 if invalid). */
+size_t vs_pose_stereo_workspace_size(int W, int H, const vs_pose_params *p);
+
+/* The averaged pose of a later stereo pair (left2, right2: W x H RGB, same
+ * pitch as left1) relative to frame 1's left camera, whose cloud is xyz1:
+ * the corners of left1 once, their ZSSD matches in left2 and in right2,
+ * EPnP with its inlier rounds for each (as vs_pose_estimate), then
+ * vs_pose_average with `baseline`.  out: 14 doubles as vs_pose_average.
+ * Errors: VS_EINVAL, VS_EWORKSPACE, VS_ECUDA. */
+int vs_pose_estimate_stereo(const uint8_t *left1, const uint8_t *left2, const uint8_t *right2, const float *xyz1,
+                            int W, int H, int pitch, const vs_camera *cam, double baseline,
+                            const vs_pose_params *p, double *out, void *workspace, size_t ws_bytes,
+                            void *stream);
+
 /* Name of a status code. */
 const char *vs_status_string(int status);
 

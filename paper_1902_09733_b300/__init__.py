@@ -239,6 +239,10 @@ def _load(path: str) -> ctypes.CDLL:
         "vs_zssd_match": ([P, P, I, I, I, P, I, ctypes.POINTER(_PoseParams), P, P, P], I),
         "vs_epnp": ([P, P, I, cam_p, P, P], I),
         "vs_pose_estimate": ([P, P, P, I, I, I, cam_p, ctypes.POINTER(_PoseParams), P, P, S, P], I),
+        "vs_pose_average": ([P, P, ctypes.c_double, P, P], I),
+        "vs_pose_stereo_workspace_size": ([I, I, ctypes.POINTER(_PoseParams)], S),
+        "vs_pose_estimate_stereo": ([P, P, P, P, I, I, I, cam_p, ctypes.c_double, ctypes.POINTER(_PoseParams), P,
+                                     P, S, P], I),
         "vs_check_test_shrink": ([ctypes.c_longlong], I),
     }
     for name, (args, res) in sig.items():
@@ -726,6 +730,43 @@ def pose_estimate(rgb1: torch.Tensor, rgb2: torch.Tensor, xyz1: torch.Tensor, ca
     _check("vs_pose_estimate", lib().vs_pose_estimate(rgb1.data_ptr(), rgb2.data_ptr(), xyz1.data_ptr(), W, H, 3 * W,
                                                       ctypes.byref(c), ctypes.byref(p), out.data_ptr(),
                                                       workspace.data_ptr(), workspace.numel(), _stream(stream)))
+    return out
+
+
+def pose_average(left: torch.Tensor, right: torch.Tensor, baseline: float, stream=None) -> torch.Tensor:
+    """Section 2.3: the left and right poses of a later stereo pair (14 float64
+    each, as :func:`pose_estimate`) averaged through the virtual rig; (14,)."""
+    left = left.to(torch.float64).contiguous()
+    right = right.to(torch.float64).contiguous()
+    out = torch.empty(14, dtype=torch.float64, device=left.device)
+    _check("vs_pose_average", lib().vs_pose_average(left.data_ptr(), right.data_ptr(), float(baseline),
+                                                    out.data_ptr(), _stream(stream)))
+    return out
+
+
+def pose_stereo_workspace_size(W: int, H: int, params: PoseParams) -> int:
+    p = params.c()
+    return int(lib().vs_pose_stereo_workspace_size(W, H, ctypes.byref(p)))
+
+
+def pose_estimate_stereo(left1: torch.Tensor, left2: torch.Tensor, right2: torch.Tensor, xyz1: torch.Tensor,
+                         cam: Camera, baseline: float, params: PoseParams, workspace=None,
+                         stream=None) -> torch.Tensor:
+    """The averaged pose of a later stereo pair (left2, right2) relative to
+    frame 1's left camera, from frame 1's cloud: (14,) as :func:`pose_average`."""
+    H, W = _rgb(left1, "left1")
+    _rgb(left2, "left2")
+    _rgb(right2, "right2")
+    if tuple(xyz1.shape) != (H, W, 3) or xyz1.dtype != torch.float32 or not xyz1.is_contiguous():
+        raise ValueError("xyz1 must be a contiguous (H, W, 3) float32 tensor")
+    if workspace is None:
+        workspace = torch.empty(pose_stereo_workspace_size(W, H, params), dtype=torch.uint8, device=left1.device)
+    out = torch.empty(14, dtype=torch.float64, device=left1.device)
+    c, p = cam.c(), params.c()
+    _check("vs_pose_estimate_stereo",
+           lib().vs_pose_estimate_stereo(left1.data_ptr(), left2.data_ptr(), right2.data_ptr(), xyz1.data_ptr(), W, H,
+                                         3 * W, ctypes.byref(c), float(baseline), ctypes.byref(p), out.data_ptr(),
+                                         workspace.data_ptr(), workspace.numel(), _stream(stream)))
     return out
 
 

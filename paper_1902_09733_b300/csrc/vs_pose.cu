@@ -28,6 +28,8 @@
 
 #include <math.h>
 
+#include <cmath>
+
 namespace vs {
 namespace {
 
@@ -1245,6 +1247,86 @@ bool pose_params_ok(int W, int H, const vs_pose_params *p)
            p->margin >= p->radius + 1 && 2 * p->margin < W && 2 * p->margin < H;
 }
 
+// ---------------------------------------------------------------------------
+// Section 2.3: the left and right poses of a later stereo pair, averaged
+
+struct AvgArgs {
+    const double *left, *right;   // 14 doubles each: R (9), T (3), error, inliers
+    double baseline;
+    double *out;
+};
+
+// One warp.  The right estimate is moved to the left camera through the
+// rig (T + (baseline, 0, 0)); R is the polar factor of M = R_left + R_right,
+// sum_i d_i (M v_i / s_i) v_i^T over the eigenvectors v_i of M^T M (s_i the
+// square roots of its eigenvalues), with d = -1 on the smallest pair when
+// det M < 0 (never for two rotations less than 180 degrees apart).
+__global__ void __launch_bounds__(32) k_pose_average(AvgArgs a)
+{
+    pdl_begin();
+    __shared__ double js[21];
+    const int lane = threadIdx.x;
+    const double nan = __longlong_as_double(0x7FF8000000000000LL);
+    double RL[9], TL[3], RR[9], TR[3];
+    bool okL = true, okR = true;
+    for (int k = 0; k < 9; ++k) {
+        RL[k] = a.left[k];
+        RR[k] = a.right[k];
+        okL = okL && isfinite(RL[k]);
+        okR = okR && isfinite(RR[k]);
+    }
+    for (int k = 0; k < 3; ++k) {
+        TL[k] = a.left[9 + k];
+        TR[k] = a.right[9 + k] + (k == 0 ? a.baseline : 0.0);
+        okL = okL && isfinite(TL[k]);
+        okR = okR && isfinite(TR[k]);
+    }
+    if (!okL || !okR) {   // one estimate or none
+        if (lane == 0) {
+            const double *R = okL ? RL : RR, *T = okL ? TL : TR;
+            const double *src = okL ? a.left : a.right;
+            for (int k = 0; k < 9; ++k)
+                a.out[k] = okL || okR ? R[k] : nan;
+            for (int k = 0; k < 3; ++k)
+                a.out[9 + k] = okL || okR ? T[k] : nan;
+            a.out[12] = okL || okR ? src[12] : nan;
+            a.out[13] = okL || okR ? src[13] : 0.0;
+        }
+        return;
+    }
+    double M[9];
+    for (int k = 0; k < 9; ++k)
+        M[k] = RL[k] + RR[k];
+    if (lane == 0)
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c)
+                js[3 * r + c] = M[r] * M[c] + M[3 + r] * M[3 + c] + M[6 + r] * M[6 + c];
+    __syncwarp();
+    jacobi3_warp(js, js + 9, js + 18);
+    const double *V = js + 9, *ev = js + 18;
+    const double detM = M[0] * (M[4] * M[8] - M[5] * M[7]) - M[1] * (M[3] * M[8] - M[5] * M[6]) +
+                        M[2] * (M[3] * M[7] - M[4] * M[6]);
+    double R[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < 3; ++i) {   // eigenvalues ascending: i = 0 is the smallest pair
+        const double s = sqrt(fmax(ev[i], 0.0));
+        const double d = (i == 0 && detM < 0.0) ? -1.0 : 1.0;
+        double u[3];
+        for (int r = 0; r < 3; ++r)
+            u[r] = (M[3 * r] * V[i] + M[3 * r + 1] * V[3 + i] + M[3 * r + 2] * V[6 + i]) / s;
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c)
+                R[3 * r + c] += d * u[r] * V[3 * c + i];
+    }
+    if (lane == 0) {
+        for (int k = 0; k < 9; ++k)
+            a.out[k] = R[k];
+        for (int k = 0; k < 3; ++k)
+            a.out[9 + k] = 0.5 * (TL[k] + TR[k]);
+        a.out[12] = 0.5 * (a.left[12] + a.right[12]);
+        a.out[13] = a.left[13] + a.right[13];
+    }
+}
+
 struct PoseLayout {
     size_t r25, corners, pos, cost, P, uv, total;
 };
@@ -1304,6 +1386,61 @@ int launch_epnp(const double *P, const double *uv, int n, const vs_camera *cam, 
     return launch_status();
 }
 
+// ZSSD matches of the corners of frame 1 in frame 2, their points from
+// frame 1's cloud, EPnP with its inlier rounds into out (14 doubles).
+int pose_from_corners(const uint8_t *rgb1, const uint8_t *rgb2, const float *xyz1, int W, int H, int pitch,
+                      const vs_camera *cam, const vs_pose_params *p, const int32_t *corners, int n, double *pos,
+                      int64_t *cost, double *P, double *uv, double *out, cudaStream_t st)
+{
+    int rc = launch_zssd(rgb1, rgb2, W, H, pitch, corners, n, p, pos, cost, st);
+    if (rc == VS_OK) {
+        GatherArgs g{corners, xyz1, pos, W, n, P, uv};
+        launch_pdl(k_pose_gather, dim3((n + 127) / 128), dim3(128), st, g);
+        note_launch();
+        rc = launch_status();
+    }
+    if (rc == VS_OK)
+        rc = launch_epnp(P, uv, n, cam, out, st);
+    return rc;
+}
+
+int launch_average(const double *left, const double *right, double baseline, double *out, cudaStream_t st)
+{
+    AvgArgs a{left, right, baseline, out};
+    launch_pdl(k_pose_average, dim3(1), dim3(32), st, a);
+    note_launch();
+    return launch_status();
+}
+
+// vs_pose_estimate_stereo: the single-pose layout, then the second set of
+// matches and points and the two estimates.
+struct StereoLayout {
+    PoseLayout base;
+    size_t pos2, cost2, P2, uv2, outL, outR, total;
+};
+
+StereoLayout stereo_layout(int W, int H, const vs_pose_params *p)
+{
+    StereoLayout l;
+    l.base = pose_layout(W, H, p);
+    const size_t nc = (size_t)p->grid * p->grid;
+    size_t off = l.base.total;
+    l.pos2 = off;
+    off = align_up(off + nc * 2 * sizeof(double), 256);
+    l.cost2 = off;
+    off = align_up(off + nc * sizeof(int64_t), 256);
+    l.P2 = off;
+    off = align_up(off + nc * 3 * sizeof(double), 256);
+    l.uv2 = off;
+    off = align_up(off + nc * 2 * sizeof(double), 256);
+    l.outL = off;
+    off = align_up(off + 14 * sizeof(double), 256);
+    l.outR = off;
+    off = align_up(off + 14 * sizeof(double), 256);
+    l.total = off;
+    return l;
+}
+
 // The EPnP kernel's reduction space (160 KB) is dynamic shared memory: allowed
 // once per device.
 bool epnp_ready()
@@ -1330,6 +1467,19 @@ bool epnp_ready()
 extern "C" size_t vs_pose_workspace_size(int W, int H, const vs_pose_params *p)
 {
     return vs::pose_params_ok(W, H, p) ? vs::pose_layout(W, H, p).total : 0;
+}
+
+extern "C" size_t vs_pose_stereo_workspace_size(int W, int H, const vs_pose_params *p)
+{
+    return vs::pose_params_ok(W, H, p) ? vs::stereo_layout(W, H, p).total : 0;
+}
+
+extern "C" int vs_pose_average(const double *left, const double *right, double baseline, double *out, void *stream)
+{
+    vs::NvtxRange nvtx_range("vs_pose_average");
+    if (!left || !right || !out || !std::isfinite(baseline))
+        return VS_EINVAL;
+    return vs::launch_average(left, right, baseline, out, (cudaStream_t)stream);
 }
 
 extern "C" int vs_harris_response(const uint8_t *rgb, int W, int H, int pitch, int64_t *r25, void *stream)
@@ -1409,14 +1559,46 @@ extern "C" int vs_pose_estimate(const uint8_t *rgb1, const uint8_t *rgb2, const 
     if (rc == VS_OK)
         rc = launch_cells(r25, W, H, p, corners, st);
     if (rc == VS_OK)
-        rc = launch_zssd(rgb1, rgb2, W, H, pitch, corners, n, p, pos, cost, st);
-    if (rc == VS_OK) {
-        GatherArgs g{corners, xyz1, pos, W, n, P, uv};
-        launch_pdl(k_pose_gather, dim3((n + 127) / 128), dim3(128), st, g);
-        note_launch();
-        rc = launch_status();
-    }
+        rc = pose_from_corners(rgb1, rgb2, xyz1, W, H, pitch, cam, p, corners, n, pos, cost, P, uv, out, st);
+    return rc;
+}
+
+extern "C" int vs_pose_estimate_stereo(const uint8_t *left1, const uint8_t *left2, const uint8_t *right2,
+                                       const float *xyz1, int W, int H, int pitch, const vs_camera *cam,
+                                       double baseline, const vs_pose_params *p, double *out, void *workspace,
+                                       size_t ws_bytes, void *stream)
+{
+    using namespace vs;
+    NvtxRange nvtx_range("vs_pose_estimate_stereo");
+    if (!left1 || !left2 || !right2 || !xyz1 || !cam || !out || pitch < 3 * W || !pose_params_ok(W, H, p) ||
+        !(cam->fx > 0.0f) || !(cam->fy > 0.0f) || !std::isfinite(baseline))
+        return VS_EINVAL;
+    const StereoLayout l = stereo_layout(W, H, p);
+    if (!workspace || !aligned(workspace, 256) || ws_bytes < l.total)
+        return VS_EWORKSPACE;
+    if (!epnp_ready())
+        return VS_ECUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint8_t *ws = static_cast<uint8_t *>(workspace);
+    auto at = [&](size_t off) { return ws + off; };
+    int64_t *r25 = reinterpret_cast<int64_t *>(at(l.base.r25));
+    int32_t *corners = reinterpret_cast<int32_t *>(at(l.base.corners));
+    double *outL = reinterpret_cast<double *>(at(l.outL)), *outR = reinterpret_cast<double *>(at(l.outR));
+    const int n = p->grid * p->grid;
+    int rc = launch_harris(left1, W, H, pitch, r25, st);
     if (rc == VS_OK)
-        rc = launch_epnp(P, uv, n, cam, out, st);
+        rc = launch_cells(r25, W, H, p, corners, st);
+    if (rc == VS_OK)
+        rc = pose_from_corners(left1, left2, xyz1, W, H, pitch, cam, p, corners, n,
+                               reinterpret_cast<double *>(at(l.base.pos)), reinterpret_cast<int64_t *>(at(l.base.cost)),
+                               reinterpret_cast<double *>(at(l.base.P)), reinterpret_cast<double *>(at(l.base.uv)),
+                               outL, st);
+    if (rc == VS_OK)
+        rc = pose_from_corners(left1, right2, xyz1, W, H, pitch, cam, p, corners, n,
+                               reinterpret_cast<double *>(at(l.pos2)), reinterpret_cast<int64_t *>(at(l.cost2)),
+                               reinterpret_cast<double *>(at(l.P2)), reinterpret_cast<double *>(at(l.uv2)), outR,
+                               st);
+    if (rc == VS_OK)
+        rc = launch_average(outL, outR, baseline, out, st);
     return rc;
 }

@@ -195,3 +195,25 @@ def test_smooth_bp_workspace_and_host_checks(lib):
     assert lib.vs_sp_select_kernels(2) == vs.VS_EINVAL
     assert lib.vs_sp_status(256, 64, 338, 190, ctypes.byref(c), None) == vs.VS_EWORKSPACE
     assert lib.vs_sp_status(256, 1 << 30, 338, 190, ctypes.byref(bad_p), None) == vs.VS_EINVAL
+
+
+def test_pose_workspaces_and_host_checks(lib):
+    p = vs.PoseParams(grid=30, margin=40, threshold25=0, radius=5, search=32)
+    single = vs.pose_workspace_size(2704, 1520, p)
+    stereo = vs.pose_stereo_workspace_size(2704, 1520, p)
+    assert single >= 2704 * 1520 * 8
+    # a second set of matches and points (pos 16, cost 8, P 24, uv 16 bytes per cell) and two outputs
+    assert single + 900 * 64 <= stereo <= single + 900 * 64 + 8 * 256
+    bad = vs.PoseParams(grid=30, margin=5, threshold25=0, radius=5, search=32)   # margin < radius + 1
+    assert vs.pose_stereo_workspace_size(2704, 1520, bad) == 0
+    c = vs.Camera(1400.0, 1400.0, 1351.5, 759.5).c()
+    pp = p.c()
+    fake = 256
+    assert lib.vs_pose_average(None, fake, 0.15, fake, None) == vs.VS_EINVAL
+    assert lib.vs_pose_average(fake, fake, float("nan"), fake, None) == vs.VS_EINVAL
+    assert lib.vs_pose_estimate_stereo(fake, fake, None, fake, 2704, 1520, 3 * 2704, ctypes.byref(c), 0.15,
+                                       ctypes.byref(pp), fake, fake, stereo, None) == vs.VS_EINVAL
+    assert lib.vs_pose_estimate_stereo(fake, fake, fake, fake, 2704, 1520, 3 * 2704, ctypes.byref(c), 0.15,
+                                       ctypes.byref(pp), fake, fake, stereo - 1, None) == vs.VS_EWORKSPACE
+    assert lib.vs_pose_estimate_stereo(fake, fake, fake, fake, 2704, 1520, 3 * 2704, ctypes.byref(c),
+                                       float("inf"), ctypes.byref(pp), fake, fake, stereo, None) == vs.VS_EINVAL
