@@ -1182,9 +1182,16 @@ __global__ void __launch_bounds__(kEpnpThreads) k_epnp(EpnpArgs a)
         const double med = __longlong_as_double(key[(n - 1) / 2]), med_hi = __longlong_as_double(key[n / 2]);
         __syncthreads();   // the scratch is the reductions' again
         const double thr = fmax(2.0, 3.0 * (0.5 * (med + med_hi)));
-        for (int i = threadIdx.x; i < a.n; i += blockDim.x)
-            inl[i] = errs[i] < thr;
-        __syncthreads();
+        int changed = 0;
+        for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+            const unsigned char m = errs[i] < thr;
+            changed |= m != inl[i];
+            inl[i] = m;
+        }
+        // the same points as the last solve give the same pose, whose errors
+        // give the same points again: nothing is left to do
+        if (!__syncthreads_or(changed))
+            break;
         cnt[0] = 0.0;
         for (int i = threadIdx.x; i < a.n; i += blockDim.x)
             cnt[0] += inl[i];
