@@ -30,11 +30,11 @@ struct JbuArgs {
     float a_r;       // log2(e) / (2 sigma_r^2)
     float *disp, *xyz;
     float fx, cx, cy, fx_over_fy, baseline;
-    // scale 4: the spatial exponent of tap t (window radius <= 3, up to 49
-    // taps) for the pixel at (px, py) of its 4 x 4 block, (|p-q|^2 - |p-c|^2) a_s,
-    // at [(4 py + px) 49 + t]; in the kernel parameters, so each tap's
-    // multiply-add reads it from the constant bank
-    float sp_as[16 * 49];
+    // scales 2, 4, 8: the spatial exponent of tap t (window radius <= 3, up
+    // to 49 taps) for the pixel at (px, py) of its s x s block,
+    // (|p-q|^2 - |p-c|^2) a_s, at [(s py + px) 49 + t]; in the kernel
+    // parameters, so each tap's multiply-add reads it from the constant bank
+    float sp_as[64 * 49];
 };
 
 __device__ __forceinline__ float ex2(float x)
@@ -141,17 +141,19 @@ __global__ void __launch_bounds__(kTileW *kThreadsY) k_jbu(JbuArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// scale 4: one thread per low-res window centre
+// scales 2, 4 and 8: one thread per low-res window centre
 //
-// With s = 4 the 4 x 4 full-res pixels x = 4k..4k+3, y = 4l..4l+3 all have
-// the window centre (k, l), so one thread loads the (2R+1)^2 taps once into
-// registers and evaluates all 16 pixels.  For a tap q and pixel p:
+// With s = S the S x S full-res pixels x = S k .. S k + S - 1, y = S l ..
+// S l + S - 1 all have the window centre (k, l), so one thread loads the
+// (2R+1)^2 taps once into registers and evaluates all S^2 pixels, a row of S
+// at a time.  For a tap q and pixel p:
 //   |I_p - I_q|^2 = |I_p|^2 + (|I_q|^2 - 2 I_p.I_q)
 // where I_p.I_q is one dp4a; the |I_p|^2 term is the same for every tap of
 // p and cancels against the reference tap, so only v_q = |I_q|^2 - 2 I_p.I_q
 // is formed.  The reference tap is the one with the smallest v_q; the
 // spatial offsets relative to the window centre (the nearest tap) are
-// compile-time constants of the pixel's position in its 4 x 4 block, so
+// constants of the pixel's position in its S x S block (kernel parameters),
+// so
 //   exponent = (v_q - v_min) * a_r + (|p-q|^2 - |p-c|^2) * a_s >= 0
 // and the window always holds a tap of weight >= 2^-(spatial spread); the
 // host takes this kernel only while that spread is <= 100, so the
@@ -170,8 +172,34 @@ constexpr uint32_t kVMagic = 0x4B000000u + kVBias;   // float bits of 2^23 + kVB
 constexpr uint32_t kOffFrameBits = 0x7F000000u;      // float bits of 2^127
 constexpr float kMinAr = 0x1p-100f;                  // floor of a_r on this path
 
-template <int R, bool kXYZ>
-__global__ void __launch_bounds__(kS4CentresX *kS4CentresY, 4) k_jbu_s4(JbuArgs a)
+// The S pixels of row y from full-res column S k on, as 24-bit RGB words.
+// Rows start on 4-byte boundaries (checked on the host): for S = 4 and 8 the
+// 3 S bytes are whole words; for S = 2 they are three 16-bit halves.
+template <int S>
+__device__ __forceinline__ void guide_pixels(const JbuArgs &a, int y, int k, uint32_t (&ip)[S])
+{
+    const uint8_t *row = a.guide_full + (size_t)y * a.guide_full_pitch;
+    if constexpr (S == 2) {
+        const uint16_t *h = reinterpret_cast<const uint16_t *>(row + (size_t)k * 6);
+        const uint32_t h0 = h[0], h1 = h[1], h2 = h[2];
+        ip[0] = h0 | ((h1 & 0xFFu) << 16);
+        ip[1] = (h1 >> 8) | (h2 << 8);
+    } else {
+        constexpr int NW = 3 * S / 4;
+        const uint32_t *g = reinterpret_cast<const uint32_t *>(row + (size_t)k * 3 * S);
+        uint32_t w[NW + 1];
+#pragma unroll
+        for (int i = 0; i < NW; ++i)
+            w[i] = g[i];
+        w[NW] = 0u;
+#pragma unroll
+        for (int q = 0; q < S; ++q)   // pixel q: bytes 3q .. 3q + 2
+            ip[q] = __funnelshift_r(w[(3 * q) / 4], w[(3 * q) / 4 + 1], 8 * ((3 * q) % 4)) & 0xFFFFFFu;
+    }
+}
+
+template <int S, int R, bool kXYZ>
+__global__ void __launch_bounds__(kS4CentresX *kS4CentresY, 4) k_jbu_sq(JbuArgs a)
 {
     pdl_begin();
     constexpr int D = 2 * R + 1;
@@ -210,19 +238,18 @@ __global__ void __launch_bounds__(kS4CentresX *kS4CentresY, 4) k_jbu_s4(JbuArgs 
             tl[j * D + i] = (float)(v.x >> 24);
         }
 
+    // rows unrolled up to S = 4 (each tap's spatial term then is a constant-
+    // bank operand of its multiply-add); at S = 8 a loop (one load each)
+#pragma unroll(S <= 4 ? S : 1)
+    for (int py = 0; py < S; ++py) {
+        const int y = S * l + py;
+        if (y >= a.H)   // the last block row of a frame whose height is not a multiple of S
+            break;
+        uint32_t ip[S];
+        guide_pixels<S>(a, y, k, ip);
+        float dres[S];
 #pragma unroll
-    for (int py = 0; py < 4; ++py) {
-        const int y = 4 * l + py;
-        if (y >= a.H)   // the last block row of a frame whose height is not a multiple of 4
-            continue;
-        const uint32_t *gp = reinterpret_cast<const uint32_t *>(a.guide_full + (size_t)y * a.guide_full_pitch +
-                                                                 (size_t)k * 12);
-        const uint32_t g0 = gp[0], g1 = gp[1], g2 = gp[2];
-        const uint32_t ip[4] = {g0 & 0xFFFFFFu, prmt(g0, g1, 0x7543u) & 0xFFFFFFu,
-                                prmt(g1, g2, 0x7432u) & 0xFFFFFFu, g2 >> 8};
-        float dres[4];
-#pragma unroll
-        for (int px = 0; px < 4; ++px) {
+        for (int px = 0; px < S; ++px) {
             int v[D * D];   // float bits of 2^23 + kVBias + v_q (2^127 off the frame)
             int vmin = 0x7FFFFFFF;
 #pragma unroll
@@ -232,33 +259,36 @@ __global__ void __launch_bounds__(kS4CentresX *kS4CentresY, 4) k_jbu_s4(JbuArgs 
             }
             const float fmin = __int_as_float(vmin);
             float num = 0.0f, den = 0.0f;
-            // spatial terms: p_down - q = ((px + 0.5)/4 - 0.5 - i, (py + 0.5)/4 - 0.5 - j)
+            // spatial terms: p_down - q = ((px + 0.5)/S - 0.5 - i, (py + 0.5)/S - 0.5 - j)
 #pragma unroll
-            for (int j = 0; j < D; ++j) {
-#pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    const int t = j * D + i;
-                    const float e = fmaf(__int_as_float(v[t]) - fmin, a.a_r, a.sp_as[(4 * py + px) * 49 + t]);
-                    const float wgt = ex2(-e);
-                    num = fmaf(wgt, tl[t], num);
-                    den += wgt;
-                }
+            for (int t = 0; t < D * D; ++t) {
+                const float e = fmaf(__int_as_float(v[t]) - fmin, a.a_r, a.sp_as[(S * py + px) * 49 + t]);
+                const float wgt = ex2(-e);
+                num = fmaf(wgt, tl[t], num);
+                den += wgt;
             }
             // den >= 2^-100 (the reference tap) and <= 49: the fast reciprocal
             // division is within 2 ulp here
-            dres[px] = __fdividef(4.0f * num, den);
+            dres[px] = __fdividef((float)S * num, den);
         }
-        const size_t p = (size_t)y * a.W + (size_t)4 * k;
-        if (a.disp)
-            *reinterpret_cast<float4 *>(a.disp + p) = make_float4(dres[0], dres[1], dres[2], dres[3]);
-        if (kXYZ) {
-            float o[12];
+        const size_t p = (size_t)y * a.W + (size_t)S * k;
+        if (a.disp) {
+            if constexpr (S == 2) {
+                *reinterpret_cast<float2 *>(a.disp + p) = make_float2(dres[0], dres[1]);
+            } else {
 #pragma unroll
-            for (int px = 0; px < 4; ++px) {
+                for (int q = 0; q < S; q += 4)
+                    *reinterpret_cast<float4 *>(a.disp + p + q) = make_float4(dres[q], dres[q + 1], dres[q + 2], dres[q + 3]);
+            }
+        }
+        if (kXYZ) {
+            float o[3 * S];
+#pragma unroll
+            for (int px = 0; px < S; ++px) {
                 float X = __int_as_float(0x7fc00000), Y = X, Z = X;
                 if (dres[px] > 0.0f) {
-                    const float bd = __fdividef(a.baseline, dres[px]);   // dres <= 4 * 255
-                    X = ((float)(4 * k + px) - a.cx) * bd;
+                    const float bd = __fdividef(a.baseline, dres[px]);   // dres <= S * 255
+                    X = ((float)(S * k + px) - a.cx) * bd;
                     Y = ((float)y - a.cy) * a.fx_over_fy * bd;
                     Z = a.fx * bd;
                 }
@@ -266,25 +296,43 @@ __global__ void __launch_bounds__(kS4CentresX *kS4CentresY, 4) k_jbu_s4(JbuArgs 
                 o[3 * px + 1] = Y;
                 o[3 * px + 2] = Z;
             }
-            float4 *dst = reinterpret_cast<float4 *>(a.xyz + 3 * p);
-            dst[0] = make_float4(o[0], o[1], o[2], o[3]);
-            dst[1] = make_float4(o[4], o[5], o[6], o[7]);
-            dst[2] = make_float4(o[8], o[9], o[10], o[11]);
+            if constexpr (S == 2) {
+                float2 *dst = reinterpret_cast<float2 *>(a.xyz + 3 * p);
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+                    dst[q] = make_float2(o[2 * q], o[2 * q + 1]);
+            } else {
+                float4 *dst = reinterpret_cast<float4 *>(a.xyz + 3 * p);
+#pragma unroll
+                for (int q = 0; q < 3 * S / 4; ++q)
+                    dst[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+            }
         }
     }
 }
 
-template <bool kXYZ>
-void launch_jbu_s4(const JbuArgs &a, cudaStream_t st)
+template <int S, bool kXYZ>
+void launch_jbu_sq(const JbuArgs &a, cudaStream_t st)
 {
     dim3 grid((a.w + kS4CentresX - 1) / kS4CentresX, (a.h + kS4CentresY - 1) / kS4CentresY);
     const int block = kS4CentresX * kS4CentresY;
     switch (a.r) {
-    case 0: launch_pdl(k_jbu_s4<0, kXYZ>, dim3(grid), dim3(block), st, a); break;
-    case 1: launch_pdl(k_jbu_s4<1, kXYZ>, dim3(grid), dim3(block), st, a); break;
-    case 2: launch_pdl(k_jbu_s4<2, kXYZ>, dim3(grid), dim3(block), st, a); break;
-    default: launch_pdl(k_jbu_s4<3, kXYZ>, dim3(grid), dim3(block), st, a); break;
+    case 0: launch_pdl(k_jbu_sq<S, 0, kXYZ>, dim3(grid), dim3(block), st, a); break;
+    case 1: launch_pdl(k_jbu_sq<S, 1, kXYZ>, dim3(grid), dim3(block), st, a); break;
+    case 2: launch_pdl(k_jbu_sq<S, 2, kXYZ>, dim3(grid), dim3(block), st, a); break;
+    default: launch_pdl(k_jbu_sq<S, 3, kXYZ>, dim3(grid), dim3(block), st, a); break;
     }
+}
+
+template <bool kXYZ>
+void launch_jbu_scaled(const JbuArgs &a, cudaStream_t st)
+{
+    if (a.s == 2)
+        launch_jbu_sq<2, kXYZ>(a, st);
+    else if (a.s == 4)
+        launch_jbu_sq<4, kXYZ>(a, st);
+    else
+        launch_jbu_sq<8, kXYZ>(a, st);
 }
 
 struct ReprojArgs {
@@ -368,41 +416,45 @@ int jbu_common(const uint8_t *labels, int w, int h, int labels_pitch, const uint
     a.cy = cam ? cam->cy : 0.0f;
     a.fx_over_fy = cam ? cam->fx / cam->fy : 0.0f;
     a.baseline = baseline;
-    // spatial exponents of the scale-4 windows: p_down - q = (ox - (i - r), oy - (j - r)),
-    // (ox, oy) = ((px + 0.5) / 4 - 0.5, (py + 0.5) / 4 - 0.5); the squared distances are
-    // exact in FP32 and the product with a_s rounds as it would on the device
-    for (int k = 0; k < 16 * 49; ++k)
+    // spatial exponents of the scale-2/4/8 windows: p_down - q = (ox - (i - r), oy - (j - r)),
+    // (ox, oy) = ((px + 0.5) / s - 0.5, (py + 0.5) / s - 0.5); the squared distances are
+    // exact in FP32 (s is a power of two) and the product with a_s rounds as it would on
+    // the device
+    for (int k = 0; k < 64 * 49; ++k)
         a.sp_as[k] = 0.0f;
-    float sp_spread = 0.0f;   // largest spatial exponent of a scale-4 window
-    if (s == 4 && a.r <= 3) {
+    const bool sq_scale = s == 2 || s == 4 || s == 8;
+    float sp_spread = 0.0f;   // largest spatial exponent of a window
+    if (sq_scale && a.r <= 3) {
         const int D = 2 * a.r + 1;
-        for (int py = 0; py < 4; ++py)
-            for (int px = 0; px < 4; ++px)
+        const float inv_s = 1.0f / (float)s;
+        for (int py = 0; py < s; ++py)
+            for (int px = 0; px < s; ++px)
                 for (int j = 0; j < D; ++j)
                     for (int i = 0; i < D; ++i) {
-                        const float ox = (px + 0.5f) * 0.25f - 0.5f, oy = (py + 0.5f) * 0.25f - 0.5f;
+                        const float ox = (px + 0.5f) * inv_s - 0.5f, oy = (py + 0.5f) * inv_s - 0.5f;
                         const float dx = ox - (float)(i - a.r), dy = oy - (float)(j - a.r);
                         const float sp = (dx * dx + dy * dy) - (ox * ox + oy * oy);
-                        a.sp_as[(4 * py + px) * 49 + j * D + i] = sp * a.a_s;
+                        a.sp_as[(s * py + px) * 49 + j * D + i] = sp * a.a_s;
                         sp_spread = fmaxf(sp_spread, sp * a.a_s);
                     }
     }
     dim3 grid((W + kTileW - 1) / kTileW, (H + kTileH - 1) / kTileH);
     dim3 block(kTileW, kThreadsY);
-    // the scale-4 kernel needs whole 4-pixel groups on every row and
-    // 4/16-byte aligned rows for its vector loads and stores
-    // and a spatial spread that keeps the reference tap's weight >= 2^-100
-    const bool s4 = s == 4 && W % 4 == 0 && guide_full_pitch % 4 == 0 && aligned(guide_full, 4) &&
+    // the block kernels need whole s-pixel groups on every row, 4-byte aligned
+    // guide rows for their word loads, 16-byte aligned outputs for their
+    // vector stores, and a spatial spread that keeps the reference tap's
+    // weight >= 2^-100
+    const bool sq = sq_scale && W % s == 0 && guide_full_pitch % 4 == 0 && aligned(guide_full, 4) &&
                     (!disp || aligned(disp, 16)) && (!xyz || aligned(xyz, 16)) && sp_spread <= 100.0f;
     const int slot = prof_begin(kProfJbu, st);
-    if (s4) {
+    if (sq) {
         // a_r below 2^-100 makes every in-frame range term < 2^-80, which
         // changes no weight; the floor keeps off-frame taps at weight 0
         a.a_r = fmaxf(a.a_r, kMinAr);
         if (xyz)
-            launch_jbu_s4<true>(a, st);
+            launch_jbu_scaled<true>(a, st);
         else
-            launch_jbu_s4<false>(a, st);
+            launch_jbu_scaled<false>(a, st);
     } else if (xyz) {
         launch_pdl(k_jbu<true>, dim3(grid), dim3(block), st, a);
     } else {
