@@ -316,6 +316,9 @@ def _assert_xyz_close(a, b, disp_ref):
     (30, 62, vs.JBUParams(2, 2, 1.0, 5000.0)),
     (44, 60, vs.JBUParams(4, 3, 0.25, 12.0)),   # spatial spread beyond the scale-4 kernel's range
     (40, 64, vs.JBUParams(4, 2, 1.0, 2.0)),     # narrow range term: many pixels' weights underflow
+    (151, 260, vs.JBUParams(2, 2, 1.0, 12.0)),  # scale-2 block kernel over several CTAs, odd height
+    (200, 520, vs.JBUParams(8, 2, 1.0, 12.0)),  # scale-8 block kernel (rows in a loop) over several CTAs
+    (203, 264, vs.JBUParams(8, 3, 0.6, 9.0)),   # scale 8, ragged last block row
 ])
 def test_jbu_and_reproject_small(H, W, jp):
     for smooth in (True, False):
