@@ -5,9 +5,9 @@
 // dot product per row and channel, no byte-to-float conversions), rounded
 // half up; the kernel writes the full-resolution RGB and reduces every s x s
 // block to the low-res RGB mean and its grey.  One launch per frame, no
-// intermediate buffers.  k_remap_s4 serves scale 4 without rotation (the
-// pair pipeline); k_remap_down everything else, staging its tile in shared
-// memory for the block means.
+// intermediate buffers.  k_remap_sq serves scales 2, 4 and 8 without
+// rotation (the pair pipeline); k_remap_down everything else, staging its
+// tile in shared memory for the block means.
 #include "vs_common.cuh"
 
 namespace vs {
@@ -244,100 +244,161 @@ __global__ void __launch_bounds__(kRemapThreads) k_remap_down(RemapArgs a)
     }
 }
 
-// Scale-4 kernel for the common case: no rotation, W and H multiples of 4
-// and below 2^22, word-aligned source and destination rows, frame offsets
-// below 2^31.  A CTA
-// covers 64 x 16 destination pixels; warp w takes block row w >> 1 and half
-// w & 1 of the tile, lane (r, i) = (lane >> 3, lane & 7) the 4 pixels of row
-// r of 4 x 4 block i.  Per quad, pixel coordinates come from exact float
-// arithmetic (integer-valued floats via the 2^23 mantissa, floors by a
-// round-down add of 1.5 x 2^23) instead of conversions; a quad whose four
-// footprints are inside the frame takes the word gathers with no further
-// checks, any other quad the general per-pixel sampler.  The 4 x 4 block
-// means are summed across the four lanes of a block with two shuffles.
 constexpr float kFloorMagic = 12582912.0f;        // 1.5 x 2^23
 constexpr uint32_t kFloorMagicBits = 0x4B400000u;
 
-__global__ void __launch_bounds__(256) k_remap_s4(RemapArgs a)
+// The quad of four destination pixels u0 .. u0 + 3 of row v (inside the
+// frame): coordinates from exact float arithmetic (integer-valued floats via
+// the 2^23 mantissa, floors by a round-down add of 1.5 x 2^23) instead of
+// conversions; when all four footprints are inside the frame, word gathers
+// with no further checks, otherwise the general per-pixel sampler.  Writes
+// the 12 bytes to dst (if wanted) and returns them packed in w.
+__device__ __forceinline__ void remap_quad(const RemapArgs &a, int u0, int v, uint32_t (&w)[3])
+{
+    uint32_t vv[4][3];
+    float yn = __fmul_rn(__fsub_rn(exact_float(v), a.cy), a.inv_fy);
+    uint32_t off[4], axq[4], ayq[4];
+    bool fast = true;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float xn = __fmul_rn(__fsub_rn(exact_float(u0 + q), a.cx), a.inv_fx);
+        float sx, sy;
+        distort(a, xn, yn, sx, sy);
+        // floors as integer-valued floats in [2^23, 2^24), exact for |s| < 2^22;
+        // any other s (NaN and infinities too) gives an x0 / y0 that fails the
+        // interior test below, since W and H are below 2^22
+        const float bx = __fadd_rd(sx, kFloorMagic), by = __fadd_rd(sy, kFloorMagic);
+        const int x0 = (int)(__float_as_uint(bx) - kFloorMagicBits);
+        const int y0 = (int)(__float_as_uint(by) - kFloorMagicBits);
+        fast = fast && (unsigned)x0 < (unsigned)(a.W - 2) && (unsigned)y0 < (unsigned)(a.H - 1);
+        // round(frac * 4096) as the low bits of an integer-valued float
+        axq[q] = __float_as_uint(fmaf(sx - (bx - kFloorMagic), 4096.0f, kFloorMagic)) - kFloorMagicBits;
+        ayq[q] = __float_as_uint(fmaf(sy - (by - kFloorMagic), 4096.0f, kFloorMagic)) - kFloorMagicBits;
+        off[q] = (uint32_t)y0 * (uint32_t)a.src_pitch + 3u * (uint32_t)x0;   // used only when fast
+    }
+    if (fast) {
+        const uint32_t *src32 = reinterpret_cast<const uint32_t *>(a.src);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t t_rg, t_b, b_rg, b_b;
+            taps_words(src32 + (off[q] >> 2), a.src_pitch >> 2, off[q] & 3u, t_rg, t_b, b_rg, b_b);
+            blend(t_rg, t_b, b_rg, b_b, axq[q], ayq[q], vv[q]);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            sample_px(a, u0 + q, v, vv[q]);
+    }
+    // the rounded bytes (bits 24..31) packed as R0 G0 B0 R1 | G1 B1 R2 G2 | B2 R3 G3 B3
+    w[0] = prmt(prmt(vv[0][0], vv[0][1], 0x0073u), prmt(vv[0][2], vv[1][0], 0x0073u), 0x5410u);
+    w[1] = prmt(prmt(vv[1][1], vv[1][2], 0x0073u), prmt(vv[2][0], vv[2][1], 0x0073u), 0x5410u);
+    w[2] = prmt(prmt(vv[2][2], vv[3][0], 0x0073u), prmt(vv[3][1], vv[3][2], 0x0073u), 0x5410u);
+    if (a.dst) {
+        uint32_t *d32 = reinterpret_cast<uint32_t *>(a.dst + (size_t)v * a.dst_pitch + (size_t)u0 * 3);
+        d32[0] = w[0];
+        d32[1] = w[1];
+        d32[2] = w[2];
+    }
+}
+
+// Scale-2/4/8 kernel for the common case: no rotation, W a multiple of 4 and
+// of s, H a multiple of s, both below 2^22, word-aligned source and
+// destination rows, frame offsets below 2^31.  A CTA covers 64 x 16
+// destination pixels and every lane one quad of 4 pixels of a row
+// (remap_quad); the s x s block means are summed across the lanes of a
+// block with shuffles:
+//   s = 4: warp w takes block row w >> 1 and half w & 1 of the tile, lane
+//          (r, i) = (lane >> 3, lane & 7) row r of block i: one quad per
+//          block row, two shuffles;
+//   s = 8: warp w takes block row w >> 2 and blocks 2 (w & 3), 2 (w & 3) + 1,
+//          lane (b, r, h) = (lane >> 4, (lane >> 1) & 7, lane & 1) quad h of
+//          row r of block b: four shuffles;
+//   s = 2: warp w takes block row w, lane (r, q) = (lane >> 4, lane & 15) row
+//          r of quad q, which spans two blocks: one shuffle.
+template <int S>
+__global__ void __launch_bounds__(256) k_remap_sq(RemapArgs a)
 {
     pdl_begin();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r = lane >> 3, qi = lane & 7;
-    const int yl = blockIdx.y * 4 + (warp >> 1);       // low-res row = block row
-    if (4 * yl >= a.H)                                 // the whole warp (H is a multiple of 4)
+    int r, yl, xl, u0;
+    if constexpr (S == 4) {
+        r = lane >> 3;
+        yl = blockIdx.y * 4 + (warp >> 1);
+        xl = blockIdx.x * 16 + 8 * (warp & 1) + (lane & 7);
+        u0 = 4 * xl;
+    } else if constexpr (S == 8) {
+        r = (lane >> 1) & 7;
+        yl = blockIdx.y * 2 + (warp >> 2);
+        xl = blockIdx.x * 8 + 2 * (warp & 3) + (lane >> 4);
+        u0 = 8 * xl + 4 * (lane & 1);
+    } else {
+        r = lane >> 4;
+        yl = blockIdx.y * 8 + warp;
+        u0 = blockIdx.x * 64 + 4 * (lane & 15);
+        xl = u0 / 2;
+    }
+    if (S * yl >= a.H)   // the whole warp (H is a multiple of S)
         return;
-    const int xl = blockIdx.x * 16 + 8 * (warp & 1) + qi;   // low-res column = quad of the row
-    const int v = 4 * yl + r, u0 = 4 * xl;
-    const bool inside = u0 < a.W;                      // whole quad (W is a multiple of 4)
+    const int v = S * yl + r;
+    const bool inside = u0 < a.W;   // whole quad (W is a multiple of 4)
     uint32_t w[3] = {0u, 0u, 0u};
-    if (inside) {
-        uint32_t vv[4][3];
-        float yn = __fmul_rn(__fsub_rn(exact_float(v), a.cy), a.inv_fy);
-        uint32_t off[4], axq[4], ayq[4];
-        bool fast = true;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float xn = __fmul_rn(__fsub_rn(exact_float(u0 + q), a.cx), a.inv_fx);
-            float sx, sy;
-            distort(a, xn, yn, sx, sy);
-            // floors as integer-valued floats in [2^23, 2^24), exact for |s| < 2^22;
-            // any other s (NaN and infinities too) gives an x0 / y0 that fails the
-            // interior test below, since W and H are below 2^22
-            const float bx = __fadd_rd(sx, kFloorMagic), by = __fadd_rd(sy, kFloorMagic);
-            const int x0 = (int)(__float_as_uint(bx) - kFloorMagicBits);
-            const int y0 = (int)(__float_as_uint(by) - kFloorMagicBits);
-            fast = fast && (unsigned)x0 < (unsigned)(a.W - 2) && (unsigned)y0 < (unsigned)(a.H - 1);
-            // round(frac * 4096) as the low bits of an integer-valued float
-            axq[q] = __float_as_uint(fmaf(sx - (bx - kFloorMagic), 4096.0f, kFloorMagic)) - kFloorMagicBits;
-            ayq[q] = __float_as_uint(fmaf(sy - (by - kFloorMagic), 4096.0f, kFloorMagic)) - kFloorMagicBits;
-            off[q] = (uint32_t)y0 * (uint32_t)a.src_pitch + 3u * (uint32_t)x0;   // used only when fast
+    if (inside)
+        remap_quad(a, u0, v, w);
+    if (!a.low_rgb && !a.low_gray)
+        return;
+    auto put = [&](int x, uint32_t R, uint32_t G, uint32_t B) {
+        if (a.low_rgb) {
+            uint8_t *d = a.low_rgb + (size_t)yl * a.low_rgb_pitch + (size_t)x * 3;
+            d[0] = (uint8_t)R;
+            d[1] = (uint8_t)G;
+            d[2] = (uint8_t)B;
         }
-        if (fast) {
-            const uint32_t *src32 = reinterpret_cast<const uint32_t *>(a.src);
+        if (a.low_gray)
+            a.low_gray[(size_t)yl * a.low_gray_pitch + x] = (uint8_t)((77u * R + 150u * G + 29u * B + 128u) >> 8);
+    };
+    const unsigned full = 0xFFFFFFFFu;
+    if constexpr (S == 2) {
+        // the quad's bytes R0 G0 B0 R1 | G1 B1 R2 G2 | B2 R3 G3 B3: pixels 0-1
+        // belong to block xl, pixels 2-3 to block xl + 1
+        const uint32_t rA = __dp4a(w[0], 0x01000001u, 0u);
+        const uint32_t gA = __dp4a(w[0], 0x00000100u, __dp4a(w[1], 0x00000001u, 0u));
+        const uint32_t bA = __dp4a(w[0], 0x00010000u, __dp4a(w[1], 0x00000100u, 0u));
+        const uint32_t rB = __dp4a(w[1], 0x00010000u, __dp4a(w[2], 0x00000100u, 0u));
+        const uint32_t gB = __dp4a(w[1], 0x01000000u, __dp4a(w[2], 0x00010000u, 0u));
+        const uint32_t bB = __dp4a(w[2], 0x01000001u, 0u);
+        uint32_t pA = rA | (gA << 16), pB = rB | (gB << 16), qAB = bA | (bB << 16);   // sums <= 4 x 255
+        pA += __shfl_xor_sync(full, pA, 16);
+        pB += __shfl_xor_sync(full, pB, 16);
+        qAB += __shfl_xor_sync(full, qAB, 16);
+        if (r != 0 || !inside)
+            return;
+        put(xl, ((pA & 0xFFFFu) + 2u) >> 2, ((pA >> 16) + 2u) >> 2, ((qAB & 0xFFFFu) + 2u) >> 2);
+        put(xl + 1, ((pB & 0xFFFFu) + 2u) >> 2, ((pB >> 16) + 2u) >> 2, ((qAB >> 16) + 2u) >> 2);
+    } else {
+        // row sums of the quad per channel, then the block's other quads
+        const uint32_t sr = __dp4a(w[0], 0x01000001u, __dp4a(w[1], 0x00010000u, __dp4a(w[2], 0x00000100u, 0u)));
+        const uint32_t sg = __dp4a(w[0], 0x00000100u, __dp4a(w[1], 0x01000001u, __dp4a(w[2], 0x00010000u, 0u)));
+        const uint32_t sb = __dp4a(w[0], 0x00010000u, __dp4a(w[1], 0x00000100u, __dp4a(w[2], 0x01000001u, 0u)));
+        uint32_t rg = sr | (sg << 16), b = sb;   // each block sum <= 64 x 255 < 2^16
+        if constexpr (S == 4) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                uint32_t t_rg, t_b, b_rg, b_b;
-                taps_words(src32 + (off[q] >> 2), a.src_pitch >> 2, off[q] & 3u, t_rg, t_b, b_rg, b_b);
-                blend(t_rg, t_b, b_rg, b_b, axq[q], ayq[q], vv[q]);
+            for (int o = 8; o <= 16; o <<= 1) {
+                rg += __shfl_xor_sync(full, rg, o);
+                b += __shfl_xor_sync(full, b, o);
             }
         } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                sample_px(a, u0 + q, v, vv[q]);
+            for (int o = 1; o <= 8; o <<= 1) {
+                rg += __shfl_xor_sync(full, rg, o);
+                b += __shfl_xor_sync(full, b, o);
+            }
         }
-        // the rounded bytes (bits 24..31) packed as R0 G0 B0 R1 | G1 B1 R2 G2 | B2 R3 G3 B3
-        w[0] = prmt(prmt(vv[0][0], vv[0][1], 0x0073u), prmt(vv[0][2], vv[1][0], 0x0073u), 0x5410u);
-        w[1] = prmt(prmt(vv[1][1], vv[1][2], 0x0073u), prmt(vv[2][0], vv[2][1], 0x0073u), 0x5410u);
-        w[2] = prmt(prmt(vv[2][2], vv[3][0], 0x0073u), prmt(vv[3][1], vv[3][2], 0x0073u), 0x5410u);
-        if (a.dst) {
-            uint32_t *d32 = reinterpret_cast<uint32_t *>(a.dst + (size_t)v * a.dst_pitch + (size_t)u0 * 3);
-            d32[0] = w[0];
-            d32[1] = w[1];
-            d32[2] = w[2];
-        }
+        constexpr uint32_t kHalf = S * S / 2, kShift = S == 4 ? 4 : 6;
+        const bool lead = S == 4 ? r == 0 : (lane & 15) == 0;
+        if (!lead || !inside)
+            return;
+        put(xl, ((rg & 0xFFFFu) + kHalf) >> kShift, ((rg >> 16) + kHalf) >> kShift, (b + kHalf) >> kShift);
     }
-    if (!a.low_rgb && !a.low_gray)
-        return;
-    // row sums of the quad per channel, then the block's four rows
-    const uint32_t sr = __dp4a(w[0], 0x01000001u, __dp4a(w[1], 0x00010000u, __dp4a(w[2], 0x00000100u, 0u)));
-    const uint32_t sg = __dp4a(w[0], 0x00000100u, __dp4a(w[1], 0x01000001u, __dp4a(w[2], 0x00010000u, 0u)));
-    const uint32_t sb = __dp4a(w[0], 0x00010000u, __dp4a(w[1], 0x00000100u, __dp4a(w[2], 0x01000001u, 0u)));
-    uint32_t rg = sr | (sg << 16), b = sb;   // each sum <= 16 x 255 < 2^16
-    rg += __shfl_xor_sync(0xFFFFFFFFu, rg, 8);
-    b += __shfl_xor_sync(0xFFFFFFFFu, b, 8);
-    rg += __shfl_xor_sync(0xFFFFFFFFu, rg, 16);
-    b += __shfl_xor_sync(0xFFFFFFFFu, b, 16);
-    if (r != 0 || !inside)
-        return;
-    const uint32_t R = ((rg & 0xFFFFu) + 8u) >> 4, G = ((rg >> 16) + 8u) >> 4, B = (b + 8u) >> 4;
-    if (a.low_rgb) {
-        uint8_t *d = a.low_rgb + (size_t)yl * a.low_rgb_pitch + (size_t)xl * 3;
-        d[0] = (uint8_t)R;
-        d[1] = (uint8_t)G;
-        d[2] = (uint8_t)B;
-    }
-    if (a.low_gray)
-        a.low_gray[(size_t)yl * a.low_gray_pitch + xl] = (uint8_t)((77u * R + 150u * G + 29u * B + 128u) >> 8);
 }
 
 }  // namespace
@@ -403,15 +464,21 @@ extern "C" int vs_rectify_remap(const uint8_t *src, int W, int H, int src_pitch,
     a.has_R = R9 != nullptr;
     for (int i = 0; i < 9; ++i)
         a.R[i] = R9 ? R9[i] : (i % 4 == 0 ? 1.0f : 0.0f);
-    // the scale-4 kernel: whole 4 x 4 blocks, word-aligned rows both ways,
-    // no rotation, 32-bit source offsets, and the low-res output wanted
-    const bool s4 = want_low && s == 4 && !a.has_R && W % 4 == 0 && H % 4 == 0 && W < (1 << 22) &&
-                    H < (1 << 22) && a.src_words && (dst == nullptr || a.dst_vec) &&
+    // the block kernel: scale 2, 4 or 8, whole s x s blocks and 4-pixel
+    // quads, word-aligned rows both ways, no rotation, 32-bit source offsets,
+    // and the low-res output wanted
+    const bool sq = want_low && (s == 2 || s == 4 || s == 8) && !a.has_R && W % 4 == 0 && W % s == 0 &&
+                    H % s == 0 && W < (1 << 22) && H < (1 << 22) && a.src_words && (dst == nullptr || a.dst_vec) &&
                     (long long)H * src_pitch < (1LL << 31);
     const int slot = prof_begin(kProfRemap, (cudaStream_t)stream);
-    if (s4) {
+    if (sq) {
         dim3 grid((W + 63) / 64, (H + 15) / 16);
-        launch_pdl(k_remap_s4, dim3(grid), dim3(256), (cudaStream_t)stream, a);
+        if (s == 2)
+            launch_pdl(k_remap_sq<2>, dim3(grid), dim3(256), (cudaStream_t)stream, a);
+        else if (s == 4)
+            launch_pdl(k_remap_sq<4>, dim3(grid), dim3(256), (cudaStream_t)stream, a);
+        else
+            launch_pdl(k_remap_sq<8>, dim3(grid), dim3(256), (cudaStream_t)stream, a);
     } else {
         const int tfw = a.tlw * s, tfh = a.tlh * s;
         dim3 grid((W + tfw - 1) / tfw, (H + tfh - 1) / tfh);

@@ -200,7 +200,8 @@ def _check_remap(src, cam, R, s):
     return diff
 
 
-@pytest.mark.parametrize("H,W,s", [(48, 64, 4), (45, 61, 4), (37, 50, 3), (20, 33, 1), (64, 80, 16)])
+@pytest.mark.parametrize("H,W,s", [(48, 64, 4), (45, 61, 4), (37, 50, 3), (20, 33, 1), (64, 80, 16),
+                                   (46, 68, 2), (48, 72, 8), (96, 160, 8), (34, 132, 2)])
 def test_remap_downsample_small(H, W, s):
     g = np.random.default_rng(H * W)
     src = g.integers(0, 256, size=(H, W, 3)).astype(np.uint8)
@@ -232,29 +233,31 @@ def test_remap_full_size_terrain_frame():
     assert (diff > 0).mean() < 1e-3      # only rounding ties may flip
 
 
-def test_remap_scale4_kernel_matches_general_kernel():
-    """Word-aligned rows at scale 4 take the scale-4 kernel, rows at an odd
-    pitch the general one: same bytes on the 2.7K frame, with and without
-    the full-resolution and low-res RGB outputs."""
+@pytest.mark.parametrize("s", [2, 4, 8])
+def test_remap_block_kernel_matches_general_kernel(s):
+    """Word-aligned rows at scales 2, 4 and 8 take the block kernel, rows at
+    an odd pitch the general one: same bytes on the 2.7K frame, with and
+    without the full-resolution and low-res RGB outputs."""
     left, _ = synth.terrain_pair(0)
     H, W, _ = left.shape
-    d1, lr1, lg1 = vs.rectify_remap(dev(left), CAM2K, scale=4)
+    d1, lr1, lg1 = vs.rectify_remap(dev(left), CAM2K, scale=s)
     big = torch.zeros((H, W + 1, 3), dtype=torch.uint8, device="cuda")
     big[:, :W] = dev(left)
-    d2, lr2, lg2 = vs.rectify_remap(big[:, :W], CAM2K, scale=4)
-    _, _, lg3 = vs.rectify_remap(dev(left), CAM2K, scale=4, dst=None, low_rgb=None)
+    d2, lr2, lg2 = vs.rectify_remap(big[:, :W], CAM2K, scale=s)
+    _, _, lg3 = vs.rectify_remap(dev(left), CAM2K, scale=s, dst=None, low_rgb=None)
     np.testing.assert_array_equal(host(d1), host(d2))
     np.testing.assert_array_equal(host(lr1), host(lr2))
     np.testing.assert_array_equal(host(lg1), host(lg2))
     np.testing.assert_array_equal(host(lg1), host(lg3))
 
 
-def test_remap_scale4_kernel_with_rays_leaving_the_frame():
-    """Strong pincushion on a frame the scale-4 kernel takes: many quads fall
+@pytest.mark.parametrize("s", [2, 4, 8])
+def test_remap_block_kernel_with_rays_leaving_the_frame(s):
+    """Strong pincushion on a frame the block kernel takes: many quads fall
     back to the per-pixel sampler near the border."""
     g = np.random.default_rng(14)
-    src = g.integers(0, 256, size=(148, 200, 3)).astype(np.uint8)
-    _check_remap(src, vs.Camera(60.0, 60.0, 99.5, 73.5, 1.5, 0.5), None, 4)
+    src = g.integers(0, 256, size=(144, 200, 3)).astype(np.uint8)
+    _check_remap(src, vs.Camera(60.0, 60.0, 99.5, 71.5, 1.5, 0.5), None, s)
 
 
 def test_remap_pitched_and_low_only():
