@@ -11,19 +11,24 @@
 //                of their 8 neighbours in (R, then the smaller raster index))
 //                reduced to the cell's largest (R, smaller index).
 // k_zssd         one CTA per corner: the patch and frame 2's search region
-//                in shared memory, one displacement per thread at a time,
-//                n Z = n sum D^2 - (sum D)^2 exact in int64, the first
-//                smallest in raster order of (dy, dx), then the parabola
-//                through the two neighbouring costs on each axis (FP64).
+//                as packed luma in shared memory, one displacement per
+//                thread at a time, n Z = n sum D^2 - (sum D)^2 exact in
+//                integers from dp4a sums, the first smallest in raster order
+//                of (dy, dx), then the parabola through the two neighbouring
+//                costs on each axis (FP64).
 // k_epnp         one CTA, FP64: the points as weighted sums of four control
 //                points (centroid and principal axes), the 12 x 12 normal
 //                matrix of Eq. 6 (in normalised image coordinates: each
-//                equation divided by fx or fy) and its four smallest eigenvectors (cyclic
-//                Jacobi), the control points' camera coordinates from N = 1,
-//                2, 3 of them (distance constraints, then Gauss-Newton on all
-//                four), [R, T] by orthogonal Procrustes (Eq. 7), the best
-//                reprojection error; then twice more on the points whose
-//                error is below max(2 px, 3 x the median).
+//                equation divided by fx or fy) and its four smallest
+//                eigenvectors (cyclic Jacobi on three warps), the control
+//                points' camera coordinates from N = 1, 2, 3 of them
+//                (distance constraints, then Gauss-Newton on all four; one
+//                warp each), [R, T] by orthogonal Procrustes (Eq. 7), the
+//                best reprojection error; then up to twice more on the
+//                points whose error is below max(2 px, 3 x the median).
+// k_pose_average the poses of a later pair's left and right images (the
+//                right one moved through the virtual rig) averaged: the
+//                rotation nearest to their sum, the mean translation.
 #include "vs_common.cuh"
 
 #include <math.h>
