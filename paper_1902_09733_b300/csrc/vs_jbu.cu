@@ -238,9 +238,12 @@ __global__ void __launch_bounds__(kS4CentresX *kS4CentresY, 4) k_jbu_sq(JbuArgs 
             tl[j * D + i] = (float)(v.x >> 24);
         }
 
-    // rows unrolled up to S = 4 (each tap's spatial term then is a constant-
-    // bank operand of its multiply-add); at S = 8 a loop (one load each)
-#pragma unroll(S <= 4 ? S : 1)
+    // the rows unrolled at S = 2 (each tap's spatial term then is a
+    // constant-bank operand of its multiply-add); from S = 4 on a loop (one
+    // constant load per tap), whose smaller code measured faster: 39.6
+    // against 44.0 us per 2.7K launch at S = 4, where the unrolled 16 pixels
+    // x 25 taps stalled on instruction fetch
+#pragma unroll(S <= 2 ? S : 1)
     for (int py = 0; py < S; ++py) {
         const int y = S * l + py;
         if (y >= a.H)   // the last block row of a frame whose height is not a multiple of S
