@@ -25,7 +25,9 @@
 // k_bp_labels for the colour the last sweep did not label.
 //
 // k_bp_sweep: two threads per active pixel, each owning a pair of outgoing
-// directions (left/right or up/down).  A thread packs the pair into the two
+// directions (left/right or up/down); the two pairs of a CTA's 64 pixels run
+// in different warps (threads 0-63 left/right, 64-127 up/down), so a warp's
+// choice of operands is fixed at compile time.  A thread packs the pair into the two
 // 16-bit halves of 32-bit words, one word per label, and runs the O(L)
 // distance transform of the truncated-linear cost (forward pass, backward
 // pass, cap at min + Ts, shift to min 0) for both directions at once with
@@ -443,6 +445,7 @@ struct SweepArgs {
     int zero_in;            // incoming = 0 (first iteration of the coarsest level)
     int materialize;        // also store the incoming used into the own slots
     uint32_t c2, ts2;       // (c, c) and (Ts, Ts) packed
+    uint32_t k256;          // 256 as a run-time value: x + y * k256 stays one integer multiply-add
     uint8_t *labels;        // last level-0 iteration: labels of the active colour
     int labels_pitch;
     int *status;            // set to VS_ETIMEOUT by a kernel that gives up a bounded wait
@@ -522,17 +525,18 @@ struct CostChunk<uint16_t> {
 // The sweep of one level-iteration for the CTA `block` of a launch; the
 // plain kernel passes blockIdx.x, the batched kernel its position within
 // its job.
-template <int LP, typename CostT, bool BYTES, bool FULL, bool LABELS, bool PRELOAD, bool SMEM>
-__device__ __forceinline__ void sweep_pixel(const SweepArgs &a, int pair, int x, int y, const bool (&has)[4],
+template <int LP, typename CostT, bool BYTES, bool FULL, bool LABELS, bool PRELOAD, bool SMEM, int PAIR>
+__device__ __forceinline__ void sweep_pixel(const SweepArgs &a, int x, int y, const bool (&has)[4],
                                             const uint8_t *const (&in)[4], const bool (&use)[4],
                                             const uint8_t *cost, uint8_t *own);
 
 template <int LP, typename CostT, bool BYTES, bool FULL, bool LABELS, bool PRELOAD>
 __device__ __forceinline__ void sweep_body(const SweepArgs &a, unsigned block)
 {
-    const unsigned idx = block * kSweepThreads + threadIdx.x;
-    const int pair = (int)(idx & 1u);
-    const unsigned slot = idx >> 1;   // over rows padded to whole 16-slot groups
+    // slots over rows padded to whole 16-slot groups; direction pair by warp
+    constexpr int kSlots = kSweepThreads / 2;
+    const int pair = (int)(threadIdx.x / kSlots);
+    const unsigned slot = block * kSlots + (threadIdx.x & (kSlots - 1));
     const unsigned rowslots = 16u * (unsigned)a.wg;
     if (slot >= (unsigned)a.h * rowslots)
         return;
@@ -571,20 +575,24 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, unsigned block)
     const uint8_t *cost = reinterpret_cast<const uint8_t *>(a.cost) +
                           slot_base(a.color * a.h + y, xh, a.wg, (LP / 16) * (int)sizeof(CostT));
     uint8_t *own = a.msg + slot_base(a.color * 4 * a.h + y, xh, a.wg, LP / 16);
-    sweep_pixel<LP, CostT, BYTES, FULL, LABELS, PRELOAD, false>(a, pair, x, y, has, in, use, cost, own);
+    if (pair == 0)
+        sweep_pixel<LP, CostT, BYTES, FULL, LABELS, PRELOAD, false, 0>(a, x, y, has, in, use, cost, own);
+    else
+        sweep_pixel<LP, CostT, BYTES, FULL, LABELS, PRELOAD, false, 1>(a, x, y, has, in, use, cost, own);
 }
 
-// The message update of one pixel for one direction pair (pair 0: left /
+// The message update of one pixel for one direction pair (PAIR 0: left /
 // right, 1: up / down) once the sources are known: in[k] = piece 0 of the
 // incoming message from direction k (read only where use[k]), cost = piece 0
 // of the data term, own = this pixel's slot of direction 0 (for
 // materialize).  SMEM: the sources are a shared-memory copy (plain loads,
 // no L2 hint).
-template <int LP, typename CostT, bool BYTES, bool FULL, bool LABELS, bool PRELOAD, bool SMEM>
-__device__ __forceinline__ void sweep_pixel(const SweepArgs &a, int pair, int x, int y, const bool (&has)[4],
+template <int LP, typename CostT, bool BYTES, bool FULL, bool LABELS, bool PRELOAD, bool SMEM, int PAIR>
+__device__ __forceinline__ void sweep_pixel(const SweepArgs &a, int x, int y, const bool (&has)[4],
                                             const uint8_t *const (&in)[4], const bool (&use)[4],
                                             const uint8_t *cost, uint8_t *own)
 {
+    constexpr int pair = PAIR;
     const size_t dir_stride = (size_t)a.h * a.wg * (LP / 16) * kPieceStride;   // bytes between directions
 
     constexpr int NPRE = PRELOAD ? LP / 16 : 1;
@@ -633,10 +641,14 @@ __device__ __forceinline__ void sweep_pixel(const SweepArgs &a, int pair, int x,
             // (h_A, h_B) 16-bit pairs
 #pragma unroll
             for (int wi = 0; wi < 4; ++wi) {
+                // A, B = directions 2 PAIR, 2 PAIR + 1; the other pair's two
+                // incoming are summed once for both
                 const uint32_t c4 = cc.word(wi);
-                const uint32_t s4 = c4 + (&m[0].x)[wi] + (&m[1].x)[wi] + (&m[2].x)[wi] + (&m[3].x)[wi];
-                const uint32_t a4 = s4 - (pair ? (&m[2].x)[wi] : (&m[0].x)[wi]);
-                const uint32_t b4 = s4 - (pair ? (&m[3].x)[wi] : (&m[1].x)[wi]);
+                const uint32_t mA = (&m[2 * PAIR].x)[wi], mB = (&m[2 * PAIR + 1].x)[wi];
+                const uint32_t oth = (&m[2 - 2 * PAIR].x)[wi] + (&m[3 - 2 * PAIR].x)[wi];
+                const uint32_t a4 = c4 + oth + mB;
+                const uint32_t b4 = c4 + oth + mA;
+                const uint32_t s4 = a4 + mA;   // the belief sum (labels only)
                 const uint32_t x01 = prmt(a4, b4, 0x5140u);    // A0 B0 A1 B1
                 const uint32_t x23 = prmt(a4, b4, 0x7362u);    // A2 B2 A3 B3
                 uint32_t wq[4] = {prmt(x01, 0u, 0x4140u), prmt(x01, 0u, 0x4342u), prmt(x23, 0u, 0x4140u),
@@ -644,7 +656,7 @@ __device__ __forceinline__ void sweep_pixel(const SweepArgs &a, int pair, int x,
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int d = 16 * j + 4 * wi + q;
-                    if (LABELS && (FULL || d < a.L))
+                    if (LABELS && PAIR == 0 && (FULL || d < a.L))
                         best_key = min(best_key, (((s4 >> (8 * q)) & 0xFFu) << 8) | (uint32_t)d);
                     uint32_t wv = wq[q];
                     if (!FULL && d >= a.L)
@@ -662,7 +674,7 @@ __device__ __forceinline__ void sweep_pixel(const SweepArgs &a, int pair, int x,
                 const uint32_t pud = pair_bytes((&m[2].x)[wi], (&m[3].x)[wi], i & 3);
                 const uint32_t t = plr + pud;                       // (L+U, R+D), no carry
                 const uint32_t s2 = t + prmt(t, t, 0x1032u) + cc.dup(i);   // (S, S)
-                if (LABELS && (FULL || d < a.L))
+                if (LABELS && PAIR == 0 && (FULL || d < a.L))
                     best_key = min(best_key, ((s2 & 0xFFFFu) << 8) | (uint32_t)d);
                 uint32_t wv = s2 - (pair ? pud : plr);              // (h_A, h_B)
                 if (!FULL && d >= a.L)
@@ -707,10 +719,12 @@ __device__ __forceinline__ void sweep_pixel(const SweepArgs &a, int pair, int x,
         uint32_t oa[4], ob[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const uint32_t t01 = prmt(o[4 * q], o[4 * q + 1], 0x6420u);
-            const uint32_t t23 = prmt(o[4 * q + 2], o[4 * q + 3], 0x6420u);
-            oa[q] = prmt(t01, t23, 0x6420u);
-            ob[q] = prmt(t01, t23, 0x7531u);
+            // outputs are in [0, Ts], Ts <= 127: o0 + 256 o1 = (A0 A1 B0 B1)
+            // without carries, one multiply-add off the integer ALU pipe
+            const uint32_t t01 = o[4 * q] + o[4 * q + 1] * a.k256;
+            const uint32_t t23 = o[4 * q + 2] + o[4 * q + 3] * a.k256;
+            oa[q] = prmt(t01, t23, 0x5410u);
+            ob[q] = prmt(t01, t23, 0x7632u);
         }
         if (dstA)
             st_piece_keep(dstA, j, make_uint4(oa[0], oa[1], oa[2], oa[3]), pol);
@@ -735,17 +749,20 @@ __device__ __forceinline__ void sweep_pixel(const SweepArgs &a, int pair, int x,
 // shuffle step for two lanes, two for four.  The chain per lane is NS times
 // shorter; the corrections touch all labels in parallel.
 
-template <int LP, typename CostT, bool BYTES, bool FULL, int NS>
-__device__ __forceinline__ void sweep_split_body(const SweepArgs &a, unsigned block)
+// Threads 0-63 of a CTA take direction pair 0 (left / right) of its pixels,
+// 64-127 pair 1 (up / down): PAIR is fixed per warp, as in sweep_body.
+template <int LP, typename CostT, bool BYTES, bool FULL, int NS, int PAIR>
+__device__ __forceinline__ void sweep_split_pair(const SweepArgs &a, unsigned block)
 {
     static_assert(NS == 2 || NS == 4, "label blocks per direction pair");
     constexpr int HL = LP / NS;  // labels per lane
     constexpr int HC = HL / 16;  // 16-label chunks per lane
     static_assert(HC >= 1 && HL % 16 == 0, "whole 16-label chunks per lane");
-    const unsigned idx = block * kSweepThreads + threadIdx.x;
-    const int half = (int)(idx % NS);   // label block of this lane
-    const int pair = (int)((idx / NS) & 1u);
-    const unsigned slot = idx / (2 * NS);   // over rows padded to whole 16-slot groups
+    constexpr int pair = PAIR;
+    constexpr int kHalfThreads = kSweepThreads / 2;
+    const int half = (int)(threadIdx.x % NS);   // label block of this lane
+    // over rows padded to whole 16-slot groups
+    const unsigned slot = block * (kHalfThreads / NS) + (threadIdx.x & (kHalfThreads - 1)) / NS;
     const unsigned rowslots = 16u * (unsigned)a.wg;
     int y = 0, xh = 0, x = 0;
     bool valid = slot < (unsigned)a.h * rowslots;
@@ -886,10 +903,10 @@ __device__ __forceinline__ void sweep_split_body(const SweepArgs &a, unsigned bl
         uint32_t oa[4], ob[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const uint32_t t01 = prmt(o[4 * q], o[4 * q + 1], 0x6420u);
-            const uint32_t t23 = prmt(o[4 * q + 2], o[4 * q + 3], 0x6420u);
-            oa[q] = prmt(t01, t23, 0x6420u);
-            ob[q] = prmt(t01, t23, 0x7531u);
+            const uint32_t t01 = o[4 * q] + o[4 * q + 1] * a.k256;   // (A0 A1 B0 B1), as in sweep_pixel
+            const uint32_t t23 = o[4 * q + 2] + o[4 * q + 3] * a.k256;
+            oa[q] = prmt(t01, t23, 0x5410u);
+            ob[q] = prmt(t01, t23, 0x7632u);
         }
         const int j = half * HC + jj;
         if (dstA)
@@ -897,6 +914,15 @@ __device__ __forceinline__ void sweep_split_body(const SweepArgs &a, unsigned bl
         if (dstB)
             st_piece(dstB, j, make_uint4(ob[0], ob[1], ob[2], ob[3]));
     }
+}
+
+template <int LP, typename CostT, bool BYTES, bool FULL, int NS>
+__device__ __forceinline__ void sweep_split_body(const SweepArgs &a, unsigned block)
+{
+    if (threadIdx.x < kSweepThreads / 2)
+        sweep_split_pair<LP, CostT, BYTES, FULL, NS, 0>(a, block);
+    else
+        sweep_split_pair<LP, CostT, BYTES, FULL, NS, 1>(a, block);
 }
 
 template <int LP, typename CostT, bool BYTES, bool FULL, bool LABELS, bool PRELOAD>
@@ -981,7 +1007,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_staged(SweepArgs a)
     };
     if (threadIdx.x == 0 && (int)blockIdx.x < ntiles)
         issue(blockIdx.x, 0);
-    const int sl = threadIdx.x >> 1, pair = threadIdx.x & 1;
+    const int sl = threadIdx.x & (kStageSlots - 1), pair = threadIdx.x / kStageSlots;   // pair by warp
     const unsigned rowslots = 16u * (unsigned)a.wg;
     int it = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
@@ -1025,7 +1051,10 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_staged(SweepArgs a)
             // the slots of missing neighbours hold 0 (k_cost01 of this call), so
             // all four directions are read as they are
             const bool all[4] = {true, true, true, true};
-            sweep_pixel<LP, uint8_t, true, FULL, LABELS, false, true>(a, pair, x, y, has, in, all, cost, nullptr);
+            if (pair == 0)
+                sweep_pixel<LP, uint8_t, true, FULL, LABELS, false, true, 0>(a, x, y, has, in, all, cost, nullptr);
+            else
+                sweep_pixel<LP, uint8_t, true, FULL, LABELS, false, true, 1>(a, x, y, has, in, all, cost, nullptr);
         }
         __syncthreads();
     }
@@ -2065,6 +2094,7 @@ SweepArgs sweep_args(const BpLayout &lay, uint8_t *ws, const vs_bp_params *p, in
     const int ceff = std::min(p->smooth_slope, p->smooth_trunc);   // same V for any larger slope
     a.c2 = (uint32_t)ceff * 0x10001u;
     a.ts2 = (uint32_t)p->smooth_trunc * 0x10001u;
+    a.k256 = 256u;
     a.color = t & 1;
     a.from_parent = (t == 0 && l + 1 < lay.levels);
     a.zero_in = (t == 0 && l + 1 == lay.levels);
