@@ -981,17 +981,18 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_staged(SweepArgs a)
         tc::mbar_init(bar + 1, 1);
     }
     __syncthreads();
-    pdl_begin();
     const int ngroups = a.h * a.wg;   // 16-slot groups of one colour
     const int ntiles = (ngroups + 3) / 4;
     const size_t arr = (size_t)ngroups * NP * kPieceStride;   // one colour-direction array
     const uint8_t *msg_in = a.msg + (size_t)a.color * 4 * arr;
     const uint8_t *cost_in = static_cast<const uint8_t *>(a.cost) + (size_t)a.color * arr;
-    auto issue = [&](int tile, int buf) {
+    // part 1: the phase's byte count and the data term; part 2: the messages
+    auto issue = [&](int tile, int buf, int part) {
         const size_t off = (size_t)tile * 4 * NP * kPieceStride;
         const uint32_t bytes = (uint32_t)min(4, ngroups - 4 * tile) * NP * kPieceStride;
         uint8_t *dst = sm + buf * kStage;
-        tc::mbar_expect_tx(bar + buf, 5 * bytes);
+        if (part & 1)
+            tc::mbar_expect_tx(bar + buf, 5 * bytes);
         if (a.withhold_copies)   // nothing completes the phase: the bounded wait runs out
             return;
         bool in_range = chk(cost_in + off, bytes, kSiteBulkCopy);
@@ -1000,13 +1001,25 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_staged(SweepArgs a)
             in_range = in_range && chk(msg_in + k * arr + off, bytes, kSiteBulkCopy);
         if (!in_range)   // (checked build) the wait runs out and the call reports VS_ETIMEOUT
             return;
+        if (part & 2) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-            tc::bulk_g2s(dst + k * kBlock, msg_in + k * arr + off, bytes, bar + buf);
-        tc::bulk_g2s(dst + 4 * kBlock, cost_in + off, bytes, bar + buf);
+            for (int k = 0; k < 4; ++k)
+                tc::bulk_g2s(dst + k * kBlock, msg_in + k * arr + off, bytes, bar + buf);
+        }
+        if (part & 1)
+            tc::bulk_g2s(dst + 4 * kBlock, cost_in + off, bytes, bar + buf);
     };
+    // The first tile's data term is copied before the wait for the previous
+    // kernel: this kernel runs from a level's second iteration on, so the
+    // previous kernel is a sweep of the same level, and this launch is
+    // scheduled only once every CTA of that sweep has passed its own wait --
+    // the data term's writer (k_cost01) and every other earlier kernel have
+    // finished by then, and no sweep writes the data term.
     if (threadIdx.x == 0 && (int)blockIdx.x < ntiles)
-        issue(blockIdx.x, 0);
+        issue(blockIdx.x, 0, 1);
+    pdl_begin();
+    if (threadIdx.x == 0 && (int)blockIdx.x < ntiles)
+        issue(blockIdx.x, 0, 2);
     const int sl = threadIdx.x & (kStageSlots - 1), pair = threadIdx.x / kStageSlots;   // pair by warp
     const unsigned rowslots = 16u * (unsigned)a.wg;
     int it = 0;
@@ -1016,7 +1029,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_staged(SweepArgs a)
         // the stage of `next` was read in the previous round, which every
         // thread has left (the barrier at the end of the loop)
         if (threadIdx.x == 0 && next < ntiles)
-            issue(next, buf ^ 1);
+            issue(next, buf ^ 1, 3);
         const bool arrived = tc::mbar_wait(bar + buf, (uint32_t)(it >> 1) & 1u);
         if (!__syncthreads_and(arrived)) {
             // The copies did not complete within the bound: report it and issue
