@@ -254,21 +254,28 @@ __device__ __forceinline__ uint4 cost0_chunk_slow(const Cost01Args &a, const uin
 // place with funnel shifts; per 4 labels one byte permute reverses them, one
 // SIMD absolute difference forms |IL - IR|, and the truncation runs on 2 x u16
 // lanes (no byte-lane minimum in hardware).
-__global__ void __launch_bounds__(128) k_cost01(Cost01Args a)
+__device__ __forceinline__ void cost01_pixel(const Cost01Args &a, int X, int Y, int j, int chunks);
+
+// Block (32, Lp / 16): threadIdx.y is the label chunk; grid (X tiles of 32,
+// rows), the rows strided by gridDim.y (at most 65535).
+__global__ void __launch_bounds__(256) k_cost01(Cost01Args a)
 {
     pdl_begin();
     const int chunks = a.Lp / 16;
-    const int nxb = (a.w1 + 31) / 32;
-    const unsigned idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx == 0 && chk(a.status, 4, kSiteStatus))
+    if ((blockIdx.x | blockIdx.y | threadIdx.x | threadIdx.y) == 0 && chk(a.status, 4, kSiteStatus))
         *a.status = VS_OK;
-    unsigned t = idx >> 5;
-    const int j = (int)(t % (unsigned)chunks);
-    t /= (unsigned)chunks;
-    const int X = 32 * (int)(t % (unsigned)nxb) + (int)(idx & 31u);
-    const int Y = (int)(t / (unsigned)nxb);
-    if (Y >= a.h1 || X >= a.w1)
+    const int j = (int)threadIdx.y;
+    const int X = 32 * (int)blockIdx.x + (int)threadIdx.x;
+    if (X >= a.w1)
         return;
+    for (int Y = (int)blockIdx.y; Y < a.h1; Y += (int)gridDim.y)
+        cost01_pixel(a, X, Y, j, chunks);
+}
+
+// The level-1 pixel (X, Y) and its four level-0 children, labels 16 j ..
+// 16 j + 15.
+__device__ __forceinline__ void cost01_pixel(const Cost01Args &a, int X, int Y, int j, int chunks)
+{
     uint32_t acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const uint32_t td2 = (uint32_t)a.Td * 0x00010001u;
     const int s0 = 2 * X - 16 * j - 15;   // first right-image column of the row window
@@ -2172,9 +2179,9 @@ void launch_costs(const BpLayout &lay, uint8_t *ws, const uint8_t *left, const u
         a.status = reinterpret_cast<int *>(ws + lay.status_off);
         a.msg0 = ws + lay.msg_off[0];
         a.msg1 = lay.levels > 1 ? ws + lay.msg_off[1] : nullptr;
-        const long long n = (long long)a.h1 * ((a.w1 + 31) / 32) * (lay.Lp / 16) * 32;
+        const dim3 grid((unsigned)((a.w1 + 31) / 32), (unsigned)std::min(a.h1, 65535));
         const int slot = prof_begin(kProfBpOther, st);
-        launch_pdl(k_cost01, dim3((unsigned)((n + 127) / 128)), dim3(128), st, a);
+        launch_pdl(k_cost01, grid, dim3(32, (unsigned)(lay.Lp / 16)), st, a);
         prof_end(slot, st);
         note_launch();
     }
