@@ -153,6 +153,28 @@ __host__ __device__ __forceinline__ size_t slot_base(int row, int xh, int wg, in
 {
     return ((((size_t)row * wg + (xh >> 4)) * np) * 16 + (xh & 15)) * 16;
 }
+// n / d for 0 <= n < 2^31 and a divisor fixed for the launch, as one wide
+// multiply and a shift instead of a division sequence.  With l = ceil(log2 d),
+// p = 31 + l and m = ceil(2^p / d): 0 <= m d - 2^p < d <= 2^l, so
+// n m / 2^p = n / d + n (m d - 2^p) / (d 2^p) lies in [n / d, n / d + 1 / d)
+// for every n < 2^31 and its floor is floor(n / d) (Granlund and Montgomery,
+// division by invariant integers using multiplication, 1994); m < 2^32.
+struct FastDiv {
+    uint32_t m, p;
+};
+inline FastDiv fast_div(uint32_t d)
+{
+    uint32_t l = 0;
+    while ((1ull << l) < d)
+        ++l;
+    const uint32_t p = 31 + l;
+    return FastDiv{(uint32_t)(((1ull << p) + d - 1) / d), p};
+}
+__device__ __forceinline__ uint32_t div_by(uint32_t n, const FastDiv &f)
+{
+    return (uint32_t)(((uint64_t)n * f.m) >> f.p);
+}
+
 // Every global 16-byte piece goes through these (bounds-checked in the
 // checked build; shared-memory copies use them too, and chk() accepts none
 // of those addresses, so the sweeps that read shared memory pass SMEM to
@@ -374,6 +396,7 @@ struct CostDownArgs {
     int wf, hf, wgf;       // fine dims (width, height, slot groups per row)
     int wc, hc, wgc;       // coarse dims
     int Lp;
+    FastDiv div_chunks, div_wgc, div_hc;   // by Lp / 8, wgc, hc
 };
 
 // Coarse data term: the sum over the in-frame 2x2 children.  Child
@@ -389,12 +412,13 @@ __global__ void k_cost_down(CostDownArgs a)
         return;
     const int lane = (int)(idx & 15u);
     unsigned t = idx >> 4;
-    const int j = (int)(t % chunks);
-    t /= chunks;
-    const int g = (int)(t % (unsigned)a.wgc);
-    const unsigned row = t / (unsigned)a.wgc;
-    const int y = (int)(row % (unsigned)a.hc);
-    const int c = (int)(row / (unsigned)a.hc);
+    const unsigned t1 = div_by(t, a.div_chunks);
+    const int j = (int)(t - t1 * chunks);
+    t = t1;
+    const unsigned row = div_by(t, a.div_wgc);
+    const int g = (int)(t - row * (unsigned)a.wgc);
+    const int c = (int)div_by(row, a.div_hc);
+    const int y = (int)(row - (unsigned)c * (unsigned)a.hc);
     const int xh = 16 * g + lane;
     const int x = 2 * xh + ((c + y) & 1);
     if (x >= a.wc)
@@ -453,6 +477,7 @@ struct SweepArgs {
     int materialize;        // also store the incoming used into the own slots
     uint32_t c2, ts2;       // (c, c) and (Ts, Ts) packed
     uint32_t k256;          // 256 as a run-time value: x + y * k256 stays one integer multiply-add
+    FastDiv div_rowslots;   // by 16 wg, the slots of a padded row
     uint8_t *labels;        // last level-0 iteration: labels of the active colour
     int labels_pitch;
     int *status;            // set to VS_ETIMEOUT by a kernel that gives up a bounded wait
@@ -547,7 +572,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, unsigned block)
     const unsigned rowslots = 16u * (unsigned)a.wg;
     if (slot >= (unsigned)a.h * rowslots)
         return;
-    const int y = (int)(slot / rowslots);
+    const int y = (int)div_by(slot, a.div_rowslots);
     const int xh = (int)(slot - (unsigned)y * rowslots);
     const int x = 2 * xh + ((a.color + y) & 1);
     if (x >= a.w)
@@ -774,7 +799,7 @@ __device__ __forceinline__ void sweep_split_pair(const SweepArgs &a, unsigned bl
     int y = 0, xh = 0, x = 0;
     bool valid = slot < (unsigned)a.h * rowslots;
     if (valid) {
-        y = (int)(slot / rowslots);
+        y = (int)div_by(slot, a.div_rowslots);
         xh = (int)(slot - (unsigned)y * rowslots);
         x = 2 * xh + ((a.color + y) & 1);
         valid = x < a.w;
@@ -1060,7 +1085,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_staged(SweepArgs a)
             return;
         }
         const unsigned slot = (unsigned)tile * kStageSlots + (unsigned)sl;
-        const int y = (int)(slot / rowslots);
+        const int y = (int)div_by(slot, a.div_rowslots);
         const int xh = (int)(slot - (unsigned)y * rowslots);
         const int x = 2 * xh + ((a.color + y) & 1);
         if (y < a.h && x < a.w) {
@@ -2115,6 +2140,7 @@ SweepArgs sweep_args(const BpLayout &lay, uint8_t *ws, const vs_bp_params *p, in
     a.c2 = (uint32_t)ceff * 0x10001u;
     a.ts2 = (uint32_t)p->smooth_trunc * 0x10001u;
     a.k256 = 256u;
+    a.div_rowslots = fast_div(16u * (uint32_t)a.wg);
     a.color = t & 1;
     a.from_parent = (t == 0 && l + 1 < lay.levels);
     a.zero_in = (t == 0 && l + 1 == lay.levels);
@@ -2199,6 +2225,9 @@ void launch_costs(const BpLayout &lay, uint8_t *ws, const uint8_t *left, const u
         a.hc = lay.h[l];
         a.wgc = lay.wg[l];
         a.Lp = lay.Lp;
+        a.div_chunks = fast_div((uint32_t)lay.Lp / 8u);
+        a.div_wgc = fast_div((uint32_t)a.wgc);
+        a.div_hc = fast_div((uint32_t)a.hc);
         const long long n = 2LL * a.hc * a.wgc * 16 * (lay.Lp / 8);
         const int slot = prof_begin(kProfBpOther, st);
         launch_pdl(k_cost_down, dim3((unsigned)((n + block - 1) / block)), dim3(block), st, a);
