@@ -557,10 +557,32 @@ struct CostChunk<uint16_t> {
 // The sweep of one level-iteration for the CTA `block` of a launch; the
 // plain kernel passes blockIdx.x, the batched kernel its position within
 // its job.
-template <int LP, typename CostT, bool BYTES, bool FULL, bool LABELS, bool PRELOAD, bool SMEM, int PAIR>
-__device__ __forceinline__ void sweep_pixel(const SweepArgs &a, int x, int y, const bool (&has)[4],
-                                            const uint8_t *const (&in)[4], const bool (&use)[4],
-                                            const uint8_t *cost, uint8_t *own);
+template <int LP, typename CostT, bool BYTES, bool FULL, bool LABELS, bool PRELOAD, bool SMEM, int PAIR, typename Dsts>
+__device__ __forceinline__ void sweep_pixel(const SweepArgs &a, int x, int y, const uint8_t *const (&in)[4],
+                                            const bool (&use)[4], const uint8_t *cost, uint8_t *own,
+                                            const Dsts &dsts);
+
+// Where pixel (x, y) sends the two messages of direction pair PAIR: A = the
+// left / up neighbour's slot, B = the right / down neighbour's, in the other
+// colour's arrays; null where the neighbour is missing.
+template <int LP, int PAIR>
+__device__ __forceinline__ void sweep_dsts(const SweepArgs &a, int x, int y, const bool (&has)[4], uint8_t *&dstA,
+                                           uint8_t *&dstB)
+{
+    const int ncolor = a.color ^ 1;
+    dstA = dstB = nullptr;
+    if (PAIR == 0) {
+        if (has[0])
+            dstA = a.msg + slot_base((ncolor * 4 + 1) * a.h + y, (x - 1) >> 1, a.wg, LP / 16);
+        if (has[1])
+            dstB = a.msg + slot_base((ncolor * 4 + 0) * a.h + y, (x + 1) >> 1, a.wg, LP / 16);
+    } else {
+        if (has[2])
+            dstA = a.msg + slot_base((ncolor * 4 + 3) * a.h + (y - 1), x >> 1, a.wg, LP / 16);
+        if (has[3])
+            dstB = a.msg + slot_base((ncolor * 4 + 2) * a.h + (y + 1), x >> 1, a.wg, LP / 16);
+    }
+}
 
 template <int LP, typename CostT, bool BYTES, bool FULL, bool LABELS, bool PRELOAD>
 __device__ __forceinline__ void sweep_body(const SweepArgs &a, unsigned block)
@@ -608,21 +630,24 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, unsigned block)
                           slot_base(a.color * a.h + y, xh, a.wg, (LP / 16) * (int)sizeof(CostT));
     uint8_t *own = a.msg + slot_base(a.color * 4 * a.h + y, xh, a.wg, LP / 16);
     if (pair == 0)
-        sweep_pixel<LP, CostT, BYTES, FULL, LABELS, PRELOAD, false, 0>(a, x, y, has, in, use, cost, own);
+        sweep_pixel<LP, CostT, BYTES, FULL, LABELS, PRELOAD, false, 0>(
+            a, x, y, in, use, cost, own, [&](uint8_t *&A, uint8_t *&B) { sweep_dsts<LP, 0>(a, x, y, has, A, B); });
     else
-        sweep_pixel<LP, CostT, BYTES, FULL, LABELS, PRELOAD, false, 1>(a, x, y, has, in, use, cost, own);
+        sweep_pixel<LP, CostT, BYTES, FULL, LABELS, PRELOAD, false, 1>(
+            a, x, y, in, use, cost, own, [&](uint8_t *&A, uint8_t *&B) { sweep_dsts<LP, 1>(a, x, y, has, A, B); });
 }
 
 // The message update of one pixel for one direction pair (PAIR 0: left /
 // right, 1: up / down) once the sources are known: in[k] = piece 0 of the
 // incoming message from direction k (read only where use[k]), cost = piece 0
 // of the data term, own = this pixel's slot of direction 0 (for
-// materialize).  SMEM: the sources are a shared-memory copy (plain loads,
+// materialize), dsts(A, B) sets the two destination slots (called after the
+// forward pass).  SMEM: the sources are a shared-memory copy (plain loads,
 // no L2 hint).
-template <int LP, typename CostT, bool BYTES, bool FULL, bool LABELS, bool PRELOAD, bool SMEM, int PAIR>
-__device__ __forceinline__ void sweep_pixel(const SweepArgs &a, int x, int y, const bool (&has)[4],
-                                            const uint8_t *const (&in)[4], const bool (&use)[4],
-                                            const uint8_t *cost, uint8_t *own)
+template <int LP, typename CostT, bool BYTES, bool FULL, bool LABELS, bool PRELOAD, bool SMEM, int PAIR, typename Dsts>
+__device__ __forceinline__ void sweep_pixel(const SweepArgs &a, int x, int y, const uint8_t *const (&in)[4],
+                                            const bool (&use)[4], const uint8_t *cost, uint8_t *own,
+                                            const Dsts &dsts)
 {
     constexpr int pair = PAIR;
     const size_t dir_stride = (size_t)a.h * a.wg * (LP / 16) * kPieceStride;   // bytes between directions
@@ -720,20 +745,9 @@ __device__ __forceinline__ void sweep_pixel(const SweepArgs &a, int x, int y, co
     if (LABELS && pair == 0 && chk(a.labels + (size_t)y * a.labels_pitch + x, 1, kSiteLabel))
         a.labels[(size_t)y * a.labels_pitch + x] = (uint8_t)(best_key & 0xFFu);
 
-    // destinations: A = left / up neighbour, B = right / down neighbour
-    const int ncolor = a.color ^ 1;
-    uint8_t *dstA = nullptr, *dstB = nullptr;
-    if (pair == 0) {
-        if (has[0])
-            dstA = a.msg + slot_base((ncolor * 4 + 1) * a.h + y, (x - 1) >> 1, a.wg, LP / 16);
-        if (has[1])
-            dstB = a.msg + slot_base((ncolor * 4 + 0) * a.h + y, (x + 1) >> 1, a.wg, LP / 16);
-    } else {
-        if (has[2])
-            dstA = a.msg + slot_base((ncolor * 4 + 3) * a.h + (y - 1), x >> 1, a.wg, LP / 16);
-        if (has[3])
-            dstB = a.msg + slot_base((ncolor * 4 + 2) * a.h + (y + 1), x >> 1, a.wg, LP / 16);
-    }
+    // destinations (after the forward pass: fewer live registers during it)
+    uint8_t *dstA, *dstB;
+    dsts(dstA, dstB);
 
     // -H in both 16-bit lanes, for the fused add-min of the output
     const uint32_t negH2 = ((0u - (H2 & 0xFFFFu)) & 0xFFFFu) | ((0u - (H2 >> 16)) << 16);
@@ -1017,6 +1031,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_staged(SweepArgs a)
     const int ntiles = (ngroups + 3) / 4;
     const size_t arr = (size_t)ngroups * NP * kPieceStride;   // one colour-direction array
     const uint8_t *msg_in = a.msg + (size_t)a.color * 4 * arr;
+    uint8_t *const msg_out = a.msg + (size_t)(a.color ^ 1) * 4 * arr;
     const uint8_t *cost_in = static_cast<const uint8_t *>(a.cost) + (size_t)a.color * arr;
     // part 1: the phase's byte count and the data term; part 2: the messages
     auto issue = [&](int tile, int buf, int part) {
@@ -1096,10 +1111,25 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_staged(SweepArgs a)
             // the slots of missing neighbours hold 0 (k_cost01 of this call), so
             // all four directions are read as they are
             const bool all[4] = {true, true, true, true};
+            // destinations as 32-bit offsets into the other colour's arrays
+            // (each below 2^31 bytes on this kernel)
+            auto off = [&](int yy, int xs) {
+                return (((uint32_t)yy * (uint32_t)a.wg + ((uint32_t)xs >> 4)) * (uint32_t)(NP * 16) +
+                        ((uint32_t)xs & 15u)) *
+                       16u;
+            };
             if (pair == 0)
-                sweep_pixel<LP, uint8_t, true, FULL, LABELS, false, true, 0>(a, x, y, has, in, all, cost, nullptr);
+                sweep_pixel<LP, uint8_t, true, FULL, LABELS, false, true, 0>(
+                    a, x, y, in, all, cost, nullptr, [&](uint8_t *&A, uint8_t *&B) {
+                        A = has[0] ? msg_out + arr + off(y, (x - 1) >> 1) : nullptr;
+                        B = has[1] ? msg_out + off(y, (x + 1) >> 1) : nullptr;
+                    });
             else
-                sweep_pixel<LP, uint8_t, true, FULL, LABELS, false, true, 1>(a, x, y, has, in, all, cost, nullptr);
+                sweep_pixel<LP, uint8_t, true, FULL, LABELS, false, true, 1>(
+                    a, x, y, in, all, cost, nullptr, [&](uint8_t *&A, uint8_t *&B) {
+                        A = has[2] ? msg_out + 3 * arr + off(y - 1, x >> 1) : nullptr;
+                        B = has[3] ? msg_out + 2 * arr + off(y + 1, x >> 1) : nullptr;
+                    });
         }
         __syncthreads();
     }
@@ -1852,6 +1882,8 @@ bool launch_staged_lp(const SweepArgs &a, bool full, bool labels, cudaStream_t s
 
 bool launch_staged(int Lp, const SweepArgs &a, cudaStream_t st)
 {
+    if ((size_t)a.h * a.wg * (size_t)(Lp / 16) * kPieceStride >= (size_t(1) << 31))
+        return false;   // the kernel's 32-bit offsets into one colour-direction array
     const bool full = a.L == Lp, labels = a.labels != nullptr;
     switch (Lp) {
     case 16: return launch_staged_lp<16>(a, full, labels, st);
