@@ -70,8 +70,9 @@ typedef struct {
  * tile of the level in shared memory with a halo that shrinks by one pixel
  * per iteration (fewer than k where tile and halo would not fit shared
  * memory); 0 (automatic) runs fused tiles on the coarse levels where
- * vs_bp_autotune measured them faster for levels of that size, one kernel
- * per iteration elsewhere.  The workspace of k != 1 holds one more message
+ * vs_bp_autotune measured them faster for levels of that size, and on
+ * coarse levels of at most 240 000 label-pixels (width x height x padded
+ * labels) that it has not measured, one kernel per iteration elsewhere.  The workspace of k != 1 holds one more message
  * buffer (the largest level that may be fused).  The general path runs one
  * kernel per iteration whatever iters_per_tile says. */
 typedef struct {

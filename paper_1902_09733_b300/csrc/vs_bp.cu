@@ -2031,16 +2031,21 @@ struct FusedTune {
 };
 std::vector<FusedTune> g_fused_tune;
 
-// Automatic mode without a recorded plan: one kernel per iteration.
-// Measured on B300 in graph replays (676 x 380, 64 labels, 4 x 10): levels
-// 1 / 2 / 3 take 41 / 29 / 25 us unfused against 80 / 41 / 25 us for the
-// fastest fused plans -- with programmatic dependent launch a coarse sweep
-// costs 2.5-4 us, less than a fused tile's repeated halo work and its one
-// CTA per SM.  Fused launches win only on small levels (16 labels at 80 x 60
-// to 160 x 90: 10.4 -> 8.3 us per level), so they run where vs_bp_autotune
-// measured them faster, or when iters_per_tile asks for them.
-FusedPlan fused_auto_default(const BpLayout &, const vs_bp_params *, int)
+// Automatic mode without a recorded plan.  Measured on B300 in graph
+// replays (676 x 380, 64 labels, 4 x 10): levels 1 / 2 / 3 take 41 / 29 / 25
+// us unfused against 80 / 41 / 25 us for the fastest fused plans -- with
+// programmatic dependent launch a coarse sweep costs 2.5-4 us, less than a
+// fused tile's repeated halo work and its one CTA per SM.  Fused launches win
+// on small levels (16 labels at 80 x 60 to 160 x 90: 10.4 -> 8.3 us per
+// level; the 160 x 120, 16-label pair 34.3 -> 32.6 us per call), so a coarse
+// level of at most 240 000 label-pixels runs all its iterations fused;
+// larger ones run one kernel per iteration unless vs_bp_autotune measured a
+// fused plan faster or iters_per_tile asks for one.
+constexpr long long kFusedAutoLabelPixels = 240000;
+FusedPlan fused_auto_default(const BpLayout &lay, const vs_bp_params *p, int l)
 {
+    if ((long long)lay.w[l] * lay.h[l] * lay.Lp <= kFusedAutoLabelPixels)
+        return fused_default(lay, l, p->iters);
     return FusedPlan{0, 0, 0, 0};
 }
 
