@@ -164,6 +164,7 @@ struct FastDiv {
 };
 inline FastDiv fast_div(uint32_t d)
 {
+    d = d ? d : 1u;   // every divisor here counts slots, groups or rows of a level: never 0
     uint32_t l = 0;
     while ((1ull << l) < d)
         ++l;
