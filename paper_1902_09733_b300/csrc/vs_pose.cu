@@ -16,7 +16,8 @@
 //                integers from dp4a sums, the first smallest in raster order
 //                of (dy, dx), then the parabola through the two neighbouring
 //                costs on each axis (FP64).
-// k_epnp         one CTA, FP64: the points as weighted sums of four control
+// k_epnp         one CTA per problem (the left and right poses of a stereo
+//                pair side by side), FP64: the points as weighted sums of four control
 //                points (centroid and principal axes), the 12 x 12 normal
 //                matrix of Eq. 6 (in normalised image coordinates: each
 //                equation divided by fx or fy) and its four smallest
@@ -630,6 +631,13 @@ struct EpnpArgs {
     double *out;        // R (9, row-major), T (3), mean error of the inliers, inlier count
 };
 
+// Independent problems of one launch, one CTA each (the left and right
+// poses of a stereo pair run side by side on two SMs).
+constexpr int kMaxEpnpJobs = 2;
+struct EpnpJobs {
+    EpnpArgs job[kMaxEpnpJobs];
+};
+
 __constant__ int kPairI[6] = {0, 0, 0, 1, 1, 2};
 __constant__ int kPairJ[6] = {1, 2, 3, 2, 3, 3};
 
@@ -1102,9 +1110,10 @@ __device__ void epnp_solve(const EpnpArgs &a, const unsigned char *inl, EpnpShar
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kEpnpThreads) k_epnp(EpnpArgs a)
+__global__ void __launch_bounds__(kEpnpThreads) k_epnp(const __grid_constant__ EpnpJobs jobs)
 {
     pdl_begin();
+    const EpnpArgs &a = jobs.job[blockIdx.x];
     __shared__ unsigned char inl[kMaxPts];
     __shared__ EpnpShared sh;
     extern __shared__ double red[];   // 80 x blockDim
@@ -1390,19 +1399,32 @@ int launch_zssd(const uint8_t *rgb1, const uint8_t *rgb2, int W, int H, int pitc
     return launch_status();
 }
 
-int launch_epnp(const double *P, const double *uv, int n, const vs_camera *cam, double *out, cudaStream_t st)
+// njobs (1 or 2) problems in one launch.
+int launch_epnp_jobs(const EpnpJobs &jobs, int njobs, cudaStream_t st)
 {
-    EpnpArgs a{P, uv, n, cam->fx, cam->fy, cam->cx, cam->cy, out};
-    launch_pdl_smem(k_epnp, dim3(1), dim3(kEpnpThreads), (size_t)80 * kEpnpThreads * sizeof(double), st, a);
+    launch_pdl_smem(k_epnp, dim3((unsigned)njobs), dim3(kEpnpThreads), (size_t)80 * kEpnpThreads * sizeof(double),
+                    st, jobs);
     note_launch();
     return launch_status();
 }
 
-// ZSSD matches of the corners of frame 1 in frame 2, their points from
-// frame 1's cloud, EPnP with its inlier rounds into out (14 doubles).
-int pose_from_corners(const uint8_t *rgb1, const uint8_t *rgb2, const float *xyz1, int W, int H, int pitch,
-                      const vs_camera *cam, const vs_pose_params *p, const int32_t *corners, int n, double *pos,
-                      int64_t *cost, double *P, double *uv, double *out, cudaStream_t st)
+EpnpArgs epnp_args(const double *P, const double *uv, int n, const vs_camera *cam, double *out)
+{
+    return EpnpArgs{P, uv, n, cam->fx, cam->fy, cam->cx, cam->cy, out};
+}
+
+int launch_epnp(const double *P, const double *uv, int n, const vs_camera *cam, double *out, cudaStream_t st)
+{
+    EpnpJobs jobs{};
+    jobs.job[0] = epnp_args(P, uv, n, cam, out);
+    return launch_epnp_jobs(jobs, 1, st);
+}
+
+// ZSSD matches of the corners of frame 1 in frame 2 and their points from
+// frame 1's cloud (P, uv: the EPnP input).
+int match_points(const uint8_t *rgb1, const uint8_t *rgb2, const float *xyz1, int W, int H, int pitch,
+                 const vs_pose_params *p, const int32_t *corners, int n, double *pos, int64_t *cost, double *P,
+                 double *uv, cudaStream_t st)
 {
     int rc = launch_zssd(rgb1, rgb2, W, H, pitch, corners, n, p, pos, cost, st);
     if (rc == VS_OK) {
@@ -1411,6 +1433,15 @@ int pose_from_corners(const uint8_t *rgb1, const uint8_t *rgb2, const float *xyz
         note_launch();
         rc = launch_status();
     }
+    return rc;
+}
+
+// The matches, then EPnP with its inlier rounds into out (14 doubles).
+int pose_from_corners(const uint8_t *rgb1, const uint8_t *rgb2, const float *xyz1, int W, int H, int pitch,
+                      const vs_camera *cam, const vs_pose_params *p, const int32_t *corners, int n, double *pos,
+                      int64_t *cost, double *P, double *uv, double *out, cudaStream_t st)
+{
+    int rc = match_points(rgb1, rgb2, xyz1, W, H, pitch, p, corners, n, pos, cost, P, uv, st);
     if (rc == VS_OK)
         rc = launch_epnp(P, uv, n, cam, out, st);
     return rc;
@@ -1600,16 +1631,20 @@ extern "C" int vs_pose_estimate_stereo(const uint8_t *left1, const uint8_t *left
     int rc = launch_harris(left1, W, H, pitch, r25, st);
     if (rc == VS_OK)
         rc = launch_cells(r25, W, H, p, corners, st);
+    double *PL = reinterpret_cast<double *>(at(l.base.P)), *uvL = reinterpret_cast<double *>(at(l.base.uv));
+    double *PR = reinterpret_cast<double *>(at(l.P2)), *uvR = reinterpret_cast<double *>(at(l.uv2));
     if (rc == VS_OK)
-        rc = pose_from_corners(left1, left2, xyz1, W, H, pitch, cam, p, corners, n,
-                               reinterpret_cast<double *>(at(l.base.pos)), reinterpret_cast<int64_t *>(at(l.base.cost)),
-                               reinterpret_cast<double *>(at(l.base.P)), reinterpret_cast<double *>(at(l.base.uv)),
-                               outL, st);
+        rc = match_points(left1, left2, xyz1, W, H, pitch, p, corners, n, reinterpret_cast<double *>(at(l.base.pos)),
+                          reinterpret_cast<int64_t *>(at(l.base.cost)), PL, uvL, st);
     if (rc == VS_OK)
-        rc = pose_from_corners(left1, right2, xyz1, W, H, pitch, cam, p, corners, n,
-                               reinterpret_cast<double *>(at(l.pos2)), reinterpret_cast<int64_t *>(at(l.cost2)),
-                               reinterpret_cast<double *>(at(l.P2)), reinterpret_cast<double *>(at(l.uv2)), outR,
-                               st);
+        rc = match_points(left1, right2, xyz1, W, H, pitch, p, corners, n, reinterpret_cast<double *>(at(l.pos2)),
+                          reinterpret_cast<int64_t *>(at(l.cost2)), PR, uvR, st);
+    if (rc == VS_OK) {   // the two poses side by side, one CTA each
+        EpnpJobs jobs{};
+        jobs.job[0] = epnp_args(PL, uvL, n, cam, outL);
+        jobs.job[1] = epnp_args(PR, uvR, n, cam, outR);
+        rc = launch_epnp_jobs(jobs, 2, st);
+    }
     if (rc == VS_OK)
         rc = launch_average(outL, outR, baseline, out, st);
     return rc;
