@@ -630,6 +630,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs &a, unsigned block)
     const uint8_t *cost = reinterpret_cast<const uint8_t *>(a.cost) +
                           slot_base(a.color * a.h + y, xh, a.wg, (LP / 16) * (int)sizeof(CostT));
     uint8_t *own = a.msg + slot_base(a.color * 4 * a.h + y, xh, a.wg, LP / 16);
+    // only now wait for the previous kernel: the index work above overlaps
+    // its last wave (nothing above reads memory it writes)
+    pdl_begin();
     if (pair == 0)
         sweep_pixel<LP, CostT, BYTES, FULL, LABELS, PRELOAD, false, 0>(
             a, x, y, in, use, cost, own, [&](uint8_t *&A, uint8_t *&B) { sweep_dsts<LP, 0>(a, x, y, has, A, B); });
@@ -843,6 +846,7 @@ __device__ __forceinline__ void sweep_split_pair(const SweepArgs &a, unsigned bl
                           slot_base(a.color * a.h + y, xh, a.wg, (LP / 16) * (int)sizeof(CostT));
     uint8_t *own = a.msg + slot_base(a.color * 4 * a.h + y, xh, a.wg, LP / 16);
     const size_t dir_stride = (size_t)a.h * a.wg * (LP / 16) * kPieceStride;   // bytes between directions
+    pdl_begin();   // the index work above overlaps the previous kernel's last wave
 
     uint32_t F[HL];
     uint32_t H2 = kBig2;
@@ -975,14 +979,12 @@ __device__ __forceinline__ void sweep_split_body(const SweepArgs &a, unsigned bl
 template <int LP, typename CostT, bool BYTES, bool FULL, bool LABELS, bool PRELOAD>
 __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep(SweepArgs a)
 {
-    pdl_begin();
     sweep_body<LP, CostT, BYTES, FULL, LABELS, PRELOAD>(a, blockIdx.x);
 }
 
 template <int LP, typename CostT, bool BYTES, bool FULL, int NS>
 __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_split(SweepArgs a)
 {
-    pdl_begin();
     sweep_split_body<LP, CostT, BYTES, FULL, NS>(a, blockIdx.x);
 }
 
@@ -1506,7 +1508,6 @@ __device__ __forceinline__ int batch_job(const BatchArgs &b, unsigned block)
 template <int LP, typename CostT, bool BYTES, bool FULL, bool LABELS, bool PRELOAD>
 __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_batch(const __grid_constant__ BatchArgs b)
 {
-    pdl_begin();
     const int j = batch_job(b, blockIdx.x);
     sweep_body<LP, CostT, BYTES, FULL, LABELS, PRELOAD>(b.job[j], blockIdx.x - b.first_block[j]);
 }
@@ -1514,7 +1515,6 @@ __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_batch(const __grid_c
 template <int LP, typename CostT, bool BYTES, bool FULL, int NS>
 __global__ void __launch_bounds__(kSweepThreads) k_bp_sweep_split_batch(const __grid_constant__ BatchArgs b)
 {
-    pdl_begin();
     const int j = batch_job(b, blockIdx.x);
     sweep_split_body<LP, CostT, BYTES, FULL, NS>(b.job[j], blockIdx.x - b.first_block[j]);
 }
