@@ -404,7 +404,6 @@ struct CostDownArgs {
 // (2x+i, 2y+j) has colour (i+j)&1 and column slot x.  8 labels per thread.
 __global__ void k_cost_down(CostDownArgs a)
 {
-    pdl_begin();
     // threads in memory order: (row, group, 8-label chunk j, slot in group)
     const unsigned chunks = (unsigned)a.Lp / 8u;
     const int np16 = a.Lp / 16;
@@ -424,6 +423,7 @@ __global__ void k_cost_down(CostDownArgs a)
     const int x = 2 * xh + ((c + y) & 1);
     if (x >= a.wc)
         return;
+    pdl_begin();   // the index work above overlaps the previous kernel's last wave
     uint32_t acc[4] = {0, 0, 0, 0};   // 8 x u16
 #pragma unroll
     for (int jj = 0; jj < 2; ++jj) {
@@ -1582,7 +1582,6 @@ __global__ void k_bp_labels(LabelArgs a)
 template <int LP, bool FULL>
 __global__ void __launch_bounds__(128) k_bp_labels_bytes(LabelArgs a)
 {
-    pdl_begin();
     const int xh = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     const int c = a.color;
@@ -1596,6 +1595,7 @@ __global__ void __launch_bounds__(128) k_bp_labels_bytes(LabelArgs a)
 #pragma unroll
     for (int k = 0; k < 4; ++k)
         in[k] = a.msg + slot_base((c * 4 + k) * a.h + y, xh, a.wg, NP);
+    pdl_begin();   // the index work above overlaps the previous kernel's last wave
     uint32_t best2 = 0xFFFFFFFFu;   // smallest key of the even / odd labels of each pair
 #pragma unroll
     for (int j = 0; j < NP; ++j) {

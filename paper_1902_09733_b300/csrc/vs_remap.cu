@@ -276,6 +276,9 @@ __device__ __forceinline__ void remap_quad(const RemapArgs &a, int u0, int v, ui
         ayq[q] = __float_as_uint(fmaf(sy - (by - kFloorMagic), 4096.0f, kFloorMagic)) - kFloorMagicBits;
         off[q] = (uint32_t)y0 * (uint32_t)a.src_pitch + 3u * (uint32_t)x0;   // used only when fast
     }
+    // only now wait for the previous kernel (which may still read the
+    // buffers this one writes): the lens model above overlaps its last wave
+    pdl_begin();
     if (fast) {
         const uint32_t *src32 = reinterpret_cast<const uint32_t *>(a.src);
 #pragma unroll
@@ -318,7 +321,6 @@ __device__ __forceinline__ void remap_quad(const RemapArgs &a, int u0, int v, ui
 template <int S>
 __global__ void __launch_bounds__(256) k_remap_sq(RemapArgs a)
 {
-    pdl_begin();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int r, yl, xl, u0;
     if constexpr (S == 4) {
