@@ -252,8 +252,12 @@ def test_stereo_pose_on_gpu_rendered_flight_frames(t, target):
     cam = vs.Camera(*cam6[:4])
     b = 0.05 * k
     out = vs.pose_estimate_stereo(l1, l2, r2, xyz, cam, b, p).cpu().numpy()
-    eL = vs.pose_estimate(l1, l2, xyz, cam, p).cpu().numpy()
-    eR = vs.pose_estimate(l1, r2, xyz, cam, p).cpu().numpy()
+    eLd = vs.pose_estimate(l1, l2, xyz, cam, p)
+    eRd = vs.pose_estimate(l1, r2, xyz, cam, p)
+    # the stereo call solves both problems in one launch (one CTA each): its
+    # estimates are the single calls' bit for bit, averaged by the same kernel
+    np.testing.assert_array_equal(out, vs.pose_average(eLd, eRd, b).cpu().numpy())
+    eL, eR = eLd.cpu().numpy(), eRd.cpu().numpy()
     Rw, Tw = opose.pose_average(eL[:9].reshape(3, 3), eL[9:12], eR[:9].reshape(3, 3), eR[9:12], b)
     np.testing.assert_allclose(out[:9].reshape(3, 3), Rw, atol=1e-12)
     np.testing.assert_allclose(out[9:12], Tw, atol=1e-12)
