@@ -56,6 +56,13 @@ enum ProfTag {
 int prof_begin(int tag, cudaStream_t st);
 void prof_end(int slot, cudaStream_t st);
 
+// Both frames of a pair through the block remap kernel in one launch (the
+// left frame's full-res, low-res RGB and grey outputs, the right frame's
+// grey); VS_EINVAL where that kernel does not apply (vs_remap.cu).
+int remap_pair(const uint8_t *left, const uint8_t *right, int W, int H, int pitch, const vs_camera *cam, int scale,
+               uint8_t *dst, int dst_pitch, uint8_t *low_rgb, int low_rgb_pitch, uint8_t *gray_l, uint8_t *gray_r,
+               int gray_pitch, cudaStream_t st);
+
 // Programmatic dependent launch.  Every kernel of the library starts with
 // pdl_begin(): it waits until the previous kernel on the stream has finished
 // and its writes are visible (a no-op when launched without the attribute),

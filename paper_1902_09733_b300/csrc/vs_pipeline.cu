@@ -250,15 +250,22 @@ extern "C" int vs_pair_run(const vs_pair_config *cfg, const uint8_t *left_src, c
         return VS_EWORKSPACE;
     uint8_t *ws = reinterpret_cast<uint8_t *>(workspace);
     const int W = cfg->W, H = cfg->H, s = cfg->jbu.scale;
-    int rc = vs_rectify_remap(left_src, W, H, 3 * W, &cfg->cam, nullptr, ws + lay.rect_l, 3 * W, s,
-                              ws + lay.low_rgb, 3 * lay.w, ws + lay.gray_l, lay.w, stream);
-    if (rc != VS_OK)
+    // the right frame only feeds the matcher: its full-res copy is not needed,
+    // and with the block kernel it is sampled in the left frame's launch
+    int rc = remap_pair(left_src, right_src, W, H, 3 * W, &cfg->cam, s, ws + lay.rect_l, 3 * W, ws + lay.low_rgb,
+                        3 * lay.w, ws + lay.gray_l, ws + lay.gray_r, lay.w, (cudaStream_t)stream);
+    if (rc != VS_OK && rc != VS_EINVAL)
         return rc;
-    // the right frame only feeds the matcher: its full-res copy is not needed
-    rc = vs_rectify_remap(right_src, W, H, 3 * W, &cfg->cam, nullptr, nullptr, 0, s, nullptr, 0,
-                          ws + lay.gray_r, lay.w, stream);
-    if (rc != VS_OK)
-        return rc;
+    if (rc == VS_EINVAL) {   // not for the block kernel: one frame at a time
+        rc = vs_rectify_remap(left_src, W, H, 3 * W, &cfg->cam, nullptr, ws + lay.rect_l, 3 * W, s, ws + lay.low_rgb,
+                              3 * lay.w, ws + lay.gray_l, lay.w, stream);
+        if (rc != VS_OK)
+            return rc;
+        rc = vs_rectify_remap(right_src, W, H, 3 * W, &cfg->cam, nullptr, nullptr, 0, s, nullptr, 0,
+                              ws + lay.gray_r, lay.w, stream);
+        if (rc != VS_OK)
+            return rc;
+    }
     rc = vs_bp_stereo(ws + lay.gray_l, ws + lay.gray_r, lay.w, lay.h, lay.w, &cfg->bp, ws + lay.labels, lay.w,
                       ws + lay.bp, lay.bp_bytes, stream);
     if (rc != VS_OK)

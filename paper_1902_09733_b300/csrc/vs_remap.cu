@@ -32,6 +32,11 @@ struct RemapArgs {
     int src_words;          // src rows start on 4-byte boundaries (aligned word gathers)
     float R[9];
     int has_R;
+    // k_remap_sq<S, true>: a second frame of the same camera and size sampled
+    // at the same coordinates, only its low-res grey written
+    const uint8_t *src2;
+    uint8_t *low_gray2;
+    int src2_pitch, low_gray2_pitch;
 };
 
 __device__ __forceinline__ uint32_t tap(const uint8_t *src, int pitch, int W, int H, int x, int y, int ch)
@@ -109,7 +114,8 @@ __device__ __forceinline__ void taps_words(const uint32_t *q0, int pitch32, uint
 
 // One destination pixel anywhere in the frame: blend accumulators as
 // blend() returns them, 2^23 (byte 0) for rays that miss the frame.
-__device__ __forceinline__ void sample_px(const RemapArgs &a, int u, int v, uint32_t (&vv)[3])
+__device__ __forceinline__ void sample_px(const RemapArgs &a, const uint8_t *src, int src_pitch, int u, int v,
+                                          uint32_t (&vv)[3])
 {
     vv[0] = vv[1] = vv[2] = 1u << 23;
     float xn, yn;
@@ -125,9 +131,9 @@ __device__ __forceinline__ void sample_px(const RemapArgs &a, int u, int v, uint
     const uint32_t ayq = (uint32_t)__float2int_rn((sy - fy0) * 4096.0f);
     uint32_t t_rg, t_b, b_rg, b_b;
     if (x0 >= 0 && y0 >= 0 && x0 + 2 < a.W && y0 + 1 < a.H && a.src_words) {
-        const uint8_t *p0 = a.src + (size_t)y0 * a.src_pitch + 3 * x0;
+        const uint8_t *p0 = src + (size_t)y0 * src_pitch + 3 * x0;
         const uint32_t o = (uint32_t)(reinterpret_cast<uintptr_t>(p0) & 3u);
-        taps_words(reinterpret_cast<const uint32_t *>(p0 - o), a.src_pitch >> 2, o, t_rg, t_b, b_rg, b_b);
+        taps_words(reinterpret_cast<const uint32_t *>(p0 - o), src_pitch >> 2, o, t_rg, t_b, b_rg, b_b);
     } else {
         // byte loads, with frame checks where a tap may be outside
         uint32_t tq[2][2][3];   // [row][column][channel]
@@ -137,7 +143,7 @@ __device__ __forceinline__ void sample_px(const RemapArgs &a, int u, int v, uint
             for (int jx = 0; jx < 2; ++jx)
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch)
-                    tq[jy][jx][ch] = tap(a.src, a.src_pitch, a.W, a.H, x0 + jx, y0 + jy, ch);
+                    tq[jy][jx][ch] = tap(src, src_pitch, a.W, a.H, x0 + jx, y0 + jy, ch);
         t_rg = tq[0][0][0] | (tq[0][1][0] << 8) | (tq[0][0][1] << 16) | (tq[0][1][1] << 24);
         t_b = tq[0][0][2] | (tq[0][1][2] << 8);
         b_rg = tq[1][0][0] | (tq[1][1][0] << 8) | (tq[1][0][1] << 16) | (tq[1][1][1] << 24);
@@ -168,7 +174,7 @@ __global__ void __launch_bounds__(kRemapThreads) k_remap_down(RemapArgs a)
             const int lu = lu0 + q, u = u0 + lu;
             uint32_t vv[3] = {1u << 23, 1u << 23, 1u << 23};
             if (lu < tfw && u < a.W && v < a.H)
-                sample_px(a, u, v, vv);
+                sample_px(a, a.src, a.src_pitch, u, v, vv);
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch)
                 out[3 * q + ch] = (uint8_t)(vv[ch] >> 24);
@@ -253,9 +259,37 @@ constexpr uint32_t kFloorMagicBits = 0x4B400000u;
 // conversions; when all four footprints are inside the frame, word gathers
 // with no further checks, otherwise the general per-pixel sampler.  Writes
 // the 12 bytes to dst (if wanted) and returns them packed in w.
-__device__ __forceinline__ void remap_quad(const RemapArgs &a, int u0, int v, uint32_t (&w)[3])
+// The quad's four pixels of `src` at the coordinates remap_quad found,
+// packed as R0 G0 B0 R1 | G1 B1 R2 G2 | B2 R3 G3 B3.
+__device__ __forceinline__ void sample_quad(const RemapArgs &a, const uint8_t *src, bool fast, const uint32_t (&off)[4],
+                                            const uint32_t (&axq)[4], const uint32_t (&ayq)[4], int u0, int v,
+                                            uint32_t (&w)[3])
 {
     uint32_t vv[4][3];
+    if (fast) {
+        const uint32_t *src32 = reinterpret_cast<const uint32_t *>(src);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t t_rg, t_b, b_rg, b_b;
+            taps_words(src32 + (off[q] >> 2), a.src_pitch >> 2, off[q] & 3u, t_rg, t_b, b_rg, b_b);
+            blend(t_rg, t_b, b_rg, b_b, axq[q], ayq[q], vv[q]);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            sample_px(a, src, a.src_pitch, u0 + q, v, vv[q]);
+    }
+    // the rounded bytes (bits 24..31)
+    w[0] = prmt(prmt(vv[0][0], vv[0][1], 0x0073u), prmt(vv[0][2], vv[1][0], 0x0073u), 0x5410u);
+    w[1] = prmt(prmt(vv[1][1], vv[1][2], 0x0073u), prmt(vv[2][0], vv[2][1], 0x0073u), 0x5410u);
+    w[2] = prmt(prmt(vv[2][2], vv[3][0], 0x0073u), prmt(vv[3][1], vv[3][2], 0x0073u), 0x5410u);
+}
+
+// The lens model of a quad of four destination pixels once, then the
+// samples of a.src (stored to a.dst when given) and, with PAIR, of a.src2.
+template <bool PAIR>
+__device__ __forceinline__ void remap_quad(const RemapArgs &a, int u0, int v, uint32_t (&w)[3], uint32_t (&w2)[3])
+{
     float yn = __fmul_rn(__fsub_rn(exact_float(v), a.cy), a.inv_fy);
     uint32_t off[4], axq[4], ayq[4];
     bool fast = true;
@@ -279,29 +313,15 @@ __device__ __forceinline__ void remap_quad(const RemapArgs &a, int u0, int v, ui
     // only now wait for the previous kernel (which may still read the
     // buffers this one writes): the lens model above overlaps its last wave
     pdl_begin();
-    if (fast) {
-        const uint32_t *src32 = reinterpret_cast<const uint32_t *>(a.src);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            uint32_t t_rg, t_b, b_rg, b_b;
-            taps_words(src32 + (off[q] >> 2), a.src_pitch >> 2, off[q] & 3u, t_rg, t_b, b_rg, b_b);
-            blend(t_rg, t_b, b_rg, b_b, axq[q], ayq[q], vv[q]);
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            sample_px(a, u0 + q, v, vv[q]);
-    }
-    // the rounded bytes (bits 24..31) packed as R0 G0 B0 R1 | G1 B1 R2 G2 | B2 R3 G3 B3
-    w[0] = prmt(prmt(vv[0][0], vv[0][1], 0x0073u), prmt(vv[0][2], vv[1][0], 0x0073u), 0x5410u);
-    w[1] = prmt(prmt(vv[1][1], vv[1][2], 0x0073u), prmt(vv[2][0], vv[2][1], 0x0073u), 0x5410u);
-    w[2] = prmt(prmt(vv[2][2], vv[3][0], 0x0073u), prmt(vv[3][1], vv[3][2], 0x0073u), 0x5410u);
+    sample_quad(a, a.src, fast, off, axq, ayq, u0, v, w);
     if (a.dst) {
         uint32_t *d32 = reinterpret_cast<uint32_t *>(a.dst + (size_t)v * a.dst_pitch + (size_t)u0 * 3);
         d32[0] = w[0];
         d32[1] = w[1];
         d32[2] = w[2];
     }
+    if (PAIR)   // the second frame at the same coordinates (same size and row pitch)
+        sample_quad(a, a.src2, fast, off, axq, ayq, u0, v, w2);
 }
 
 // Scale-2/4/8 kernel for the common case: no rotation, W a multiple of 4 and
@@ -318,7 +338,7 @@ __device__ __forceinline__ void remap_quad(const RemapArgs &a, int u0, int v, ui
 //          row r of block b: four shuffles;
 //   s = 2: warp w takes block row w, lane (r, q) = (lane >> 4, lane & 15) row
 //          r of quad q, which spans two blocks: one shuffle.
-template <int S>
+template <int S, bool PAIR>
 __global__ void __launch_bounds__(256) k_remap_sq(RemapArgs a)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -343,10 +363,10 @@ __global__ void __launch_bounds__(256) k_remap_sq(RemapArgs a)
         return;
     const int v = S * yl + r;
     const bool inside = u0 < a.W;   // whole quad (W is a multiple of 4)
-    uint32_t w[3] = {0u, 0u, 0u};
+    uint32_t w[3] = {0u, 0u, 0u}, w2[3] = {0u, 0u, 0u};
     if (inside)
-        remap_quad(a, u0, v, w);
-    if (!a.low_rgb && !a.low_gray)
+        remap_quad<PAIR>(a, u0, v, w, w2);
+    if (!a.low_rgb && !a.low_gray && !PAIR)
         return;
     auto put = [&](int x, uint32_t R, uint32_t G, uint32_t B) {
         if (a.low_rgb) {
@@ -359,61 +379,70 @@ __global__ void __launch_bounds__(256) k_remap_sq(RemapArgs a)
             a.low_gray[(size_t)yl * a.low_gray_pitch + x] = (uint8_t)((77u * R + 150u * G + 29u * B + 128u) >> 8);
     };
     const unsigned full = 0xFFFFFFFFu;
-    if constexpr (S == 2) {
-        // the quad's bytes R0 G0 B0 R1 | G1 B1 R2 G2 | B2 R3 G3 B3: pixels 0-1
-        // belong to block xl, pixels 2-3 to block xl + 1
-        const uint32_t rA = __dp4a(w[0], 0x01000001u, 0u);
-        const uint32_t gA = __dp4a(w[0], 0x00000100u, __dp4a(w[1], 0x00000001u, 0u));
-        const uint32_t bA = __dp4a(w[0], 0x00010000u, __dp4a(w[1], 0x00000100u, 0u));
-        const uint32_t rB = __dp4a(w[1], 0x00010000u, __dp4a(w[2], 0x00000100u, 0u));
-        const uint32_t gB = __dp4a(w[1], 0x01000000u, __dp4a(w[2], 0x00010000u, 0u));
-        const uint32_t bB = __dp4a(w[2], 0x01000001u, 0u);
-        uint32_t pA = rA | (gA << 16), pB = rB | (gB << 16), qAB = bA | (bB << 16);   // sums <= 4 x 255
-        pA += __shfl_xor_sync(full, pA, 16);
-        pB += __shfl_xor_sync(full, pB, 16);
-        qAB += __shfl_xor_sync(full, qAB, 16);
-        if (r != 0 || !inside)
-            return;
-        put(xl, ((pA & 0xFFFFu) + 2u) >> 2, ((pA >> 16) + 2u) >> 2, ((qAB & 0xFFFFu) + 2u) >> 2);
-        put(xl + 1, ((pB & 0xFFFFu) + 2u) >> 2, ((pB >> 16) + 2u) >> 2, ((qAB >> 16) + 2u) >> 2);
-    } else {
-        // row sums of the quad per channel, then the block's other quads
-        const uint32_t sr = __dp4a(w[0], 0x01000001u, __dp4a(w[1], 0x00010000u, __dp4a(w[2], 0x00000100u, 0u)));
-        const uint32_t sg = __dp4a(w[0], 0x00000100u, __dp4a(w[1], 0x01000001u, __dp4a(w[2], 0x00010000u, 0u)));
-        const uint32_t sb = __dp4a(w[0], 0x00010000u, __dp4a(w[1], 0x00000100u, __dp4a(w[2], 0x01000001u, 0u)));
-        uint32_t rg = sr | (sg << 16), b = sb;   // each block sum <= 64 x 255 < 2^16
-        if constexpr (S == 4) {
-#pragma unroll
-            for (int o = 8; o <= 16; o <<= 1) {
-                rg += __shfl_xor_sync(full, rg, o);
-                b += __shfl_xor_sync(full, b, o);
-            }
+    // block means of one frame's words, handed to `out` by the block's lead lanes
+    auto means = [&](const uint32_t (&w)[3], auto &&out) {
+        if constexpr (S == 2) {
+            // the quad's bytes R0 G0 B0 R1 | G1 B1 R2 G2 | B2 R3 G3 B3: pixels 0-1
+            // belong to block xl, pixels 2-3 to block xl + 1
+            const uint32_t rA = __dp4a(w[0], 0x01000001u, 0u);
+            const uint32_t gA = __dp4a(w[0], 0x00000100u, __dp4a(w[1], 0x00000001u, 0u));
+            const uint32_t bA = __dp4a(w[0], 0x00010000u, __dp4a(w[1], 0x00000100u, 0u));
+            const uint32_t rB = __dp4a(w[1], 0x00010000u, __dp4a(w[2], 0x00000100u, 0u));
+            const uint32_t gB = __dp4a(w[1], 0x01000000u, __dp4a(w[2], 0x00010000u, 0u));
+            const uint32_t bB = __dp4a(w[2], 0x01000001u, 0u);
+            uint32_t pA = rA | (gA << 16), pB = rB | (gB << 16), qAB = bA | (bB << 16);   // sums <= 4 x 255
+            pA += __shfl_xor_sync(full, pA, 16);
+            pB += __shfl_xor_sync(full, pB, 16);
+            qAB += __shfl_xor_sync(full, qAB, 16);
+            if (r != 0 || !inside)
+                return;
+            out(xl, ((pA & 0xFFFFu) + 2u) >> 2, ((pA >> 16) + 2u) >> 2, ((qAB & 0xFFFFu) + 2u) >> 2);
+            out(xl + 1, ((pB & 0xFFFFu) + 2u) >> 2, ((pB >> 16) + 2u) >> 2, ((qAB >> 16) + 2u) >> 2);
         } else {
+            // row sums of the quad per channel, then the block's other quads
+            const uint32_t sr = __dp4a(w[0], 0x01000001u, __dp4a(w[1], 0x00010000u, __dp4a(w[2], 0x00000100u, 0u)));
+            const uint32_t sg = __dp4a(w[0], 0x00000100u, __dp4a(w[1], 0x01000001u, __dp4a(w[2], 0x00010000u, 0u)));
+            const uint32_t sb = __dp4a(w[0], 0x00010000u, __dp4a(w[1], 0x00000100u, __dp4a(w[2], 0x01000001u, 0u)));
+            uint32_t rg = sr | (sg << 16), b = sb;   // each block sum <= 64 x 255 < 2^16
+            if constexpr (S == 4) {
 #pragma unroll
-            for (int o = 1; o <= 8; o <<= 1) {
-                rg += __shfl_xor_sync(full, rg, o);
-                b += __shfl_xor_sync(full, b, o);
+                for (int o = 8; o <= 16; o <<= 1) {
+                    rg += __shfl_xor_sync(full, rg, o);
+                    b += __shfl_xor_sync(full, b, o);
+                }
+            } else {
+#pragma unroll
+                for (int o = 1; o <= 8; o <<= 1) {
+                    rg += __shfl_xor_sync(full, rg, o);
+                    b += __shfl_xor_sync(full, b, o);
+                }
             }
+            constexpr uint32_t kHalf = S * S / 2, kShift = S == 4 ? 4 : 6;
+            const bool lead = S == 4 ? r == 0 : (lane & 15) == 0;
+            if (!lead || !inside)
+                return;
+            out(xl, ((rg & 0xFFFFu) + kHalf) >> kShift, ((rg >> 16) + kHalf) >> kShift, (b + kHalf) >> kShift);
         }
-        constexpr uint32_t kHalf = S * S / 2, kShift = S == 4 ? 4 : 6;
-        const bool lead = S == 4 ? r == 0 : (lane & 15) == 0;
-        if (!lead || !inside)
-            return;
-        put(xl, ((rg & 0xFFFFu) + kHalf) >> kShift, ((rg >> 16) + kHalf) >> kShift, (b + kHalf) >> kShift);
-    }
+    };
+    means(w, put);
+    if (PAIR)   // the second frame: its grey only
+        means(w2, [&](int x, uint32_t R, uint32_t G, uint32_t B) {
+            a.low_gray2[(size_t)yl * a.low_gray2_pitch + x] = (uint8_t)((77u * R + 150u * G + 29u * B + 128u) >> 8);
+        });
 }
 
 }  // namespace
 }  // namespace vs
 
-extern "C" int vs_rectify_remap(const uint8_t *src, int W, int H, int src_pitch,
-                                const vs_camera *cam, const float *R9,
-                                uint8_t *dst, int dst_pitch, int scale,
-                                uint8_t *low_rgb, int low_rgb_pitch,
-                                uint8_t *low_gray, int low_gray_pitch, void *stream)
+namespace vs {
+namespace {
+
+// The arguments of one frame's remap after the checks of vs_rectify_remap;
+// *sq tells whether the block kernel k_remap_sq serves them.
+int remap_args(const uint8_t *src, int W, int H, int src_pitch, const vs_camera *cam, const float *R9, uint8_t *dst,
+               int dst_pitch, int scale, uint8_t *low_rgb, int low_rgb_pitch, uint8_t *low_gray, int low_gray_pitch,
+               RemapArgs &a, bool &sq)
 {
-    vs::NvtxRange nvtx_range("vs_rectify_remap");
-    using namespace vs;
     if (!src || !cam || W <= 0 || H <= 0 || src_pitch < 3 * W)
         return VS_EINVAL;
     if (!dst && !low_rgb && !low_gray)
@@ -436,7 +465,7 @@ extern "C" int vs_rectify_remap(const uint8_t *src, int W, int H, int src_pitch,
     if (low_gray && low_gray_pitch < w)
         return VS_EINVAL;
 
-    RemapArgs a;
+    a = RemapArgs{};
     a.src = src;
     a.dst = dst;
     a.low_rgb = low_rgb;
@@ -469,20 +498,73 @@ extern "C" int vs_rectify_remap(const uint8_t *src, int W, int H, int src_pitch,
     // the block kernel: scale 2, 4 or 8, whole s x s blocks and 4-pixel
     // quads, word-aligned rows both ways, no rotation, 32-bit source offsets,
     // and the low-res output wanted
-    const bool sq = want_low && (s == 2 || s == 4 || s == 8) && !a.has_R && W % 4 == 0 && W % s == 0 &&
-                    H % s == 0 && W < (1 << 22) && H < (1 << 22) && a.src_words && (dst == nullptr || a.dst_vec) &&
-                    (long long)H * src_pitch < (1LL << 31);
+    sq = want_low && (s == 2 || s == 4 || s == 8) && !a.has_R && W % 4 == 0 && W % s == 0 && H % s == 0 &&
+         W < (1 << 22) && H < (1 << 22) && a.src_words && (dst == nullptr || a.dst_vec) &&
+         (long long)H * src_pitch < (1LL << 31);
+    return VS_OK;
+}
+
+template <bool PAIR>
+void launch_remap_sq(const RemapArgs &a, cudaStream_t st)
+{
+    dim3 grid((a.W + 63) / 64, (a.H + 15) / 16);
+    if (a.s == 2)
+        launch_pdl(k_remap_sq<2, PAIR>, dim3(grid), dim3(256), st, a);
+    else if (a.s == 4)
+        launch_pdl(k_remap_sq<4, PAIR>, dim3(grid), dim3(256), st, a);
+    else
+        launch_pdl(k_remap_sq<8, PAIR>, dim3(grid), dim3(256), st, a);
+}
+
+}  // namespace
+
+// Both frames of a pair in one launch of the block kernel: the lens model of
+// each destination quad once, the left frame sampled with the outputs of
+// vs_rectify_remap, the right frame's low-res grey beside it.  Returns
+// VS_EINVAL where the block kernel does not apply (the caller then remaps
+// the frames one at a time).
+int remap_pair(const uint8_t *left, const uint8_t *right, int W, int H, int pitch, const vs_camera *cam, int scale,
+               uint8_t *dst, int dst_pitch, uint8_t *low_rgb, int low_rgb_pitch, uint8_t *gray_l, uint8_t *gray_r,
+               int gray_pitch, cudaStream_t st)
+{
+    RemapArgs a;
+    bool sq = false;
+    int rc = remap_args(left, W, H, pitch, cam, nullptr, dst, dst_pitch, scale, low_rgb, low_rgb_pitch, gray_l,
+                        gray_pitch, a, sq);
+    if (rc != VS_OK || !sq || !right || !gray_r || !aligned(right, 4))
+        return VS_EINVAL;
+    a.src2 = right;
+    a.src2_pitch = pitch;
+    a.low_gray2 = gray_r;
+    a.low_gray2_pitch = gray_pitch;
+    const int slot = prof_begin(kProfRemap, st);
+    launch_remap_sq<true>(a, st);
+    prof_end(slot, st);
+    note_launch();
+    return launch_status();
+}
+
+}  // namespace vs
+
+extern "C" int vs_rectify_remap(const uint8_t *src, int W, int H, int src_pitch,
+                                const vs_camera *cam, const float *R9,
+                                uint8_t *dst, int dst_pitch, int scale,
+                                uint8_t *low_rgb, int low_rgb_pitch,
+                                uint8_t *low_gray, int low_gray_pitch, void *stream)
+{
+    vs::NvtxRange nvtx_range("vs_rectify_remap");
+    using namespace vs;
+    RemapArgs a;
+    bool sq = false;
+    const int rc = remap_args(src, W, H, src_pitch, cam, R9, dst, dst_pitch, scale, low_rgb, low_rgb_pitch, low_gray,
+                              low_gray_pitch, a, sq);
+    if (rc != VS_OK)
+        return rc;
     const int slot = prof_begin(kProfRemap, (cudaStream_t)stream);
     if (sq) {
-        dim3 grid((W + 63) / 64, (H + 15) / 16);
-        if (s == 2)
-            launch_pdl(k_remap_sq<2>, dim3(grid), dim3(256), (cudaStream_t)stream, a);
-        else if (s == 4)
-            launch_pdl(k_remap_sq<4>, dim3(grid), dim3(256), (cudaStream_t)stream, a);
-        else
-            launch_pdl(k_remap_sq<8>, dim3(grid), dim3(256), (cudaStream_t)stream, a);
+        launch_remap_sq<false>(a, (cudaStream_t)stream);
     } else {
-        const int tfw = a.tlw * s, tfh = a.tlh * s;
+        const int tfw = a.tlw * a.s, tfh = a.tlh * a.s;
         dim3 grid((W + tfw - 1) / tfw, (H + tfh - 1) / tfh);
         launch_pdl(k_remap_down, dim3(grid), dim3(kRemapThreads), (cudaStream_t)stream, a);
     }

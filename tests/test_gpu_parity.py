@@ -360,6 +360,26 @@ def _pair_cfg():
     return vs.PairConfig(2704, 1520, CAM2K, 0.5, BP_CFG2, JBU_CFG2)
 
 
+@pytest.mark.parametrize("s", [2, 4, 8])
+def test_pair_driver_matches_frame_by_frame_calls(s):
+    """The pair driver remaps both frames in one launch of the block kernel
+    (the lens model of each quad once, both frames sampled at it); its cloud
+    equals, bit for bit, the one from the public per-frame calls."""
+    W, H = 1024, 568   # a multiple of 8 both ways; 568 = 71 x 8 leaves ragged CTA rows
+    rng = np.random.default_rng(40 + s)
+    left = (rng.integers(0, 256, (H, W, 3))).astype(np.uint8)
+    right = np.roll(left, -3 * s, axis=1)
+    bp = vs.BPParams(labels=32, levels=3, iters=5, data_trunc=20, smooth_slope=10, smooth_trunc=40)
+    jbu = vs.JBUParams(scale=s, radius=2, sigma_s=1.0, sigma_r=12.0)
+    cfg = vs.PairConfig(W, H, CAM2K, 0.5, bp, jbu)
+    dl, lrl, lgl = vs.rectify_remap(dev(left), cfg.cam, scale=s)
+    _, _, lgr = vs.rectify_remap(dev(right), cfg.cam, scale=s, dst=None, low_rgb=None)
+    lab = vs.bp_stereo(lgl, lgr, cfg.bp)
+    _, xyz = vs.guided_upsample_reproject(lab, lrl, dl, cfg.jbu, cfg.cam, cfg.baseline)
+    _, xyz2 = vs.pair_run(cfg, dev(left), dev(right))
+    np.testing.assert_array_equal(host(xyz2), host(xyz))
+
+
 def test_full_pair_stage_by_stage(terrain):
     """The 2.7K pipeline of the benchmark, each stage against the oracle on the
     GPU's own inputs to that stage."""
